@@ -1,0 +1,373 @@
+"""Benchmark of the fused ZNCC + DT + WTA path on the paper-shaped workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                    [--storage f32|f16] [--workload paper_1280x384]
+
+One step = one pass of the whole path (window statistics, ZNCC fused with the first
+horizontal DT pair, the remaining DT passes, WTA fused into the last vertical pair) over one
+synthetic 1280x384 pair, D = 128, 9x9 window, sigma_s = 20, sigma_r = 0.1, 3 iterations.
+Inputs are resident in HBM; L2 is flushed (a 256 MB write) before every timed step and the
+flush is outside the step's CUDA events. Rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle (the only reference this method has) on the host
+cores, one full pair per step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gdisp/s & fps at 1280x384 D=128 (ZNCC+DT+WTA); served p50/p99 vs plain"
+SIG_S, SIG_R, ITERS = 20.0, 0.1, 3
+WORKLOADS = {
+    "paper_1280x384": dict(h=384, w=1280, d=128, win=9),
+    "precision_1920x1080": dict(h=1080, w=1920, d=256, win=11),
+    "plain_320x96": dict(h=96, w=320, d=32, win=9),
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def workload_desc(name, storage):
+    wl = WORKLOADS[name]
+    return (f"{name}: {wl['w']}x{wl['h']} D={wl['d']} win={wl['win']}x{wl['win']} DT "
+            f"sigma_s={SIG_S} sigma_r={SIG_R} iters={ITERS if name != 'plain_320x96' else 0} "
+            f"{storage.upper()} volume storage; seeded synthetic pair (blurred noise, slanted "
+            f"planes, 5% occlusion bands, gain/offset/noise)")
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# the CPU oracle (the cpu_baseline leg and the reference arm)
+
+def time_oracle(pair, wl, iters, max_seconds=12.0, min_runs=1, max_runs=5):
+    import oracle
+    cores = host_cores()
+    oracle.load()
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max_runs:
+        t0 = time.perf_counter()
+        oracle.run(pair.left, pair.right, wl["d"], wl["win"] // 2, SIG_S, SIG_R, iters,
+                   nthreads=cores)
+        times.append(time.perf_counter() - t0)
+        if len(times) >= min_runs and time.perf_counter() - t_start > max_seconds:
+            break
+    return times, cores
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from synth import config_pair
+    wl = WORKLOADS[args.workload]
+    pair = config_pair(args.workload)
+    iters = ITERS if args.workload != "plain_320x96" else 0
+    import oracle
+    cores = host_cores()
+    oracle.load()
+    for _ in range(args.warmup):
+        oracle.run(pair.left, pair.right, wl["d"], wl["win"] // 2, SIG_S, SIG_R, iters,
+                   nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(pair.left, pair.right, wl["d"], wl["win"] // 2, SIG_S, SIG_R, iters,
+                   nthreads=cores)
+    dt = (time.perf_counter() - t0) / args.steps
+    units = wl["w"] * wl["h"] * wl["d"]
+    value = units / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gdisp/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3, 3), "fps": round(1.0 / dt, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(args.workload, "f64"),
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "Gdisp/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"one full {wl['w']}x{wl['h']} D={wl['d']} pair per step"},
+        "e2e": {"value": round(value, 6), "unit": "Gdisp/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+
+def algorithmic_bytes(kind, wl, elt_bytes):
+    """Algorithmic HBM bytes of one launch of a kernel kind (cost-volume traffic; the images,
+    statistics and weights are below 1%)."""
+    n = wl["w"] * wl["h"] * wl["d"]
+    return {
+        "dt_hpair": 2 * elt_bytes * n,        # read + write the volume
+        "dt_vpair": 2 * elt_bytes * n,
+        "dt_vpair_wta": elt_bytes * n,         # read only; WTA keys stay in L2
+        "zncc_cost_hpair": elt_bytes * n,      # write only
+        "zncc_cost": elt_bytes * n,
+    }.get(kind)
+
+
+def load_traffic(kind, digest):
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = t.get("kernels", {}).get(kind)
+    if not ent or t.get("source_digest") != digest:
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def run_gb300(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2212_00476_gb300 import build as zbuild
+    from paper_2212_00476_gb300 import zncc as Z
+    from synth import config_pair
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]
+    iters = ITERS if args.workload != "plain_320x96" else 0
+    storage = Z.ZNCC_F32 if args.storage == "f32" else Z.ZNCC_F16
+    elt_bytes = 4 if storage == Z.ZNCC_F32 else 2
+    pair = config_pair(args.workload)
+    H, W, D = wl["h"], wl["w"], wl["d"]
+
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Z.ZnccContext(W, H, D, wl["win"], stream=stream)
+    left = torch.from_numpy(pair.left).to(dev)
+    right = torch.from_numpy(pair.right).to(dev)
+    disp = torch.empty((H, W), dtype=torch.int16, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.zncc_run(left, right, disp, SIG_S, SIG_R, iters, storage)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-step CUDA events on the context's stream ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = Z.launch_count()
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        t_wall0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()
+                starts[i].record(stream)
+                step()
+                ends[i].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    launches = Z.launch_count() - n0
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+
+    # ---- per-kernel durations: the same steps again, each kernel between CUDA events ----
+    ctx.profile_enable(True)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            step()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    kinds = {k: v for k, v in prof.items() if algorithmic_bytes(k, wl, elt_bytes)}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms = kinds[dom][0] / kinds[dom][1]
+    dom_bytes = algorithmic_bytes(dom, wl, elt_bytes)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+
+    # ---- end to end through the public host-buffer call ----
+    lh = torch.from_numpy(pair.left).pin_memory().numpy()
+    rh = torch.from_numpy(pair.right).pin_memory().numpy()
+    dh = torch.empty((H, W), dtype=torch.int16).pin_memory().numpy().view(np.uint16)
+    for _ in range(max(1, args.warmup)):
+        ctx.zncc_run_host(lh, rh, dh, SIG_S, SIG_R, iters, storage)
+    e2e_times = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.zncc_run_host(lh, rh, dh, SIG_S, SIG_R, iters, storage)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    units = W * H * D
+    value = world * units / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gdisp/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "fps": round(world * 1e3 / ms, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": workload_desc(args.workload, args.storage),
+                   "l2": "flushed before every timed step (256 MB write outside the step events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "step_ms_min": round(min(step_ms), 4), "wall_ms_per_step_incl_flush":
+                   round(t_wall * 1e3 / args.steps, 4)},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                     "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "traffic": load_traffic(dom, zbuild._sources_digest()),
+                     "algorithmic_bytes_per_launch": dom_bytes,
+                     "launch_ms": round(dom_ms, 5)},
+        "kernels_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in prof.items()},
+        "e2e": {"value": round(world * units / e2e_s / 1e9, 3), "unit": "Gdisp/s",
+                "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 2 * W * H,
+                "ms_per_step": round(e2e_s * 1e3, 4)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times, cores = time_oracle(pair, wl, iters)
+        tb = sum(times) / len(times)
+        line["cpu_baseline"] = {"value": round(units / tb / 1e9, 6), "unit": "Gdisp/s",
+                                "cores": cores, "kind": "oracle",
+                                "sample": f"{len(times)} full {W}x{H} D={D} pair(s), "
+                                          f"{tb:.2f} s each"}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper_1280x384")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,147 @@
+/*
+ * zncc.h -- C ABI of libzncc.so: ZNCC matching cost, domain-transformation (DT) cost
+ * aggregation and winner-take-all (WTA) disparity on one GB300 GPU (sm_103a).
+ *
+ * Method: arXiv 2212.00476, "Efficient stereo matching on embedded GPUs with zero-means
+ * cross correlation".
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Images are uint8 grayscale, H rows of W pixels, row pitch `pitch` bytes (>= W).
+ *    `left` is the reference image I_R, `right` the target image I_T (Sec. III-A): pixel
+ *    (x, y) of the left image is matched to (x - d, y) of the right image, d in [0, D).
+ *  - Pixel reads outside an image are clamped to its nearest edge pixel (also for target
+ *    centres x - d < 0).
+ *  - Cost volumes are dense [H][W][D] arrays, the disparity axis fastest, of float
+ *    (ZNCC_F32) or IEEE half (ZNCC_F16). Element (x, y, d) is at ((y * W) + x) * D + d.
+ *  - Disparity maps are uint16 [H][W] (row pitch W).
+ *  - Pointers named *_host are host memory; every other buffer pointer is device memory
+ *    of the current CUDA device. The caller owns every buffer it passes; the library never
+ *    frees or keeps them. Device buffers must stay valid until the work queued on the
+ *    context's stream has completed.
+ *  - Calls are asynchronous on the context's stream unless stated otherwise. They return a
+ *    status and never abort or throw. On ZNCC_ECUDA the CUDA error text is available from
+ *    zncc_last_error(). A context is not thread-safe: use one per host thread or stream.
+ *  - Window side `win` = 2r+1 must be odd and in [3, 15]. Window sums are exact in int32
+ *    (the largest, n*Q - S^2, stays below 2^31 for every allowed window).
+ *  - W and H must be in [1, 4096] (a DT line is processed inside one thread block), D in
+ *    [1, 1024].
+ */
+#ifndef ZNCC_H_
+#define ZNCC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ZNCC_OK = 0,
+    ZNCC_EINVAL = 1,        /* an argument is out of range or a pointer is NULL          */
+    ZNCC_ENOMEM = 2,        /* a device or host allocation failed                        */
+    ZNCC_ECUDA = 3,         /* a CUDA runtime call failed; see zncc_last_error()          */
+    ZNCC_EBUSY = 4,         /* the server is shutting down or full                       */
+    ZNCC_ENOTREADY = 5,     /* serve_poll: the request has not finished yet              */
+    ZNCC_ETIMEOUT = 6,      /* serve_poll / serve_destroy: a bounded wait ran out         */
+    ZNCC_EUNSUPPORTED = 7   /* a size the kernels do not handle                          */
+} zncc_status;
+
+typedef enum { ZNCC_F32 = 0, ZNCC_F16 = 1 } zncc_dtype;
+
+typedef struct zncc_ctx zncc_ctx;
+
+/* Create a context for W x H pairs, disparities [0, max_disp), window side `win`.
+ * Allocates the context's device scratch (window statistics, DT edge weights, the WTA
+ * key map) on the current device; the cost volume of zncc_run is allocated on first use.
+ * Sec. III-A defines the problem (I_R, I_T, D, window l = 2r+1). */
+zncc_status zncc_create(int width, int height, int max_disp, int win, zncc_ctx** out);
+
+/* Free the context and its scratch. Synchronizes the context's stream first. */
+zncc_status zncc_destroy(zncc_ctx* ctx);
+
+/* Bind a CUDA stream (cudaStream_t passed as void*; NULL = legacy default stream). */
+zncc_status zncc_set_stream(zncc_ctx* ctx, void* cuda_stream);
+
+/* Bytes of a [H][W][D] cost volume of the given storage type (0 on bad arguments). */
+size_t zncc_volume_bytes(const zncc_ctx* ctx, zncc_dtype dtype);
+
+/* Window statistics of one image (Sec. IV-B-1, Eq. (sum1)): for each centre (x, y),
+ * S = sum of the (2r+1)^2 clamped pixels, Q = sum of their squares (exact int32), and
+ * inv_sigma = 1/sqrt(n*Q - S^2) as float (0 when the window is flat), n = (2r+1)^2.
+ * This is the per-image term of the rewritten cost, Eq. (2). Any output may be NULL.
+ * Outputs are device [H][W]. */
+zncc_status zncc_window_stats(zncc_ctx* ctx, const uint8_t* img, int pitch, int32_t* S,
+                              int32_t* Q, float* inv_sigma);
+
+/* ZNCC cost volume, Eq. (1) computed through Eq. (2): C(x,y,d) in [-1, 1],
+ * C = (n*P - S_R*S_T) / sqrt((n*Q_R - S_R^2)(n*Q_T - S_T^2)) with P the window sum of
+ * I_R(x+i,y+j) * I_T(x-d+i,y+j); 0 where either window is flat.
+ * cost: device [H][W][D] of `dtype`. */
+zncc_status zncc_cost_volume(zncc_ctx* ctx, const uint8_t* left, const uint8_t* right,
+                             int pitch, void* cost, zncc_dtype dtype);
+
+/* DT cost aggregation in place (Sec. III-B, Eqs. (3)-(6) with the weights of Eq. (11)),
+ * `iters` times the pass chain left-to-right, right-to-left, up-to-down, down-to-up.
+ * Weights: W = K * exp(-|G(p) - G(q)| / sigma_r), K = exp(-1/sigma_s), G = guide / 255
+ * (guide = the reference/left image), p and q the two pixels of the step. Each pass
+ * computes out = (1-K) * in + W * out(previous pixel in scan order), starting from
+ * (1-K) * in at its first pixel: the paper's literal chain times (1-K)^(4*iters), which
+ * keeps |cost| <= 1 and leaves the WTA result unchanged. sigma_s > 0, sigma_r > 0,
+ * iters >= 0. cost: device [H][W][D] of `dtype` (F16: each pass rounds its output to half). */
+zncc_status dt_aggregate(zncc_ctx* ctx, const uint8_t* guide_left, int pitch, void* cost,
+                         zncc_dtype dtype, float sigma_s, float sigma_r, int iters);
+
+/* WTA disparity (Sec. III-C, Eq. (WTA1)): for each pixel the smallest d with the largest
+ * cost (argmin of 1 - C). cost: device [H][W][D]; disp: device uint16 [H][W]. */
+zncc_status wta_disparity(zncc_ctx* ctx, const void* cost, zncc_dtype dtype, uint16_t* disp);
+
+/* The fused path: window statistics, ZNCC fused with the first horizontal DT pass pair,
+ * the remaining DT passes, and WTA fused into the last vertical pass pair, so that the
+ * volume is written once per horizontal/vertical hand-over and never read back for WTA.
+ * iters == 0 computes ZNCC and WTA in one kernel without storing any volume.
+ * `storage` is the type of the context-owned intermediate volume (F16 halves its traffic).
+ * left/right: device images; disp: device uint16 [H][W]. Sec. V-C fuses ZNCC with L2R and
+ * WTA with D2U in the same way. */
+zncc_status zncc_run(zncc_ctx* ctx, const uint8_t* left, const uint8_t* right, int pitch,
+                     float sigma_s, float sigma_r, int iters, zncc_dtype storage,
+                     uint16_t* disp);
+
+/* zncc_run from host memory: copies the two images (row pitch `pitch`) to context-owned
+ * device buffers, runs the fused path, copies the disparity map back to disp_host
+ * (uint16 [H][W]) and synchronizes the stream before returning. Host buffers may be
+ * pageable or pinned (pinned copies run asynchronously with respect to other streams). */
+zncc_status zncc_run_host(zncc_ctx* ctx, const uint8_t* left_host, const uint8_t* right_host,
+                          int pitch, float sigma_s, float sigma_r, int iters,
+                          zncc_dtype storage, uint16_t* disp_host);
+
+/* Text of the last error recorded on this context ("" if none). Valid until the next call
+ * on the context. ctx == NULL returns the last error of a failed zncc_create. */
+const char* zncc_last_error(const zncc_ctx* ctx);
+
+/* Static text for a status code. */
+const char* zncc_status_string(zncc_status status);
+
+/* Number of kernels this library has launched in this process (all contexts). */
+uint64_t zncc_kernel_launch_count(void);
+
+/* Per-kernel timing, for measurement. While enabled, every kernel the context launches is
+ * bracketed by two CUDA events recorded on the context's stream (events are created on
+ * demand and reused). */
+zncc_status zncc_profile_enable(zncc_ctx* ctx, int enable);
+
+/* Synchronizes the context's stream, then writes for each kernel kind k < nkinds the summed
+ * device time in milliseconds (total_ms[k]) and the number of launches (launches[k]) since
+ * the previous read, and forgets them. Kinds are named by zncc_profile_kind_name. */
+zncc_status zncc_profile_read(zncc_ctx* ctx, double* total_ms, uint64_t* launches, int nkinds);
+
+/* Number of kernel kinds, and the static name of kind k (NULL when out of range). */
+int zncc_profile_nkinds(void);
+const char* zncc_profile_kind_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZNCC_H_ */

@@ -1,0 +1,506 @@
+// api.cu -- the C ABI of libzncc.so (declared in include/zncc.h): argument checks, the
+// context's device scratch, and the launch sequence of each call.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "zncc.h"
+
+using namespace zncc;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+thread_local std::string g_create_error;
+
+struct Dims {
+    int nch, ds, lpc;
+};
+
+// Kernel kinds for per-kernel timing (zncc_profile_*).
+enum Kind {
+    K_STATS = 0, K_WEIGHTS, K_ZNCC_RAW, K_ZNCC_HPAIR, K_ZNCC_WTA, K_DT_HPAIR, K_DT_VPAIR,
+    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_WTA_FINAL, K_NKINDS
+};
+const char* const kKindNames[K_NKINDS] = {
+    "window_stats", "dt_weights", "zncc_cost", "zncc_cost_hpair", "zncc_cost_wta",
+    "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume", "wta_finalize"};
+
+struct ProfRecord {
+    int kind, ev0, ev1;
+};
+
+}  // namespace
+
+struct zncc_ctx {
+    int W = 0, H = 0, D = 0, win = 0, r = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // per-image window statistics (left over [0, W), right over [-(D-1), W))
+    int* SL = nullptr;
+    float* ISL = nullptr;
+    int* SR = nullptr;
+    float* ISR = nullptr;
+    // DT edge weights: eh [H][W], evt [W][H]
+    float* eh = nullptr;
+    float* evt = nullptr;
+    unsigned long long* keys = nullptr;   // [H][W] WTA keys
+    // the fused path's intermediate volume, allocated on first use
+    void* vol = nullptr;
+    size_t vol_bytes = 0;
+    // device copies for zncc_run_host
+    uint8_t* img = nullptr;               // 2 x [H][W]
+    uint16_t* disp = nullptr;             // [H][W]
+    // per-kernel timing
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;
+    int events_used = 0;
+    std::vector<ProfRecord> records;
+};
+
+namespace {
+
+zncc_status fail(zncc_ctx* c, zncc_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+zncc_status cuda_fail(zncc_ctx* c, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, ZNCC_ECUDA, m);
+}
+
+#define ZNCC_CUDA(c, call, what)                       \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+// An event of the context's pool (grown on demand), or -1 if one cannot be created.
+int prof_event(zncc_ctx* c) {
+    if (c->events_used == (int)c->events.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        c->events.push_back(e);
+    }
+    return c->events_used++;
+}
+
+#define ZNCC_LAUNCH(c, kind, call, what)                                      \
+    do {                                                                      \
+        g_launches.fetch_add(1, std::memory_order_relaxed);                   \
+        int ev0_ = -1;                                                        \
+        if ((c)->profiling && (ev0_ = prof_event(c)) >= 0)                    \
+            cudaEventRecord((c)->events[ev0_], (c)->stream);                  \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what);                 \
+        int ev1_ = ev0_ >= 0 ? prof_event(c) : -1;                            \
+        if (ev1_ >= 0) {                                                      \
+            cudaEventRecord((c)->events[ev1_], (c)->stream);                  \
+            (c)->records.push_back(ProfRecord{(kind), ev0_, ev1_});           \
+        }                                                                     \
+    } while (0)
+
+// Disparities per block and lines per block of a DT line pair of length n: a block keeps
+// n x ds costs in registers (ds * n <= 32768 floats, at most 128 KB), 16 positions x 4
+// disparities per thread.
+// The chunk count is padded so that a line's threads fill whole warps (every warp-wide
+// shuffle then has all 32 lanes); padded chunks lie past the line end and hold zeros.
+int padded_chunks(int n, int ds) {
+    const int per_warp = 32 / (ds / kG);
+    const int nch = (n + kL - 1) / kL;
+    return (nch + per_warp - 1) / per_warp * per_warp;
+}
+
+Dims line_dims(int n) {
+    Dims d;
+    d.ds = n <= 1024 ? 32 : (n <= 2048 ? 16 : 8);
+    d.nch = padded_chunks(n, d.ds);
+    const int per_line = d.nch * (d.ds / kG);
+    d.lpc = std::max(1, std::min(8, (256 + per_line - 1) / per_line));
+    while (d.lpc > 1 && d.lpc * per_line > 512) --d.lpc;   // blocks are at most 512 threads
+    return d;
+}
+
+// The ZNCC row kernel: one row x 16 (8 above 2048 columns) disparities per block.
+Dims row_dims(int W) {
+    Dims d;
+    d.ds = W <= 2048 ? 16 : 8;
+    d.nch = padded_chunks(W, d.ds);
+    d.lpc = 1;
+    return d;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+zncc_status check_images(zncc_ctx* c, const void* a, const void* b, int pitch) {
+    if (!a || !b) return fail(c, ZNCC_EINVAL, "image pointer is NULL");
+    if (pitch < c->W) return fail(c, ZNCC_EINVAL, "pitch is smaller than the width");
+    return ZNCC_OK;
+}
+
+zncc_status check_dt(zncc_ctx* c, float sigma_s, float sigma_r, int iters) {
+    if (!(sigma_s > 0.0f) || !isfinite(sigma_s)) return fail(c, ZNCC_EINVAL, "sigma_s must be > 0");
+    if (!(sigma_r > 0.0f) || !isfinite(sigma_r)) return fail(c, ZNCC_EINVAL, "sigma_r must be > 0");
+    if (iters < 0 || iters > 64) return fail(c, ZNCC_EINVAL, "iters must be in [0, 64]");
+    return ZNCC_OK;
+}
+
+// Window statistics of both images into the context scratch.
+zncc_status run_stats(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch) {
+    ZNCC_LAUNCH(c, K_STATS, launch_window_stats(left, pitch, c->W, c->H, c->r, 0, c->W, c->SL, nullptr,
+                                       c->ISL, c->stream), "window statistics (left)");
+    ZNCC_LAUNCH(c, K_STATS, launch_window_stats(right, pitch, c->W, c->H, c->r, -(c->D - 1), c->W + c->D - 1,
+                                       c->SR, nullptr, c->ISR, c->stream), "window statistics (right)");
+    return ZNCC_OK;
+}
+
+zncc_status run_weights(zncc_ctx* c, const uint8_t* guide, int pitch, float sigma_s, float sigma_r) {
+    const float K = (float)exp(-1.0 / (double)sigma_s);
+    const float inv = (float)(1.0 / (255.0 * (double)sigma_r));
+    ZNCC_LAUNCH(c, K_WEIGHTS, launch_dt_weights(guide, pitch, c->W, c->H, K, inv, c->eh, c->evt, c->stream),
+                "DT edge weights");
+    return ZNCC_OK;
+}
+
+RowArgs row_args(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch) {
+    RowArgs a;
+    memset(&a, 0, sizeof(a));
+    const Dims rd = row_dims(c->W);
+    a.left = left;
+    a.right = right;
+    a.pitch = pitch;
+    a.W = c->W;
+    a.H = c->H;
+    a.D = c->D;
+    a.SL = c->SL;
+    a.ISL = c->ISL;
+    a.SR = c->SR;
+    a.ISR = c->ISR;
+    a.nch = rd.nch;
+    a.ds = rd.ds;
+    a.d_begin = 0;
+    a.d_end = c->D;
+    a.dstride = c->D;
+    a.d_out0 = 0;
+    a.eh = c->eh;
+    a.keys = c->keys;
+    return a;
+}
+
+bool volume_vec(const void* vol, int dtype, long long dstride) {
+    return dstride % 4 == 0 && aligned(vol, dtype == 0 ? 16 : 8);
+}
+
+// One DT pair along rows (horiz) or columns of a [H][W][dstride] volume.
+zncc_status run_line_pair(zncc_ctx* c, void* vol, int dtype, long long dstride, bool horiz,
+                          float s, int mode) {
+    LineArgs a;
+    memset(&a, 0, sizeof(a));
+    const int n = horiz ? c->W : c->H;
+    const Dims d = line_dims(n);
+    a.vol = vol;
+    a.elem_stride = horiz ? dstride : (long long)c->W * dstride;
+    a.line_stride = horiz ? (long long)c->W * dstride : dstride;
+    a.n = n;
+    a.nlines = horiz ? c->H : c->W;
+    a.dcount = c->D;
+    a.ds = d.ds;
+    a.lpc = d.lpc;
+    a.nch = d.nch;
+    a.ew = horiz ? c->eh : c->evt;
+    a.ew_line_stride = horiz ? c->W : c->H;
+    a.s = s;
+    a.vec = volume_vec(vol, dtype, dstride) ? 1 : 0;
+    a.keys = c->keys;
+    a.pix_line = horiz ? c->W : 1;
+    a.pix_pos = horiz ? 1 : c->W;
+    a.d_base = 0;
+    ZNCC_LAUNCH(c, horiz ? K_DT_HPAIR : (mode == kLineWta ? K_DT_VPAIR_WTA : K_DT_VPAIR), launch_line_pair(a, mode, dtype, c->stream), horiz ? "DT horizontal pair" : "DT vertical pair");
+    return ZNCC_OK;
+}
+
+#define ZNCC_TRY(expr)                   \
+    do {                                 \
+        zncc_status s_ = (expr);         \
+        if (s_ != ZNCC_OK) return s_;    \
+    } while (0)
+
+template <typename T>
+void free_dev(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void release(zncc_ctx* c) {
+    free_dev(c->SL);
+    free_dev(c->ISL);
+    free_dev(c->SR);
+    free_dev(c->ISR);
+    free_dev(c->eh);
+    free_dev(c->evt);
+    free_dev(c->keys);
+    free_dev(c->vol);
+    free_dev(c->img);
+    free_dev(c->disp);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    c->events.clear();
+    c->records.clear();
+    c->events_used = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+zncc_status zncc_create(int width, int height, int max_disp, int win, zncc_ctx** out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, ZNCC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (width < 1 || height < 1) return fail(nullptr, ZNCC_EINVAL, "width and height must be >= 1");
+    if (width > 4096 || height > 4096)
+        return fail(nullptr, ZNCC_EUNSUPPORTED, "width and height must be <= 4096");
+    if (max_disp < 1) return fail(nullptr, ZNCC_EINVAL, "max_disp must be >= 1");
+    if (max_disp > 1024) return fail(nullptr, ZNCC_EUNSUPPORTED, "max_disp must be <= 1024");
+    if (win < 3 || win > 15 || win % 2 == 0)
+        return fail(nullptr, ZNCC_EINVAL, "win must be odd and in [3, 15]");
+    zncc_ctx* c = new (std::nothrow) zncc_ctx();
+    if (!c) return fail(nullptr, ZNCC_ENOMEM, "host allocation failed");
+    c->W = width;
+    c->H = height;
+    c->D = max_disp;
+    c->win = win;
+    c->r = win / 2;
+    cudaError_t e = cudaGetDevice(&c->device);
+    const size_t npix = (size_t)width * height;
+    const size_t nright = (size_t)(width + max_disp - 1) * height;
+    if (e == cudaSuccess) e = cudaMalloc(&c->SL, npix * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->ISL, npix * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->SR, nright * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->ISR, nright * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->eh, npix * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->evt, npix * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->keys, npix * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        zncc_status s = e == cudaErrorMemoryAllocation ? ZNCC_ENOMEM : ZNCC_ECUDA;
+        std::string m = std::string("zncc_create: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        release(c);
+        delete c;
+        return fail(nullptr, s, m);
+    }
+    *out = c;
+    return ZNCC_OK;
+}
+
+zncc_status zncc_destroy(zncc_ctx* c) {
+    if (!c) return ZNCC_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    release(c);
+    delete c;
+    return ZNCC_OK;
+}
+
+zncc_status zncc_set_stream(zncc_ctx* c, void* stream) {
+    if (!c) return ZNCC_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return ZNCC_OK;
+}
+
+size_t zncc_volume_bytes(const zncc_ctx* c, zncc_dtype dtype) {
+    if (!c || (dtype != ZNCC_F32 && dtype != ZNCC_F16)) return 0;
+    return (size_t)c->W * c->H * c->D * (dtype == ZNCC_F32 ? 4 : 2);
+}
+
+zncc_status zncc_window_stats(zncc_ctx* c, const uint8_t* img, int pitch, int32_t* S, int32_t* Q,
+                              float* inv_sigma) {
+    if (!c) return ZNCC_EINVAL;
+    c->err.clear();
+    if (!img) return fail(c, ZNCC_EINVAL, "image pointer is NULL");
+    if (pitch < c->W) return fail(c, ZNCC_EINVAL, "pitch is smaller than the width");
+    if (!S && !Q && !inv_sigma) return ZNCC_OK;
+    ZNCC_LAUNCH(c, K_STATS, launch_window_stats(img, pitch, c->W, c->H, c->r, 0, c->W, S, Q, inv_sigma, c->stream),
+                "window statistics");
+    return ZNCC_OK;
+}
+
+zncc_status zncc_cost_volume(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch,
+                             void* cost, zncc_dtype dtype) {
+    if (!c) return ZNCC_EINVAL;
+    c->err.clear();
+    ZNCC_TRY(check_images(c, left, right, pitch));
+    if (!cost) return fail(c, ZNCC_EINVAL, "cost pointer is NULL");
+    if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
+    ZNCC_TRY(run_stats(c, left, right, pitch));
+    RowArgs a = row_args(c, left, right, pitch);
+    a.vol = cost;
+    a.vec = volume_vec(cost, dtype, c->D) ? 1 : 0;
+    ZNCC_LAUNCH(c, K_ZNCC_RAW, launch_zncc_row(c->r, a, kModeRaw, dtype, c->stream), "ZNCC cost");
+    return ZNCC_OK;
+}
+
+zncc_status dt_aggregate(zncc_ctx* c, const uint8_t* guide, int pitch, void* cost, zncc_dtype dtype,
+                         float sigma_s, float sigma_r, int iters) {
+    if (!c) return ZNCC_EINVAL;
+    c->err.clear();
+    if (!guide) return fail(c, ZNCC_EINVAL, "guide pointer is NULL");
+    if (pitch < c->W) return fail(c, ZNCC_EINVAL, "pitch is smaller than the width");
+    if (!cost) return fail(c, ZNCC_EINVAL, "cost pointer is NULL");
+    if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
+    ZNCC_TRY(check_dt(c, sigma_s, sigma_r, iters));
+    if (iters == 0) return ZNCC_OK;
+    ZNCC_TRY(run_weights(c, guide, pitch, sigma_s, sigma_r));
+    const float s = (float)(1.0 - exp(-1.0 / (double)sigma_s));
+    for (int it = 0; it < iters; ++it) {
+        ZNCC_TRY(run_line_pair(c, cost, dtype, c->D, true, s, kLineStore));
+        ZNCC_TRY(run_line_pair(c, cost, dtype, c->D, false, s, kLineStore));
+    }
+    return ZNCC_OK;
+}
+
+zncc_status wta_disparity(zncc_ctx* c, const void* cost, zncc_dtype dtype, uint16_t* disp) {
+    if (!c) return ZNCC_EINVAL;
+    c->err.clear();
+    if (!cost || !disp) return fail(c, ZNCC_EINVAL, "cost or disp pointer is NULL");
+    if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
+    ZNCC_LAUNCH(c, K_WTA_VOLUME, launch_wta_volume(cost, dtype, c->W, c->H, c->D, disp, c->stream), "WTA");
+    return ZNCC_OK;
+}
+
+zncc_status zncc_run(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch, float sigma_s,
+                     float sigma_r, int iters, zncc_dtype storage, uint16_t* disp) {
+    if (!c) return ZNCC_EINVAL;
+    c->err.clear();
+    ZNCC_TRY(check_images(c, left, right, pitch));
+    if (!disp) return fail(c, ZNCC_EINVAL, "disp pointer is NULL");
+    if (storage != ZNCC_F32 && storage != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
+    ZNCC_TRY(check_dt(c, sigma_s, sigma_r, iters));
+    const size_t npix = (size_t)c->W * c->H;
+
+    ZNCC_TRY(run_stats(c, left, right, pitch));
+    ZNCC_CUDA(c, cudaMemsetAsync(c->keys, 0, npix * sizeof(unsigned long long), c->stream), "key reset");
+    RowArgs a = row_args(c, left, right, pitch);
+    if (iters == 0) {
+        ZNCC_LAUNCH(c, K_ZNCC_WTA, launch_zncc_row(c->r, a, kModeWta, 0, c->stream), "ZNCC + WTA");
+    } else {
+        const int dt = storage == ZNCC_F32 ? 0 : 1;
+        const long long dstride = (c->D + 3) / 4 * 4;   // padded so every access is vectorised
+        const size_t need = npix * (size_t)dstride * (dt == 0 ? 4 : 2);
+        if (c->vol_bytes < need) {
+            free_dev(c->vol);
+            c->vol_bytes = 0;
+            cudaError_t e = cudaMalloc(&c->vol, need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, e == cudaErrorMemoryAllocation ? ZNCC_ENOMEM : ZNCC_ECUDA,
+                            std::string("cost volume allocation: ") + cudaGetErrorString(e));
+            }
+            c->vol_bytes = need;
+        }
+        ZNCC_TRY(run_weights(c, left, pitch, sigma_s, sigma_r));
+        const float s = (float)(1.0 - exp(-1.0 / (double)sigma_s));
+        a.vol = c->vol;
+        a.dstride = dstride;
+        a.vec = volume_vec(c->vol, dt, dstride) ? 1 : 0;
+        a.s = s;
+        ZNCC_LAUNCH(c, K_ZNCC_HPAIR, launch_zncc_row(c->r, a, kModeHPair, dt, c->stream), "ZNCC + horizontal DT pair");
+        for (int it = 0; it < iters; ++it) {
+            const bool last = it == iters - 1;
+            ZNCC_TRY(run_line_pair(c, c->vol, dt, dstride, false, s, last ? kLineWta : kLineStore));
+            if (!last) ZNCC_TRY(run_line_pair(c, c->vol, dt, dstride, true, s, kLineStore));
+        }
+    }
+    ZNCC_LAUNCH(c, K_WTA_FINAL, launch_wta_finalize(c->keys, (int)npix, disp, c->stream), "WTA keys to disparities");
+    return ZNCC_OK;
+}
+
+zncc_status zncc_run_host(zncc_ctx* c, const uint8_t* left_host, const uint8_t* right_host, int pitch,
+                          float sigma_s, float sigma_r, int iters, zncc_dtype storage,
+                          uint16_t* disp_host) {
+    if (!c) return ZNCC_EINVAL;
+    c->err.clear();
+    ZNCC_TRY(check_images(c, left_host, right_host, pitch));
+    if (!disp_host) return fail(c, ZNCC_EINVAL, "disp_host pointer is NULL");
+    const size_t npix = (size_t)c->W * c->H;
+    if (!c->img) {
+        cudaError_t e = cudaMalloc(&c->img, 2 * npix);
+        if (e == cudaSuccess) e = cudaMalloc(&c->disp, npix * sizeof(uint16_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_dev(c->img);
+            free_dev(c->disp);
+            return fail(c, ZNCC_ENOMEM, std::string("image buffers: ") + cudaGetErrorString(e));
+        }
+    }
+    ZNCC_CUDA(c, cudaMemcpy2DAsync(c->img, c->W, left_host, pitch, c->W, c->H, cudaMemcpyHostToDevice, c->stream),
+              "left image upload");
+    ZNCC_CUDA(c, cudaMemcpy2DAsync(c->img + npix, c->W, right_host, pitch, c->W, c->H, cudaMemcpyHostToDevice,
+                                   c->stream), "right image upload");
+    ZNCC_TRY(zncc_run(c, c->img, c->img + npix, c->W, sigma_s, sigma_r, iters, storage, c->disp));
+    ZNCC_CUDA(c, cudaMemcpyAsync(disp_host, c->disp, npix * sizeof(uint16_t), cudaMemcpyDeviceToHost, c->stream),
+              "disparity download");
+    ZNCC_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    return ZNCC_OK;
+}
+
+const char* zncc_last_error(const zncc_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+const char* zncc_status_string(zncc_status s) {
+    switch (s) {
+        case ZNCC_OK: return "ZNCC_OK";
+        case ZNCC_EINVAL: return "ZNCC_EINVAL";
+        case ZNCC_ENOMEM: return "ZNCC_ENOMEM";
+        case ZNCC_ECUDA: return "ZNCC_ECUDA";
+        case ZNCC_EBUSY: return "ZNCC_EBUSY";
+        case ZNCC_ENOTREADY: return "ZNCC_ENOTREADY";
+        case ZNCC_ETIMEOUT: return "ZNCC_ETIMEOUT";
+        case ZNCC_EUNSUPPORTED: return "ZNCC_EUNSUPPORTED";
+    }
+    return "unknown status";
+}
+
+uint64_t zncc_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+zncc_status zncc_profile_enable(zncc_ctx* c, int enable) {
+    if (!c) return ZNCC_EINVAL;
+    c->profiling = enable != 0;
+    return ZNCC_OK;
+}
+
+zncc_status zncc_profile_read(zncc_ctx* c, double* total_ms, uint64_t* launches, int nkinds) {
+    if (!c || nkinds < 0 || (nkinds > 0 && (!total_ms || !launches))) return ZNCC_EINVAL;
+    c->err.clear();
+    for (int k = 0; k < nkinds; ++k) {
+        total_ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    ZNCC_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    for (const ProfRecord& r : c->records) {
+        float ms = 0.0f;
+        ZNCC_CUDA(c, cudaEventElapsedTime(&ms, c->events[r.ev0], c->events[r.ev1]), "event time");
+        if (r.kind < nkinds) {
+            total_ms[r.kind] += ms;
+            launches[r.kind] += 1;
+        }
+    }
+    c->records.clear();
+    c->events_used = 0;
+    return ZNCC_OK;
+}
+
+int zncc_profile_nkinds(void) { return K_NKINDS; }
+
+const char* zncc_profile_kind_name(int kind) {
+    return kind >= 0 && kind < K_NKINDS ? kKindNames[kind] : nullptr;
+}
+
+}  // extern "C"

@@ -1,0 +1,17 @@
+// zncc_row.cu -- instantiates k_zncc_row for one window radius. The build compiles this
+// file once per radius 1..7 (window sides 3..15) with -DZNCC_R=<radius>, in parallel.
+#include "zncc_row.cuh"
+
+#ifndef ZNCC_R
+#error "compile with -DZNCC_R=<window radius 1..7>"
+#endif
+
+#define ZNCC_CAT2(a, b) a##b
+#define ZNCC_CAT(a, b) ZNCC_CAT2(a, b)
+
+namespace zncc {
+cudaError_t ZNCC_CAT(launch_zncc_row_r, ZNCC_R)(const RowArgs& a, int mode, int dtype,
+                                                cudaStream_t st) {
+    return launch_zncc_row_impl<ZNCC_R>(a, mode, dtype, st);
+}
+}  // namespace zncc

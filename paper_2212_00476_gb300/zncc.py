@@ -1,0 +1,178 @@
+"""Thin ctypes binding of libzncc.so (include/zncc.h): argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels; PyTorch only provides device
+memory and streams. There is no CPU fallback: if the library is missing or cannot be
+loaded, every call raises.
+
+The methods of ZnccContext carry the names of the C calls they wrap:
+
+    zncc_window_stats, zncc_cost_volume, dt_aggregate, wta_disparity, zncc_run, zncc_run_host
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libzncc.so")
+
+ZNCC_OK, ZNCC_EINVAL, ZNCC_ENOMEM, ZNCC_ECUDA, ZNCC_EBUSY, ZNCC_ENOTREADY, ZNCC_ETIMEOUT, \
+    ZNCC_EUNSUPPORTED = range(8)
+ZNCC_F32, ZNCC_F16 = 0, 1
+STATUS_NAMES = ["ZNCC_OK", "ZNCC_EINVAL", "ZNCC_ENOMEM", "ZNCC_ECUDA", "ZNCC_EBUSY",
+                "ZNCC_ENOTREADY", "ZNCC_ETIMEOUT", "ZNCC_EUNSUPPORTED"]
+
+# every entry point declared in include/zncc.h: (name, restype, argtypes)
+_vp, _i, _f, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+SIGNATURES = [
+    ("zncc_create", _i, [_i, _i, _i, _i, ctypes.POINTER(_vp)]),
+    ("zncc_destroy", _i, [_vp]),
+    ("zncc_set_stream", _i, [_vp, _vp]),
+    ("zncc_volume_bytes", _sz, [_vp, _i]),
+    ("zncc_window_stats", _i, [_vp, _vp, _i, _vp, _vp, _vp]),
+    ("zncc_cost_volume", _i, [_vp, _vp, _vp, _i, _vp, _i]),
+    ("dt_aggregate", _i, [_vp, _vp, _i, _vp, _i, _f, _f, _i]),
+    ("wta_disparity", _i, [_vp, _vp, _i, _vp]),
+    ("zncc_run", _i, [_vp, _vp, _vp, _i, _f, _f, _i, _i, _vp]),
+    ("zncc_run_host", _i, [_vp, _vp, _vp, _i, _f, _f, _i, _i, _vp]),
+    ("zncc_last_error", ctypes.c_char_p, [_vp]),
+    ("zncc_status_string", ctypes.c_char_p, [_i]),
+    ("zncc_kernel_launch_count", ctypes.c_uint64, []),
+    ("zncc_profile_enable", _i, [_vp, _i]),
+    ("zncc_profile_read", _i, [_vp, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_uint64), _i]),
+    ("zncc_profile_nkinds", _i, []),
+    ("zncc_profile_kind_name", ctypes.c_char_p, [_i]),
+]
+
+_lib = None
+_lock = threading.Lock()
+
+
+class ZnccError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+def lib():
+    """The loaded library (built in-tree by build() / __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_2212_00476_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _ptr(t) -> int:
+    """Device pointer of a torch tensor (must be contiguous)."""
+    assert t.is_contiguous(), "tensors passed to libzncc must be contiguous"
+    return t.data_ptr()
+
+
+def launch_count() -> int:
+    return int(lib().zncc_kernel_launch_count())
+
+
+class ZnccContext:
+    """A libzncc context for W x H pairs, disparities [0, max_disp), window side `win`."""
+
+    def __init__(self, width: int, height: int, max_disp: int, win: int, stream=None):
+        L = lib()
+        h = _vp()
+        st = L.zncc_create(int(width), int(height), int(max_disp), int(win), ctypes.byref(h))
+        if st != ZNCC_OK:
+            raise ZnccError(st, L.zncc_last_error(None).decode())
+        self._h = h
+        self.W, self.H, self.D, self.win = int(width), int(height), int(max_disp), int(win)
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- lifetime ---------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().zncc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st):
+        if st != ZNCC_OK:
+            raise ZnccError(st, lib().zncc_last_error(self._h).decode())
+
+    def set_stream(self, stream):
+        """Bind a torch.cuda.Stream (or a raw cudaStream_t int, or None)."""
+        raw = getattr(stream, "cuda_stream", stream)
+        self._check(lib().zncc_set_stream(self._h, raw or None))
+
+    def volume_bytes(self, dtype: int = ZNCC_F32) -> int:
+        return int(lib().zncc_volume_bytes(self._h, dtype))
+
+    def profile_enable(self, on: bool = True):
+        self._check(lib().zncc_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel kind: (total device ms, launches)} since the previous read."""
+        L = lib()
+        n = L.zncc_profile_nkinds()
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_uint64 * n)()
+        self._check(L.zncc_profile_read(self._h, ms, cnt, n))
+        return {L.zncc_profile_kind_name(k).decode(): (ms[k], int(cnt[k])) for k in range(n)
+                if cnt[k]}
+
+    # -- the C calls --------------------------------------------------------------------
+    def zncc_window_stats(self, img, S=None, Q=None, inv_sigma=None):
+        self._check(lib().zncc_window_stats(self._h, _ptr(img), img.stride(0),
+                                            _ptr(S) if S is not None else None,
+                                            _ptr(Q) if Q is not None else None,
+                                            _ptr(inv_sigma) if inv_sigma is not None else None))
+
+    def zncc_cost_volume(self, left, right, cost, dtype: int = ZNCC_F32):
+        self._check(lib().zncc_cost_volume(self._h, _ptr(left), _ptr(right), left.stride(0),
+                                           _ptr(cost), dtype))
+
+    def dt_aggregate(self, guide, cost, sigma_s: float, sigma_r: float, iters: int,
+                     dtype: int = ZNCC_F32):
+        self._check(lib().dt_aggregate(self._h, _ptr(guide), guide.stride(0), _ptr(cost), dtype,
+                                       float(sigma_s), float(sigma_r), int(iters)))
+
+    def wta_disparity(self, cost, disp, dtype: int = ZNCC_F32):
+        self._check(lib().wta_disparity(self._h, _ptr(cost), dtype, _ptr(disp)))
+
+    def zncc_run(self, left, right, disp, sigma_s: float, sigma_r: float, iters: int,
+                 storage: int = ZNCC_F32):
+        self._check(lib().zncc_run(self._h, _ptr(left), _ptr(right), left.stride(0),
+                                   float(sigma_s), float(sigma_r), int(iters), int(storage),
+                                   _ptr(disp)))
+
+    def zncc_run_host(self, left: np.ndarray, right: np.ndarray, disp: np.ndarray,
+                      sigma_s: float, sigma_r: float, iters: int, storage: int = ZNCC_F32):
+        assert left.dtype == np.uint8 and right.dtype == np.uint8 and disp.dtype == np.uint16
+        assert left.flags.c_contiguous and right.flags.c_contiguous and disp.flags.c_contiguous
+        self._check(lib().zncc_run_host(self._h, left.ctypes.data, right.ctypes.data,
+                                        left.strides[0], float(sigma_s), float(sigma_r),
+                                        int(iters), int(storage), disp.ctypes.data))

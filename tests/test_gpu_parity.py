@@ -1,0 +1,301 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances (written here, derived in the design doc):
+  window sums S, Q          bit-exact
+  ZNCC cost                 |gpu - oracle| <= 1e-5 absolute
+  aggregated cost (FP32)    |gpu - oracle| <= 1e-4 * A_hat(x, y), A_hat = DT of an all-ones plane
+  disparity                 exact, except pixels whose oracle best-vs-second gap is below
+                            1e-5 (1e-5 * A_hat after aggregation); those are counted, not failed
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import config_pair, make_pair
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2212_00476_gb300 import zncc as Z  # noqa: E402
+
+SIG_S, SIG_R = 20.0, 0.1
+ZNCC_TOL = 1e-5
+AGG_TOL = 1e-4
+GAP_TOL = 1e-5
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host_u16(t):
+    return t.cpu().numpy().view(np.uint16)
+
+
+def rand_pair(h, w, d, seed, disp="rects"):
+    return make_pair(h, w, d, seed=seed, disp=disp)
+
+
+def gpu_cost(ctx, left, right, dtype=Z.ZNCC_F32):
+    H, W = left.shape
+    tdt = torch.float32 if dtype == Z.ZNCC_F32 else torch.float16
+    c = torch.empty((H, W, ctx.D), dtype=tdt, device="cuda")
+    ctx.zncc_cost_volume(dev(left), dev(right), c, dtype)
+    torch.cuda.synchronize()
+    return c
+
+
+def check_disp(gpu, ref, gap, scale, what):
+    """Exact outside near-ties; returns the number of near-tie pixels skipped."""
+    near = gap < GAP_TOL * scale
+    bad = (gpu != ref) & ~near
+    assert not bad.any(), f"{what}: {int(bad.sum())} disparities differ away from near-ties " \
+                          f"(first at {np.argwhere(bad)[:5].tolist()})"
+    return int(near.sum())
+
+
+# ---------------------------------------------------------------------------------------
+STATS_CASES = [(96, 320, 4), (17, 37, 1), (5, 3, 7), (1, 1, 2), (64, 1, 3), (1, 70, 5),
+               (40, 2100, 6), (33, 129, 7)]
+
+
+@pytest.mark.parametrize("h,w,r", STATS_CASES)
+def test_window_stats_bit_exact(h, w, r):
+    rng = np.random.default_rng(h * 1000 + w + r)
+    img = rng.integers(0, 256, (h, w), dtype=np.uint8)
+    img[: h // 2, : w // 3] = 77                          # flat region: inv_sigma = 0
+    ctx = Z.ZnccContext(w, h, 4, 2 * r + 1)
+    S = torch.empty((h, w), dtype=torch.int32, device="cuda")
+    Q = torch.empty_like(S)
+    I = torch.empty((h, w), dtype=torch.float32, device="cuda")
+    ctx.zncc_window_stats(dev(img), S, Q, I)
+    torch.cuda.synchronize()
+    S_ref, Q_ref = oracle.window_sums(img, r)
+    assert np.array_equal(S.cpu().numpy(), S_ref)
+    assert np.array_equal(Q.cpu().numpy(), Q_ref)
+    n = (2 * r + 1) ** 2
+    var = n * Q_ref - S_ref * S_ref
+    ref_is = np.where(var > 0, 1.0 / np.sqrt(np.maximum(var, 1)), 0.0)
+    got = I.cpu().numpy().astype(np.float64)
+    assert np.array_equal(got == 0, var == 0)
+    assert np.allclose(got, ref_is, rtol=4e-7, atol=0)
+    ctx.close()
+
+
+def test_window_stats_pitched_image():
+    rng = np.random.default_rng(5)
+    big = rng.integers(0, 256, (20, 64), dtype=np.uint8)
+    img_t = dev(big)                                      # pitch 64, width 50
+    ctx = Z.ZnccContext(50, 20, 4, 5)
+    S = torch.empty((20, 50), dtype=torch.int32, device="cuda")
+    assert Z.lib().zncc_window_stats(ctx._h, img_t.data_ptr(), 64, S.data_ptr(), None,
+                                     None) == Z.ZNCC_OK
+    torch.cuda.synchronize()
+    S_ref, _ = oracle.window_sums(big[:, :50], 2)
+    assert np.array_equal(S.cpu().numpy(), S_ref)
+
+
+# ---------------------------------------------------------------------------------------
+COST_CASES = [(96, 320, 32, 9), (17, 37, 13, 3), (5, 7, 20, 5), (1, 1, 1, 3), (40, 100, 64, 15),
+              (33, 70, 8, 11), (24, 50, 16, 13), (1, 64, 4, 7), (64, 1, 4, 7), (6, 2100, 8, 3),
+              (20, 45, 33, 9)]
+
+
+@pytest.mark.parametrize("h,w,d,win", COST_CASES)
+def test_cost_volume_matches_oracle(h, w, d, win):
+    p = rand_pair(h, w, max(d, 1), seed=h * 7 + w + d + win)
+    ctx = Z.ZnccContext(w, h, d, win)
+    c = gpu_cost(ctx, p.left, p.right).cpu().numpy().astype(np.float64)
+    ref = oracle.zncc_volume(p.left, p.right, d, win // 2)
+    err = np.abs(c - ref).max()
+    assert err <= ZNCC_TOL, f"max |dC| = {err}"
+    ctx.close()
+
+
+def test_cost_volume_fp16_storage_is_rounded_fp32():
+    p = rand_pair(30, 90, 24, seed=9)
+    ctx = Z.ZnccContext(90, 30, 24, 9)
+    c32 = gpu_cost(ctx, p.left, p.right, Z.ZNCC_F32)
+    c16 = gpu_cost(ctx, p.left, p.right, Z.ZNCC_F16)
+    assert torch.equal(c32.half(), c16)
+
+
+def test_zero_variance_gives_zero_cost():
+    left = np.full((12, 40), 100, np.uint8)
+    right = np.random.default_rng(3).integers(0, 256, (12, 40), dtype=np.uint8)
+    ctx = Z.ZnccContext(40, 12, 8, 5)
+    c = gpu_cost(ctx, left, right)
+    assert (c == 0).all()
+
+
+# ---------------------------------------------------------------------------------------
+DT_CASES = [(13, 37, 8, 1), (13, 37, 8, 3), (1, 50, 4, 2), (50, 1, 4, 2), (384, 40, 4, 1),
+            (20, 1100, 4, 1), (3, 2100, 4, 1), (1030, 3, 4, 1), (16, 30, 5, 3), (7, 9, 70, 2)]
+
+
+@pytest.mark.parametrize("h,w,d,iters", DT_CASES)
+def test_dt_aggregate_matches_oracle(h, w, d, iters):
+    rng = np.random.default_rng(h + 31 * w + d)
+    guide = make_pair(h, w, 4, seed=h + w).left
+    C = rng.uniform(-1, 1, (h, w, d)).astype(np.float32)
+    ctx = Z.ZnccContext(w, h, d, 3)
+    t = dev(C)
+    ctx.dt_aggregate(dev(guide), t, SIG_S, SIG_R, iters)
+    torch.cuda.synchronize()
+    got = t.cpu().numpy().astype(np.float64)
+    w4 = oracle.dt_weights(guide, SIG_S, SIG_R)
+    ref = oracle.dt_aggregate(C.astype(np.float64), w4, SIG_S, iters)
+    A = oracle.ones_response(guide, SIG_S, SIG_R, iters)
+    rel = (np.abs(got - ref) / A[:, :, None]).max()
+    assert rel <= AGG_TOL, f"max |dC|/A_hat = {rel}"
+
+
+def test_dt_aggregate_fp16_storage_error_is_small():
+    h, w, d = 40, 90, 16
+    rng = np.random.default_rng(1)
+    guide = make_pair(h, w, 4, seed=2).left
+    C = rng.uniform(-1, 1, (h, w, d)).astype(np.float32)
+    ctx = Z.ZnccContext(w, h, d, 3)
+    t = dev(C).half()
+    ctx.dt_aggregate(dev(guide), t, SIG_S, SIG_R, 3, Z.ZNCC_F16)
+    torch.cuda.synchronize()
+    got = t.float().cpu().numpy().astype(np.float64)
+    ref = oracle.dt_aggregate(C.astype(np.float16).astype(np.float64),
+                              oracle.dt_weights(guide, SIG_S, SIG_R), SIG_S, 3)
+    A = oracle.ones_response(guide, SIG_S, SIG_R, 3)
+    rel = (np.abs(got - ref) / A[:, :, None]).max()
+    assert rel < 1e-2, rel
+
+
+def test_dt_iters_zero_is_identity():
+    C = np.random.default_rng(0).uniform(-1, 1, (8, 9, 4)).astype(np.float32)
+    ctx = Z.ZnccContext(9, 8, 4, 3)
+    t = dev(C)
+    ctx.dt_aggregate(dev(np.zeros((8, 9), np.uint8)), t, SIG_S, SIG_R, 0)
+    assert np.array_equal(t.cpu().numpy(), C)
+
+
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("h,w,d", [(10, 12, 9), (33, 17, 64), (1, 1, 1), (5, 300, 130)])
+def test_wta_disparity_matches_oracle(h, w, d):
+    rng = np.random.default_rng(h * w + d)
+    C = rng.uniform(-1, 1, (h, w, d)).astype(np.float32)
+    C[0, 0, :] = 0.25                                   # all tied: smallest d wins
+    if d > 3:
+        C[-1, -1, [1, d - 1]] = 2.0                     # two-way tie
+    ctx = Z.ZnccContext(w, h, d, 3)
+    disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.wta_disparity(dev(C), disp)
+    ref, _, _ = oracle.wta(C.astype(np.float64))
+    assert np.array_equal(host_u16(disp), ref)
+    # the same through the half path
+    disp16 = torch.empty_like(disp)
+    ctx.wta_disparity(dev(C.astype(np.float16)), disp16, Z.ZNCC_F16)
+    ref16, _, _ = oracle.wta(C.astype(np.float16).astype(np.float64))
+    assert np.array_equal(host_u16(disp16), ref16)
+
+
+# ---------------------------------------------------------------------------------------
+RUN_CASES = [(96, 320, 32, 9, 0), (96, 320, 32, 9, 1), (96, 320, 32, 9, 3), (37, 61, 13, 5, 3),
+             (20, 45, 33, 7, 2), (1, 40, 8, 3, 1), (40, 1, 8, 3, 1), (3, 2100, 8, 3, 1),
+             (64, 200, 48, 15, 3)]
+
+
+@pytest.mark.parametrize("h,w,d,win,iters", RUN_CASES)
+def test_fused_run_matches_oracle(h, w, d, win, iters):
+    p = rand_pair(h, w, d, seed=h + w + d + win + iters)
+    ctx = Z.ZnccContext(w, h, d, win)
+    disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, iters, Z.ZNCC_F32)
+    got = host_u16(disp)
+    ref, gap = oracle.run(p.left, p.right, d, win // 2, SIG_S, SIG_R, iters)
+    scale = oracle.ones_response(p.left, SIG_S, SIG_R, iters) if iters else 1.0
+    check_disp(got, ref, gap, scale, f"zncc_run {h}x{w} D={d} win={win} iters={iters}")
+
+
+def test_unfused_chain_equals_oracle_and_fused():
+    """cost volume -> dt_aggregate -> wta_disparity gives the oracle's map, like zncc_run."""
+    h, w, d, win, iters = 48, 160, 32, 9, 3
+    p = rand_pair(h, w, d, seed=77)
+    ctx = Z.ZnccContext(w, h, d, win)
+    L, R = dev(p.left), dev(p.right)
+    c = torch.empty((h, w, d), dtype=torch.float32, device="cuda")
+    ctx.zncc_cost_volume(L, R, c)
+    ctx.dt_aggregate(L, c, SIG_S, SIG_R, iters)
+    d1 = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.wta_disparity(c, d1)
+    d2 = torch.empty_like(d1)
+    ctx.zncc_run(L, R, d2, SIG_S, SIG_R, iters)
+    ref, gap, Cref = oracle.run(p.left, p.right, d, win // 2, SIG_S, SIG_R, iters, want_cost=True)
+    A = oracle.ones_response(p.left, SIG_S, SIG_R, iters)
+    rel = (np.abs(c.cpu().numpy() - Cref) / A[:, :, None]).max()
+    assert rel <= AGG_TOL, rel
+    check_disp(host_u16(d1), ref, gap, A, "unfused chain")
+    check_disp(host_u16(d2), ref, gap, A, "fused run")
+
+
+def test_run_host_equals_device_run():
+    h, w, d = 50, 120, 24
+    p = rand_pair(h, w, d, seed=5)
+    ctx = Z.ZnccContext(w, h, d, 9)
+    disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, 3)
+    host = np.zeros((h, w), np.uint16)
+    ctx.zncc_run_host(p.left, p.right, host, SIG_S, SIG_R, 3)
+    assert np.array_equal(host, host_u16(disp))
+
+
+def test_fp16_storage_run_mismatch_rate_small():
+    h, w, d = 96, 320, 32
+    p = rand_pair(h, w, d, seed=12)
+    ctx = Z.ZnccContext(w, h, d, 9)
+    disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, 3, Z.ZNCC_F16)
+    ref, _ = oracle.run(p.left, p.right, d, 4, SIG_S, SIG_R, 3)
+    rate = (host_u16(disp) != ref).mean()
+    assert rate < 0.01, rate
+
+
+def test_invalid_arguments_report_einval():
+    ctx = Z.ZnccContext(16, 8, 4, 3)
+    img = torch.zeros((8, 16), dtype=torch.uint8, device="cuda")
+    disp = torch.empty((8, 16), dtype=torch.int16, device="cuda")
+    with pytest.raises(Z.ZnccError) as e:
+        ctx.zncc_run(img, img, disp, -1.0, SIG_R, 1)
+    assert e.value.status == Z.ZNCC_EINVAL
+    with pytest.raises(Z.ZnccError):
+        ctx.zncc_run(img, img, disp, SIG_S, 0.0, 1)
+    with pytest.raises(Z.ZnccError):
+        ctx.zncc_run(img, img, disp, SIG_S, SIG_R, -1)
+    assert Z.lib().zncc_run(ctx._h, None, img.data_ptr(), 16, 1.0, 1.0, 1, 0,
+                            disp.data_ptr()) == Z.ZNCC_EINVAL
+    assert Z.lib().zncc_run(ctx._h, img.data_ptr(), img.data_ptr(), 15, 1.0, 1.0, 1, 0,
+                            disp.data_ptr()) == Z.ZNCC_EINVAL
+    assert Z.lib().zncc_cost_volume(ctx._h, img.data_ptr(), img.data_ptr(), 16,
+                                    disp.data_ptr(), 7) == Z.ZNCC_EINVAL
+
+
+# ---------------------------------------------------------------------------------------
+def test_full_size_paper_workload_matches_oracle():
+    """1280x384, D = 128, 9x9, sigma_s = 20, sigma_r = 0.1, 3 iterations, FP32: the launch
+    configuration the benchmark times, against the full oracle."""
+    p = config_pair("paper_1280x384")
+    h, w = p.left.shape
+    ctx = Z.ZnccContext(w, h, 128, 9)
+    disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    L, R = dev(p.left), dev(p.right)
+    ctx.zncc_run(L, R, disp, SIG_S, SIG_R, 3, Z.ZNCC_F32)
+    ref, gap, Cref = oracle.run(p.left, p.right, 128, 4, SIG_S, SIG_R, 3, want_cost=True)
+    A = oracle.ones_response(p.left, SIG_S, SIG_R, 3)
+    skipped = check_disp(host_u16(disp), ref, gap, A, "paper workload")
+    assert skipped < 0.001 * h * w
+    # aggregated cost at every element through the unfused calls
+    c = torch.empty((h, w, 128), dtype=torch.float32, device="cuda")
+    ctx.zncc_cost_volume(L, R, c)
+    ctx.dt_aggregate(L, c, SIG_S, SIG_R, 3)
+    rel = (np.abs(c.cpu().numpy() - Cref) / A[:, :, None]).max()
+    assert rel <= AGG_TOL, rel
+    # and accuracy against the synthetic ground truth (context for the method, not parity)
+    v = p.valid
+    assert (host_u16(disp)[v] == p.gt[v]).mean() > 0.5
