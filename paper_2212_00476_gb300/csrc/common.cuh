@@ -35,12 +35,18 @@ __device__ __forceinline__ void ld4(const float* p, int nvalid, bool vec, float 
     }
 }
 
+// Half values travel as raw 16-bit patterns inside 32-bit words (low half = lower address);
+// __ushort_as_half / __half_as_ushort convert without type-punned pointer accesses.
+__device__ __forceinline__ float half_lo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))); }
+__device__ __forceinline__ float half_hi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+__device__ __forceinline__ unsigned half_pack(float lo, float hi) {
+    return (unsigned)__half_as_ushort(__float2half_rn(lo)) | ((unsigned)__half_as_ushort(__float2half_rn(hi)) << 16);
+}
+
 __device__ __forceinline__ void ld4(const __half* p, int nvalid, bool vec, float (&o)[4]) {
     if (vec && nvalid == 4) {
-        uint2 t = *reinterpret_cast<const uint2*>(p);
-        float2 a = __half22float2(*reinterpret_cast<__half2*>(&t.x));
-        float2 b = __half22float2(*reinterpret_cast<__half2*>(&t.y));
-        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+        const uint2 t = *reinterpret_cast<const uint2*>(p);
+        o[0] = half_lo(t.x); o[1] = half_hi(t.x); o[2] = half_lo(t.y); o[3] = half_hi(t.y);
     } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j) o[j] = j < nvalid ? __half2float(p[j]) : 0.0f;
@@ -59,12 +65,7 @@ __device__ __forceinline__ void st4(float* p, int nvalid, bool vec, const float 
 
 __device__ __forceinline__ void st4(__half* p, int nvalid, bool vec, const float (&o)[4]) {
     if (vec && nvalid == 4) {
-        __half2 a = __floats2half2_rn(o[0], o[1]);
-        __half2 b = __floats2half2_rn(o[2], o[3]);
-        uint2 t;
-        t.x = *reinterpret_cast<unsigned*>(&a);
-        t.y = *reinterpret_cast<unsigned*>(&b);
-        *reinterpret_cast<uint2*>(p) = t;
+        *reinterpret_cast<uint2*>(p) = make_uint2(half_pack(o[0], o[1]), half_pack(o[2], o[3]));
     } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
