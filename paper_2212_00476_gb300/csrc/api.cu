@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -20,22 +21,20 @@ namespace {
 std::atomic<uint64_t> g_launches{0};
 thread_local std::string g_create_error;
 
-struct Dims {
-    int nch, ds, lpc;
-};
-
 // Kernel kinds for per-kernel timing (zncc_profile_*).
 enum Kind {
-    K_STATS = 0, K_WEIGHTS, K_ZNCC_RAW, K_ZNCC_HPAIR, K_ZNCC_WTA, K_DT_HPAIR, K_DT_VPAIR,
-    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_WTA_FINAL, K_NKINDS
+    K_STATS = 0, K_COEF, K_ZNCC_RAW, K_ZNCC_HPAIR, K_ZNCC_WTA, K_DT_HPAIR, K_DT_VPAIR,
+    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_NKINDS
 };
 const char* const kKindNames[K_NKINDS] = {
-    "window_stats", "dt_weights", "zncc_cost", "zncc_cost_hpair", "zncc_cost_wta",
-    "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume", "wta_finalize"};
+    "window_stats", "dt_coef", "zncc_cost", "zncc_cost_hpair", "zncc_cost_wta",
+    "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume"};
 
 struct ProfRecord {
     int kind, ev0, ev1;
 };
+
+constexpr int kTargetBlocks = 1216;   // about eight blocks per SM on a 152-SM GB300
 
 }  // namespace
 
@@ -44,22 +43,14 @@ struct zncc_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     std::string err;
-    // per-image window statistics (left over [0, W), right over [-(D-1), W))
-    int* SL = nullptr;
-    float* ISL = nullptr;
-    int* SR = nullptr;
-    float* ISR = nullptr;
-    // DT edge weights: eh [H][W], evt [W][H]
-    float* eh = nullptr;
-    float* evt = nullptr;
-    unsigned long long* keys = nullptr;   // [H][W] WTA keys
-    // the fused path's intermediate volume, allocated on first use
-    void* vol = nullptr;
+    int2* statL = nullptr;        // [H][W]       left window statistics (S, 1/sigma)
+    int2* statR = nullptr;        // [H][W+D-1]   right window statistics, centres -(D-1)..W-1
+    float4* coefH = nullptr;      // [H][W]       horizontal DT coefficients
+    float4* coefV = nullptr;      // [W][H]       vertical DT coefficients
+    void* vol = nullptr;          // the fused path's intermediate volume (on first use)
     size_t vol_bytes = 0;
-    // device copies for zncc_run_host
-    uint8_t* img = nullptr;               // 2 x [H][W]
-    uint16_t* disp = nullptr;             // [H][W]
-    // per-kernel timing
+    uint8_t* img = nullptr;       // device copies for zncc_run_host: 2 x [H][W]
+    uint16_t* disp = nullptr;     // [H][W]
     bool profiling = false;
     std::vector<cudaEvent_t> events;
     int events_used = 0;
@@ -79,10 +70,16 @@ zncc_status cuda_fail(zncc_ctx* c, cudaError_t e, const char* what) {
     return fail(c, ZNCC_ECUDA, m);
 }
 
-#define ZNCC_CUDA(c, call, what)                       \
-    do {                                               \
-        cudaError_t e_ = (call);                       \
-        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+#define ZNCC_CUDA(c, call, what)                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what);     \
+    } while (0)
+
+#define ZNCC_TRY(expr)                   \
+    do {                                 \
+        zncc_status s_ = (expr);         \
+        if (s_ != ZNCC_OK) return s_;    \
     } while (0)
 
 // An event of the context's pool (grown on demand), or -1 if one cannot be created.
@@ -110,37 +107,30 @@ int prof_event(zncc_ctx* c) {
         }                                                                     \
     } while (0)
 
-// Disparities per block and lines per block of a DT line pair of length n: a block keeps
-// n x ds costs in registers (ds * n <= 32768 floats, at most 128 KB), 16 positions x 4
-// disparities per thread.
+// Lanes per chunk (4 disparities each) for a line of n positions: the n/16 chunks of a line
+// times tq lanes must fit one block of at most 512 threads.
+int lanes_for(int n) { return n <= 1024 ? 8 : (n <= 2048 ? 4 : 2); }
+
 // The chunk count is padded so that a line's threads fill whole warps (every warp-wide
 // shuffle then has all 32 lanes); padded chunks lie past the line end and hold zeros.
-int padded_chunks(int n, int ds) {
-    const int per_warp = 32 / (ds / kG);
+int padded_chunks(int n, int tq) {
+    const int per_warp = 32 / tq;
     const int nch = (n + kL - 1) / kL;
     return (nch + per_warp - 1) / per_warp * per_warp;
 }
 
-Dims line_dims(int n) {
-    Dims d;
-    d.ds = n <= 1024 ? 32 : (n <= 2048 ? 16 : 8);
-    d.nch = padded_chunks(n, d.ds);
-    const int per_line = d.nch * (d.ds / kG);
-    d.lpc = std::max(1, std::min(8, (256 + per_line - 1) / per_line));
-    while (d.lpc > 1 && d.lpc * per_line > 512) --d.lpc;   // blocks are at most 512 threads
-    return d;
-}
-
-// The ZNCC row kernel: one row x 16 (8 above 2048 columns) disparities per block.
-Dims row_dims(int W) {
-    Dims d;
-    d.ds = W <= 2048 ? 16 : 8;
-    d.nch = padded_chunks(W, d.ds);
-    d.lpc = 1;
-    return d;
+// Disparity slices per block: about kTargetBlocks blocks in all, equal runs per block.
+int slices_per_block(int nslices, int blocks_x) {
+    const int per = std::max(1, blocks_x * nslices / kTargetBlocks);
+    const int groups = std::max(1, (nslices + per - 1) / per);
+    return (nslices + groups - 1) / groups;
 }
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+bool volume_vec(const void* vol, int dtype, long long dstride) {
+    return dstride % 4 == 0 && aligned(vol, dtype == 0 ? 16 : 8);
+}
 
 zncc_status check_images(zncc_ctx* c, const void* a, const void* b, int pitch) {
     if (!a || !b) return fail(c, ZNCC_EINVAL, "image pointer is NULL");
@@ -155,85 +145,84 @@ zncc_status check_dt(zncc_ctx* c, float sigma_s, float sigma_r, int iters) {
     return ZNCC_OK;
 }
 
+float scale_s2(float sigma_s) {
+    const double s = 1.0 - exp(-1.0 / (double)sigma_s);
+    return (float)(s * s);
+}
+
 // Window statistics of both images into the context scratch.
 zncc_status run_stats(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch) {
-    ZNCC_LAUNCH(c, K_STATS, launch_window_stats(left, pitch, c->W, c->H, c->r, 0, c->W, c->SL, nullptr,
-                                       c->ISL, c->stream), "window statistics (left)");
+    ZNCC_LAUNCH(c, K_STATS, launch_window_stats(left, pitch, c->W, c->H, c->r, 0, c->W, nullptr, nullptr,
+                                                nullptr, c->statL, c->stream), "window statistics (left)");
     ZNCC_LAUNCH(c, K_STATS, launch_window_stats(right, pitch, c->W, c->H, c->r, -(c->D - 1), c->W + c->D - 1,
-                                       c->SR, nullptr, c->ISR, c->stream), "window statistics (right)");
+                                                nullptr, nullptr, nullptr, c->statR, c->stream),
+                "window statistics (right)");
     return ZNCC_OK;
 }
 
-zncc_status run_weights(zncc_ctx* c, const uint8_t* guide, int pitch, float sigma_s, float sigma_r) {
+zncc_status run_coef(zncc_ctx* c, const uint8_t* guide, int pitch, float sigma_s, float sigma_r) {
     const float K = (float)exp(-1.0 / (double)sigma_s);
     const float inv = (float)(1.0 / (255.0 * (double)sigma_r));
-    ZNCC_LAUNCH(c, K_WEIGHTS, launch_dt_weights(guide, pitch, c->W, c->H, K, inv, c->eh, c->evt, c->stream),
-                "DT edge weights");
+    ZNCC_LAUNCH(c, K_COEF, launch_dt_coef(guide, pitch, c->W, c->H, K, inv, c->coefH, c->coefV, c->stream),
+                "DT coefficients");
     return ZNCC_OK;
 }
 
-RowArgs row_args(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch) {
+RowArgs row_args(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch, int mode) {
     RowArgs a;
     memset(&a, 0, sizeof(a));
-    const Dims rd = row_dims(c->W);
     a.left = left;
     a.right = right;
     a.pitch = pitch;
     a.W = c->W;
     a.H = c->H;
     a.D = c->D;
-    a.SL = c->SL;
-    a.ISL = c->ISL;
-    a.SR = c->SR;
-    a.ISR = c->ISR;
-    a.nch = rd.nch;
-    a.ds = rd.ds;
-    a.d_begin = 0;
-    a.d_end = c->D;
+    a.statL = c->statL;
+    a.statR = c->statR;
+    a.tq = lanes_for(c->W);
+    a.nch = padded_chunks(c->W, a.tq);
+    a.d_lo = 0;
+    a.d_hi = c->D;
+    const int nslices = (c->D + kG * a.tq - 1) / (kG * a.tq);
+    a.spb = mode == kModeWta ? nslices : slices_per_block(nslices, c->H);
     a.dstride = c->D;
     a.d_out0 = 0;
-    a.eh = c->eh;
-    a.keys = c->keys;
+    a.coef = c->coefH;
     return a;
 }
 
-bool volume_vec(const void* vol, int dtype, long long dstride) {
-    return dstride % 4 == 0 && aligned(vol, dtype == 0 ? 16 : 8);
-}
-
 // One DT pair along rows (horiz) or columns of a [H][W][dstride] volume.
-zncc_status run_line_pair(zncc_ctx* c, void* vol, int dtype, long long dstride, bool horiz,
-                          float s, int mode) {
+zncc_status run_line_pair(zncc_ctx* c, void* vol, int dtype, long long dstride, bool horiz, float s2,
+                          int mode, uint16_t* disp) {
     LineArgs a;
     memset(&a, 0, sizeof(a));
     const int n = horiz ? c->W : c->H;
-    const Dims d = line_dims(n);
     a.vol = vol;
     a.elem_stride = horiz ? dstride : (long long)c->W * dstride;
     a.line_stride = horiz ? (long long)c->W * dstride : dstride;
     a.n = n;
     a.nlines = horiz ? c->H : c->W;
     a.dcount = c->D;
-    a.ds = d.ds;
-    a.lpc = d.lpc;
-    a.nch = d.nch;
-    a.ew = horiz ? c->eh : c->evt;
-    a.ew_line_stride = horiz ? c->W : c->H;
-    a.s = s;
+    a.d_base = 0;
+    a.tq = lanes_for(n);
+    a.nch = padded_chunks(n, a.tq);
+    const int per_line = a.nch * a.tq;
+    a.lpc = std::max(1, std::min(8, 256 / per_line));
+    const int nslices = (c->D + kG * a.tq - 1) / (kG * a.tq);
+    a.spb = mode == kLineWta ? nslices : slices_per_block(nslices, (a.nlines + a.lpc - 1) / a.lpc);
+    a.coef = horiz ? c->coefH : c->coefV;
+    a.coef_line_stride = horiz ? c->W : c->H;
+    a.s2 = s2;
     a.vec = volume_vec(vol, dtype, dstride) ? 1 : 0;
-    a.keys = c->keys;
+    a.wta.disp = disp;
+    a.wta.first = 1;
+    a.wta.last = 1;
     a.pix_line = horiz ? c->W : 1;
     a.pix_pos = horiz ? 1 : c->W;
-    a.d_base = 0;
-    ZNCC_LAUNCH(c, horiz ? K_DT_HPAIR : (mode == kLineWta ? K_DT_VPAIR_WTA : K_DT_VPAIR), launch_line_pair(a, mode, dtype, c->stream), horiz ? "DT horizontal pair" : "DT vertical pair");
+    const int kind = horiz ? K_DT_HPAIR : (mode == kLineWta ? K_DT_VPAIR_WTA : K_DT_VPAIR);
+    ZNCC_LAUNCH(c, kind, launch_line_pair(a, mode, dtype, c->stream), horiz ? "DT horizontal pair" : "DT vertical pair");
     return ZNCC_OK;
 }
-
-#define ZNCC_TRY(expr)                   \
-    do {                                 \
-        zncc_status s_ = (expr);         \
-        if (s_ != ZNCC_OK) return s_;    \
-    } while (0)
 
 template <typename T>
 void free_dev(T*& p) {
@@ -242,13 +231,10 @@ void free_dev(T*& p) {
 }
 
 void release(zncc_ctx* c) {
-    free_dev(c->SL);
-    free_dev(c->ISL);
-    free_dev(c->SR);
-    free_dev(c->ISR);
-    free_dev(c->eh);
-    free_dev(c->evt);
-    free_dev(c->keys);
+    free_dev(c->statL);
+    free_dev(c->statR);
+    free_dev(c->coefH);
+    free_dev(c->coefV);
     free_dev(c->vol);
     free_dev(c->img);
     free_dev(c->disp);
@@ -283,13 +269,10 @@ zncc_status zncc_create(int width, int height, int max_disp, int win, zncc_ctx**
     cudaError_t e = cudaGetDevice(&c->device);
     const size_t npix = (size_t)width * height;
     const size_t nright = (size_t)(width + max_disp - 1) * height;
-    if (e == cudaSuccess) e = cudaMalloc(&c->SL, npix * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&c->ISL, npix * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&c->SR, nright * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&c->ISR, nright * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&c->eh, npix * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&c->evt, npix * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&c->keys, npix * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->statL, npix * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&c->statR, nright * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&c->coefH, npix * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&c->coefV, npix * sizeof(float4));
     if (e != cudaSuccess) {
         zncc_status s = e == cudaErrorMemoryAllocation ? ZNCC_ENOMEM : ZNCC_ECUDA;
         std::string m = std::string("zncc_create: ") + cudaGetErrorString(e);
@@ -328,8 +311,8 @@ zncc_status zncc_window_stats(zncc_ctx* c, const uint8_t* img, int pitch, int32_
     if (!img) return fail(c, ZNCC_EINVAL, "image pointer is NULL");
     if (pitch < c->W) return fail(c, ZNCC_EINVAL, "pitch is smaller than the width");
     if (!S && !Q && !inv_sigma) return ZNCC_OK;
-    ZNCC_LAUNCH(c, K_STATS, launch_window_stats(img, pitch, c->W, c->H, c->r, 0, c->W, S, Q, inv_sigma, c->stream),
-                "window statistics");
+    ZNCC_LAUNCH(c, K_STATS, launch_window_stats(img, pitch, c->W, c->H, c->r, 0, c->W, S, Q, inv_sigma,
+                                                nullptr, c->stream), "window statistics");
     return ZNCC_OK;
 }
 
@@ -341,7 +324,7 @@ zncc_status zncc_cost_volume(zncc_ctx* c, const uint8_t* left, const uint8_t* ri
     if (!cost) return fail(c, ZNCC_EINVAL, "cost pointer is NULL");
     if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
     ZNCC_TRY(run_stats(c, left, right, pitch));
-    RowArgs a = row_args(c, left, right, pitch);
+    RowArgs a = row_args(c, left, right, pitch, kModeRaw);
     a.vol = cost;
     a.vec = volume_vec(cost, dtype, c->D) ? 1 : 0;
     ZNCC_LAUNCH(c, K_ZNCC_RAW, launch_zncc_row(c->r, a, kModeRaw, dtype, c->stream), "ZNCC cost");
@@ -358,11 +341,11 @@ zncc_status dt_aggregate(zncc_ctx* c, const uint8_t* guide, int pitch, void* cos
     if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
     ZNCC_TRY(check_dt(c, sigma_s, sigma_r, iters));
     if (iters == 0) return ZNCC_OK;
-    ZNCC_TRY(run_weights(c, guide, pitch, sigma_s, sigma_r));
-    const float s = (float)(1.0 - exp(-1.0 / (double)sigma_s));
+    ZNCC_TRY(run_coef(c, guide, pitch, sigma_s, sigma_r));
+    const float s2 = scale_s2(sigma_s);
     for (int it = 0; it < iters; ++it) {
-        ZNCC_TRY(run_line_pair(c, cost, dtype, c->D, true, s, kLineStore));
-        ZNCC_TRY(run_line_pair(c, cost, dtype, c->D, false, s, kLineStore));
+        ZNCC_TRY(run_line_pair(c, cost, dtype, c->D, true, s2, kLineStore, nullptr));
+        ZNCC_TRY(run_line_pair(c, cost, dtype, c->D, false, s2, kLineStore, nullptr));
     }
     return ZNCC_OK;
 }
@@ -387,39 +370,41 @@ zncc_status zncc_run(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int
     const size_t npix = (size_t)c->W * c->H;
 
     ZNCC_TRY(run_stats(c, left, right, pitch));
-    ZNCC_CUDA(c, cudaMemsetAsync(c->keys, 0, npix * sizeof(unsigned long long), c->stream), "key reset");
-    RowArgs a = row_args(c, left, right, pitch);
     if (iters == 0) {
+        RowArgs a = row_args(c, left, right, pitch, kModeWta);
+        a.wta.disp = disp;
+        a.wta.first = 1;
+        a.wta.last = 1;
         ZNCC_LAUNCH(c, K_ZNCC_WTA, launch_zncc_row(c->r, a, kModeWta, 0, c->stream), "ZNCC + WTA");
-    } else {
-        const int dt = storage == ZNCC_F32 ? 0 : 1;
-        const long long dstride = (c->D + 3) / 4 * 4;   // padded so every access is vectorised
-        const size_t need = npix * (size_t)dstride * (dt == 0 ? 4 : 2);
-        if (c->vol_bytes < need) {
-            free_dev(c->vol);
-            c->vol_bytes = 0;
-            cudaError_t e = cudaMalloc(&c->vol, need);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                return fail(c, e == cudaErrorMemoryAllocation ? ZNCC_ENOMEM : ZNCC_ECUDA,
-                            std::string("cost volume allocation: ") + cudaGetErrorString(e));
-            }
-            c->vol_bytes = need;
-        }
-        ZNCC_TRY(run_weights(c, left, pitch, sigma_s, sigma_r));
-        const float s = (float)(1.0 - exp(-1.0 / (double)sigma_s));
-        a.vol = c->vol;
-        a.dstride = dstride;
-        a.vec = volume_vec(c->vol, dt, dstride) ? 1 : 0;
-        a.s = s;
-        ZNCC_LAUNCH(c, K_ZNCC_HPAIR, launch_zncc_row(c->r, a, kModeHPair, dt, c->stream), "ZNCC + horizontal DT pair");
-        for (int it = 0; it < iters; ++it) {
-            const bool last = it == iters - 1;
-            ZNCC_TRY(run_line_pair(c, c->vol, dt, dstride, false, s, last ? kLineWta : kLineStore));
-            if (!last) ZNCC_TRY(run_line_pair(c, c->vol, dt, dstride, true, s, kLineStore));
-        }
+        return ZNCC_OK;
     }
-    ZNCC_LAUNCH(c, K_WTA_FINAL, launch_wta_finalize(c->keys, (int)npix, disp, c->stream), "WTA keys to disparities");
+    const int dt = storage == ZNCC_F32 ? 0 : 1;
+    const long long dstride = (c->D + 3) / 4 * 4;   // padded so every access is vectorised
+    const size_t need = npix * (size_t)dstride * (dt == 0 ? 4 : 2);
+    if (c->vol_bytes < need) {
+        free_dev(c->vol);
+        c->vol_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->vol, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, e == cudaErrorMemoryAllocation ? ZNCC_ENOMEM : ZNCC_ECUDA,
+                        std::string("cost volume allocation: ") + cudaGetErrorString(e));
+        }
+        c->vol_bytes = need;
+    }
+    ZNCC_TRY(run_coef(c, left, pitch, sigma_s, sigma_r));
+    const float s2 = scale_s2(sigma_s);
+    RowArgs a = row_args(c, left, right, pitch, kModeHPair);
+    a.vol = c->vol;
+    a.dstride = dstride;
+    a.vec = volume_vec(c->vol, dt, dstride) ? 1 : 0;
+    a.s2 = s2;
+    ZNCC_LAUNCH(c, K_ZNCC_HPAIR, launch_zncc_row(c->r, a, kModeHPair, dt, c->stream), "ZNCC + horizontal DT pair");
+    for (int it = 0; it < iters; ++it) {
+        const bool last = it == iters - 1;
+        ZNCC_TRY(run_line_pair(c, c->vol, dt, dstride, false, s2, last ? kLineWta : kLineStore, disp));
+        if (!last) ZNCC_TRY(run_line_pair(c, c->vol, dt, dstride, true, s2, kLineStore, nullptr));
+    }
     return ZNCC_OK;
 }
 

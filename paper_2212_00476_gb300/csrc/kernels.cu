@@ -1,4 +1,6 @@
-// kernels.cu -- window statistics, DT edge weights, DT line pairs and WTA kernels.
+// kernels.cu -- window statistics, DT coefficients, DT line pairs and WTA kernels.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "zncc_row.cuh"
@@ -11,9 +13,10 @@ namespace zncc {
 // horizontal window sum of those. S, Q exact int32; inv_sigma = 1/sqrt(n Q - S^2) or 0.
 // n Q - S^2 < 2^31 for every window side <= 15 (its maximum is n^2 * 127.5^2), so it is
 // computed modulo 2^32 in unsigned arithmetic even where n Q alone would not fit.
+// `packed` receives (S, inv_sigma bits) per centre for the cost kernel.
 __global__ void k_window_stats(const uint8_t* __restrict__ img, int pitch, int W, int H, int r,
                                int x_begin, int nx, int* __restrict__ S, int* __restrict__ Q,
-                               float* __restrict__ isig) {
+                               float* __restrict__ isig, int2* __restrict__ packed) {
     extern __shared__ int sm_stats[];
     const int y = blockIdx.x;
     const int ncol = nx + 2 * r;
@@ -39,107 +42,196 @@ __global__ void k_window_stats(const uint8_t* __restrict__ img, int pitch, int W
             q += cq[t + i];
         }
         const size_t o = (size_t)y * nx + t;
+        const int var = (int)(n * (unsigned)q - (unsigned)s * (unsigned)s);
+        const float is = var > 0 ? 1.0f / sqrtf((float)var) : 0.0f;
         if (S) S[o] = s;
         if (Q) Q[o] = q;
-        if (isig) {
-            const int var = (int)(n * (unsigned)q - (unsigned)s * (unsigned)s);
-            isig[o] = var > 0 ? 1.0f / sqrtf((float)var) : 0.0f;
-        }
+        if (isig) isig[o] = is;
+        if (packed) packed[o] = make_int2(s, __float_as_int(is));
     }
 }
 
 cudaError_t launch_window_stats(const uint8_t* img, int pitch, int W, int H, int r, int x_begin,
-                                int nx, int* S, int* Q, float* isig, cudaStream_t st) {
+                                int nx, int* S, int* Q, float* isig, int2* packed, cudaStream_t st) {
     const size_t smem = 2 * sizeof(int) * (size_t)(nx + 2 * r);
-    k_window_stats<<<H, 256, smem, st>>>(img, pitch, W, H, r, x_begin, nx, S, Q, isig);
+    k_window_stats<<<H, 256, smem, st>>>(img, pitch, W, H, r, x_begin, nx, S, Q, isig, packed);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------
-// DT edge weights (Sec. III-B, Eq. (11)): the weight of the step between two neighbouring
-// pixels p, q is K * exp(-|G(p) - G(q)| / sigma_r), G = guide / 255. eh[y][x] is the step
-// (x-1, y) -> (x, y); evt[x][y] (stored transposed, so a column is contiguous) the step
-// (x, y-1) -> (x, y); both 0 where the step leaves the image.
-__global__ void k_dt_weights(const uint8_t* __restrict__ g, int pitch, int W, int H, float K,
-                             float inv_sr255, float* __restrict__ eh, float* __restrict__ evt) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= W) return;
-    const int c = g[(size_t)y * pitch + x];
-    float wh = 0.0f, wv = 0.0f;
-    if (x > 0) wh = K * expf(-fabsf((float)(c - (int)g[(size_t)y * pitch + x - 1])) * inv_sr255);
-    if (y > 0) wv = K * expf(-fabsf((float)(c - (int)g[(size_t)(y - 1) * pitch + x])) * inv_sr255);
-    eh[(size_t)y * W + x] = wh;
-    evt[(size_t)x * H + y] = wv;
+// DT coefficients (Sec. III-B, Eq. (11)). The weight of the step between two neighbouring
+// pixels p, q is K * exp(-|G(p) - G(q)| / sigma_r), G = guide / 255. For each line (rows for
+// the horizontal passes, columns for the vertical ones) and position p, with w(p) the weight
+// of the step p-1 -> p (0 at p = 0 and past the line end):
+//   (w(p), prod_{j=c..p} w(j), w(p+1), prod_{j=p..c+15} w(j+1)),  c = chunk start (16 | c).
+// coefH is [H][W]; coefV is [W][H] (a column is contiguous). One thread per chunk.
+__global__ void k_dt_coef(const uint8_t* __restrict__ g, int pitch, int W, int H, float K,
+                          float inv_sr255, float4* __restrict__ coefH, float4* __restrict__ coefV) {
+    const int nchH = (W + kL - 1) / kL, nchV = (H + kL - 1) / kL;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool horiz = idx < H * nchH;
+    if (!horiz) idx -= H * nchH;
+    if (!horiz && idx >= W * nchV) return;
+    const int n = horiz ? W : H;
+    const int line = horiz ? idx / nchH : idx / nchV;
+    const int c = (horiz ? idx - line * nchH : idx - line * nchV) * kL;
+    auto pix = [&](int p) -> int {
+        return horiz ? g[(size_t)line * pitch + p] : g[(size_t)p * pitch + line];
+    };
+    float w[kL + 1];
+#pragma unroll
+    for (int i = 0; i <= kL; ++i) {
+        const int p = c + i;
+        w[i] = (p >= 1 && p < n) ? K * expf(-fabsf((float)(pix(p) - pix(p - 1))) * inv_sr255) : 0.0f;
+    }
+    float A[kL], B[kL];
+    float acc = 1.0f;
+#pragma unroll
+    for (int i = 0; i < kL; ++i) {
+        acc *= w[i];
+        A[i] = acc;
+    }
+    acc = 1.0f;
+#pragma unroll
+    for (int i = kL - 1; i >= 0; --i) {
+        acc *= w[i + 1];
+        B[i] = acc;
+    }
+    float4* out = horiz ? coefH + (size_t)line * W : coefV + (size_t)line * H;
+#pragma unroll
+    for (int i = 0; i < kL; ++i)
+        if (c + i < n) out[c + i] = make_float4(w[i], A[i], w[i + 1], B[i]);
 }
 
-cudaError_t launch_dt_weights(const uint8_t* guide, int pitch, int W, int H, float K,
-                              float inv_sr255, float* eh, float* evt, cudaStream_t st) {
-    dim3 grid((W + 127) / 128, H);
-    k_dt_weights<<<grid, 128, 0, st>>>(guide, pitch, W, H, K, inv_sr255, eh, evt);
+cudaError_t launch_dt_coef(const uint8_t* guide, int pitch, int W, int H, float K, float inv_sr255,
+                           float4* coefH, float4* coefV, cudaStream_t st) {
+    const int total = H * ((W + kL - 1) / kL) + W * ((H + kL - 1) / kL);
+    k_dt_coef<<<(total + 127) / 128, 128, 0, st>>>(guide, pitch, W, H, K, inv_sr255, coefH, coefV);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------
 // DT line pair (Sec. III-B, Eqs. (3)-(6)): the forward and the backward recursive pass
 // along rows (L2R then R2L) or columns (U2D then D2U) of a cost volume, in place, or, for
-// the last pair of the chain, folded into the WTA keys without writing the volume back
-// (Sec. V-C fuses WTA with D2U in the same way). Block = lpc lines x one disparity slice.
+// the last pair of the chain, folded into a per-pixel running best without writing the
+// volume back (Sec. V-C fuses WTA with D2U in the same way). Block = lpc lines x a run of
+// spb disparity slices (4*tq disparities each); the lines' coefficients are staged once.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
-    extern __shared__ float smem_f[];
-    const int ds = a.ds, tq = ds / kG, nch = a.nch;
-    const int per_line = nch * tq;
+    extern __shared__ float4 smem4[];
+    const int tq = a.tq, nch = a.nch, ds = kG * tq;
+    const int per_line = nch * tq, nwl = per_line >> 5, span = nch * kL;
     const int li = threadIdx.x / per_line;
-    const int rem = threadIdx.x - li * per_line;
-    const int k = rem / tq, dq = rem - (rem / tq) * tq;
+    const int tl = threadIdx.x - li * per_line;
+    const int k = tl / tq, dq = tl - k * tq;
+    const int lane = threadIdx.x & 31, wl = tl >> 5;
     const int line0 = blockIdx.x * a.lpc;
     const int line = line0 + li;
-    const int dl = blockIdx.y * ds + dq * kG;             // local disparity index
-    const int nvalid = max(0, min(4, a.dcount - dl));
     const bool line_ok = line < a.nlines;
-    const bool vec = a.vec != 0;
+    const int pX = plane_of(span);
 
-    DtShared sm = dt_carve(smem_f, a.lpc, nch, ds);
-    dt_stage_weights(sm, a.ew, a.ew_line_stride, line0, a.nlines, a.lpc, nch, a.n);
+    float4* co_all = smem4;                                            // [lpc][4 pX]
+    float4* sb_all = smem4 + a.lpc * 4 * pX;                           // [lpc][2 nwl tq]
+    float* sa_all = reinterpret_cast<float*>(sb_all + a.lpc * 2 * nwl * tq);
+    float* rbv_all = sa_all + a.lpc * 2 * nwl * tq;                    // [lpc][4 pX] (Wta)
+    int* rbd_all = reinterpret_cast<int*>(rbv_all + a.lpc * 4 * pX);
+    const float4* co = co_all + li * 4 * pX;
+    float4* sb = sb_all + li * 2 * nwl * tq;
+    float* sa = sa_all + li * 2 * nwl * tq;
+    float* rbv = rbv_all + li * 4 * pX;
+    int* rbd = rbd_all + li * 4 * pX;
 
-    T* vol = reinterpret_cast<T*>(a.vol);
-    T* base = vol + (size_t)(line_ok ? line : 0) * a.line_stride + dl;
-    float v[kL][4];
-#pragma unroll
-    for (int i = 0; i < kL; ++i) {
-        const int pos = k * kL + i;
-        if (line_ok && pos < a.n && nvalid > 0) ld4(base + (size_t)pos * a.elem_stride, nvalid, vec, v[i]);
-        else v[i][0] = v[i][1] = v[i][2] = v[i][3] = 0.0f;
-    }
-    __syncthreads();
-    dt_chunk_products(sm, li, k, dq);
-    __syncthreads();
-    dt_line_pair(v, sm, li, k, dq, nch, ds, a.s);
-
-    if constexpr (MODE == kLineWta) {
-#pragma unroll
-        for (int i = 0; i < kL; ++i) {
-            const int pos = k * kL + i;
-            const bool ok = line_ok && pos < a.n;
-            const size_t pix = ok ? (size_t)line * a.pix_line + (size_t)pos * a.pix_pos : 0;
-            wta_fold(v[i], nvalid, a.d_base + dl, tq, dq, ok, a.keys + pix);
+    for (int l2 = 0; l2 < a.lpc; ++l2) {
+        const int ln = line0 + l2;
+        const bool ok = ln < a.nlines;
+        for (int t = threadIdx.x; t < span; t += blockDim.x) {
+            co_all[l2 * 4 * pX + cidx(t, pX)] =
+                ok && t < a.n ? __ldg(a.coef + (size_t)ln * a.coef_line_stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (MODE == kLineWta) {
+                const bool in = ok && t < a.n && !a.wta.first;
+                const size_t pix = (size_t)ln * a.pix_line + (size_t)t * a.pix_pos;
+                rbv_all[l2 * 4 * pX + p4(t, pX)] = in ? a.wta.bestv[pix] : -INFINITY;
+                rbd_all[l2 * 4 * pX + p4(t, pX)] = in ? a.wta.bestd[pix] : 0;
+            }
         }
-        return;
     }
+    __syncthreads();
+
+    const int nslices = (a.dcount + ds - 1) / ds;
+    const int s_begin = blockIdx.y * a.spb;
+    const int s_end = min(nslices, s_begin + a.spb);
+    T* vol = reinterpret_cast<T*>(a.vol);
+    const bool vec = a.vec != 0;
+    for (int sl = s_begin; sl < s_end; ++sl) {
+        const int dl = sl * ds + dq * kG;                              // entry of d_first
+        const int nvalid = max(0, min(4, a.dcount - dl));
+        // the chunk's first element; consecutive positions are elem_stride entries apart
+        T* const base = vol + (size_t)(line_ok ? line : 0) * a.line_stride + (size_t)(k * kL) * a.elem_stride + dl;
+        const bool any = line_ok && nvalid > 0;
+        const int npos = a.n - k * kL;
+        float v[kL][4];
+        {
+            const T* q = base;
 #pragma unroll
-    for (int i = 0; i < kL; ++i) {
-        const int pos = k * kL + i;
-        if (line_ok && pos < a.n && nvalid > 0) st4(base + (size_t)pos * a.elem_stride, nvalid, vec, v[i]);
+            for (int i = 0; i < kL; ++i) {
+                if (any && i < npos) ld4(q, nvalid, vec, v[i]);
+                else v[i][0] = v[i][1] = v[i][2] = v[i][3] = 0.0f;
+                q += a.elem_stride;
+            }
+        }
+        dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2);
+        if constexpr (MODE == kLineWta) {
+#pragma unroll
+            for (int i = 0; i < kL; ++i) {
+                float best;
+                int bd;
+                wta_group(v[i], nvalid, a.d_base + dl, tq, best, bd);
+                const int pos = k * kL + i;
+                if (dq == 0 && pos < a.n && best > rbv[p4(pos, pX)]) {
+                    rbv[p4(pos, pX)] = best;
+                    rbd[p4(pos, pX)] = bd;
+                }
+            }
+        } else {
+            T* q = base;
+#pragma unroll
+            for (int i = 0; i < kL; ++i) {
+                if (any && i < npos) st4(q, nvalid, vec, v[i]);
+                q += a.elem_stride;
+            }
+        }
+    }
+    if constexpr (MODE == kLineWta) {
+        if (dq == 0 && line_ok) {
+#pragma unroll
+            for (int i = 0; i < kL; ++i) {
+                const int pos = k * kL + i;
+                if (pos >= a.n) break;
+                const size_t pix = (size_t)line * a.pix_line + (size_t)pos * a.pix_pos;
+                if (a.wta.last) a.wta.disp[pix] = (uint16_t)rbd[p4(pos, pX)];
+                else {
+                    a.wta.bestv[pix] = rbv[p4(pos, pX)];
+                    a.wta.bestd[pix] = rbd[p4(pos, pX)];
+                }
+            }
+        }
     }
 }
 
-size_t line_pair_smem_bytes(int lpc, int nch, int ds) { return dt_shared_bytes(lpc, nch, ds); }
+size_t line_pair_smem_bytes(int mode, const LineArgs& a) {
+    const int pX = plane_of(a.nch * kL);
+    const int nwl = a.nch * a.tq / 32;
+    size_t b = (size_t)a.lpc * (16ull * 4 * pX + dt_scan_bytes(nwl, a.tq));
+    if (mode == kLineWta) b += (size_t)a.lpc * 8 * 4 * pX;
+    return b;
+}
 
 cudaError_t launch_line_pair(const LineArgs& a, int mode, int dtype, cudaStream_t st) {
-    dim3 grid((a.nlines + a.lpc - 1) / a.lpc, (a.dcount + a.ds - 1) / a.ds);
-    dim3 block(a.lpc * a.nch * (a.ds / kG));
-    const size_t smem = line_pair_smem_bytes(a.lpc, a.nch, a.ds);
+    const int ds = kG * a.tq;
+    const int nslices = (a.dcount + ds - 1) / ds;
+    dim3 grid((a.nlines + a.lpc - 1) / a.lpc, (nslices + a.spb - 1) / a.spb);
+    dim3 block(a.lpc * a.nch * a.tq);
+    const size_t smem = line_pair_smem_bytes(mode, a);
     void (*fn)(LineArgs) = nullptr;
     if (mode == kLineStore) fn = dtype == 0 ? k_line_pair<float, kLineStore> : k_line_pair<__half, kLineStore>;
     else fn = dtype == 0 ? k_line_pair<float, kLineWta> : k_line_pair<__half, kLineWta>;
@@ -165,8 +257,8 @@ __global__ void k_wta_volume(const T* __restrict__ cost, int npix, int D, uint16
         if (v > best) { best = v; bd = d; }
     }
     for (int off = 16; off > 0; off >>= 1) {
-        const float ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
-        const int od = __shfl_xor_sync(0xFFFFFFFFu, bd, off);
+        const float ob = __shfl_xor_sync(kFull, best, off);
+        const int od = __shfl_xor_sync(kFull, bd, off);
         if (ob > best || (ob == best && od < bd)) { best = ob; bd = od; }
     }
     if (lane == 0) disp[warp] = (uint16_t)(bd == 0x7FFFFFFF ? 0 : bd);
@@ -181,19 +273,9 @@ cudaError_t launch_wta_volume(const void* cost, int dtype, int W, int H, int D, 
     return cudaGetLastError();
 }
 
-__global__ void k_wta_finalize(const unsigned long long* __restrict__ keys, int npix,
-                               uint16_t* __restrict__ disp) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < npix) disp[p] = (uint16_t)wta_key_disp(keys[p]);
+size_t zncc_row_smem_bytes(int R, int mode, const RowArgs& a, int nthreads) {
+    return zncc_row_smem(R, mode, a, nthreads);
 }
-
-cudaError_t launch_wta_finalize(const unsigned long long* keys, int npix, uint16_t* disp,
-                                cudaStream_t st) {
-    k_wta_finalize<<<(npix + 255) / 256, 256, 0, st>>>(keys, npix, disp);
-    return cudaGetLastError();
-}
-
-size_t zncc_row_smem_bytes(int R, int mode, int nch, int ds) { return zncc_row_smem(R, mode, nch, ds); }
 
 cudaError_t launch_zncc_row(int R, const RowArgs& a, int mode, int dtype, cudaStream_t st) {
     switch (R) {

@@ -9,54 +9,61 @@ namespace zncc {
 enum { kModeRaw = 0, kModeHPair = 1, kModeWta = 2 };   // k_zncc_row variants
 enum { kLineStore = 0, kLineWta = 1 };                  // k_line_pair variants
 
+// WTA output of a launch: a running best (value, d) per pixel that persists across launches
+// which split the disparity range, and the disparity map written by the last one.
+struct WtaOut {
+    float* bestv;             // [H][W] (read unless first, written unless last)
+    int* bestd;               // [H][W]
+    uint16_t* disp;           // [H][W] (written by the last launch)
+    int first, last;
+};
+
 struct RowArgs {
     const uint8_t* left;
     const uint8_t* right;
     int pitch, W, H, D;
-    const int* SL;            // [H][W]           window sums of the left image
-    const float* ISL;         // [H][W]           1/sigma of the left image
-    const int* SR;            // [H][W+D-1]       right image, centre c at column c+D-1
-    const float* ISR;
-    int nch, ds;              // chunks per row (ceil(W/16)) and disparities per block
-    int d_begin, d_end;       // disparity range of this launch
-    void* vol;                // output [H][W][dstride] of float or half
-    long long dstride;        // elements per pixel in the output
-    int d_out0;               // disparity stored at index 0 of a pixel's entries
+    const int2* statL;        // [H][W]       (window sum S, 1/sigma as float bits), left image
+    const int2* statR;        // [H][W+D-1]   the same for the right image, centre c at c+D-1
+    int nch, tq;              // chunks per row (padded to whole warps), lanes per chunk
+    int d_lo, d_hi;           // disparity range of this launch (d_lo a multiple of 4)
+    int spb;                  // disparity slices (4 * tq each) per block
+    void* vol;                // output [H][W][dstride] of float or half (Raw / HPair)
+    long long dstride;        // entries per pixel in the output
+    int d_out0;               // disparity stored at entry 0 of a pixel
     int vec;                  // 16-byte (float) / 8-byte (half) accesses allowed
-    const float* eh;          // [H][W] horizontal edge weights (HPair mode)
-    float s;                  // 1 - K
-    unsigned long long* keys; // [H][W] WTA keys (Wta mode)
+    const float4* coef;       // [H][W] horizontal DT coefficients (HPair)
+    float s2;                 // (1 - K)^2
+    WtaOut wta;               // (Wta)
 };
 
 struct LineArgs {
     void* vol;                // float or half cost volume
-    long long elem_stride;    // elements between consecutive positions of a line
-    long long line_stride;    // elements between consecutive lines
+    long long elem_stride;    // entries between consecutive positions of a line
+    long long line_stride;    // entries between consecutive lines
     int n, nlines;            // line length, number of lines
-    int dcount;               // valid disparities per pixel entry (<= elements per pixel)
-    int ds, lpc, nch;         // disparities per block, lines per block, chunks per line
-    const float* ew;          // edge weights: ew[line * ew_line_stride + pos]
-    long long ew_line_stride;
-    float s;
+    int dcount;               // valid disparity entries per pixel
+    int d_base;               // disparity of entry 0 (WTA)
+    int tq, lpc, nch, spb;    // lanes per chunk, lines per block, chunks per line, slices per block
+    const float4* coef;       // coefficients: coef[line * coef_line_stride + pos]
+    long long coef_line_stride;
+    float s2;
     int vec;
-    unsigned long long* keys; // WTA: key of pixel line*pix_line + pos*pix_pos
+    WtaOut wta;               // (Wta): pixel of (line, pos) is line * pix_line + pos * pix_pos
     long long pix_line, pix_pos;
-    int d_base;               // disparity of local index 0 (WTA)
 };
 
-size_t zncc_row_smem_bytes(int R, int mode, int nch, int ds);
-size_t line_pair_smem_bytes(int lpc, int nch, int ds);
+size_t zncc_row_smem_bytes(int R, int mode, const RowArgs& a, int nthreads);
+size_t line_pair_smem_bytes(int mode, const LineArgs& a);
 
 cudaError_t launch_zncc_row(int R, const RowArgs& a, int mode, int dtype, cudaStream_t st);
 cudaError_t launch_line_pair(const LineArgs& a, int mode, int dtype, cudaStream_t st);
 cudaError_t launch_window_stats(const uint8_t* img, int pitch, int W, int H, int r, int x_begin,
-                                int nx, int* S, int* Q, float* isig, cudaStream_t st);
-cudaError_t launch_dt_weights(const uint8_t* guide, int pitch, int W, int H, float K,
-                              float inv_sr255, float* eh, float* evt, cudaStream_t st);
+                                int nx, int* S, int* Q, float* isig, int2* packed,
+                                cudaStream_t st);
+cudaError_t launch_dt_coef(const uint8_t* guide, int pitch, int W, int H, float K,
+                           float inv_sr255, float4* coefH, float4* coefV, cudaStream_t st);
 cudaError_t launch_wta_volume(const void* cost, int dtype, int W, int H, int D, uint16_t* disp,
                               cudaStream_t st);
-cudaError_t launch_wta_finalize(const unsigned long long* keys, int npix, uint16_t* disp,
-                                cudaStream_t st);
 
 // per-radius launchers, one translation unit each
 #define ZNCC_DECLARE_ROW(R) \

@@ -1,16 +1,19 @@
-// zncc_row.cuh -- ZNCC cost of one image row for a slice of disparities, optionally fused
+// zncc_row.cuh -- ZNCC cost of one image row for a range of disparities, optionally fused
 // with the first horizontal DT pass pair (Sec. V-C fuses the cost with L2R the same way) or
-// with WTA (no aggregation). Instantiated once per window radius R in zncc_rN.cu.
+// with WTA (no aggregation). Instantiated once per window radius R in zncc_row.cu.
 #pragma once
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "kernels.h"
 
 namespace zncc {
 
-// Block (row y, disparity slice [d0, d0+ds)): thread (chunk k, dq) computes the costs of
-// pixels x in [16k, 16k+16) for the four disparities d0 + 4dq .. d0 + 4dq + 3. The chunk
-// count is padded to whole warps; pixels x >= W are computed from clamped reads and dropped.
+// Block (row y, a run of spb disparity slices of 4*tq disparities): thread (chunk k, dq)
+// computes the costs of pixels x in [16k, 16k+16) for the four disparities d0 + 4dq ..
+// d0 + 4dq + 3 of each slice. The chunk count is padded to whole warps; pixels x >= W are
+// computed from clamped reads and dropped.
 //
 // Cost (Eq. (1) through Eq. (2)): with P = sum over the window of I_R(x+i, y+j) *
 // I_T(x-d+i, y+j), n = (2R+1)^2 and the window sums S of each image,
@@ -25,7 +28,8 @@ namespace zncc {
 // the target columns of its four disparities in a sliding register window (one new
 // shared-memory load per step serves all four, since column x'-d at step x' is column
 // (x'-1)-(d-1) of the previous step), and turns the running prefix of column sums into the
-// window sums P(x) = prefix(x+R) - prefix(x-R-1).
+// window sums P(x) = prefix(x+R) - prefix(x-R-1). The packed bands are staged once per
+// block and serve all of its disparity slices.
 template <int R, typename T, int MODE>
 __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
     constexpr int l = 2 * R + 1;
@@ -33,28 +37,31 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
     extern __shared__ uint4 smem_u4[];
 
     const int y = blockIdx.x;
-    const int ds = a.ds, tq = ds / kG, nch = a.nch;
-    const int d0 = a.d_begin + blockIdx.y * ds;
-    const int tid = threadIdx.x;
-    const int dq = tid % tq, k = tid / tq;
-    const int span = nch * kL;
+    const int tq = a.tq, ds = kG * tq, nch = a.nch, span = nch * kL;
     const int W = a.W, H = a.H;
+    const int tid = threadIdx.x;
+    const int k = tid / tq, dq = tid - k * tq;
+    const int lane = tid & 31, wl = tid >> 5, nwl = blockDim.x >> 5;
+    const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
+    const int s_begin = blockIdx.y * a.spb;
+    const int s_end = min(nslices, s_begin + a.spb);
+    // every lane's disparities lie in [blk_lo, blk_hi)
+    const int blk_lo = a.d_lo + s_begin * ds, blk_hi = a.d_lo + s_end * ds;
 
-    // ---- shared memory carve (all arrays in the four-plane layout) ----
-    const int NLP = span + 2 * R;              // left columns x' in [-R, span+R)
-    const int NRP = span + 2 * R + ds - 1;     // right columns x'' in [xr0, xr0+NRP)
-    const int xr0 = -R - (d0 + ds - 1);
-    const int NSR = span + ds - 1;             // target centres c in [c0, c0+NSR)
-    const int c0 = -(d0 + ds - 1);
-    const int pLP = plane_of(NLP), pRP = plane_of(NRP), pSL = plane_of(span), pSR = plane_of(NSR);
+    // ---- shared memory carve ----
+    const int NLP = span + 2 * R;                      // left columns x' in [-R, span+R)
+    const int NRP = span + 2 * R + (blk_hi - blk_lo) - 1;
+    const int xr0 = -R - (blk_hi - 1);                 // right columns x'' in [xr0, xr0+NRP)
+    const int pLP = plane_of(NLP), pRP = plane_of(NRP), pX = plane_of(span);
     uint4* LP = smem_u4;
     uint4* RP = LP + 4 * pLP;
-    int* SL = reinterpret_cast<int*>(RP + 4 * pRP);
-    float* ISL = reinterpret_cast<float*>(SL + 4 * pSL);
-    int* SR = reinterpret_cast<int*>(ISL + 4 * pSL);
-    float* ISR = reinterpret_cast<float*>(SR + 4 * pSR);
+    float4* co = reinterpret_cast<float4*>(RP + 4 * pRP);           // HPair
+    float4* sb = co + 4 * pX;
+    float* sa = reinterpret_cast<float*>(sb + 2 * nwl * tq);
+    float* rbv = reinterpret_cast<float*>(RP + 4 * pRP);             // Wta
+    int* rbd = reinterpret_cast<int*>(rbv + 4 * pX);
 
-    // ---- stage the packed bands and the window statistics ----
+    // ---- stage the packed bands (and the DT coefficients / the running best) ----
     for (int t = tid; t < NLP + NRP; t += blockDim.x) {
         const bool is_left = t < NLP;
         const int ix = is_left ? t : t - NLP;
@@ -66,125 +73,156 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
             const int yc = min(max(y - R + j, 0), H - 1);
             w[j >> 2] |= (unsigned)img[(size_t)yc * a.pitch + xc] << (8 * (j & 3));
         }
-        uint4 pk = make_uint4(w[0], w[1], w[2], w[3]);
+        const uint4 pk = make_uint4(w[0], w[1], w[2], w[3]);
         if (is_left) LP[p4(ix, pLP)] = pk;
         else RP[p4(ix, pRP)] = pk;
     }
-    for (int t = tid; t < span; t += blockDim.x) {
-        const bool in = t < W;
-        SL[p4(t, pSL)] = in ? a.SL[(size_t)y * W + t] : 0;
-        ISL[p4(t, pSL)] = in ? a.ISL[(size_t)y * W + t] : 0.0f;
+    if constexpr (MODE == kModeHPair) {
+        for (int t = tid; t < span; t += blockDim.x)
+            co[cidx(t, pX)] = t < W ? __ldg(a.coef + (size_t)y * W + t) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const int WE = W + a.D - 1;   // extended target statistics: centre c at column c + D - 1
-    for (int t = tid; t < NSR; t += blockDim.x) {
-        const int gi = c0 + t + a.D - 1;
-        const bool in = gi >= 0 && c0 + t < W;
-        SR[p4(t, pSR)] = in ? a.SR[(size_t)y * WE + gi] : 0;
-        ISR[p4(t, pSR)] = in ? a.ISR[(size_t)y * WE + gi] : 0.0f;
+    if constexpr (MODE == kModeWta) {
+        for (int t = tid; t < span; t += blockDim.x) {
+            const bool in = t < W && !a.wta.first;
+            rbv[p4(t, pX)] = in ? a.wta.bestv[(size_t)y * W + t] : -INFINITY;
+            rbd[p4(t, pX)] = in ? a.wta.bestd[(size_t)y * W + t] : 0;
+        }
     }
     __syncthreads();
 
-    // ---- window sums of products P for 16 pixels x 4 disparities ----
     const int x0 = k * kL;
-    const int d_first = d0 + dq * kG;
-    int P[kL][4];
-#pragma unroll
-    for (int i = 0; i < kL; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) P[i][j] = 0;
-
-    // RP index of column x' - d_first - j at step t (x' = x0 - R + t): base + t - j
-    const int rbase = x0 - R - d_first - xr0;          // >= 3 since 4dq + 3 <= ds - 1
-    uint4 rp[4];
-    rp[1] = RP[p4(rbase - 1, pRP)];
-    rp[2] = RP[p4(rbase - 2, pRP)];
-    rp[3] = RP[p4(rbase - 3, pRP)];
-    unsigned pre[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-    for (int t = 0; t < kL + 2 * R; ++t) {
-        const uint4 lp = LP[p4(x0 + t, pLP)];
-        rp[0] = RP[p4(rbase + t, pRP)];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            unsigned cs = __dp4a(lp.x, rp[j].x, 0u);
-            if (NW > 1) cs = __dp4a(lp.y, rp[j].y, cs);
-            if (NW > 2) cs = __dp4a(lp.z, rp[j].z, cs);
-            if (NW > 3) cs = __dp4a(lp.w, rp[j].w, cs);
-            pre[j] += cs;
-            if (t - 2 * R >= 0 && t - 2 * R < kL) P[t - 2 * R][j] += (int)pre[j];
-            if (t + 1 < kL) P[t + 1][j] -= (int)pre[j];
-        }
-        rp[3] = rp[2];
-        rp[2] = rp[1];
-        rp[1] = rp[0];
-    }
-
-    // ---- normalization, Eq. (2) ----
     const unsigned n = (unsigned)(l * l);
-    const int nvalid = max(0, min(4, a.d_end - d_first));
-    float v[kL][4];
+    const int WE = W + a.D - 1;
+    const int2* statR = a.statR + (size_t)y * WE + (a.D - 1);   // centre c at statR[c]
+    const int2* statL = a.statL + (size_t)y * W;
+    T* out = reinterpret_cast<T*>(a.vol);
+    const bool vec = a.vec != 0;
+
+    for (int sl = s_begin; sl < s_end; ++sl) {
+        const int d_first = a.d_lo + sl * ds + dq * kG;
+        const int nvalid = max(0, min(4, a.d_hi - d_first));
+
+        // ---- window sums of products P for 16 pixels x 4 disparities ----
+        int P[kL][4];
 #pragma unroll
-    for (int i = 0; i < kL; ++i) {
-        const int x = x0 + i;
-        const unsigned sl = (unsigned)at4(SL, x0, i, pSL);
-        const float isl = at4(ISL, x0, i, pSL);
-        // target centre x - d_first - j sits at SR index x - d_first - j - c0
-        const int sbase = x - d_first - c0;
+        for (int i = 0; i < kL; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const unsigned sr = (unsigned)SR[p4(sbase - j, pSR)];
-            const float isr = ISR[p4(sbase - j, pSR)];
-            const unsigned num = n * (unsigned)P[i][j] - sl * sr;
-            const bool ok = x < W && j < nvalid;
-            v[i][j] = ok ? (float)(int)num * isl * isr : 0.0f;
+            for (int j = 0; j < 4; ++j) P[i][j] = 0;
+        // RP index of column x' - d_first - j at step t (x' = x0 - R + t) is rbase + t - j
+        const int rbase = x0 - R - d_first - xr0;      // >= 3: d_first + 3 < blk_hi
+        uint4 rp[4];
+        rp[1] = RP[p4(rbase - 1, pRP)];
+        rp[2] = RP[p4(rbase - 2, pRP)];
+        rp[3] = RP[p4(rbase - 3, pRP)];
+        unsigned pre[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int t = 0; t < kL + 2 * R; ++t) {
+            const uint4 lp = LP[p4(x0 + t, pLP)];
+            rp[0] = RP[p4(rbase + t, pRP)];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                pre[j] = __dp4a(lp.x, rp[j].x, pre[j]);
+                if (NW > 1) pre[j] = __dp4a(lp.y, rp[j].y, pre[j]);
+                if (NW > 2) pre[j] = __dp4a(lp.z, rp[j].z, pre[j]);
+                if (NW > 3) pre[j] = __dp4a(lp.w, rp[j].w, pre[j]);
+                if (t - 2 * R >= 0 && t - 2 * R < kL) P[t - 2 * R][j] += (int)pre[j];
+                if (t + 1 < kL) P[t + 1][j] -= (int)pre[j];
+            }
+            rp[3] = rp[2];
+            rp[2] = rp[1];
+            rp[1] = rp[0];
+        }
+
+        // ---- normalization, Eq. (2); the target statistics slide like the columns ----
+        const int cb = x0 - d_first;                    // target centre of (i, j) is cb + i - j
+        auto stat_r = [&](int c) -> int2 {
+            return (c > -a.D && c < W) ? __ldg(statR + c) : make_int2(0, 0);
+        };
+        int2 sr[4];
+        sr[1] = stat_r(cb - 1);
+        sr[2] = stat_r(cb - 2);
+        sr[3] = stat_r(cb - 3);
+        float v[kL][4];
+#pragma unroll
+        for (int i = 0; i < kL; ++i) {
+            const int x = x0 + i;
+            const int2 st = x < W ? __ldg(statL + x) : make_int2(0, 0);
+            sr[0] = stat_r(cb + i);
+            const float isl = __int_as_float(st.y);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const unsigned num = n * (unsigned)P[i][j] - (unsigned)st.x * (unsigned)sr[j].x;
+                const bool ok = x < W && j < nvalid;
+                v[i][j] = ok ? (float)(int)num * isl * __int_as_float(sr[j].y) : 0.0f;
+            }
+            sr[3] = sr[2];
+            sr[2] = sr[1];
+            sr[1] = sr[0];
+        }
+
+        if constexpr (MODE == kModeWta) {
+#pragma unroll
+            for (int i = 0; i < kL; ++i) {
+                float best;
+                int bd;
+                wta_group(v[i], nvalid, d_first, tq, best, bd);
+                const int x = x0 + i;
+                if (dq == 0 && x < W && best > rbv[p4(x, pX)]) {
+                    rbv[p4(x, pX)] = best;
+                    rbd[p4(x, pX)] = bd;
+                }
+            }
+            continue;
+        }
+        if constexpr (MODE == kModeHPair) dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2);
+
+        // ---- store [H][W][dstride] ----
+        if (nvalid > 0) {
+            T* q = out + ((size_t)y * W + x0) * a.dstride + (d_first - a.d_out0);
+#pragma unroll
+            for (int i = 0; i < kL; ++i) {
+                if (x0 + i < W) st4(q, nvalid, vec, v[i]);
+                q += a.dstride;
+            }
         }
     }
 
     if constexpr (MODE == kModeWta) {
+        if (dq == 0) {
 #pragma unroll
-        for (int i = 0; i < kL; ++i) {
-            const int x = x0 + i;
-            wta_fold(v[i], nvalid, d_first, tq, dq, x < W, a.keys + (size_t)y * W + min(x, W - 1));
+            for (int i = 0; i < kL; ++i) {
+                const int x = x0 + i;
+                if (x >= W) break;
+                const size_t o = (size_t)y * W + x;
+                if (a.wta.last) a.wta.disp[o] = (uint16_t)rbd[p4(x, pX)];
+                else {
+                    a.wta.bestv[o] = rbv[p4(x, pX)];
+                    a.wta.bestd[o] = rbd[p4(x, pX)];
+                }
+            }
         }
-        return;
-    }
-    if constexpr (MODE == kModeHPair) {
-        // the DT scratch reuses the band and statistics area, which is dead from here on
-        __syncthreads();
-        DtShared dsm = dt_carve(reinterpret_cast<float*>(smem_u4), 1, nch, ds);
-        dt_stage_weights(dsm, a.eh, W, y, H, 1, nch, W);
-        __syncthreads();
-        dt_chunk_products(dsm, 0, k, dq);
-        __syncthreads();
-        dt_line_pair(v, dsm, 0, k, dq, nch, ds, a.s);
-    }
-
-    // ---- store [H][W][dstride] ----
-    T* out = reinterpret_cast<T*>(a.vol);
-    const int dl = d_first - a.d_out0;
-    const bool vec = a.vec != 0;
-#pragma unroll
-    for (int i = 0; i < kL; ++i) {
-        const int x = x0 + i;
-        if (x < W && nvalid > 0)
-            st4(out + ((size_t)y * W + x) * a.dstride + dl, nvalid, vec, v[i]);
     }
 }
 
-// Host-visible shared-memory size of one block of k_zncc_row.
-inline size_t zncc_row_smem(int R, int mode, int nch, int ds) {
-    const int span = nch * kL;
-    size_t b = 16ull * 4 * (plane_of(span + 2 * R) + plane_of(span + 2 * R + ds - 1));
-    b += 8ull * 4 * (plane_of(span) + plane_of(span + ds - 1));
-    if (mode == kModeHPair && dt_shared_bytes(1, nch, ds) > b) b = dt_shared_bytes(1, nch, ds);
+// Shared-memory bytes of one block of k_zncc_row.
+inline size_t zncc_row_smem(int R, int mode, const RowArgs& a, int nthreads) {
+    const int ds = kG * a.tq, span = a.nch * kL;
+    const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
+    const int drange = std::min(a.spb, nslices) * ds;
+    size_t b = 16ull * 4 * (plane_of(span + 2 * R) + plane_of(span + 2 * R + drange - 1));
+    const int pX = plane_of(span);
+    if (mode == kModeHPair) b += 16ull * 4 * pX + dt_scan_bytes(nthreads / 32, a.tq);
+    if (mode == kModeWta) b += 8ull * 4 * pX;
     return b;
 }
 
 template <int R>
 cudaError_t launch_zncc_row_impl(const RowArgs& a, int mode, int dtype, cudaStream_t st) {
-    dim3 grid(a.H, (a.d_end - a.d_begin + a.ds - 1) / a.ds);
-    dim3 block(a.nch * (a.ds / kG));
-    size_t smem = zncc_row_smem(R, mode, a.nch, a.ds);
+    const int ds = kG * a.tq;
+    const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
+    dim3 grid(a.H, (nslices + a.spb - 1) / a.spb);
+    dim3 block(a.nch * a.tq);
+    const size_t smem = zncc_row_smem(R, mode, a, (int)block.x);
     void (*fn)(RowArgs) = nullptr;
     if (mode == kModeRaw) fn = dtype == 0 ? k_zncc_row<R, float, kModeRaw> : k_zncc_row<R, __half, kModeRaw>;
     else if (mode == kModeHPair) fn = dtype == 0 ? k_zncc_row<R, float, kModeHPair> : k_zncc_row<R, __half, kModeHPair>;
