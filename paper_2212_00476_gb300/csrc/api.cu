@@ -43,12 +43,13 @@ struct zncc_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     std::string err;
-    int2* statL = nullptr;        // [H][W]       left window statistics (S, 1/sigma)
-    int2* statR = nullptr;        // [H][W+D-1]   right window statistics, centres -(D-1)..W-1
     float4* coefH = nullptr;      // [H][W]       horizontal DT coefficients
     float4* coefV = nullptr;      // [W][H]       vertical DT coefficients
     void* vol = nullptr;          // the fused path's intermediate volume (on first use)
     size_t vol_bytes = 0;
+    float* bestv = nullptr;       // [H][W] running WTA best across launches (on first use)
+    int* bestd = nullptr;         // [H][W]
+    int smem_max = 0;             // opt-in shared memory per block of the device
     uint8_t* img = nullptr;       // device copies for zncc_run_host: 2 x [H][W]
     uint16_t* disp = nullptr;     // [H][W]
     bool profiling = false;
@@ -107,10 +108,6 @@ int prof_event(zncc_ctx* c) {
         }                                                                     \
     } while (0)
 
-// Lanes per chunk (4 disparities each) for a line of n positions: the n/16 chunks of a line
-// times tq lanes must fit one block of at most 512 threads.
-int lanes_for(int n) { return n <= 1024 ? 8 : (n <= 2048 ? 4 : 2); }
-
 // The chunk count is padded so that a line's threads fill whole warps (every warp-wide
 // shuffle then has all 32 lanes); padded chunks lie past the line end and hold zeros.
 int padded_chunks(int n, int tq) {
@@ -124,12 +121,6 @@ int slices_per_block(int nslices, int blocks_x) {
     const int per = std::max(1, blocks_x * nslices / kTargetBlocks);
     const int groups = std::max(1, (nslices + per - 1) / per);
     return (nslices + groups - 1) / groups;
-}
-
-bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-
-bool volume_vec(const void* vol, int dtype, long long dstride) {
-    return dstride % 4 == 0 && aligned(vol, dtype == 0 ? 16 : 8);
 }
 
 zncc_status check_images(zncc_ctx* c, const void* a, const void* b, int pitch) {
@@ -150,16 +141,6 @@ float scale_s2(float sigma_s) {
     return (float)(s * s);
 }
 
-// Window statistics of both images into the context scratch.
-zncc_status run_stats(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch) {
-    ZNCC_LAUNCH(c, K_STATS, launch_window_stats(left, pitch, c->W, c->H, c->r, 0, c->W, nullptr, nullptr,
-                                                nullptr, c->statL, c->stream), "window statistics (left)");
-    ZNCC_LAUNCH(c, K_STATS, launch_window_stats(right, pitch, c->W, c->H, c->r, -(c->D - 1), c->W + c->D - 1,
-                                                nullptr, nullptr, nullptr, c->statR, c->stream),
-                "window statistics (right)");
-    return ZNCC_OK;
-}
-
 zncc_status run_coef(zncc_ctx* c, const uint8_t* guide, int pitch, float sigma_s, float sigma_r) {
     const float K = (float)exp(-1.0 / (double)sigma_s);
     const float inv = (float)(1.0 / (255.0 * (double)sigma_r));
@@ -168,7 +149,30 @@ zncc_status run_coef(zncc_ctx* c, const uint8_t* guide, int pitch, float sigma_s
     return ZNCC_OK;
 }
 
-RowArgs row_args(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch, int mode) {
+void free_dev_f(float*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+zncc_status ensure_best(zncc_ctx* c) {
+    if (c->bestv) return ZNCC_OK;
+    const size_t npix = (size_t)c->W * c->H;
+    cudaError_t e = cudaMalloc(&c->bestv, npix * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->bestd, npix * sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_dev_f(c->bestv);
+        return fail(c, ZNCC_ENOMEM, std::string("WTA buffers: ") + cudaGetErrorString(e));
+    }
+    return ZNCC_OK;
+}
+
+// ZNCC row launches over the disparities [0, D): the band of a block covers its disparity
+// slices, so the slices per block shrink until the block fits in shared memory. In Wta
+// mode a block must see every disparity of its launch, so the disparity range is split
+// into several launches chained through the running best when it does not fit.
+zncc_status run_rows(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch, int mode, int dtype,
+                     void* vol, long long dstride, float s2, uint16_t* disp, int kind, const char* what) {
     RowArgs a;
     memset(&a, 0, sizeof(a));
     a.left = left;
@@ -177,21 +181,55 @@ RowArgs row_args(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pit
     a.W = c->W;
     a.H = c->H;
     a.D = c->D;
-    a.statL = c->statL;
-    a.statR = c->statR;
-    a.tq = lanes_for(c->W);
+    a.tq = c->W <= 1024 ? 8 : (c->W <= 2048 ? 4 : 2);
     a.nch = padded_chunks(c->W, a.tq);
-    a.d_lo = 0;
-    a.d_hi = c->D;
-    const int nslices = (c->D + kG * a.tq - 1) / (kG * a.tq);
-    a.spb = mode == kModeWta ? nslices : slices_per_block(nslices, c->H);
-    a.dstride = c->D;
+    a.vol = vol;
+    a.dstride = dstride;
     a.d_out0 = 0;
+    a.vec = vol && (dstride % 4 == 0) && ((uintptr_t)vol % (dtype == 0 ? 16 : 8) == 0) ? 1 : 0;
     a.coef = c->coefH;
-    return a;
+    a.s2 = s2;
+    const int threads = a.nch * a.tq;
+    const int ds = kG * a.tq;
+    const int nslices = (c->D + ds - 1) / ds;
+    if (mode != kModeWta) {
+        a.d_lo = 0;
+        a.d_hi = c->D;
+        a.spb = slices_per_block(nslices, c->H);
+        while (a.spb > 1 && zncc_row_smem_bytes(c->r, mode, a, threads) > (size_t)c->smem_max) --a.spb;
+        if (zncc_row_smem_bytes(c->r, mode, a, threads) > (size_t)c->smem_max)
+            return fail(c, ZNCC_EUNSUPPORTED, "image too wide for the cost kernel's shared memory");
+        ZNCC_LAUNCH(c, kind, launch_zncc_row(c->r, a, mode, dtype, c->stream), what);
+        return ZNCC_OK;
+    }
+    int per_launch = nslices;   // slices of one Wta launch
+    for (;;) {
+        a.d_lo = 0;
+        a.d_hi = std::min(c->D, per_launch * ds);
+        a.spb = per_launch;
+        if (zncc_row_smem_bytes(c->r, mode, a, threads) <= (size_t)c->smem_max) break;
+        if (per_launch == 1) return fail(c, ZNCC_EUNSUPPORTED, "image too wide for the cost kernel's shared memory");
+        per_launch = (per_launch + 1) / 2;
+    }
+    const int nlaunch = (nslices + per_launch - 1) / per_launch;
+    if (nlaunch > 1) ZNCC_TRY(ensure_best(c));
+    for (int g = 0; g < nlaunch; ++g) {
+        a.d_lo = g * per_launch * ds;
+        a.d_hi = std::min(c->D, (g + 1) * per_launch * ds);
+        a.spb = per_launch;
+        a.wta.bestv = c->bestv;
+        a.wta.bestd = c->bestd;
+        a.wta.disp = disp;
+        a.wta.first = g == 0;
+        a.wta.last = g == nlaunch - 1;
+        ZNCC_LAUNCH(c, kind, launch_zncc_row(c->r, a, mode, dtype, c->stream), what);
+    }
+    return ZNCC_OK;
 }
 
-// One DT pair along rows (horiz) or columns of a [H][W][dstride] volume.
+// One DT pair along rows (horiz) or columns of a [H][W][dstride] volume. The block shape is
+// the widest lane count per chunk whose block fits, streaming the next slices through shared
+// memory (async) where that fits too.
 zncc_status run_line_pair(zncc_ctx* c, void* vol, int dtype, long long dstride, bool horiz, float s2,
                           int mode, uint16_t* disp) {
     LineArgs a;
@@ -204,21 +242,34 @@ zncc_status run_line_pair(zncc_ctx* c, void* vol, int dtype, long long dstride, 
     a.nlines = horiz ? c->H : c->W;
     a.dcount = c->D;
     a.d_base = 0;
-    a.tq = lanes_for(n);
-    a.nch = padded_chunks(n, a.tq);
-    const int per_line = a.nch * a.tq;
-    a.lpc = std::max(1, std::min(8, 256 / per_line));
-    const int nslices = (c->D + kG * a.tq - 1) / (kG * a.tq);
-    a.spb = mode == kLineWta ? nslices : slices_per_block(nslices, (a.nlines + a.lpc - 1) / a.lpc);
     a.coef = horiz ? c->coefH : c->coefV;
     a.coef_line_stride = horiz ? c->W : c->H;
     a.s2 = s2;
-    a.vec = volume_vec(vol, dtype, dstride) ? 1 : 0;
+    a.vec = (dstride % 4 == 0) && ((uintptr_t)vol % (dtype == 0 ? 16 : 8) == 0) ? 1 : 0;
     a.wta.disp = disp;
     a.wta.first = 1;
     a.wta.last = 1;
     a.pix_line = horiz ? c->W : 1;
     a.pix_pos = horiz ? 1 : c->W;
+    bool found = false;
+    for (int pass = 0; pass < 2 && !found; ++pass) {          // with, then without, async
+        for (int tq = 8; tq >= 2 && !found; tq >>= 1) {
+            a.tq = tq;
+            a.nch = padded_chunks(n, tq);
+            const int per_line = a.nch * tq;
+            if (per_line > 512) continue;
+            a.async = pass == 0 ? a.vec : 0;
+            if (pass == 0 && !a.vec) continue;
+            for (a.lpc = std::max(1, std::min(8, 256 / per_line)); a.lpc >= 1; --a.lpc)
+                if (line_pair_smem_bytes(mode, dtype, a) <= (size_t)c->smem_max) {
+                    found = true;
+                    break;
+                }
+        }
+    }
+    if (!found) return fail(c, ZNCC_EUNSUPPORTED, "line too long for the DT kernel's shared memory");
+    const int nslices = (c->D + kG * a.tq - 1) / (kG * a.tq);
+    a.spb = mode == kLineWta ? nslices : slices_per_block(nslices, (a.nlines + a.lpc - 1) / a.lpc);
     const int kind = horiz ? K_DT_HPAIR : (mode == kLineWta ? K_DT_VPAIR_WTA : K_DT_VPAIR);
     ZNCC_LAUNCH(c, kind, launch_line_pair(a, mode, dtype, c->stream), horiz ? "DT horizontal pair" : "DT vertical pair");
     return ZNCC_OK;
@@ -231,11 +282,11 @@ void free_dev(T*& p) {
 }
 
 void release(zncc_ctx* c) {
-    free_dev(c->statL);
-    free_dev(c->statR);
     free_dev(c->coefH);
     free_dev(c->coefV);
     free_dev(c->vol);
+    free_dev(c->bestv);
+    free_dev(c->bestd);
     free_dev(c->img);
     free_dev(c->disp);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -267,10 +318,8 @@ zncc_status zncc_create(int width, int height, int max_disp, int win, zncc_ctx**
     c->win = win;
     c->r = win / 2;
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     const size_t npix = (size_t)width * height;
-    const size_t nright = (size_t)(width + max_disp - 1) * height;
-    if (e == cudaSuccess) e = cudaMalloc(&c->statL, npix * sizeof(int2));
-    if (e == cudaSuccess) e = cudaMalloc(&c->statR, nright * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&c->coefH, npix * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&c->coefV, npix * sizeof(float4));
     if (e != cudaSuccess) {
@@ -323,12 +372,7 @@ zncc_status zncc_cost_volume(zncc_ctx* c, const uint8_t* left, const uint8_t* ri
     ZNCC_TRY(check_images(c, left, right, pitch));
     if (!cost) return fail(c, ZNCC_EINVAL, "cost pointer is NULL");
     if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
-    ZNCC_TRY(run_stats(c, left, right, pitch));
-    RowArgs a = row_args(c, left, right, pitch, kModeRaw);
-    a.vol = cost;
-    a.vec = volume_vec(cost, dtype, c->D) ? 1 : 0;
-    ZNCC_LAUNCH(c, K_ZNCC_RAW, launch_zncc_row(c->r, a, kModeRaw, dtype, c->stream), "ZNCC cost");
-    return ZNCC_OK;
+    return run_rows(c, left, right, pitch, kModeRaw, dtype, cost, c->D, 0.0f, nullptr, K_ZNCC_RAW, "ZNCC cost");
 }
 
 zncc_status dt_aggregate(zncc_ctx* c, const uint8_t* guide, int pitch, void* cost, zncc_dtype dtype,
@@ -369,15 +413,7 @@ zncc_status zncc_run(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int
     ZNCC_TRY(check_dt(c, sigma_s, sigma_r, iters));
     const size_t npix = (size_t)c->W * c->H;
 
-    ZNCC_TRY(run_stats(c, left, right, pitch));
-    if (iters == 0) {
-        RowArgs a = row_args(c, left, right, pitch, kModeWta);
-        a.wta.disp = disp;
-        a.wta.first = 1;
-        a.wta.last = 1;
-        ZNCC_LAUNCH(c, K_ZNCC_WTA, launch_zncc_row(c->r, a, kModeWta, 0, c->stream), "ZNCC + WTA");
-        return ZNCC_OK;
-    }
+    if (iters == 0) return run_rows(c, left, right, pitch, kModeWta, 0, nullptr, 0, 0.0f, disp, K_ZNCC_WTA, "ZNCC + WTA");
     const int dt = storage == ZNCC_F32 ? 0 : 1;
     const long long dstride = (c->D + 3) / 4 * 4;   // padded so every access is vectorised
     const size_t need = npix * (size_t)dstride * (dt == 0 ? 4 : 2);
@@ -394,12 +430,8 @@ zncc_status zncc_run(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int
     }
     ZNCC_TRY(run_coef(c, left, pitch, sigma_s, sigma_r));
     const float s2 = scale_s2(sigma_s);
-    RowArgs a = row_args(c, left, right, pitch, kModeHPair);
-    a.vol = c->vol;
-    a.dstride = dstride;
-    a.vec = volume_vec(c->vol, dt, dstride) ? 1 : 0;
-    a.s2 = s2;
-    ZNCC_LAUNCH(c, K_ZNCC_HPAIR, launch_zncc_row(c->r, a, kModeHPair, dt, c->stream), "ZNCC + horizontal DT pair");
+    ZNCC_TRY(run_rows(c, left, right, pitch, kModeHPair, dt, c->vol, dstride, s2, nullptr, K_ZNCC_HPAIR,
+                      "ZNCC + horizontal DT pair"));
     for (int it = 0; it < iters; ++it) {
         const bool last = it == iters - 1;
         ZNCC_TRY(run_line_pair(c, c->vol, dt, dstride, false, s2, last ? kLineWta : kLineStore, disp));

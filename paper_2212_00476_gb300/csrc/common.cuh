@@ -18,6 +18,11 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // accesses free of bank conflicts (plain layouts put lanes 16 or 64 entries apart).
 __host__ __device__ __forceinline__ int plane_of(int len) { return ((len + 3) / 4 + 31) & ~31; }
 __device__ __forceinline__ int p4(int idx, int plane) { return (idx & 3) * plane + (idx >> 2); }
+// Entry start + i of a four-plane array, for start a multiple of 4 (i known at compile time).
+template <typename T>
+__device__ __forceinline__ T& at4(T* base, int start, int i, int plane) {
+    return base[(i & 3) * plane + (start >> 2) + (i >> 2)];
+}
 // Coefficient arrays add an XOR swizzle inside the plane (bit 1 flipped where bit 3 is set),
 // which also separates the chunks of a warp when only two lanes share a chunk.
 __device__ __forceinline__ int cidx(int pos, int plane) {
@@ -74,6 +79,37 @@ __device__ __forceinline__ void st4(__half* p, int nvalid, bool vec, const float
         for (int j = 0; j < 4; ++j)
             if (j < nvalid) p[j] = __float2half_rn(o[j]);
     }
+}
+
+// ---- asynchronous global -> shared copies (cp.async) ------------------------------------
+// A copy of `bytes` from global to shared memory that bypasses registers; with valid ==
+// false nothing is read and the destination is zero-filled. Each thread waits for its own
+// copies (cp.async.wait_group), so a thread that reads back only what it copied needs no
+// block barrier.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int src_bytes = valid ? BYTES : 0;
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(BYTES),
+                     "r"(src_bytes)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// The four consecutive disparities of one element group, read back from shared memory.
+__device__ __forceinline__ void lds4(const float* p, float (&o)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void lds4(const __half* p, float (&o)[4]) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    o[0] = half_lo(t.x); o[1] = half_hi(t.x); o[2] = half_lo(t.y); o[3] = half_hi(t.y);
 }
 
 // ---- WTA (Eq. (WTA1)): the largest cost wins, ties go to the smallest d ----------------

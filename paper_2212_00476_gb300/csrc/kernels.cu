@@ -64,49 +64,48 @@ cudaError_t launch_window_stats(const uint8_t* img, int pitch, int W, int H, int
 // the horizontal passes, columns for the vertical ones) and position p, with w(p) the weight
 // of the step p-1 -> p (0 at p = 0 and past the line end):
 //   (w(p), prod_{j=c..p} w(j), w(p+1), prod_{j=p..c+15} w(j+1)),  c = chunk start (16 | c).
-// coefH is [H][W]; coefV is [W][H] (a column is contiguous). One thread per chunk.
+// coefH is [H][W]; coefV is [W][H] (a column is contiguous). One thread per position; the
+// 16 positions of a chunk are 16 consecutive lanes, whose products are shuffle scans.
 __global__ void k_dt_coef(const uint8_t* __restrict__ g, int pitch, int W, int H, float K,
                           float inv_sr255, float4* __restrict__ coefH, float4* __restrict__ coefV) {
     const int nchH = (W + kL - 1) / kL, nchV = (H + kL - 1) / kL;
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool horiz = idx < H * nchH;
-    if (!horiz) idx -= H * nchH;
-    if (!horiz && idx >= W * nchV) return;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    int chunk = gid / kL;
+    const int i = gid & (kL - 1);
+    const bool horiz = chunk < H * nchH;
+    if (!horiz) chunk -= H * nchH;
+    const bool live = horiz || chunk < W * nchV;
     const int n = horiz ? W : H;
-    const int line = horiz ? idx / nchH : idx / nchV;
-    const int c = (horiz ? idx - line * nchH : idx - line * nchV) * kL;
-    auto pix = [&](int p) -> int {
-        return horiz ? g[(size_t)line * pitch + p] : g[(size_t)p * pitch + line];
+    const int nchl = horiz ? nchH : nchV;
+    const int line = live ? chunk / nchl : 0;
+    const int p = (live ? chunk - line * nchl : 0) * kL + i;
+    auto pix = [&](int q) -> int {
+        return horiz ? g[(size_t)line * pitch + q] : g[(size_t)q * pitch + line];
     };
-    float w[kL + 1];
+    auto weight = [&](int q) -> float {    // the step q-1 -> q
+        return (live && q >= 1 && q < n) ? K * expf(-fabsf((float)(pix(q) - pix(q - 1))) * inv_sr255) : 0.0f;
+    };
+    const float w = weight(p);
+    float wn = __shfl_down_sync(kFull, w, 1, kL);
+    if (i == kL - 1) wn = weight(p + 1);
+    float A = w, B = wn;
 #pragma unroll
-    for (int i = 0; i <= kL; ++i) {
-        const int p = c + i;
-        w[i] = (p >= 1 && p < n) ? K * expf(-fabsf((float)(pix(p) - pix(p - 1))) * inv_sr255) : 0.0f;
+    for (int off = 1; off < kL; off <<= 1) {
+        const float a2 = __shfl_up_sync(kFull, A, off, kL);
+        const float b2 = __shfl_down_sync(kFull, B, off, kL);
+        if (i >= off) A *= a2;
+        if (i + off < kL) B *= b2;
     }
-    float A[kL], B[kL];
-    float acc = 1.0f;
-#pragma unroll
-    for (int i = 0; i < kL; ++i) {
-        acc *= w[i];
-        A[i] = acc;
+    if (live && p < n) {
+        float4* out = horiz ? coefH + (size_t)line * W : coefV + (size_t)line * H;
+        out[p] = make_float4(w, A, wn, B);
     }
-    acc = 1.0f;
-#pragma unroll
-    for (int i = kL - 1; i >= 0; --i) {
-        acc *= w[i + 1];
-        B[i] = acc;
-    }
-    float4* out = horiz ? coefH + (size_t)line * W : coefV + (size_t)line * H;
-#pragma unroll
-    for (int i = 0; i < kL; ++i)
-        if (c + i < n) out[c + i] = make_float4(w[i], A[i], w[i + 1], B[i]);
 }
 
 cudaError_t launch_dt_coef(const uint8_t* guide, int pitch, int W, int H, float K, float inv_sr255,
                            float4* coefH, float4* coefV, cudaStream_t st) {
-    const int total = H * ((W + kL - 1) / kL) + W * ((H + kL - 1) / kL);
-    k_dt_coef<<<(total + 127) / 128, 128, 0, st>>>(guide, pitch, W, H, K, inv_sr255, coefH, coefV);
+    const long long total = (long long)kL * (H * ((W + kL - 1) / kL) + W * ((H + kL - 1) / kL));
+    k_dt_coef<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(guide, pitch, W, H, K, inv_sr255, coefH, coefV);
     return cudaGetLastError();
 }
 
@@ -116,6 +115,13 @@ cudaError_t launch_dt_coef(const uint8_t* guide, int pitch, int W, int H, float 
 // the last pair of the chain, folded into a per-pixel running best without writing the
 // volume back (Sec. V-C fuses WTA with D2U in the same way). Block = lpc lines x a run of
 // spb disparity slices (4*tq disparities each); the lines' coefficients are staged once.
+// With aligned 4-disparity groups (vec) each thread streams its elements of the next two
+// slices into shared memory with cp.async while the current slice is being computed.
+template <typename T>
+__host__ __device__ inline size_t line_stage_bytes(const LineArgs& a) {
+    return a.async ? 2ull * a.lpc * kL * a.nch * a.tq * (4 * sizeof(T)) : 0;
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
     extern __shared__ float4 smem4[];
@@ -130,8 +136,9 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
     const bool line_ok = line < a.nlines;
     const int pX = plane_of(span);
 
-    float4* co_all = smem4;                                            // [lpc][4 pX]
-    float4* sb_all = smem4 + a.lpc * 4 * pX;                           // [lpc][2 nwl tq]
+    T* stage = reinterpret_cast<T*>(smem4);                           // [2][lpc][kL][per_line] x 4
+    float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + line_stage_bytes<T>(a));
+    float4* sb_all = co_all + a.lpc * 4 * pX;                          // [lpc][2 nwl tq]
     float* sa_all = reinterpret_cast<float*>(sb_all + a.lpc * 2 * nwl * tq);
     float* rbv_all = sa_all + a.lpc * 2 * nwl * tq;                    // [lpc][4 pX] (Wta)
     int* rbd_all = reinterpret_cast<int*>(rbv_all + a.lpc * 4 * pX);
@@ -140,6 +147,40 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
     float* sa = sa_all + li * 2 * nwl * tq;
     float* rbv = rbv_all + li * 4 * pX;
     int* rbd = rbd_all + li * 4 * pX;
+
+    const int nslices = (a.dcount + ds - 1) / ds;
+    const int s_begin = blockIdx.y * a.spb;
+    const int s_end = min(nslices, s_begin + a.spb);
+    T* vol = reinterpret_cast<T*>(a.vol);
+    const bool vec = a.vec != 0;
+    const bool async = a.async != 0;
+    const int npos = a.n - k * kL;                                     // positions of this chunk
+    // the chunk's first element group of slice sl
+    auto chunk_base = [&](int sl) -> T* {
+        return vol + (size_t)(line_ok ? line : 0) * a.line_stride + (size_t)(k * kL) * a.elem_stride + sl * ds + dq * kG;
+    };
+    auto stage_at = [&](int buf, int i) -> T* {
+        return stage + ((size_t)((buf * a.lpc + li) * kL + i) * per_line + tl) * 4;
+    };
+    // prefetch of slice sl into stage buffer buf. With vec the entries per pixel are a
+    // multiple of 4, so a group with any valid disparity lies whole inside the volume; its
+    // entries past dcount are never stored or compared.
+    auto prefetch = [&](int sl, int buf) {
+        if (sl < s_end) {
+            const bool ok = line_ok && sl * ds + dq * kG < a.dcount;
+            const T* src = chunk_base(sl);
+#pragma unroll
+            for (int i = 0; i < kL; ++i) {
+                const bool valid = ok && i < npos;
+                cp_async<4 * sizeof(T)>(stage_at(buf, i), valid ? src + (size_t)i * a.elem_stride : vol, valid);
+            }
+        }
+        cp_async_commit();
+    };
+    if (async) {
+        prefetch(s_begin, 0);
+        prefetch(s_begin + 1, 1);
+    }
 
     for (int l2 = 0; l2 < a.lpc; ++l2) {
         const int ln = line0 + l2;
@@ -157,21 +198,17 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
     }
     __syncthreads();
 
-    const int nslices = (a.dcount + ds - 1) / ds;
-    const int s_begin = blockIdx.y * a.spb;
-    const int s_end = min(nslices, s_begin + a.spb);
-    T* vol = reinterpret_cast<T*>(a.vol);
-    const bool vec = a.vec != 0;
-    for (int sl = s_begin; sl < s_end; ++sl) {
+    for (int sl = s_begin, it = 0; sl < s_end; ++sl, ++it) {
         const int dl = sl * ds + dq * kG;                              // entry of d_first
         const int nvalid = max(0, min(4, a.dcount - dl));
-        // the chunk's first element; consecutive positions are elem_stride entries apart
-        T* const base = vol + (size_t)(line_ok ? line : 0) * a.line_stride + (size_t)(k * kL) * a.elem_stride + dl;
         const bool any = line_ok && nvalid > 0;
-        const int npos = a.n - k * kL;
         float v[kL][4];
-        {
-            const T* q = base;
+        if (async) {
+            cp_async_wait<1>();                                        // this slice's copies landed
+#pragma unroll
+            for (int i = 0; i < kL; ++i) lds4(stage_at(it & 1, i), v[i]);
+        } else {
+            const T* q = chunk_base(sl);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 if (any && i < npos) ld4(q, nvalid, vec, v[i]);
@@ -180,6 +217,8 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
             }
         }
         dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2);
+        // the stage buffer was consumed by the sweeps above: refill it with slice sl + 2
+        if (async) prefetch(sl + 2, it & 1);
         if constexpr (MODE == kLineWta) {
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
@@ -193,7 +232,7 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
                 }
             }
         } else {
-            T* q = base;
+            T* q = chunk_base(sl);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 if (any && i < npos) st4(q, nvalid, vec, v[i]);
@@ -201,6 +240,7 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
             }
         }
     }
+    if (async) cp_async_wait<0>();
     if constexpr (MODE == kLineWta) {
         if (dq == 0 && line_ok) {
 #pragma unroll
@@ -218,10 +258,11 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
     }
 }
 
-size_t line_pair_smem_bytes(int mode, const LineArgs& a) {
+size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a) {
     const int pX = plane_of(a.nch * kL);
     const int nwl = a.nch * a.tq / 32;
-    size_t b = (size_t)a.lpc * (16ull * 4 * pX + dt_scan_bytes(nwl, a.tq));
+    size_t b = dtype == 0 ? line_stage_bytes<float>(a) : line_stage_bytes<__half>(a);
+    b += (size_t)a.lpc * (16ull * 4 * pX + dt_scan_bytes(nwl, a.tq));
     if (mode == kLineWta) b += (size_t)a.lpc * 8 * 4 * pX;
     return b;
 }
@@ -231,7 +272,7 @@ cudaError_t launch_line_pair(const LineArgs& a, int mode, int dtype, cudaStream_
     const int nslices = (a.dcount + ds - 1) / ds;
     dim3 grid((a.nlines + a.lpc - 1) / a.lpc, (nslices + a.spb - 1) / a.spb);
     dim3 block(a.lpc * a.nch * a.tq);
-    const size_t smem = line_pair_smem_bytes(mode, a);
+    const size_t smem = line_pair_smem_bytes(mode, dtype, a);
     void (*fn)(LineArgs) = nullptr;
     if (mode == kLineStore) fn = dtype == 0 ? k_line_pair<float, kLineStore> : k_line_pair<__half, kLineStore>;
     else fn = dtype == 0 ? k_line_pair<float, kLineWta> : k_line_pair<__half, kLineWta>;

@@ -22,8 +22,6 @@ struct RowArgs {
     const uint8_t* left;
     const uint8_t* right;
     int pitch, W, H, D;
-    const int2* statL;        // [H][W]       (window sum S, 1/sigma as float bits), left image
-    const int2* statR;        // [H][W+D-1]   the same for the right image, centre c at c+D-1
     int nch, tq;              // chunks per row (padded to whole warps), lanes per chunk
     int d_lo, d_hi;           // disparity range of this launch (d_lo a multiple of 4)
     int spb;                  // disparity slices (4 * tq each) per block
@@ -47,13 +45,14 @@ struct LineArgs {
     const float4* coef;       // coefficients: coef[line * coef_line_stride + pos]
     long long coef_line_stride;
     float s2;
-    int vec;
+    int vec;                  // 16-byte (float) / 8-byte (half) accesses allowed
+    int async;                // vec, and the next slices are streamed through shared memory
     WtaOut wta;               // (Wta): pixel of (line, pos) is line * pix_line + pos * pix_pos
     long long pix_line, pix_pos;
 };
 
 size_t zncc_row_smem_bytes(int R, int mode, const RowArgs& a, int nthreads);
-size_t line_pair_smem_bytes(int mode, const LineArgs& a);
+size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a);
 
 cudaError_t launch_zncc_row(int R, const RowArgs& a, int mode, int dtype, cudaStream_t st);
 cudaError_t launch_line_pair(const LineArgs& a, int mode, int dtype, cudaStream_t st);

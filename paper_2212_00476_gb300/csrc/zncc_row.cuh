@@ -29,7 +29,9 @@ namespace zncc {
 // shared-memory load per step serves all four, since column x'-d at step x' is column
 // (x'-1)-(d-1) of the previous step), and turns the running prefix of column sums into the
 // window sums P(x) = prefix(x+R) - prefix(x-R-1). The packed bands are staged once per
-// block and serve all of its disparity slices.
+// block and serve all of its disparity slices; the window statistics of both images
+// (Sec. IV-B-1, Eq. (sum1)) come from the same packed columns: a column's pixel sum is
+// __dp4a(word, 0x01010101) and its sum of squares __dp4a(word, word), slid like P.
 template <int R, typename T, int MODE>
 __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
     constexpr int l = 2 * R + 1;
@@ -52,13 +54,17 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
     const int NLP = span + 2 * R;                      // left columns x' in [-R, span+R)
     const int NRP = span + 2 * R + (blk_hi - blk_lo) - 1;
     const int xr0 = -R - (blk_hi - 1);                 // right columns x'' in [xr0, xr0+NRP)
-    const int pLP = plane_of(NLP), pRP = plane_of(NRP), pX = plane_of(span);
+    const int NSR = span + (blk_hi - blk_lo) - 1;      // right centres c in [c0, c0+NSR)
+    const int c0 = -(blk_hi - 1);
+    const int pLP = plane_of(NLP), pRP = plane_of(NRP), pX = plane_of(span), pSR = plane_of(NSR);
     uint4* LP = smem_u4;
     uint4* RP = LP + 4 * pLP;
-    float4* co = reinterpret_cast<float4*>(RP + 4 * pRP);           // HPair
+    int2* SL = reinterpret_cast<int2*>(RP + 4 * pRP);               // (S, 1/sigma bits) per x
+    int2* SR = SL + 4 * pX;                                          // per right centre
+    float4* co = reinterpret_cast<float4*>(SR + 4 * pSR);            // HPair
     float4* sb = co + 4 * pX;
     float* sa = reinterpret_cast<float*>(sb + 2 * nwl * tq);
-    float* rbv = reinterpret_cast<float*>(RP + 4 * pRP);             // Wta
+    float* rbv = reinterpret_cast<float*>(SR + 4 * pSR);             // Wta
     int* rbd = reinterpret_cast<int*>(rbv + 4 * pX);
 
     // ---- stage the packed bands (and the DT coefficients / the running best) ----
@@ -90,11 +96,42 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
     }
     __syncthreads();
 
-    const int x0 = k * kL;
+    // ---- window statistics: 16 consecutive centres per thread, left then right ----
     const unsigned n = (unsigned)(l * l);
-    const int WE = W + a.D - 1;
-    const int2* statR = a.statR + (size_t)y * WE + (a.D - 1);   // centre c at statR[c]
-    const int2* statL = a.statL + (size_t)y * W;
+    const int nrc = (NSR + kL - 1) / kL;
+    for (int t = tid; t < nch + nrc; t += blockDim.x) {
+        const bool is_left = t < nch;
+        const int cs = is_left ? t * kL : c0 + (t - nch) * kL;     // first centre
+        const uint4* col = is_left ? LP : RP;
+        const int pc = is_left ? pLP : pRP;
+        const int ib = is_left ? cs : cs - R - xr0;                 // column index of cs - R
+        int Sx[kL], Qx[kL];
+#pragma unroll
+        for (int i = 0; i < kL; ++i) Sx[i] = Qx[i] = 0;
+        unsigned ps = 0u, pq = 0u;
+#pragma unroll
+        for (int u = 0; u < kL + 2 * R; ++u) {
+            const uint4 w = col[p4(ib + u, pc)];
+            ps = __dp4a(w.x, 0x01010101u, ps);
+            pq = __dp4a(w.x, w.x, pq);
+            if (NW > 1) { ps = __dp4a(w.y, 0x01010101u, ps); pq = __dp4a(w.y, w.y, pq); }
+            if (NW > 2) { ps = __dp4a(w.z, 0x01010101u, ps); pq = __dp4a(w.z, w.z, pq); }
+            if (NW > 3) { ps = __dp4a(w.w, 0x01010101u, ps); pq = __dp4a(w.w, w.w, pq); }
+            if (u - 2 * R >= 0 && u - 2 * R < kL) { Sx[u - 2 * R] += (int)ps; Qx[u - 2 * R] += (int)pq; }
+            if (u + 1 < kL) { Sx[u + 1] -= (int)ps; Qx[u + 1] -= (int)pq; }
+        }
+#pragma unroll
+        for (int i = 0; i < kL; ++i) {
+            const int var = (int)(n * (unsigned)Qx[i] - (unsigned)Sx[i] * (unsigned)Sx[i]);
+            const float is = var > 0 ? 1.0f / sqrtf((float)var) : 0.0f;
+            const int2 st = make_int2(Sx[i], __float_as_int(is));
+            if (is_left) SL[p4(cs + i, pX)] = st;
+            else if (cs + i - c0 < NSR) SR[p4(cs + i - c0, pSR)] = st;
+        }
+    }
+    __syncthreads();
+
+    const int x0 = k * kL;
     T* out = reinterpret_cast<T*>(a.vol);
     const bool vec = a.vec != 0;
 
@@ -134,20 +171,17 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
         }
 
         // ---- normalization, Eq. (2); the target statistics slide like the columns ----
-        const int cb = x0 - d_first;                    // target centre of (i, j) is cb + i - j
-        auto stat_r = [&](int c) -> int2 {
-            return (c > -a.D && c < W) ? __ldg(statR + c) : make_int2(0, 0);
-        };
+        const int cb = x0 - d_first - c0;               // SR index of (i, j) is cb + i - j >= 3
         int2 sr[4];
-        sr[1] = stat_r(cb - 1);
-        sr[2] = stat_r(cb - 2);
-        sr[3] = stat_r(cb - 3);
+        sr[1] = SR[p4(cb - 1, pSR)];
+        sr[2] = SR[p4(cb - 2, pSR)];
+        sr[3] = SR[p4(cb - 3, pSR)];
         float v[kL][4];
 #pragma unroll
         for (int i = 0; i < kL; ++i) {
             const int x = x0 + i;
-            const int2 st = x < W ? __ldg(statL + x) : make_int2(0, 0);
-            sr[0] = stat_r(cb + i);
+            const int2 st = at4(SL, x0, i, pX);
+            sr[0] = SR[p4(cb + i, pSR)];
             const float isl = __int_as_float(st.y);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -211,6 +245,7 @@ inline size_t zncc_row_smem(int R, int mode, const RowArgs& a, int nthreads) {
     const int drange = std::min(a.spb, nslices) * ds;
     size_t b = 16ull * 4 * (plane_of(span + 2 * R) + plane_of(span + 2 * R + drange - 1));
     const int pX = plane_of(span);
+    b += 8ull * 4 * (pX + plane_of(span + drange - 1));
     if (mode == kModeHPair) b += 16ull * 4 * pX + dt_scan_bytes(nthreads / 32, a.tq);
     if (mode == kModeWta) b += 8ull * 4 * pX;
     return b;

@@ -223,6 +223,18 @@ def test_fused_run_matches_oracle(h, w, d, win, iters):
     check_disp(got, ref, gap, scale, f"zncc_run {h}x{w} D={d} win={win} iters={iters}")
 
 
+def test_wide_image_splits_wta_launches():
+    """A row too wide for one block to hold every disparity band: the cost + WTA kernel splits
+    the disparity range into launches chained through a running best."""
+    h, w, d, win = 4, 4000, 1024, 3
+    p = rand_pair(h, w, d, seed=3)
+    ctx = Z.ZnccContext(w, h, d, win)
+    disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, 0)
+    ref, gap = oracle.run(p.left, p.right, d, win // 2, SIG_S, SIG_R, 0)
+    check_disp(host_u16(disp), ref, gap, 1.0, "wide WTA split")
+
+
 def test_unfused_chain_equals_oracle_and_fused():
     """cost volume -> dt_aggregate -> wta_disparity gives the oracle's map, like zncc_run."""
     h, w, d, win, iters = 48, 160, 32, 9, 3
