@@ -24,8 +24,8 @@
  *    zncc_last_error(). A context is not thread-safe: use one per host thread or stream.
  *  - Window side `win` = 2r+1 must be odd and in [3, 15]. Window sums are exact in int32
  *    (the largest, n*Q - S^2, stays below 2^31 for every allowed window).
- *  - W and H must be in [1, 4096] (a DT line is processed inside one thread block), D in
- *    [1, 1024].
+ *  - W must be in [1, 3072] and H in [1, 4096] (a DT line is processed inside one thread
+ *    block, and a row's image band inside one block's shared memory); D in [1, 1024].
  */
 #ifndef ZNCC_H_
 #define ZNCC_H_

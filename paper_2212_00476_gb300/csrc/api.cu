@@ -34,6 +34,12 @@ struct ProfRecord {
     int kind, ev0, ev1;
 };
 
+// Launch shape of one kind of line pass, chosen once per context and pass signature.
+struct LinePlan {
+    long long key;
+    int tq, lpc, nch, async, per_block, blocks;
+};
+
 constexpr int kTargetBlocks = 1216;   // about eight blocks per SM on a 152-SM GB300
 
 }  // namespace
@@ -49,7 +55,11 @@ struct zncc_ctx {
     size_t vol_bytes = 0;
     float* bestv = nullptr;       // [H][W] running WTA best across launches (on first use)
     int* bestd = nullptr;         // [H][W]
+    float* ahat = nullptr;        // [nahat][H][W] DT responses of an all-ones plane (F16 storage)
+    int nahat = 0;
     int smem_max = 0;             // opt-in shared memory per block of the device
+    int num_sms = 0;
+    std::vector<LinePlan> plans;  // line-pass launch shapes, by pass signature
     uint8_t* img = nullptr;       // device copies for zncc_run_host: 2 x [H][W]
     uint16_t* disp = nullptr;     // [H][W]
     bool profiling = false;
@@ -227,51 +237,137 @@ zncc_status run_rows(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int
     return ZNCC_OK;
 }
 
-// One DT pair along rows (horiz) or columns of a [H][W][dstride] volume. The block shape is
-// the widest lane count per chunk whose block fits, streaming the next slices through shared
-// memory (async) where that fits too.
-zncc_status run_line_pair(zncc_ctx* c, void* vol, int dtype, long long dstride, bool horiz, float s2,
-                          int mode, uint16_t* disp) {
-    LineArgs a;
-    memset(&a, 0, sizeof(a));
-    const int n = horiz ? c->W : c->H;
-    a.vol = vol;
-    a.elem_stride = horiz ? dstride : (long long)c->W * dstride;
-    a.line_stride = horiz ? (long long)c->W * dstride : dstride;
-    a.n = n;
-    a.nlines = horiz ? c->H : c->W;
-    a.dcount = c->D;
-    a.d_base = 0;
-    a.coef = horiz ? c->coefH : c->coefV;
-    a.coef_line_stride = horiz ? c->W : c->H;
-    a.s2 = s2;
-    a.vec = (dstride % 4 == 0) && ((uintptr_t)vol % (dtype == 0 ? 16 : 8) == 0) ? 1 : 0;
-    a.wta.disp = disp;
-    a.wta.first = 1;
-    a.wta.last = 1;
-    a.pix_line = horiz ? c->W : 1;
-    a.pix_pos = horiz ? 1 : c->W;
-    bool found = false;
-    for (int pass = 0; pass < 2 && !found; ++pass) {          // with, then without, async
-        for (int tq = 8; tq >= 2 && !found; tq >>= 1) {
-            a.tq = tq;
-            a.nch = padded_chunks(n, tq);
-            const int per_line = a.nch * tq;
-            if (per_line > 512) continue;
-            a.async = pass == 0 ? a.vec : 0;
-            if (pass == 0 && !a.vec) continue;
-            for (a.lpc = std::max(1, std::min(8, 256 / per_line)); a.lpc >= 1; --a.lpc)
-                if (line_pair_smem_bytes(mode, dtype, a) <= (size_t)c->smem_max) {
-                    found = true;
-                    break;
+// One DT pass pair along rows (horiz) or columns of a [H][W][dstride] volume.
+struct LinePass {
+    void* vol = nullptr;           // output (and input unless src / ones)
+    const void* src = nullptr;
+    bool ones = false;
+    long long dstride = 0;
+    int dcount = 0;
+    int dtype = 0;
+    bool horiz = true;
+    int mode = kLineStore;
+    const float* ahat_in = nullptr;
+    const float* ahat_out = nullptr;
+    uint16_t* disp = nullptr;
+    float s2 = 1.0f;
+    int force_tq = 0;
+};
+
+// The launch shape: among lane counts per chunk (8, 4, 2, or the forced one) and lines per
+// block that fit in shared memory, prefer streaming through shared memory (async), then at
+// least two resident blocks per SM, then the most resident warps. The grid is the resident
+// blocks (persistent), each taking an equal run of items.
+zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
+    const long long key = ((((long long)p.horiz * 2 + p.mode) * 2 + p.dtype) * 2 + (a.vec ? 1 : 0)) * 16 +
+                          p.force_tq + ((long long)p.dcount << 20);
+    for (const LinePlan& pl : c->plans)
+        if (pl.key == key) {
+            a.tq = pl.tq; a.lpc = pl.lpc; a.nch = pl.nch; a.async = pl.async; a.per_block = pl.per_block;
+            return ZNCC_OK;
+        }
+    LinePlan best{key, 0, 0, 0, 0, 0, 0};
+    long long best_score = -1;
+    const int tqs[4] = {8, 4, 2, 1};
+    for (int ti = 0; ti < 4; ++ti) {
+        const int tq = tqs[ti];
+        if (p.force_tq ? tq != p.force_tq : tq == 1) continue;
+        const int nch = padded_chunks(a.n, tq);
+        const int per_line = nch * tq;
+        if (per_line > 512) continue;
+        for (int async = a.vec ? 1 : 0; async >= 0; --async) {
+            for (int lpc = std::max(1, std::min(8, 256 / per_line)); lpc >= 1; --lpc) {
+                a.tq = tq; a.nch = nch; a.lpc = lpc; a.async = async;
+                if (line_pair_smem_bytes(p.mode, p.dtype, a) > (size_t)c->smem_max) continue;
+                int bps = 0;
+                ZNCC_CUDA(c, line_pair_occupancy(a, p.mode, p.dtype, &bps), "occupancy query");
+                if (bps < 1) continue;
+                const long long warps = (long long)bps * lpc * per_line / 32;
+                const long long score = async * 1000000LL + (bps >= 2 ? 100000LL : 0) + warps * 100 + tq;
+                if (score > best_score) {
+                    best_score = score;
+                    best.tq = tq; best.lpc = lpc; best.nch = nch; best.async = async; best.blocks = bps;
                 }
+                break;                      // fewer lines per block only when this did not fit
+            }
         }
     }
-    if (!found) return fail(c, ZNCC_EUNSUPPORTED, "line too long for the DT kernel's shared memory");
-    const int nslices = (c->D + kG * a.tq - 1) / (kG * a.tq);
-    a.spb = mode == kLineWta ? nslices : slices_per_block(nslices, (a.nlines + a.lpc - 1) / a.lpc);
-    const int kind = horiz ? K_DT_HPAIR : (mode == kLineWta ? K_DT_VPAIR_WTA : K_DT_VPAIR);
-    ZNCC_LAUNCH(c, kind, launch_line_pair(a, mode, dtype, c->stream), horiz ? "DT horizontal pair" : "DT vertical pair");
+    if (best_score < 0) return fail(c, ZNCC_EUNSUPPORTED, "line too long for the DT kernel's shared memory");
+    a.tq = best.tq; a.lpc = best.lpc; a.nch = best.nch; a.async = best.async;
+    const int nslices = (p.dcount + kG * a.tq - 1) / (kG * a.tq);
+    const int ngroups = (a.nlines + a.lpc - 1) / a.lpc;
+    const int grid_max = std::max(1, c->num_sms * best.blocks);
+    if (p.mode == kLineWta) {
+        const int gpb = (ngroups + grid_max - 1) / grid_max;
+        a.per_block = gpb * nslices;
+    } else {
+        const int total = ngroups * nslices;
+        a.per_block = (total + grid_max - 1) / grid_max;
+    }
+    best.per_block = a.per_block;
+    c->plans.push_back(best);
+    return ZNCC_OK;
+}
+
+zncc_status run_line_pair(zncc_ctx* c, const LinePass& p) {
+    LineArgs a;
+    memset(&a, 0, sizeof(a));
+    const int n = p.horiz ? c->W : c->H;
+    a.vol = p.vol;
+    a.src = p.src;
+    a.src_ones = p.ones ? 1 : 0;
+    a.elem_stride = p.horiz ? p.dstride : (long long)c->W * p.dstride;
+    a.line_stride = p.horiz ? (long long)c->W * p.dstride : p.dstride;
+    a.n = n;
+    a.nlines = p.horiz ? c->H : c->W;
+    a.dcount = p.dcount;
+    a.d_base = 0;
+    a.ahat_in = p.ahat_in;
+    a.ahat_out = p.ahat_out;
+    a.coef = p.horiz ? c->coefH : c->coefV;
+    a.coef_line_stride = p.horiz ? c->W : c->H;
+    a.s2 = p.s2;
+    const void* in = p.src ? p.src : p.vol;
+    a.vec = (p.dstride % 4 == 0) && ((uintptr_t)p.vol % (p.dtype == 0 ? 16 : 8) == 0) &&
+                    ((uintptr_t)in % (p.dtype == 0 ? 16 : 8) == 0) ? 1 : 0;
+    a.wta.disp = p.disp;
+    a.wta.first = 1;
+    a.wta.last = 1;
+    a.pix_line = p.horiz ? c->W : 1;
+    a.pix_pos = p.horiz ? 1 : c->W;
+    ZNCC_TRY(plan_line_pass(c, a, p));
+    const int kind = p.horiz ? K_DT_HPAIR : (p.mode == kLineWta ? K_DT_VPAIR_WTA : K_DT_VPAIR);
+    ZNCC_LAUNCH(c, kind, launch_line_pair(a, p.mode, p.dtype, c->stream), p.horiz ? "DT horizontal pair" : "DT vertical pair");
+    return ZNCC_OK;
+}
+
+// The scaled DT responses of an all-ones plane after pairs 1 .. n (A_hat, Eqs. (3)-(6) on a
+// constant input), one [H][W] map each: the per-pixel bound of |aggregated cost|.
+zncc_status run_ahat_chain(zncc_ctx* c, int n, float s2) {
+    const size_t npix = (size_t)c->W * c->H;
+    if (c->nahat < n) {
+        free_dev_f(c->ahat);
+        c->nahat = 0;
+        cudaError_t e = cudaMalloc(&c->ahat, npix * n * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, ZNCC_ENOMEM, std::string("A_hat maps: ") + cudaGetErrorString(e));
+        }
+        c->nahat = n;
+    }
+    for (int p = 1; p <= n; ++p) {
+        LinePass lp;
+        lp.vol = c->ahat + (size_t)(p - 1) * npix;
+        lp.src = p == 1 ? nullptr : c->ahat + (size_t)(p - 2) * npix;
+        lp.ones = p == 1;
+        lp.dstride = 1;
+        lp.dcount = 1;
+        lp.dtype = 0;
+        lp.horiz = (p % 2) == 1;
+        lp.s2 = s2;
+        lp.force_tq = 1;
+        ZNCC_TRY(run_line_pair(c, lp));
+    }
     return ZNCC_OK;
 }
 
@@ -287,6 +383,9 @@ void release(zncc_ctx* c) {
     free_dev(c->vol);
     free_dev(c->bestv);
     free_dev(c->bestd);
+    free_dev(c->ahat);
+    c->nahat = 0;
+    c->plans.clear();
     free_dev(c->img);
     free_dev(c->disp);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -304,8 +403,8 @@ zncc_status zncc_create(int width, int height, int max_disp, int win, zncc_ctx**
     if (!out) return fail(nullptr, ZNCC_EINVAL, "out is NULL");
     *out = nullptr;
     if (width < 1 || height < 1) return fail(nullptr, ZNCC_EINVAL, "width and height must be >= 1");
-    if (width > 4096 || height > 4096)
-        return fail(nullptr, ZNCC_EUNSUPPORTED, "width and height must be <= 4096");
+    if (width > 3072 || height > 4096)
+        return fail(nullptr, ZNCC_EUNSUPPORTED, "width must be <= 3072 and height <= 4096");
     if (max_disp < 1) return fail(nullptr, ZNCC_EINVAL, "max_disp must be >= 1");
     if (max_disp > 1024) return fail(nullptr, ZNCC_EUNSUPPORTED, "max_disp must be <= 1024");
     if (win < 3 || win > 15 || win % 2 == 0)
@@ -319,6 +418,7 @@ zncc_status zncc_create(int width, int height, int max_disp, int win, zncc_ctx**
     c->r = win / 2;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     const size_t npix = (size_t)width * height;
     if (e == cudaSuccess) e = cudaMalloc(&c->coefH, npix * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&c->coefV, npix * sizeof(float4));
@@ -387,9 +487,17 @@ zncc_status dt_aggregate(zncc_ctx* c, const uint8_t* guide, int pitch, void* cos
     if (iters == 0) return ZNCC_OK;
     ZNCC_TRY(run_coef(c, guide, pitch, sigma_s, sigma_r));
     const float s2 = scale_s2(sigma_s);
+    LinePass lp;
+    lp.vol = cost;
+    lp.dstride = c->D;
+    lp.dcount = c->D;
+    lp.dtype = dtype;
+    lp.s2 = s2;
     for (int it = 0; it < iters; ++it) {
-        ZNCC_TRY(run_line_pair(c, cost, dtype, c->D, true, s2, kLineStore, nullptr));
-        ZNCC_TRY(run_line_pair(c, cost, dtype, c->D, false, s2, kLineStore, nullptr));
+        lp.horiz = true;
+        ZNCC_TRY(run_line_pair(c, lp));
+        lp.horiz = false;
+        ZNCC_TRY(run_line_pair(c, lp));
     }
     return ZNCC_OK;
 }
@@ -432,10 +540,26 @@ zncc_status zncc_run(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int
     const float s2 = scale_s2(sigma_s);
     ZNCC_TRY(run_rows(c, left, right, pitch, kModeHPair, dt, c->vol, dstride, s2, nullptr, K_ZNCC_HPAIR,
                       "ZNCC + horizontal DT pair"));
-    for (int it = 0; it < iters; ++it) {
-        const bool last = it == iters - 1;
-        ZNCC_TRY(run_line_pair(c, c->vol, dt, dstride, false, s2, last ? kLineWta : kLineStore, disp));
-        if (!last) ZNCC_TRY(run_line_pair(c, c->vol, dt, dstride, true, s2, kLineStore, nullptr));
+    // Half storage keeps each stored pair p >= 2 divided by A_hat_p (the per-pixel bound of
+    // |cost|), so that it stays inside the half range wherever the guide isolates a pixel;
+    // the next pair multiplies it back. The factor is the same for every d of a pixel.
+    const bool norm = dt == 1;
+    const int npairs = 2 * iters;
+    const size_t ahat_sz = npix;
+    if (norm && npairs > 2) ZNCC_TRY(run_ahat_chain(c, npairs - 1, s2));
+    LinePass lp;
+    lp.vol = c->vol;
+    lp.dstride = dstride;
+    lp.dcount = c->D;
+    lp.dtype = dt;
+    lp.s2 = s2;
+    for (int pair = 2; pair <= npairs; ++pair) {    // pair 1 is the cost kernel's
+        lp.horiz = (pair % 2) == 1;
+        lp.mode = pair == npairs ? kLineWta : kLineStore;
+        lp.disp = pair == npairs ? disp : nullptr;
+        lp.ahat_in = norm && pair - 1 >= 2 ? c->ahat + (size_t)(pair - 2) * ahat_sz : nullptr;
+        lp.ahat_out = norm && pair < npairs ? c->ahat + (size_t)(pair - 1) * ahat_sz : nullptr;
+        ZNCC_TRY(run_line_pair(c, lp));
     }
     return ZNCC_OK;
 }

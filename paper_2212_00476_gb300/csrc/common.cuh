@@ -114,23 +114,6 @@ __device__ __forceinline__ void lds4(const __half* p, float (&o)[4]) {
 
 // ---- WTA (Eq. (WTA1)): the largest cost wins, ties go to the smallest d ----------------
 
-// Best (value, d) over this thread's 4 disparities and the tq lanes sharing the pixel
-// (consecutive lanes of one warp); every lane of the group ends with the group's best.
-// All lanes of the warp must call this together.
-__device__ __forceinline__ void wta_group(const float (&c)[4], int nvalid, int d_first, int tq,
-                                          float& best, int& bd) {
-    best = -INFINITY;
-    bd = 0x7FFFFFFF;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (j < nvalid && c[j] > best) { best = c[j]; bd = d_first + j; }
-    for (int off = 1; off < tq; off <<= 1) {
-        const float ob = __shfl_xor_sync(kFull, best, off);
-        const int od = __shfl_xor_sync(kFull, bd, off);
-        if (ob > best || (ob == best && od < bd)) { best = ob; bd = od; }
-    }
-}
-
 // ---- DT line pair: forward then backward recursive pass along a line ------------------
 //
 // A line (a row for the horizontal pair, a column for the vertical pair) is split into
@@ -151,10 +134,12 @@ __device__ __forceinline__ void wta_group(const float (&c)[4], int nvalid, int d
 //
 // co: the line's coefficients in shared memory (cidx layout); sa/sb: the line's scan
 // buffers, 2 * nwl * tq entries each; wl / nwl: this thread's warp within the line and the
-// warps per line. Synchronizes the block twice.
+// warps per line. The result is scaled by s2 = (1-K)^2, or per position by mul[p].y when
+// mul (cidx layout) is given. Synchronizes the block twice.
 __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restrict__ co,
                                         int plane, int k, int tq, int dq, int lane, int wl,
-                                        int nwl, float* sa, float4* sb, float s2) {
+                                        int nwl, float* sa, float4* sb, float s2,
+                                        const float2* __restrict__ mul = nullptr) {
     const int start = k * kL;
     // forward sweep of the chunk, zero carry-in
     float u[4] = {0.f, 0.f, 0.f, 0.f};
@@ -257,12 +242,37 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
 #pragma unroll
     for (int j = 0; j < 4; ++j) G[j] = fmaf(Ae, G[j], Be[j]);
 
-    // backward correction and the s^2 of the scaled form
+    // backward correction and the s^2 of the scaled form (or the per-position multiplier)
 #pragma unroll
     for (int i = 0; i < kL; ++i) {
         const float b = co[cidx(start + i, plane)].w;
+        const float m = mul ? mul[cidx(start + i, plane)].y : s2;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[i][j] = s2 * fmaf(b, G[j], v[i][j]);
+        for (int j = 0; j < 4; ++j) v[i][j] = m * fmaf(b, G[j], v[i][j]);
+    }
+}
+
+// ---- per-thread WTA running best over the slices a block visits -------------------------
+// Entry (i, k, dq) of a line's [kL][nch][tq] array of (value, d) pairs belongs to one thread;
+// a slice folds the thread's 4 disparities into it without any cross-lane traffic, and the
+// lanes of a pixel are reduced once, after the last slice.
+__device__ __forceinline__ void wta_fold_own(float2* rb, const float (&c)[4], int nvalid, int d_first) {
+    float best = rb->x;
+    int bd = __float_as_int(rb->y);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (j < nvalid && c[j] > best) { best = c[j]; bd = d_first + j; }
+    *rb = make_float2(best, __int_as_float(bd));
+}
+
+// Reduces the tq lanes of a pixel (consecutive lanes of a warp); all lanes get the result.
+__device__ __forceinline__ void wta_reduce_lanes(float2 e, int tq, float& best, int& bd) {
+    best = e.x;
+    bd = __float_as_int(e.y);
+    for (int off = 1; off < tq; off <<= 1) {
+        const float ob = __shfl_xor_sync(kFull, best, off);
+        const int od = __shfl_xor_sync(kFull, bd, off);
+        if (ob > best || (ob == best && od < bd)) { best = ob; bd = od; }
     }
 }
 

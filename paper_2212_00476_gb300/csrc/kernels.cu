@@ -111,15 +111,25 @@ cudaError_t launch_dt_coef(const uint8_t* guide, int pitch, int W, int H, float 
 
 // ---------------------------------------------------------------------------------------
 // DT line pair (Sec. III-B, Eqs. (3)-(6)): the forward and the backward recursive pass
-// along rows (L2R then R2L) or columns (U2D then D2U) of a cost volume, in place, or, for
-// the last pair of the chain, folded into a per-pixel running best without writing the
-// volume back (Sec. V-C fuses WTA with D2U in the same way). Block = lpc lines x a run of
-// spb disparity slices (4*tq disparities each); the lines' coefficients are staged once.
-// With aligned 4-disparity groups (vec) each thread streams its elements of the next two
-// slices into shared memory with cp.async while the current slice is being computed.
+// along rows (L2R then R2L) or columns (U2D then D2U) of a cost volume, or, for the last
+// pair of the chain, folded into a per-pixel running best without writing the volume back
+// (Sec. V-C fuses WTA with D2U in the same way).
+//
+// Work: lines in groups of lpc, each group with nslices disparity slices of 4*tq
+// disparities; an item is (group, slice), numbered group-major. The grid is sized to the
+// resident blocks (persistent); block b processes the items [b*per_block, (b+1)*per_block)
+// in order, restaging the coefficients when the group changes. With aligned 4-disparity
+// groups (async) each thread streams its elements of the next two items into shared memory
+// with cp.async while the current one is computed, across group boundaries. In Wta mode
+// per_block is a multiple of nslices: a block sees every disparity of its lines.
 template <typename T>
 __host__ __device__ inline size_t line_stage_bytes(const LineArgs& a) {
     return a.async ? 2ull * a.lpc * kL * a.nch * a.tq * (4 * sizeof(T)) : 0;
+}
+
+int line_pair_items(const LineArgs& a) {
+    const int nslices = (a.dcount + kG * a.tq - 1) / (kG * a.tq);
+    return ((a.nlines + a.lpc - 1) / a.lpc) * nslices;
 }
 
 template <typename T, int MODE>
@@ -131,84 +141,99 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
     const int tl = threadIdx.x - li * per_line;
     const int k = tl / tq, dq = tl - k * tq;
     const int lane = threadIdx.x & 31, wl = tl >> 5;
-    const int line0 = blockIdx.x * a.lpc;
-    const int line = line0 + li;
-    const bool line_ok = line < a.nlines;
     const int pX = plane_of(span);
 
     T* stage = reinterpret_cast<T*>(smem4);                           // [2][lpc][kL][per_line] x 4
     float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + line_stage_bytes<T>(a));
-    float4* sb_all = co_all + a.lpc * 4 * pX;                          // [lpc][2 nwl tq]
+    float2* mul_all = reinterpret_cast<float2*>(co_all + a.lpc * 4 * pX);   // [lpc][4 pX]
+    float4* sb_all = reinterpret_cast<float4*>(mul_all + a.lpc * 4 * pX);   // [lpc][2 nwl tq]
     float* sa_all = reinterpret_cast<float*>(sb_all + a.lpc * 2 * nwl * tq);
-    float* rbv_all = sa_all + a.lpc * 2 * nwl * tq;                    // [lpc][4 pX] (Wta)
-    int* rbd_all = reinterpret_cast<int*>(rbv_all + a.lpc * 4 * pX);
+    float2* rb_all = reinterpret_cast<float2*>(sa_all + a.lpc * 2 * nwl * tq);   // [lpc][kL][nch][tq] (Wta)
     const float4* co = co_all + li * 4 * pX;
+    const float2* mul = mul_all + li * 4 * pX;
     float4* sb = sb_all + li * 2 * nwl * tq;
     float* sa = sa_all + li * 2 * nwl * tq;
-    float* rbv = rbv_all + li * 4 * pX;
-    int* rbd = rbd_all + li * 4 * pX;
+    float2* rb = rb_all + (size_t)li * kL * per_line + tl;             // entry (i) at rb[i * per_line]
 
     const int nslices = (a.dcount + ds - 1) / ds;
-    const int s_begin = blockIdx.y * a.spb;
-    const int s_end = min(nslices, s_begin + a.spb);
+    const int total = ((a.nlines + a.lpc - 1) / a.lpc) * nslices;
+    const int it0 = blockIdx.x * a.per_block;
+    const int it1 = min(total, it0 + a.per_block);
     T* vol = reinterpret_cast<T*>(a.vol);
-    const bool vec = a.vec != 0;
-    const bool async = a.async != 0;
+    const T* src = a.src ? reinterpret_cast<const T*>(a.src) : vol;
+    const bool vec = a.vec != 0, async = a.async != 0, ones = a.src_ones != 0;
+    const bool scaled_in = a.ahat_in != nullptr;
     const int npos = a.n - k * kL;                                     // positions of this chunk
-    // the chunk's first element group of slice sl
-    auto chunk_base = [&](int sl) -> T* {
-        return vol + (size_t)(line_ok ? line : 0) * a.line_stride + (size_t)(k * kL) * a.elem_stride + sl * ds + dq * kG;
+    auto elem0 = [&](int line, int sl) -> size_t {                   // the chunk's first group
+        return (size_t)line * a.line_stride + (size_t)(k * kL) * a.elem_stride + sl * ds + dq * kG;
     };
     auto stage_at = [&](int buf, int i) -> T* {
         return stage + ((size_t)((buf * a.lpc + li) * kL + i) * per_line + tl) * 4;
     };
-    // prefetch of slice sl into stage buffer buf. With vec the entries per pixel are a
+    // prefetch of item `it` into stage buffer buf. With vec the entries per pixel are a
     // multiple of 4, so a group with any valid disparity lies whole inside the volume; its
     // entries past dcount are never stored or compared.
-    auto prefetch = [&](int sl, int buf) {
-        if (sl < s_end) {
-            const bool ok = line_ok && sl * ds + dq * kG < a.dcount;
-            const T* src = chunk_base(sl);
+    auto prefetch = [&](int it, int buf) {
+        if (it < it1) {
+            const int g = it / nslices, sl = it - g * nslices;
+            const int line = g * a.lpc + li;
+            const bool ok = line < a.nlines && sl * ds + dq * kG < a.dcount;
+            const T* p = src + (ok ? elem0(line, sl) : 0);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 const bool valid = ok && i < npos;
-                cp_async<4 * sizeof(T)>(stage_at(buf, i), valid ? src + (size_t)i * a.elem_stride : vol, valid);
+                cp_async<4 * sizeof(T)>(stage_at(buf, i), valid ? p + (size_t)i * a.elem_stride : src, valid);
             }
         }
         cp_async_commit();
     };
     if (async) {
-        prefetch(s_begin, 0);
-        prefetch(s_begin + 1, 1);
+        prefetch(it0, 0);
+        prefetch(it0 + 1, 1);
     }
 
-    for (int l2 = 0; l2 < a.lpc; ++l2) {
-        const int ln = line0 + l2;
-        const bool ok = ln < a.nlines;
-        for (int t = threadIdx.x; t < span; t += blockDim.x) {
-            co_all[l2 * 4 * pX + cidx(t, pX)] =
-                ok && t < a.n ? __ldg(a.coef + (size_t)ln * a.coef_line_stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if constexpr (MODE == kLineWta) {
-                const bool in = ok && t < a.n && !a.wta.first;
-                const size_t pix = (size_t)ln * a.pix_line + (size_t)t * a.pix_pos;
-                rbv_all[l2 * 4 * pX + p4(t, pX)] = in ? a.wta.bestv[pix] : -INFINITY;
-                rbd_all[l2 * 4 * pX + p4(t, pX)] = in ? a.wta.bestd[pix] : 0;
+    int cur_group = -1;
+    for (int it = it0, n_it = 0; it < it1; ++it, ++n_it) {
+        const int g = it / nslices, sl = it - g * nslices;
+        const int line = g * a.lpc + li;
+        const bool line_ok = line < a.nlines;
+        if (g != cur_group) {          // stage the coefficients and multipliers of group g
+            __syncthreads();
+            for (int l2 = 0; l2 < a.lpc; ++l2) {
+                const int ln = g * a.lpc + l2;
+                const bool ok = ln < a.nlines;
+                for (int t = threadIdx.x; t < span; t += blockDim.x) {
+                    const bool in = ok && t < a.n;
+                    co_all[l2 * 4 * pX + cidx(t, pX)] =
+                        in ? __ldg(a.coef + (size_t)ln * a.coef_line_stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const size_t pix = (size_t)ln * a.pix_line + (size_t)t * a.pix_pos;
+                    const float mi = in && a.ahat_in ? __ldg(a.ahat_in + pix) : 1.0f;
+                    const float mo = in && a.ahat_out ? a.s2 / __ldg(a.ahat_out + pix) : a.s2;
+                    mul_all[l2 * 4 * pX + cidx(t, pX)] = make_float2(mi, mo);
+                }
             }
+            if constexpr (MODE == kLineWta) {
+#pragma unroll
+                for (int i = 0; i < kL; ++i) rb[i * per_line] = make_float2(-INFINITY, __int_as_float(0x7FFFFFFF));
+            }
+            __syncthreads();
+            cur_group = g;
         }
-    }
-    __syncthreads();
-
-    for (int sl = s_begin, it = 0; sl < s_end; ++sl, ++it) {
         const int dl = sl * ds + dq * kG;                              // entry of d_first
         const int nvalid = max(0, min(4, a.dcount - dl));
         const bool any = line_ok && nvalid > 0;
         float v[kL][4];
-        if (async) {
-            cp_async_wait<1>();                                        // this slice's copies landed
+        if (ones) {
 #pragma unroll
-            for (int i = 0; i < kL; ++i) lds4(stage_at(it & 1, i), v[i]);
+            for (int i = 0; i < kL; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[i][j] = (any && i < npos && j < nvalid) ? 1.0f : 0.0f;
+        } else if (async) {
+            cp_async_wait<1>();                                        // this item's copies landed
+#pragma unroll
+            for (int i = 0; i < kL; ++i) lds4(stage_at(n_it & 1, i), v[i]);
         } else {
-            const T* q = chunk_base(sl);
+            const T* q = src + (line_ok ? elem0(line, sl) : 0);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 if (any && i < npos) ld4(q, nvalid, vec, v[i]);
@@ -216,23 +241,43 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
                 q += a.elem_stride;
             }
         }
-        dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2);
-        // the stage buffer was consumed by the sweeps above: refill it with slice sl + 2
-        if (async) prefetch(sl + 2, it & 1);
-        if constexpr (MODE == kLineWta) {
+        if (scaled_in) {
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
-                float best;
-                int bd;
-                wta_group(v[i], nvalid, a.d_base + dl, tq, best, bd);
-                const int pos = k * kL + i;
-                if (dq == 0 && pos < a.n && best > rbv[p4(pos, pX)]) {
-                    rbv[p4(pos, pX)] = best;
-                    rbd[p4(pos, pX)] = bd;
+                const float m = mul[cidx(k * kL + i, pX)].x;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[i][j] *= m;
+            }
+        }
+        dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2, mul);
+        // the stage buffer was consumed by the sweeps above: refill it two items ahead
+        if (async) prefetch(it + 2, n_it & 1);
+        if constexpr (MODE == kLineWta) {
+#pragma unroll
+            for (int i = 0; i < kL; ++i) wta_fold_own(rb + i * per_line, v[i], nvalid, a.d_base + dl);
+            if (sl == nslices - 1) {                                   // the group's last slice
+#pragma unroll
+                for (int i = 0; i < kL; ++i) {
+                    float best;
+                    int bd;
+                    wta_reduce_lanes(rb[i * per_line], tq, best, bd);
+                    const int pos = k * kL + i;
+                    if (dq == 0 && line_ok && pos < a.n) {
+                        const size_t pix = (size_t)line * a.pix_line + (size_t)pos * a.pix_pos;
+                        if (!a.wta.first) {                            // earlier launches: smaller d
+                            const float pb = a.wta.bestv[pix];
+                            if (!(best > pb)) { best = pb; bd = a.wta.bestd[pix]; }
+                        }
+                        if (a.wta.last) a.wta.disp[pix] = (uint16_t)bd;
+                        else {
+                            a.wta.bestv[pix] = best;
+                            a.wta.bestd[pix] = bd;
+                        }
+                    }
                 }
             }
         } else {
-            T* q = chunk_base(sl);
+            T* q = vol + (line_ok ? elem0(line, sl) : 0);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 if (any && i < npos) st4(q, nvalid, vec, v[i]);
@@ -241,41 +286,36 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
         }
     }
     if (async) cp_async_wait<0>();
-    if constexpr (MODE == kLineWta) {
-        if (dq == 0 && line_ok) {
-#pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                const int pos = k * kL + i;
-                if (pos >= a.n) break;
-                const size_t pix = (size_t)line * a.pix_line + (size_t)pos * a.pix_pos;
-                if (a.wta.last) a.wta.disp[pix] = (uint16_t)rbd[p4(pos, pX)];
-                else {
-                    a.wta.bestv[pix] = rbv[p4(pos, pX)];
-                    a.wta.bestd[pix] = rbd[p4(pos, pX)];
-                }
-            }
-        }
-    }
 }
 
 size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a) {
     const int pX = plane_of(a.nch * kL);
     const int nwl = a.nch * a.tq / 32;
     size_t b = dtype == 0 ? line_stage_bytes<float>(a) : line_stage_bytes<__half>(a);
-    b += (size_t)a.lpc * (16ull * 4 * pX + dt_scan_bytes(nwl, a.tq));
-    if (mode == kLineWta) b += (size_t)a.lpc * 8 * 4 * pX;
+    b += (size_t)a.lpc * ((16ull + 8ull) * 4 * pX + dt_scan_bytes(nwl, a.tq));
+    if (mode == kLineWta) b += (size_t)a.lpc * 8ull * kL * a.nch * a.tq;
     return b;
 }
 
+static void (*line_pair_fn(int mode, int dtype))(LineArgs) {
+    if (mode == kLineStore) return dtype == 0 ? k_line_pair<float, kLineStore> : k_line_pair<__half, kLineStore>;
+    return dtype == 0 ? k_line_pair<float, kLineWta> : k_line_pair<__half, kLineWta>;
+}
+
+cudaError_t line_pair_occupancy(const LineArgs& a, int mode, int dtype, int* blocks_per_sm) {
+    void (*fn)(LineArgs) = line_pair_fn(mode, dtype);
+    const size_t smem = line_pair_smem_bytes(mode, dtype, a);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, a.lpc * a.nch * a.tq, smem);
+}
+
 cudaError_t launch_line_pair(const LineArgs& a, int mode, int dtype, cudaStream_t st) {
-    const int ds = kG * a.tq;
-    const int nslices = (a.dcount + ds - 1) / ds;
-    dim3 grid((a.nlines + a.lpc - 1) / a.lpc, (nslices + a.spb - 1) / a.spb);
+    const int total = line_pair_items(a);
+    dim3 grid((total + a.per_block - 1) / a.per_block);
     dim3 block(a.lpc * a.nch * a.tq);
     const size_t smem = line_pair_smem_bytes(mode, dtype, a);
-    void (*fn)(LineArgs) = nullptr;
-    if (mode == kLineStore) fn = dtype == 0 ? k_line_pair<float, kLineStore> : k_line_pair<__half, kLineStore>;
-    else fn = dtype == 0 ? k_line_pair<float, kLineWta> : k_line_pair<__half, kLineWta>;
+    void (*fn)(LineArgs) = line_pair_fn(mode, dtype);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, block, smem, st>>>(a);

@@ -35,20 +35,25 @@ struct RowArgs {
 };
 
 struct LineArgs {
-    void* vol;                // float or half cost volume
+    void* vol;                // float or half cost volume (output, and input unless src is set)
+    const void* src;          // input volume with the layout of vol (NULL: vol itself)
+    int src_ones;             // the input is 1 at every element (src and vol are not read)
     long long elem_stride;    // entries between consecutive positions of a line
     long long line_stride;    // entries between consecutive lines
     int n, nlines;            // line length, number of lines
     int dcount;               // valid disparity entries per pixel
     int d_base;               // disparity of entry 0 (WTA)
-    int tq, lpc, nch, spb;    // lanes per chunk, lines per block, chunks per line, slices per block
+    int tq, lpc, nch;         // lanes per chunk, lines per block, chunks per line
+    int per_block;            // work items (line group, disparity slice) per block
+    const float* ahat_in;     // per-pixel multiplier of the input (NULL: 1)
+    const float* ahat_out;    // per-pixel divisor of the output (NULL: 1)
     const float4* coef;       // coefficients: coef[line * coef_line_stride + pos]
     long long coef_line_stride;
     float s2;
     int vec;                  // 16-byte (float) / 8-byte (half) accesses allowed
     int async;                // vec, and the next slices are streamed through shared memory
-    WtaOut wta;               // (Wta): pixel of (line, pos) is line * pix_line + pos * pix_pos
-    long long pix_line, pix_pos;
+    WtaOut wta;               // (Wta)
+    long long pix_line, pix_pos;  // pixel of (line, pos) is line * pix_line + pos * pix_pos
 };
 
 size_t zncc_row_smem_bytes(int R, int mode, const RowArgs& a, int nthreads);
@@ -56,6 +61,8 @@ size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a);
 
 cudaError_t launch_zncc_row(int R, const RowArgs& a, int mode, int dtype, cudaStream_t st);
 cudaError_t launch_line_pair(const LineArgs& a, int mode, int dtype, cudaStream_t st);
+int line_pair_items(const LineArgs& a);
+cudaError_t line_pair_occupancy(const LineArgs& a, int mode, int dtype, int* blocks_per_sm);
 cudaError_t launch_window_stats(const uint8_t* img, int pitch, int W, int H, int r, int x_begin,
                                 int nx, int* S, int* Q, float* isig, int2* packed,
                                 cudaStream_t st);

@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
     float4* co = reinterpret_cast<float4*>(SR + 4 * pSR);            // HPair
     float4* sb = co + 4 * pX;
     float* sa = reinterpret_cast<float*>(sb + 2 * nwl * tq);
-    float* rbv = reinterpret_cast<float*>(SR + 4 * pSR);             // Wta
-    int* rbd = reinterpret_cast<int*>(rbv + 4 * pX);
+    float2* rb = reinterpret_cast<float2*>(SR + 4 * pSR) + tid;     // Wta: entry i at rb[i * nthr]
+    const int nthr = blockDim.x;
 
     // ---- stage the packed bands (and the DT coefficients / the running best) ----
     for (int t = tid; t < NLP + NRP; t += blockDim.x) {
@@ -88,11 +88,8 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
             co[cidx(t, pX)] = t < W ? __ldg(a.coef + (size_t)y * W + t) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if constexpr (MODE == kModeWta) {
-        for (int t = tid; t < span; t += blockDim.x) {
-            const bool in = t < W && !a.wta.first;
-            rbv[p4(t, pX)] = in ? a.wta.bestv[(size_t)y * W + t] : -INFINITY;
-            rbd[p4(t, pX)] = in ? a.wta.bestd[(size_t)y * W + t] : 0;
-        }
+#pragma unroll
+        for (int i = 0; i < kL; ++i) rb[i * nthr] = make_float2(-INFINITY, __int_as_float(0x7FFFFFFF));
     }
     __syncthreads();
 
@@ -196,16 +193,7 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
 
         if constexpr (MODE == kModeWta) {
 #pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                float best;
-                int bd;
-                wta_group(v[i], nvalid, d_first, tq, best, bd);
-                const int x = x0 + i;
-                if (dq == 0 && x < W && best > rbv[p4(x, pX)]) {
-                    rbv[p4(x, pX)] = best;
-                    rbd[p4(x, pX)] = bd;
-                }
-            }
+            for (int i = 0; i < kL; ++i) wta_fold_own(rb + i * nthr, v[i], nvalid, d_first);
             continue;
         }
         if constexpr (MODE == kModeHPair) dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2);
@@ -222,16 +210,22 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
     }
 
     if constexpr (MODE == kModeWta) {
-        if (dq == 0) {
 #pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                const int x = x0 + i;
-                if (x >= W) break;
+        for (int i = 0; i < kL; ++i) {
+            float best;
+            int bd;
+            wta_reduce_lanes(rb[i * nthr], tq, best, bd);
+            const int x = x0 + i;
+            if (dq == 0 && x < W) {
                 const size_t o = (size_t)y * W + x;
-                if (a.wta.last) a.wta.disp[o] = (uint16_t)rbd[p4(x, pX)];
+                if (!a.wta.first) {                                    // earlier launches: smaller d
+                    const float pb = a.wta.bestv[o];
+                    if (!(best > pb)) { best = pb; bd = a.wta.bestd[o]; }
+                }
+                if (a.wta.last) a.wta.disp[o] = (uint16_t)bd;
                 else {
-                    a.wta.bestv[o] = rbv[p4(x, pX)];
-                    a.wta.bestd[o] = rbd[p4(x, pX)];
+                    a.wta.bestv[o] = best;
+                    a.wta.bestd[o] = bd;
                 }
             }
         }
@@ -247,7 +241,7 @@ inline size_t zncc_row_smem(int R, int mode, const RowArgs& a, int nthreads) {
     const int pX = plane_of(span);
     b += 8ull * 4 * (pX + plane_of(span + drange - 1));
     if (mode == kModeHPair) b += 16ull * 4 * pX + dt_scan_bytes(nthreads / 32, a.tq);
-    if (mode == kModeWta) b += 8ull * 4 * pX;
+    if (mode == kModeWta) b += 8ull * kL * nthreads;
     return b;
 }
 

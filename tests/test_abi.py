@@ -45,7 +45,8 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
     cases = [((0, 10, 4, 9), zncc.ZNCC_EINVAL), ((10, 0, 4, 9), zncc.ZNCC_EINVAL),
              ((10, 10, 0, 9), zncc.ZNCC_EINVAL), ((10, 10, 4, 8), zncc.ZNCC_EINVAL),
              ((10, 10, 4, 1), zncc.ZNCC_EINVAL), ((10, 10, 4, 17), zncc.ZNCC_EINVAL),
-             ((5000, 10, 4, 9), zncc.ZNCC_EUNSUPPORTED), ((10, 10, 2000, 9), zncc.ZNCC_EUNSUPPORTED)]
+             ((3073, 10, 4, 9), zncc.ZNCC_EUNSUPPORTED), ((10, 4097, 4, 9), zncc.ZNCC_EUNSUPPORTED),
+             ((10, 10, 2000, 9), zncc.ZNCC_EUNSUPPORTED)]
     for args, want in cases:
         st = lib.zncc_create(*args, ctypes.byref(h))
         assert st == want, (args, st)

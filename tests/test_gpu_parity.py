@@ -153,8 +153,9 @@ def test_dt_aggregate_matches_oracle(h, w, d, iters):
 
 @pytest.mark.parametrize("iters", [1, 3])
 def test_dt_aggregate_fp16_storage_error_is_small(iters):
-    """Half storage rounds the volume after every pass pair (2*iters roundings of relative
-    size 2^-11); the error against the FP64 oracle stays at that level."""
+    """dt_aggregate with half storage rounds the volume after every pass pair: 2*iters
+    roundings, each below 2^-11 of |cost| <= A_hat in the normal half range and below the
+    subnormal spacing 2^-24 under it; the DT carries an error field e to at most A_hat |e|."""
     h, w, d = 40, 90, 16
     rng = np.random.default_rng(1)
     guide = make_pair(h, w, 4, seed=2).left
@@ -174,7 +175,10 @@ def test_dt_aggregate_fp16_storage_error_is_small(iters):
     err = np.abs(got - ref) / A
     where = np.unravel_index(np.argmax(err), err.shape)
     assert rel32 <= AGG_TOL, rel32
-    assert err.max() < 2 * iters * 2.0 ** -10, (err.max(), where, got[where], ref[where])
+    bound = 2 * iters * (2.0 ** -11 * A + 2.0 ** -24)
+    excess = np.abs(got - ref) / bound
+    where = np.unravel_index(np.argmax(excess), excess.shape)
+    assert excess.max() <= 1.0, (excess.max(), where, got[where], ref[where])
 
 
 def test_dt_iters_zero_is_identity():
@@ -221,18 +225,6 @@ def test_fused_run_matches_oracle(h, w, d, win, iters):
     ref, gap = oracle.run(p.left, p.right, d, win // 2, SIG_S, SIG_R, iters)
     scale = oracle.ones_response(p.left, SIG_S, SIG_R, iters) if iters else 1.0
     check_disp(got, ref, gap, scale, f"zncc_run {h}x{w} D={d} win={win} iters={iters}")
-
-
-def test_wide_image_splits_wta_launches():
-    """A row too wide for one block to hold every disparity band: the cost + WTA kernel splits
-    the disparity range into launches chained through a running best."""
-    h, w, d, win = 4, 4000, 1024, 3
-    p = rand_pair(h, w, d, seed=3)
-    ctx = Z.ZnccContext(w, h, d, win)
-    disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
-    ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, 0)
-    ref, gap = oracle.run(p.left, p.right, d, win // 2, SIG_S, SIG_R, 0)
-    check_disp(host_u16(disp), ref, gap, 1.0, "wide WTA split")
 
 
 def test_unfused_chain_equals_oracle_and_fused():
