@@ -24,11 +24,11 @@ thread_local std::string g_create_error;
 // Kernel kinds for per-kernel timing (zncc_profile_*).
 enum Kind {
     K_STATS = 0, K_COEF, K_ZNCC_RAW, K_ZNCC_HPAIR, K_ZNCC_WTA, K_DT_HPAIR, K_DT_VPAIR,
-    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_NKINDS
+    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_AHAT, K_NKINDS
 };
 const char* const kKindNames[K_NKINDS] = {
     "window_stats", "dt_coef", "zncc_cost", "zncc_cost_hpair", "zncc_cost_wta",
-    "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume"};
+    "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume", "ahat_pair"};
 
 struct ProfRecord {
     int kind, ev0, ev1;
@@ -48,6 +48,9 @@ struct zncc_ctx {
     int W = 0, H = 0, D = 0, win = 0, r = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t cur = nullptr;       // the stream launches go to (stream, or side)
+    cudaStream_t side = nullptr;      // second stream for work independent of the cost kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     float4* coefH = nullptr;      // [H][W]       horizontal DT coefficients
     float4* coefV = nullptr;      // [W][H]       vertical DT coefficients
@@ -108,12 +111,12 @@ int prof_event(zncc_ctx* c) {
         g_launches.fetch_add(1, std::memory_order_relaxed);                   \
         int ev0_ = -1;                                                        \
         if ((c)->profiling && (ev0_ = prof_event(c)) >= 0)                    \
-            cudaEventRecord((c)->events[ev0_], (c)->stream);                  \
+            cudaEventRecord((c)->events[ev0_], (c)->cur);                     \
         cudaError_t e_ = (call);                                              \
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what);                 \
         int ev1_ = ev0_ >= 0 ? prof_event(c) : -1;                            \
         if (ev1_ >= 0) {                                                      \
-            cudaEventRecord((c)->events[ev1_], (c)->stream);                  \
+            cudaEventRecord((c)->events[ev1_], (c)->cur);                     \
             (c)->records.push_back(ProfRecord{(kind), ev0_, ev1_});           \
         }                                                                     \
     } while (0)
@@ -154,7 +157,7 @@ float scale_s2(float sigma_s) {
 zncc_status run_coef(zncc_ctx* c, const uint8_t* guide, int pitch, float sigma_s, float sigma_r) {
     const float K = (float)exp(-1.0 / (double)sigma_s);
     const float inv = (float)(1.0 / (255.0 * (double)sigma_r));
-    ZNCC_LAUNCH(c, K_COEF, launch_dt_coef(guide, pitch, c->W, c->H, K, inv, c->coefH, c->coefV, c->stream),
+    ZNCC_LAUNCH(c, K_COEF, launch_dt_coef(guide, pitch, c->W, c->H, K, inv, c->coefH, c->coefV, c->cur),
                 "DT coefficients");
     return ZNCC_OK;
 }
@@ -209,7 +212,7 @@ zncc_status run_rows(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int
         while (a.spb > 1 && zncc_row_smem_bytes(c->r, mode, a, threads) > (size_t)c->smem_max) --a.spb;
         if (zncc_row_smem_bytes(c->r, mode, a, threads) > (size_t)c->smem_max)
             return fail(c, ZNCC_EUNSUPPORTED, "image too wide for the cost kernel's shared memory");
-        ZNCC_LAUNCH(c, kind, launch_zncc_row(c->r, a, mode, dtype, c->stream), what);
+        ZNCC_LAUNCH(c, kind, launch_zncc_row(c->r, a, mode, dtype, c->cur), what);
         return ZNCC_OK;
     }
     int per_launch = nslices;   // slices of one Wta launch
@@ -232,7 +235,7 @@ zncc_status run_rows(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int
         a.wta.disp = disp;
         a.wta.first = g == 0;
         a.wta.last = g == nlaunch - 1;
-        ZNCC_LAUNCH(c, kind, launch_zncc_row(c->r, a, mode, dtype, c->stream), what);
+        ZNCC_LAUNCH(c, kind, launch_zncc_row(c->r, a, mode, dtype, c->cur), what);
     }
     return ZNCC_OK;
 }
@@ -252,6 +255,7 @@ struct LinePass {
     uint16_t* disp = nullptr;
     float s2 = 1.0f;
     int force_tq = 0;
+    bool ahat = false;             // a pass of the A_hat chain (profiled separately)
 };
 
 // The launch shape: among lane counts per chunk (8, 4, 2, or the forced one) and lines per
@@ -336,8 +340,9 @@ zncc_status run_line_pair(zncc_ctx* c, const LinePass& p) {
     a.pix_line = p.horiz ? c->W : 1;
     a.pix_pos = p.horiz ? 1 : c->W;
     ZNCC_TRY(plan_line_pass(c, a, p));
-    const int kind = p.horiz ? K_DT_HPAIR : (p.mode == kLineWta ? K_DT_VPAIR_WTA : K_DT_VPAIR);
-    ZNCC_LAUNCH(c, kind, launch_line_pair(a, p.mode, p.dtype, c->stream), p.horiz ? "DT horizontal pair" : "DT vertical pair");
+    const int kind = p.ahat ? K_AHAT
+                     : (p.horiz ? K_DT_HPAIR : (p.mode == kLineWta ? K_DT_VPAIR_WTA : K_DT_VPAIR));
+    ZNCC_LAUNCH(c, kind, launch_line_pair(a, p.mode, p.dtype, c->cur), p.horiz ? "DT horizontal pair" : "DT vertical pair");
     return ZNCC_OK;
 }
 
@@ -366,6 +371,7 @@ zncc_status run_ahat_chain(zncc_ctx* c, int n, float s2) {
         lp.horiz = (p % 2) == 1;
         lp.s2 = s2;
         lp.force_tq = 1;
+        lp.ahat = true;
         ZNCC_TRY(run_line_pair(c, lp));
     }
     return ZNCC_OK;
@@ -388,6 +394,11 @@ void release(zncc_ctx* c) {
     c->plans.clear();
     free_dev(c->img);
     free_dev(c->disp);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    c->side = nullptr;
+    c->ev_fork = c->ev_join = nullptr;
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     c->records.clear();
@@ -445,6 +456,7 @@ zncc_status zncc_destroy(zncc_ctx* c) {
 zncc_status zncc_set_stream(zncc_ctx* c, void* stream) {
     if (!c) return ZNCC_EINVAL;
     c->stream = (cudaStream_t)stream;
+    c->cur = c->stream;
     return ZNCC_OK;
 }
 
@@ -461,7 +473,7 @@ zncc_status zncc_window_stats(zncc_ctx* c, const uint8_t* img, int pitch, int32_
     if (pitch < c->W) return fail(c, ZNCC_EINVAL, "pitch is smaller than the width");
     if (!S && !Q && !inv_sigma) return ZNCC_OK;
     ZNCC_LAUNCH(c, K_STATS, launch_window_stats(img, pitch, c->W, c->H, c->r, 0, c->W, S, Q, inv_sigma,
-                                                nullptr, c->stream), "window statistics");
+                                                nullptr, c->cur), "window statistics");
     return ZNCC_OK;
 }
 
@@ -507,7 +519,7 @@ zncc_status wta_disparity(zncc_ctx* c, const void* cost, zncc_dtype dtype, uint1
     c->err.clear();
     if (!cost || !disp) return fail(c, ZNCC_EINVAL, "cost or disp pointer is NULL");
     if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
-    ZNCC_LAUNCH(c, K_WTA_VOLUME, launch_wta_volume(cost, dtype, c->W, c->H, c->D, disp, c->stream), "WTA");
+    ZNCC_LAUNCH(c, K_WTA_VOLUME, launch_wta_volume(cost, dtype, c->W, c->H, c->D, disp, c->cur), "WTA");
     return ZNCC_OK;
 }
 
@@ -538,6 +550,22 @@ zncc_status zncc_run(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int
     }
     ZNCC_TRY(run_coef(c, left, pitch, sigma_s, sigma_r));
     const float s2 = scale_s2(sigma_s);
+    if (dt == 1 && iters > 1) {
+        // the A_hat maps of half storage depend only on the guide: computed on a second stream,
+        // concurrently with the cost kernel, and joined before the first stored pair is read
+        if (!c->side) {
+            ZNCC_CUDA(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
+            ZNCC_CUDA(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "fork event");
+            ZNCC_CUDA(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "join event");
+        }
+        ZNCC_CUDA(c, cudaEventRecord(c->ev_fork, c->stream), "fork");
+        ZNCC_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork");
+        c->cur = c->side;
+        const zncc_status st = run_ahat_chain(c, 2 * iters - 1, s2);
+        c->cur = c->stream;
+        ZNCC_TRY(st);
+        ZNCC_CUDA(c, cudaEventRecord(c->ev_join, c->side), "join");
+    }
     ZNCC_TRY(run_rows(c, left, right, pitch, kModeHPair, dt, c->vol, dstride, s2, nullptr, K_ZNCC_HPAIR,
                       "ZNCC + horizontal DT pair"));
     // Half storage keeps each stored pair p >= 2 divided by A_hat_p (the per-pixel bound of
@@ -546,7 +574,9 @@ zncc_status zncc_run(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int
     const bool norm = dt == 1;
     const int npairs = 2 * iters;
     const size_t ahat_sz = npix;
-    if (norm && npairs > 2) ZNCC_TRY(run_ahat_chain(c, npairs - 1, s2));
+    const bool fork = norm && npairs > 2;
+    if (fork) ZNCC_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join of the A_hat stream");
+    (void)ahat_sz;
     LinePass lp;
     lp.vol = c->vol;
     lp.dstride = dstride;

@@ -135,11 +135,19 @@ __device__ __forceinline__ void lds4(const __half* p, float (&o)[4]) {
 // co: the line's coefficients in shared memory (cidx layout); sa/sb: the line's scan
 // buffers, 2 * nwl * tq entries each; wl / nwl: this thread's warp within the line and the
 // warps per line. The result is scaled by s2 = (1-K)^2, or per position by mul[p].y when
-// mul (cidx layout) is given. Synchronizes the block twice.
+// mul (cidx layout) is given. after_forward() runs once the forward sweep has consumed the
+// input values (the caller may then overwrite where they came from). Synchronizes the
+// block twice.
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+template <typename Hook = NoHook>
 __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restrict__ co,
                                         int plane, int k, int tq, int dq, int lane, int wl,
                                         int nwl, float* sa, float4* sb, float s2,
-                                        const float2* __restrict__ mul = nullptr) {
+                                        const float2* __restrict__ mul = nullptr,
+                                        Hook after_forward = Hook()) {
     const int start = k * kL;
     // forward sweep of the chunk, zero carry-in
     float u[4] = {0.f, 0.f, 0.f, 0.f};
@@ -152,6 +160,7 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
             v[i][j] = u[j];
         }
     }
+    after_forward();
     // forward carries: inclusive scan of (A, B) over the warp's chunks, then the warps before
     float A = co[cidx(start + kL - 1, plane)].y;
     float B[4] = {u[0], u[1], u[2], u[3]};

@@ -119,12 +119,13 @@ cudaError_t launch_dt_coef(const uint8_t* guide, int pitch, int W, int H, float 
 // disparities; an item is (group, slice), numbered group-major. The grid is sized to the
 // resident blocks (persistent); block b processes the items [b*per_block, (b+1)*per_block)
 // in order, restaging the coefficients when the group changes. With aligned 4-disparity
-// groups (async) each thread streams its elements of the next two items into shared memory
-// with cp.async while the current one is computed, across group boundaries. In Wta mode
-// per_block is a multiple of nslices: a block sees every disparity of its lines.
+// groups (async) each thread streams its elements of the next item into shared memory with
+// cp.async while the current one is computed, across group boundaries: the staging buffer
+// is refilled as soon as the forward sweep has consumed it. In Wta mode per_block is a
+// multiple of nslices: a block sees every disparity of its lines.
 template <typename T>
 __host__ __device__ inline size_t line_stage_bytes(const LineArgs& a) {
-    return a.async ? 2ull * a.lpc * kL * a.nch * a.tq * (4 * sizeof(T)) : 0;
+    return a.async ? 1ull * a.lpc * kL * a.nch * a.tq * (4 * sizeof(T)) : 0;
 }
 
 int line_pair_items(const LineArgs& a) {
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
     const int lane = threadIdx.x & 31, wl = tl >> 5;
     const int pX = plane_of(span);
 
-    T* stage = reinterpret_cast<T*>(smem4);                           // [2][lpc][kL][per_line] x 4
+    T* stage = reinterpret_cast<T*>(smem4);                           // [lpc][kL][per_line] x 4
     float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + line_stage_bytes<T>(a));
     float2* mul_all = reinterpret_cast<float2*>(co_all + a.lpc * 4 * pX);   // [lpc][4 pX]
     float4* sb_all = reinterpret_cast<float4*>(mul_all + a.lpc * 4 * pX);   // [lpc][2 nwl tq]
@@ -167,13 +168,13 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
     auto elem0 = [&](int line, int sl) -> size_t {                   // the chunk's first group
         return (size_t)line * a.line_stride + (size_t)(k * kL) * a.elem_stride + sl * ds + dq * kG;
     };
-    auto stage_at = [&](int buf, int i) -> T* {
-        return stage + ((size_t)((buf * a.lpc + li) * kL + i) * per_line + tl) * 4;
+    auto stage_at = [&](int i) -> T* {
+        return stage + ((size_t)(li * kL + i) * per_line + tl) * 4;
     };
-    // prefetch of item `it` into stage buffer buf. With vec the entries per pixel are a
+    // prefetch of item `it` into the stage buffer. With vec the entries per pixel are a
     // multiple of 4, so a group with any valid disparity lies whole inside the volume; its
     // entries past dcount are never stored or compared.
-    auto prefetch = [&](int it, int buf) {
+    auto prefetch = [&](int it) {
         if (it < it1) {
             const int g = it / nslices, sl = it - g * nslices;
             const int line = g * a.lpc + li;
@@ -182,15 +183,12 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 const bool valid = ok && i < npos;
-                cp_async<4 * sizeof(T)>(stage_at(buf, i), valid ? p + (size_t)i * a.elem_stride : src, valid);
+                cp_async<4 * sizeof(T)>(stage_at(i), valid ? p + (size_t)i * a.elem_stride : src, valid);
             }
         }
         cp_async_commit();
     };
-    if (async) {
-        prefetch(it0, 0);
-        prefetch(it0 + 1, 1);
-    }
+    if (async) prefetch(it0);
 
     int cur_group = -1;
     for (int it = it0, n_it = 0; it < it1; ++it, ++n_it) {
@@ -229,9 +227,9 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v[i][j] = (any && i < npos && j < nvalid) ? 1.0f : 0.0f;
         } else if (async) {
-            cp_async_wait<1>();                                        // this item's copies landed
+            cp_async_wait<0>();                                        // this item's copies landed
 #pragma unroll
-            for (int i = 0; i < kL; ++i) lds4(stage_at(n_it & 1, i), v[i]);
+            for (int i = 0; i < kL; ++i) lds4(stage_at(i), v[i]);
         } else {
             const T* q = src + (line_ok ? elem0(line, sl) : 0);
 #pragma unroll
@@ -249,9 +247,10 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
                 for (int j = 0; j < 4; ++j) v[i][j] *= m;
             }
         }
-        dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2, mul);
-        // the stage buffer was consumed by the sweeps above: refill it two items ahead
-        if (async) prefetch(it + 2, n_it & 1);
+        // the staging buffer is free once the forward sweep has read it: fetch the next item
+        dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2, mul, [&]() {
+            if (async) prefetch(it + 1);
+        });
         if constexpr (MODE == kLineWta) {
 #pragma unroll
             for (int i = 0; i < kL; ++i) wta_fold_own(rb + i * per_line, v[i], nvalid, a.d_base + dl);
