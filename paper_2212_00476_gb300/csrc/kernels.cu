@@ -120,12 +120,12 @@ cudaError_t launch_dt_coef(const uint8_t* guide, int pitch, int W, int H, float 
 // resident blocks (persistent); block b processes the items [b*per_block, (b+1)*per_block)
 // in order, restaging the coefficients when the group changes. With aligned 4-disparity
 // groups (async) each thread streams its elements of the next item into shared memory with
-// cp.async while the current one is computed, across group boundaries: the staging buffer
-// is refilled as soon as the forward sweep has consumed it. In Wta mode per_block is a
-// multiple of nslices: a block sees every disparity of its lines.
+// cp.async while the current one is computed, across group boundaries: two staging buffers,
+// each refilled (two items ahead) as soon as the forward sweep has consumed it. In Wta mode
+// per_block is a multiple of nslices: a block sees every disparity of its lines.
 template <typename T>
 __host__ __device__ inline size_t line_stage_bytes(const LineArgs& a) {
-    return a.async ? 1ull * a.lpc * kL * a.nch * a.tq * (4 * sizeof(T)) : 0;
+    return a.async ? 2ull * a.lpc * kL * a.nch * a.tq * (4 * sizeof(T)) : 0;
 }
 
 int line_pair_items(const LineArgs& a) {
@@ -144,17 +144,17 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
     const int lane = threadIdx.x & 31, wl = tl >> 5;
     const int pX = plane_of(span);
 
-    T* stage = reinterpret_cast<T*>(smem4);                           // [lpc][kL][per_line] x 4
+    T* stage = reinterpret_cast<T*>(smem4);                           // [2][lpc][kL][per_line] x 4
     float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + line_stage_bytes<T>(a));
     float2* mul_all = reinterpret_cast<float2*>(co_all + a.lpc * 4 * pX);   // [lpc][4 pX]
     float4* sb_all = reinterpret_cast<float4*>(mul_all + a.lpc * 4 * pX);   // [lpc][2 nwl tq]
     float* sa_all = reinterpret_cast<float*>(sb_all + a.lpc * 2 * nwl * tq);
-    float2* rb_all = reinterpret_cast<float2*>(sa_all + a.lpc * 2 * nwl * tq);   // [lpc][kL][nch][tq] (Wta)
+    float2* rb_all = reinterpret_cast<float2*>(sa_all + a.lpc * 2 * nwl * tq);   // [lpc][4 pX] (Wta)
     const float4* co = co_all + li * 4 * pX;
     const float2* mul = mul_all + li * 4 * pX;
     float4* sb = sb_all + li * 2 * nwl * tq;
     float* sa = sa_all + li * 2 * nwl * tq;
-    float2* rb = rb_all + (size_t)li * kL * per_line + tl;             // entry (i) at rb[i * per_line]
+    float2* rb = rb_all + li * 4 * pX;                                 // (best, d) per position
 
     const int nslices = (a.dcount + ds - 1) / ds;
     const int total = ((a.nlines + a.lpc - 1) / a.lpc) * nslices;
@@ -168,13 +168,13 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
     auto elem0 = [&](int line, int sl) -> size_t {                   // the chunk's first group
         return (size_t)line * a.line_stride + (size_t)(k * kL) * a.elem_stride + sl * ds + dq * kG;
     };
-    auto stage_at = [&](int i) -> T* {
-        return stage + ((size_t)(li * kL + i) * per_line + tl) * 4;
+    auto stage_at = [&](int buf, int i) -> T* {
+        return stage + ((size_t)((buf * a.lpc + li) * kL + i) * per_line + tl) * 4;
     };
     // prefetch of item `it` into the stage buffer. With vec the entries per pixel are a
     // multiple of 4, so a group with any valid disparity lies whole inside the volume; its
     // entries past dcount are never stored or compared.
-    auto prefetch = [&](int it) {
+    auto prefetch = [&](int it, int buf) {
         if (it < it1) {
             const int g = it / nslices, sl = it - g * nslices;
             const int line = g * a.lpc + li;
@@ -183,12 +183,15 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 const bool valid = ok && i < npos;
-                cp_async<4 * sizeof(T)>(stage_at(i), valid ? p + (size_t)i * a.elem_stride : src, valid);
+                cp_async<4 * sizeof(T)>(stage_at(buf, i), valid ? p + (size_t)i * a.elem_stride : src, valid);
             }
         }
         cp_async_commit();
     };
-    if (async) prefetch(it0);
+    if (async) {
+        prefetch(it0, 0);
+        prefetch(it0 + 1, 1);
+    }
 
     int cur_group = -1;
     for (int it = it0, n_it = 0; it < it1; ++it, ++n_it) {
@@ -211,8 +214,8 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
                 }
             }
             if constexpr (MODE == kLineWta) {
-#pragma unroll
-                for (int i = 0; i < kL; ++i) rb[i * per_line] = make_float2(-INFINITY, __int_as_float(0x7FFFFFFF));
+                for (int t = threadIdx.x; t < a.lpc * 4 * pX; t += blockDim.x)
+                    rb_all[t] = make_float2(-INFINITY, __int_as_float(0x7FFFFFFF));
             }
             __syncthreads();
             cur_group = g;
@@ -227,9 +230,9 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v[i][j] = (any && i < npos && j < nvalid) ? 1.0f : 0.0f;
         } else if (async) {
-            cp_async_wait<0>();                                        // this item's copies landed
+            cp_async_wait<1>();                                        // this item's copies landed
 #pragma unroll
-            for (int i = 0; i < kL; ++i) lds4(stage_at(i), v[i]);
+            for (int i = 0; i < kL; ++i) lds4(stage_at(n_it & 1, i), v[i]);
         } else {
             const T* q = src + (line_ok ? elem0(line, sl) : 0);
 #pragma unroll
@@ -247,19 +250,29 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
                 for (int j = 0; j < 4; ++j) v[i][j] *= m;
             }
         }
-        // the staging buffer is free once the forward sweep has read it: fetch the next item
+        // the staging buffer is free once the forward sweep has read it: refill it two ahead
         dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2, mul, [&]() {
-            if (async) prefetch(it + 1);
+            if (async) prefetch(it + 2, n_it & 1);
         });
         if constexpr (MODE == kLineWta) {
+            // the slice's best per pixel over the tq lanes, folded into the pixel's running best
+            // (slices come in increasing d, so an equal later value keeps the smaller d)
 #pragma unroll
-            for (int i = 0; i < kL; ++i) wta_fold_own(rb + i * per_line, v[i], nvalid, a.d_base + dl);
+            for (int i = 0; i < kL; ++i) {
+                float2 e = make_float2(-INFINITY, __int_as_float(0x7FFFFFFF));
+                wta_fold_own(&e, v[i], nvalid, a.d_base + dl);
+                float best;
+                int bd;
+                wta_reduce_lanes(e, tq, best, bd);
+                float2* r = rb + p4(k * kL + i, pX);
+                if (dq == 0 && best > r->x) *r = make_float2(best, __int_as_float(bd));
+            }
             if (sl == nslices - 1) {                                   // the group's last slice
 #pragma unroll
                 for (int i = 0; i < kL; ++i) {
-                    float best;
-                    int bd;
-                    wta_reduce_lanes(rb[i * per_line], tq, best, bd);
+                    const float2 r = rb[p4(k * kL + i, pX)];
+                    float best = r.x;
+                    int bd = __float_as_int(r.y);
                     const int pos = k * kL + i;
                     if (dq == 0 && line_ok && pos < a.n) {
                         const size_t pix = (size_t)line * a.pix_line + (size_t)pos * a.pix_pos;
@@ -292,7 +305,7 @@ size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a) {
     const int nwl = a.nch * a.tq / 32;
     size_t b = dtype == 0 ? line_stage_bytes<float>(a) : line_stage_bytes<__half>(a);
     b += (size_t)a.lpc * ((16ull + 8ull) * 4 * pX + dt_scan_bytes(nwl, a.tq));
-    if (mode == kLineWta) b += (size_t)a.lpc * 8ull * kL * a.nch * a.tq;
+    if (mode == kLineWta) b += (size_t)a.lpc * 8ull * 4 * pX;
     return b;
 }
 
