@@ -259,9 +259,10 @@ struct LinePass {
 };
 
 // The launch shape: among lane counts per chunk (8, 4, 2, or the forced one) and lines per
-// block that fit in shared memory, prefer streaming through shared memory (async), then at
-// least two resident blocks per SM, then the most resident warps. The grid is the resident
-// blocks (persistent), each taking an equal run of items.
+// block that fit in shared memory, prefer whole 64-byte segments per chunk, then streaming
+// through shared memory (async), then at least two resident blocks per SM, then the most
+// resident warps. The grid is the resident blocks (persistent), each taking an equal run of
+// items.
 zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
     const long long key = ((((long long)p.horiz * 2 + p.mode) * 2 + p.dtype) * 2 + (a.vec ? 1 : 0)) * 16 +
                           p.force_tq + ((long long)p.dcount << 20);
@@ -279,6 +280,9 @@ zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
         const int nch = padded_chunks(a.n, tq);
         const int per_line = nch * tq;
         if (per_line > 512) continue;
+        // a chunk's lanes read tq * 4 contiguous entries per position: shapes whose segments
+        // are whole 64-byte DRAM bursts come first
+        const bool whole_bursts = tq * 4 * (p.dtype == 0 ? 4 : 2) >= 64;
         for (int async = a.vec ? 1 : 0; async >= 0; --async) {
             for (int lpc = std::max(1, std::min(8, 256 / per_line)); lpc >= 1; --lpc) {
                 a.tq = tq; a.nch = nch; a.lpc = lpc; a.async = async;
@@ -287,7 +291,8 @@ zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
                 ZNCC_CUDA(c, line_pair_occupancy(a, p.mode, p.dtype, &bps), "occupancy query");
                 if (bps < 1) continue;
                 const long long warps = (long long)bps * lpc * per_line / 32;
-                const long long score = async * 1000000LL + (bps >= 2 ? 100000LL : 0) + warps * 100 + tq;
+                const long long score = (whole_bursts ? 10000000LL : 0) + async * 1000000LL +
+                                        (bps >= 2 ? 100000LL : 0) + warps * 100 + tq;
                 if (score > best_score) {
                     best_score = score;
                     best.tq = tq; best.lpc = lpc; best.nch = nch; best.async = async; best.blocks = bps;

@@ -261,6 +261,40 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
     }
 }
 
+// ---- per-thread WTA running best over the slices a block visits, in registers -----------
+// rv[i]: best value of position i over this thread's disparities so far; rd: the matching
+// disparities as 16-bit fields, two per word. Ties keep the smaller d (slices arrive in
+// increasing d, and a later equal value does not replace an earlier one).
+struct WtaRegs {
+    float rv[kL];
+    unsigned rd[kL / 2];
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int i = 0; i < kL; ++i) rv[i] = -INFINITY;
+#pragma unroll
+        for (int i = 0; i < kL / 2; ++i) rd[i] = 0xFFFFFFFFu;
+    }
+    __device__ __forceinline__ void fold(const float (&v)[kL][4], int nvalid, int d_first) {
+#pragma unroll
+        for (int i = 0; i < kL; ++i) {
+            float m = -INFINITY;
+            int jj = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < nvalid && v[i][j] > m) { m = v[i][j]; jj = j; }
+            if (m > rv[i]) {
+                rv[i] = m;
+                const unsigned d = (unsigned)(d_first + jj) & 0xFFFFu;
+                rd[i >> 1] = (i & 1) ? ((rd[i >> 1] & 0x0000FFFFu) | (d << 16)) : ((rd[i >> 1] & 0xFFFF0000u) | d);
+            }
+        }
+    }
+    __device__ __forceinline__ float2 entry(int i) const {
+        const unsigned d = (i & 1) ? (rd[i >> 1] >> 16) : (rd[i >> 1] & 0xFFFFu);
+        return make_float2(rv[i], __int_as_float(d == 0xFFFFu ? 0x7FFFFFFF : (int)d));
+    }
+};
+
 // ---- per-thread WTA running best over the slices a block visits -------------------------
 // Entry (i, k, dq) of a line's [kL][nch][tq] array of (value, d) pairs belongs to one thread;
 // a slice folds the thread's 4 disparities into it without any cross-lane traffic, and the

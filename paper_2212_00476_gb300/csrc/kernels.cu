@@ -149,12 +149,10 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
     float2* mul_all = reinterpret_cast<float2*>(co_all + a.lpc * 4 * pX);   // [lpc][4 pX]
     float4* sb_all = reinterpret_cast<float4*>(mul_all + a.lpc * 4 * pX);   // [lpc][2 nwl tq]
     float* sa_all = reinterpret_cast<float*>(sb_all + a.lpc * 2 * nwl * tq);
-    float2* rb_all = reinterpret_cast<float2*>(sa_all + a.lpc * 2 * nwl * tq);   // [lpc][4 pX] (Wta)
     const float4* co = co_all + li * 4 * pX;
     const float2* mul = mul_all + li * 4 * pX;
     float4* sb = sb_all + li * 2 * nwl * tq;
     float* sa = sa_all + li * 2 * nwl * tq;
-    float2* rb = rb_all + li * 4 * pX;                                 // (best, d) per position
 
     const int nslices = (a.dcount + ds - 1) / ds;
     const int total = ((a.nlines + a.lpc - 1) / a.lpc) * nslices;
@@ -193,6 +191,7 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
         prefetch(it0 + 1, 1);
     }
 
+    WtaRegs wr;
     int cur_group = -1;
     for (int it = it0, n_it = 0; it < it1; ++it, ++n_it) {
         const int g = it / nslices, sl = it - g * nslices;
@@ -213,10 +212,7 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
                     mul_all[l2 * 4 * pX + cidx(t, pX)] = make_float2(mi, mo);
                 }
             }
-            if constexpr (MODE == kLineWta) {
-                for (int t = threadIdx.x; t < a.lpc * 4 * pX; t += blockDim.x)
-                    rb_all[t] = make_float2(-INFINITY, __int_as_float(0x7FFFFFFF));
-            }
+            if constexpr (MODE == kLineWta) wr.reset();
             __syncthreads();
             cur_group = g;
         }
@@ -255,24 +251,13 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
             if (async) prefetch(it + 2, n_it & 1);
         });
         if constexpr (MODE == kLineWta) {
-            // the slice's best per pixel over the tq lanes, folded into the pixel's running best
-            // (slices come in increasing d, so an equal later value keeps the smaller d)
-#pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                float2 e = make_float2(-INFINITY, __int_as_float(0x7FFFFFFF));
-                wta_fold_own(&e, v[i], nvalid, a.d_base + dl);
-                float best;
-                int bd;
-                wta_reduce_lanes(e, tq, best, bd);
-                float2* r = rb + p4(k * kL + i, pX);
-                if (dq == 0 && best > r->x) *r = make_float2(best, __int_as_float(bd));
-            }
+            wr.fold(v, nvalid, a.d_base + dl);
             if (sl == nslices - 1) {                                   // the group's last slice
 #pragma unroll
                 for (int i = 0; i < kL; ++i) {
-                    const float2 r = rb[p4(k * kL + i, pX)];
-                    float best = r.x;
-                    int bd = __float_as_int(r.y);
+                    float best;
+                    int bd;
+                    wta_reduce_lanes(wr.entry(i), tq, best, bd);
                     const int pos = k * kL + i;
                     if (dq == 0 && line_ok && pos < a.n) {
                         const size_t pix = (size_t)line * a.pix_line + (size_t)pos * a.pix_pos;
@@ -305,7 +290,6 @@ size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a) {
     const int nwl = a.nch * a.tq / 32;
     size_t b = dtype == 0 ? line_stage_bytes<float>(a) : line_stage_bytes<__half>(a);
     b += (size_t)a.lpc * ((16ull + 8ull) * 4 * pX + dt_scan_bytes(nwl, a.tq));
-    if (mode == kLineWta) b += (size_t)a.lpc * 8ull * 4 * pX;
     return b;
 }
 

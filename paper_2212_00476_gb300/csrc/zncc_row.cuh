@@ -64,8 +64,6 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
     float4* co = reinterpret_cast<float4*>(SR + 4 * pSR);            // HPair
     float4* sb = co + 4 * pX;
     float* sa = reinterpret_cast<float*>(sb + 2 * nwl * tq);
-    float2* rb = reinterpret_cast<float2*>(SR + 4 * pSR) + tid;     // Wta: entry i at rb[i * nthr]
-    const int nthr = blockDim.x;
 
     // ---- stage the packed bands (and the DT coefficients / the running best) ----
     for (int t = tid; t < NLP + NRP; t += blockDim.x) {
@@ -86,10 +84,6 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
     if constexpr (MODE == kModeHPair) {
         for (int t = tid; t < span; t += blockDim.x)
             co[cidx(t, pX)] = t < W ? __ldg(a.coef + (size_t)y * W + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    if constexpr (MODE == kModeWta) {
-#pragma unroll
-        for (int i = 0; i < kL; ++i) rb[i * nthr] = make_float2(-INFINITY, __int_as_float(0x7FFFFFFF));
     }
     __syncthreads();
 
@@ -131,6 +125,8 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
     const int x0 = k * kL;
     T* out = reinterpret_cast<T*>(a.vol);
     const bool vec = a.vec != 0;
+    WtaRegs wr;
+    if constexpr (MODE == kModeWta) wr.reset();
 
     for (int sl = s_begin; sl < s_end; ++sl) {
         const int d_first = a.d_lo + sl * ds + dq * kG;
@@ -192,8 +188,7 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
         }
 
         if constexpr (MODE == kModeWta) {
-#pragma unroll
-            for (int i = 0; i < kL; ++i) wta_fold_own(rb + i * nthr, v[i], nvalid, d_first);
+            wr.fold(v, nvalid, d_first);
             continue;
         }
         if constexpr (MODE == kModeHPair) dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2);
@@ -214,7 +209,7 @@ __global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
         for (int i = 0; i < kL; ++i) {
             float best;
             int bd;
-            wta_reduce_lanes(rb[i * nthr], tq, best, bd);
+            wta_reduce_lanes(wr.entry(i), tq, best, bd);
             const int x = x0 + i;
             if (dq == 0 && x < W) {
                 const size_t o = (size_t)y * W + x;
@@ -241,7 +236,6 @@ inline size_t zncc_row_smem(int R, int mode, const RowArgs& a, int nthreads) {
     const int pX = plane_of(span);
     b += 8ull * 4 * (pX + plane_of(span + drange - 1));
     if (mode == kModeHPair) b += 16ull * 4 * pX + dt_scan_bytes(nthreads / 32, a.tq);
-    if (mode == kModeWta) b += 8ull * kL * nthreads;
     return b;
 }
 
