@@ -233,6 +233,12 @@ def run_gb300(args):
     def step():
         ctx.zncc_run(left, right, disp, SIG_S, SIG_R, iters, storage)
 
+    tuned = None
+    if not args.no_autotune:
+        from paper_2212_00476_gb300 import autotune
+        with torch.cuda.stream(stream):
+            tuned = autotune.tune(ctx, left, right, disp, SIG_S, SIG_R, iters, storage)
+
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.zero_()
@@ -322,7 +328,8 @@ def run_gb300(args):
                    "l2": "flushed before every timed step (256 MB write outside the step events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "step_ms_min": round(min(step_ms), 4), "wall_ms_per_step_incl_flush":
-                   round(t_wall * 1e3 / args.steps, 4)},
+                   round(t_wall * 1e3 / args.steps, 4),
+                   "launch_shapes": tuned["settings"] if tuned else "defaults"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
@@ -361,6 +368,7 @@ def main():
     ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper_1280x384")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3

@@ -123,6 +123,22 @@ const char* zncc_last_error(const zncc_ctx* ctx);
 /* Static text for a status code. */
 const char* zncc_status_string(zncc_status status);
 
+/* Launch-shape knobs of a context (0 = automatic for every key), for autotuning:
+ *   ZNCC_TUNE_ROW_MINB2  cost kernel: 1 = register-limited variant with two blocks per SM
+ *                        where the block has at most 320 threads (default), 0 = one block
+ *   ZNCC_TUNE_ROW_SPB    cost kernel: disparity slices per block
+ *   ZNCC_TUNE_H_TQ       horizontal DT pairs: lanes per 16-pixel chunk (2, 4 or 8)
+ *   ZNCC_TUNE_V_TQ       vertical DT pairs: lanes per 16-pixel chunk (2, 4 or 8)
+ * A value a launch cannot use (too many threads or too much shared memory) makes the next
+ * call fail with ZNCC_EUNSUPPORTED. Unknown keys give ZNCC_EINVAL. */
+typedef enum {
+    ZNCC_TUNE_ROW_MINB2 = 1,
+    ZNCC_TUNE_ROW_SPB = 2,
+    ZNCC_TUNE_H_TQ = 3,
+    ZNCC_TUNE_V_TQ = 4
+} zncc_tune_key;
+zncc_status zncc_set_tuning(zncc_ctx* ctx, int key, int value);
+
 /* Number of kernels this library has launched in this process (all contexts). */
 uint64_t zncc_kernel_launch_count(void);
 

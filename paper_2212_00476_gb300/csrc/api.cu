@@ -61,6 +61,9 @@ struct zncc_ctx {
     float* ahat = nullptr;        // [nahat][H][W] DT responses of an all-ones plane (F16 storage)
     int nahat = 0;
     int smem_max = 0;             // opt-in shared memory per block of the device
+    int row_minb2 = 1;            // cost kernel: two-blocks-per-SM variant where it applies
+    int row_spb = 0;              // cost kernel: slices per block (0 = automatic)
+    int h_tq = 0, v_tq = 0;       // DT pairs: forced lanes per chunk (0 = automatic)
     int num_sms = 0;
     std::vector<LinePlan> plans;  // line-pass launch shapes, by pass signature
     uint8_t* img = nullptr;       // device copies for zncc_run_host: 2 x [H][W]
@@ -202,13 +205,14 @@ zncc_status run_rows(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int
     a.vec = vol && (dstride % 4 == 0) && ((uintptr_t)vol % (dtype == 0 ? 16 : 8) == 0) ? 1 : 0;
     a.coef = c->coefH;
     a.s2 = s2;
+    a.minb2 = c->row_minb2;
     const int threads = a.nch * a.tq;
     const int ds = kG * a.tq;
     const int nslices = (c->D + ds - 1) / ds;
     if (mode != kModeWta) {
         a.d_lo = 0;
         a.d_hi = c->D;
-        a.spb = slices_per_block(nslices, c->H);
+        a.spb = c->row_spb > 0 ? std::min(c->row_spb, nslices) : slices_per_block(nslices, c->H);
         while (a.spb > 1 && zncc_row_smem_bytes(c->r, mode, a, threads) > (size_t)c->smem_max) --a.spb;
         if (zncc_row_smem_bytes(c->r, mode, a, threads) > (size_t)c->smem_max)
             return fail(c, ZNCC_EUNSUPPORTED, "image too wide for the cost kernel's shared memory");
@@ -265,7 +269,7 @@ struct LinePass {
 // items.
 zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
     const long long key = ((((long long)p.horiz * 2 + p.mode) * 2 + p.dtype) * 2 + (a.vec ? 1 : 0)) * 16 +
-                          p.force_tq + ((long long)p.dcount << 20);
+                          p.force_tq + ((long long)p.dcount << 20) + ((long long)(p.horiz ? c->h_tq : c->v_tq) << 40);
     for (const LinePlan& pl : c->plans)
         if (pl.key == key) {
             a.tq = pl.tq; a.lpc = pl.lpc; a.nch = pl.nch; a.async = pl.async; a.per_block = pl.per_block;
@@ -274,9 +278,10 @@ zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
     LinePlan best{key, 0, 0, 0, 0, 0, 0};
     long long best_score = -1;
     const int tqs[4] = {8, 4, 2, 1};
+    const int forced = p.force_tq ? p.force_tq : (p.horiz ? c->h_tq : c->v_tq);
     for (int ti = 0; ti < 4; ++ti) {
         const int tq = tqs[ti];
-        if (p.force_tq ? tq != p.force_tq : tq == 1) continue;
+        if (forced ? tq != forced : tq == 1) continue;
         const int nch = padded_chunks(a.n, tq);
         const int per_line = nch * tq;
         if (per_line > 512) continue;
@@ -645,6 +650,25 @@ const char* zncc_status_string(zncc_status s) {
 }
 
 uint64_t zncc_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
+    if (!c) return ZNCC_EINVAL;
+    c->err.clear();
+    if (value < 0) return fail(c, ZNCC_EINVAL, "tuning values are >= 0");
+    switch (key) {
+        case ZNCC_TUNE_ROW_MINB2: c->row_minb2 = value ? 1 : 0; break;
+        case ZNCC_TUNE_ROW_SPB: c->row_spb = value; break;
+        case ZNCC_TUNE_H_TQ:
+        case ZNCC_TUNE_V_TQ:
+            if (value != 0 && value != 2 && value != 4 && value != 8)
+                return fail(c, ZNCC_EINVAL, "lanes per chunk must be 0, 2, 4 or 8");
+            (key == ZNCC_TUNE_H_TQ ? c->h_tq : c->v_tq) = value;
+            break;
+        default: return fail(c, ZNCC_EINVAL, "unknown tuning key");
+    }
+    c->plans.clear();
+    return ZNCC_OK;
+}
 
 zncc_status zncc_profile_enable(zncc_ctx* c, int enable) {
     if (!c) return ZNCC_EINVAL;

@@ -32,6 +32,7 @@ struct RowArgs {
     const float4* coef;       // [H][W] horizontal DT coefficients (HPair)
     float s2;                 // (1 - K)^2
     WtaOut wta;               // (Wta)
+    int minb2;                // use the two-blocks-per-SM variant where the block allows
 };
 
 struct LineArgs {

@@ -32,8 +32,8 @@ namespace zncc {
 // block and serve all of its disparity slices; the window statistics of both images
 // (Sec. IV-B-1, Eq. (sum1)) come from the same packed columns: a column's pixel sum is
 // __dp4a(word, 0x01010101) and its sum of squares __dp4a(word, word), slid like P.
-template <int R, typename T, int MODE>
-__global__ void __launch_bounds__(512) k_zncc_row(RowArgs a) {
+template <int R, typename T, int MODE, int MINB>
+__global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(RowArgs a) {
     constexpr int l = 2 * R + 1;
     constexpr int NW = (l + 3) / 4;     // packed words per column
     extern __shared__ uint4 smem_u4[];
@@ -246,10 +246,18 @@ cudaError_t launch_zncc_row_impl(const RowArgs& a, int mode, int dtype, cudaStre
     dim3 grid(a.H, (nslices + a.spb - 1) / a.spb);
     dim3 block(a.nch * a.tq);
     const size_t smem = zncc_row_smem(R, mode, a, (int)block.x);
+    // blocks of up to 320 threads use the variant limited to 96 registers (two resident
+    // blocks per SM); larger blocks the 128-register one
     void (*fn)(RowArgs) = nullptr;
-    if (mode == kModeRaw) fn = dtype == 0 ? k_zncc_row<R, float, kModeRaw> : k_zncc_row<R, __half, kModeRaw>;
-    else if (mode == kModeHPair) fn = dtype == 0 ? k_zncc_row<R, float, kModeHPair> : k_zncc_row<R, __half, kModeHPair>;
-    else fn = k_zncc_row<R, float, kModeWta>;
+    if (block.x <= 320 && a.minb2) {
+        if (mode == kModeRaw) fn = dtype == 0 ? k_zncc_row<R, float, kModeRaw, 2> : k_zncc_row<R, __half, kModeRaw, 2>;
+        else if (mode == kModeHPair) fn = dtype == 0 ? k_zncc_row<R, float, kModeHPair, 2> : k_zncc_row<R, __half, kModeHPair, 2>;
+        else fn = k_zncc_row<R, float, kModeWta, 2>;
+    } else {
+        if (mode == kModeRaw) fn = dtype == 0 ? k_zncc_row<R, float, kModeRaw, 1> : k_zncc_row<R, __half, kModeRaw, 1>;
+        else if (mode == kModeHPair) fn = dtype == 0 ? k_zncc_row<R, float, kModeHPair, 1> : k_zncc_row<R, __half, kModeHPair, 1>;
+        else fn = k_zncc_row<R, float, kModeWta, 1>;
+    }
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, block, smem, st>>>(a);

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_PKG, "libzncc.so")
 ZNCC_OK, ZNCC_EINVAL, ZNCC_ENOMEM, ZNCC_ECUDA, ZNCC_EBUSY, ZNCC_ENOTREADY, ZNCC_ETIMEOUT, \
     ZNCC_EUNSUPPORTED = range(8)
 ZNCC_F32, ZNCC_F16 = 0, 1
+ZNCC_TUNE_ROW_MINB2, ZNCC_TUNE_ROW_SPB, ZNCC_TUNE_H_TQ, ZNCC_TUNE_V_TQ = 1, 2, 3, 4
 STATUS_NAMES = ["ZNCC_OK", "ZNCC_EINVAL", "ZNCC_ENOMEM", "ZNCC_ECUDA", "ZNCC_EBUSY",
                 "ZNCC_ENOTREADY", "ZNCC_ETIMEOUT", "ZNCC_EUNSUPPORTED"]
 
@@ -42,6 +43,7 @@ SIGNATURES = [
     ("zncc_last_error", ctypes.c_char_p, [_vp]),
     ("zncc_status_string", ctypes.c_char_p, [_i]),
     ("zncc_kernel_launch_count", ctypes.c_uint64, []),
+    ("zncc_set_tuning", _i, [_vp, _i, _i]),
     ("zncc_profile_enable", _i, [_vp, _i]),
     ("zncc_profile_read", _i, [_vp, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_uint64), _i]),
@@ -97,6 +99,7 @@ class ZnccContext:
         if st != ZNCC_OK:
             raise ZnccError(st, L.zncc_last_error(None).decode())
         self._h = h
+        self.stream = None
         self.W, self.H, self.D, self.win = int(width), int(height), int(max_disp), int(win)
         if stream is not None:
             self.set_stream(stream)
@@ -127,9 +130,13 @@ class ZnccContext:
         """Bind a torch.cuda.Stream (or a raw cudaStream_t int, or None)."""
         raw = getattr(stream, "cuda_stream", stream)
         self._check(lib().zncc_set_stream(self._h, raw or None))
+        self.stream = stream if hasattr(stream, "cuda_stream") else None
 
     def volume_bytes(self, dtype: int = ZNCC_F32) -> int:
         return int(lib().zncc_volume_bytes(self._h, dtype))
+
+    def set_tuning(self, key: int, value: int):
+        self._check(lib().zncc_set_tuning(self._h, int(key), int(value)))
 
     def profile_enable(self, on: bool = True):
         self._check(lib().zncc_profile_enable(self._h, 1 if on else 0))
