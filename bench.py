@@ -359,6 +359,89 @@ def run_gb300(args):
     return 0
 
 
+def run_batch(args):
+    """16 seeded pairs of uneven size, disparity range and window (sizes from {640x192,
+    1280x384, 1242x375, 1920x1080}, D from {64, 128, 192}, windows from {7, 9, 11}) through
+    one batched fused run per step, replayed from a captured CUDA graph; compared with the
+    same pairs run one zncc_run after another."""
+    import torch
+
+    from paper_2212_00476_gb300 import zncc as Z
+    from synth import batch_specs, make_pair
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    specs = batch_specs(16, 300)
+    stream = torch.cuda.Stream(device=dev)
+    ctxs, L, R, D, units = [], [], [], [], 0
+    for sp in specs:
+        p = make_pair(sp["h"], sp["w"], sp["max_disp"], sp["seed"], disp="planes", occlusion_frac=0.05)
+        ctxs.append(Z.ZnccContext(sp["w"], sp["h"], sp["max_disp"], sp["win"], stream=stream))
+        L.append(torch.from_numpy(p.left).to(dev))
+        R.append(torch.from_numpy(p.right).to(dev))
+        D.append(torch.empty((sp["h"], sp["w"]), dtype=torch.int16, device=dev))
+        units += sp["w"] * sp["h"] * sp["max_disp"]
+    storage = Z.ZNCC_F32 if args.storage == "f32" else Z.ZNCC_F16
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def batched():
+        Z.zncc_run_batch(ctxs, L, R, D, SIG_S, SIG_R, ITERS, storage)
+
+    def sequential():
+        for c, l, r, d in zip(ctxs, L, R, D):
+            c.zncc_run(l, r, d, SIG_S, SIG_R, ITERS, storage)
+
+    def timed(fn, graph=None):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                flush.zero_()
+                graph.replay() if graph else fn()
+        ms = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                graph.replay() if graph else fn()
+                b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return sum(ms) / len(ms)
+
+    with torch.cuda.stream(stream):
+        batched()                              # allocations and launch plans before capture
+        sequential()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        batched()
+    n0 = Z.launch_count()
+    ms_graph = timed(None, g)
+    ms_batch = timed(batched)
+    launches = (Z.launch_count() - n0) // max(1, args.steps + args.warmup)
+    ms_seq = timed(sequential)
+    line = {
+        "metric": "aggregate Gdisp/s, 16 uneven pairs (ZNCC+DT+WTA), batched vs one pair per launch",
+        "value": round(units / (ms_graph * 1e-3) / 1e9, 3), "unit": "Gdisp/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_graph, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+        "data": "synthetic",
+        "config": {"workload": "batch_uneven16: " + ", ".join(
+            f"{sp['w']}x{sp['h']}/D{sp['max_disp']}/w{sp['win']}" for sp in specs),
+            "disparities_per_step": units, "iters": ITERS,
+            "l2": "flushed before every timed step (256 MB write outside the step events)"},
+        "batched_graph_ms": round(ms_graph, 4), "batched_ms": round(ms_batch, 4),
+        "one_pair_per_launch_ms": round(ms_seq, 4),
+        "speedup_vs_one_pair_per_launch": round(ms_seq / ms_graph, 3),
+        "launches_per_batched_step": int(launches),
+    }
+    print(json.dumps(line))
+    for c in ctxs:
+        c.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,7 +449,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper_1280x384")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch_uneven16"], default="paper_1280x384")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
@@ -374,6 +457,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch_uneven16":
+        return run_batch(args)
     return run_gb300(args)
 
 

@@ -108,6 +108,20 @@ zncc_status zncc_run(zncc_ctx* ctx, const uint8_t* left, const uint8_t* right, i
                      float sigma_s, float sigma_r, int iters, zncc_dtype storage,
                      uint16_t* disp);
 
+/* The fused path over a batch of n <= 32 pairs of uneven sizes (each with its own context,
+ * created for its W, H, D and window): every step (the DT coefficients, the cost kernel,
+ * each DT pass pair) is one persistent launch over all pairs (the cost kernel: one per
+ * distinct window size), so that small pairs share the GPU instead of leaving it idle.
+ * All launches go to the stream of ctxs[0], on which errors and timings are recorded; the
+ * contexts must be distinct and on one device. lefts[i]/rights[i]: device images of pair i
+ * (row pitch pitches[i]); disps[i]: its device uint16 disparity map. The DT parameters,
+ * iteration count and storage type are common to the batch. Results are identical to n
+ * zncc_run calls. Capturable in a CUDA graph. */
+zncc_status zncc_run_batch(zncc_ctx* const* ctxs, const uint8_t* const* lefts,
+                           const uint8_t* const* rights, const int* pitches,
+                           uint16_t* const* disps, int n, float sigma_s, float sigma_r,
+                           int iters, zncc_dtype storage);
+
 /* zncc_run from host memory: copies the two images (row pitch `pitch`) to context-owned
  * device buffers, runs the fused path, copies the disparity map back to disp_host
  * (uint16 [H][W]) and synchronizes the stream before returning. Host buffers may be

@@ -56,8 +56,6 @@ struct zncc_ctx {
     float4* coefV = nullptr;      // [W][H]       vertical DT coefficients
     void* vol = nullptr;          // the fused path's intermediate volume (on first use)
     size_t vol_bytes = 0;
-    float* bestv = nullptr;       // [H][W] running WTA best across launches (on first use)
-    int* bestd = nullptr;         // [H][W]
     float* ahat = nullptr;        // [nahat][H][W] DT responses of an all-ones plane (F16 storage)
     int nahat = 0;
     int smem_max = 0;             // opt-in shared memory per block of the device
@@ -139,6 +137,33 @@ int slices_per_block(int nslices, int blocks_x) {
     return (nslices + groups - 1) / groups;
 }
 
+template <typename T>
+void free_dev(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void release(zncc_ctx* c) {
+    free_dev(c->coefH);
+    free_dev(c->coefV);
+    free_dev(c->vol);
+    c->vol_bytes = 0;
+    free_dev(c->ahat);
+    c->nahat = 0;
+    free_dev(c->img);
+    free_dev(c->disp);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    c->side = nullptr;
+    c->ev_fork = c->ev_join = nullptr;
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    c->events.clear();
+    c->records.clear();
+    c->events_used = 0;
+    c->plans.clear();
+}
+
 zncc_status check_images(zncc_ctx* c, const void* a, const void* b, int pitch) {
     if (!a || !b) return fail(c, ZNCC_EINVAL, "image pointer is NULL");
     if (pitch < c->W) return fail(c, ZNCC_EINVAL, "pitch is smaller than the width");
@@ -157,94 +182,127 @@ float scale_s2(float sigma_s) {
     return (float)(s * s);
 }
 
-zncc_status run_coef(zncc_ctx* c, const uint8_t* guide, int pitch, float sigma_s, float sigma_r) {
-    const float K = (float)exp(-1.0 / (double)sigma_s);
-    const float inv = (float)(1.0 / (255.0 * (double)sigma_r));
-    ZNCC_LAUNCH(c, K_COEF, launch_dt_coef(guide, pitch, c->W, c->H, K, inv, c->coefH, c->coefV, c->cur),
-                "DT coefficients");
-    return ZNCC_OK;
-}
-
 void free_dev_f(float*& p) {
     if (p) cudaFree(p);
     p = nullptr;
 }
 
-zncc_status ensure_best(zncc_ctx* c) {
-    if (c->bestv) return ZNCC_OK;
-    const size_t npix = (size_t)c->W * c->H;
-    cudaError_t e = cudaMalloc(&c->bestv, npix * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&c->bestd, npix * sizeof(int));
+zncc_status alloc_dev(zncc_ctx* c, void** p, size_t bytes, const char* what) {
+    cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        free_dev_f(c->bestv);
-        return fail(c, ZNCC_ENOMEM, std::string("WTA buffers: ") + cudaGetErrorString(e));
+        *p = nullptr;
+        return fail(c, e == cudaErrorMemoryAllocation ? ZNCC_ENOMEM : ZNCC_ECUDA,
+                    std::string(what) + ": " + cudaGetErrorString(e));
     }
     return ZNCC_OK;
 }
 
-// ZNCC row launches over the disparities [0, D): the band of a block covers its disparity
-// slices, so the slices per block shrink until the block fits in shared memory. In Wta
-// mode a block must see every disparity of its launch, so the disparity range is split
-// into several launches chained through the running best when it does not fit.
-zncc_status run_rows(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch, int mode, int dtype,
-                     void* vol, long long dstride, float s2, uint16_t* disp, int kind, const char* what) {
-    RowArgs a;
-    memset(&a, 0, sizeof(a));
-    a.left = left;
-    a.right = right;
-    a.pitch = pitch;
-    a.W = c->W;
-    a.H = c->H;
-    a.D = c->D;
-    a.tq = c->W <= 1024 ? 8 : (c->W <= 2048 ? 4 : 2);
-    a.nch = padded_chunks(c->W, a.tq);
-    a.vol = vol;
-    a.dstride = dstride;
-    a.d_out0 = 0;
-    a.vec = vol && (dstride % 4 == 0) && ((uintptr_t)vol % (dtype == 0 ? 16 : 8) == 0) ? 1 : 0;
-    a.coef = c->coefH;
-    a.s2 = s2;
-    a.minb2 = c->row_minb2;
-    const int threads = a.nch * a.tq;
-    const int ds = kG * a.tq;
-    const int nslices = (c->D + ds - 1) / ds;
-    if (mode != kModeWta) {
-        a.d_lo = 0;
-        a.d_hi = c->D;
-        a.spb = c->row_spb > 0 ? std::min(c->row_spb, nslices) : slices_per_block(nslices, c->H);
-        while (a.spb > 1 && zncc_row_smem_bytes(c->r, mode, a, threads) > (size_t)c->smem_max) --a.spb;
-        if (zncc_row_smem_bytes(c->r, mode, a, threads) > (size_t)c->smem_max)
-            return fail(c, ZNCC_EUNSUPPORTED, "image too wide for the cost kernel's shared memory");
-        ZNCC_LAUNCH(c, kind, launch_zncc_row(c->r, a, mode, dtype, c->cur), what);
-        return ZNCC_OK;
+// One pair of a (possibly batched) call: its context and this call's buffers. lc, the
+// launching context, is the first pair's: its stream carries every launch, and errors and
+// per-kernel timings are recorded on it.
+struct PairIO {
+    zncc_ctx* c;
+    const uint8_t* left;
+    const uint8_t* right;
+    int pitch;
+    uint16_t* disp;
+    void* vol;              // the pair's cost volume [H][W][dstride]
+    long long dstride;
+};
+
+// DT coefficients of every pair (guide = left image), one launch.
+zncc_status run_coef(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, float sigma_r) {
+    CoefBatch b;
+    memset(&b, 0, sizeof(b));
+    b.npairs = n;
+    const float K = (float)exp(-1.0 / (double)sigma_s);
+    const float inv = (float)(1.0 / (255.0 * (double)sigma_r));
+    long long t = 0;
+    for (int i = 0; i < n; ++i) {
+        CoefArgs& a = b.p[i];
+        a.guide = io[i].left;
+        a.pitch = io[i].pitch;
+        a.W = io[i].c->W;
+        a.H = io[i].c->H;
+        a.K = K;
+        a.inv_sr255 = inv;
+        a.coefH = io[i].c->coefH;
+        a.coefV = io[i].c->coefV;
+        a.thread0 = t;
+        t += dt_coef_threads(a.W, a.H);
     }
-    int per_launch = nslices;   // slices of one Wta launch
-    for (;;) {
-        a.d_lo = 0;
-        a.d_hi = std::min(c->D, per_launch * ds);
-        a.spb = per_launch;
-        if (zncc_row_smem_bytes(c->r, mode, a, threads) <= (size_t)c->smem_max) break;
-        if (per_launch == 1) return fail(c, ZNCC_EUNSUPPORTED, "image too wide for the cost kernel's shared memory");
-        per_launch = (per_launch + 1) / 2;
-    }
-    const int nlaunch = (nslices + per_launch - 1) / per_launch;
-    if (nlaunch > 1) ZNCC_TRY(ensure_best(c));
-    for (int g = 0; g < nlaunch; ++g) {
-        a.d_lo = g * per_launch * ds;
-        a.d_hi = std::min(c->D, (g + 1) * per_launch * ds);
-        a.spb = per_launch;
-        a.wta.bestv = c->bestv;
-        a.wta.bestd = c->bestd;
-        a.wta.disp = disp;
-        a.wta.first = g == 0;
-        a.wta.last = g == nlaunch - 1;
-        ZNCC_LAUNCH(c, kind, launch_zncc_row(c->r, a, mode, dtype, c->cur), what);
+    b.total_threads = t;
+    ZNCC_LAUNCH(lc, K_COEF, launch_dt_coef(b, lc->cur), "DT coefficients");
+    return ZNCC_OK;
+}
+
+// Cost-kernel launches over the pairs (one per window radius among them). A block covers
+// one row and a run of disparity slices (the band of a block spans its slices, so the run
+// shrinks until the block fits in shared memory); in Wta mode a block covers every
+// disparity of its row.
+zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype, float s2, int kind,
+                     const char* what) {
+    bool done[kMaxBatch] = {false};
+    for (int first = 0; first < n; ++first) {
+        if (done[first]) continue;
+        const int r = io[first].c->r;
+        RowBatch b;
+        memset(&b, 0, sizeof(b));
+        b.mode = mode;
+        int threads = 0;
+        size_t smem = 0;
+        bool minb2 = true;
+        for (int i = first; i < n; ++i) {
+            if (done[i] || io[i].c->r != r) continue;
+            done[i] = true;
+            zncc_ctx* c = io[i].c;
+            RowArgs& a = b.p[b.npairs++];
+            a.left = io[i].left;
+            a.right = io[i].right;
+            a.pitch = io[i].pitch;
+            a.W = c->W;
+            a.H = c->H;
+            a.D = c->D;
+            a.tq = c->W <= 1024 ? 8 : (c->W <= 2048 ? 4 : 2);
+            a.nch = padded_chunks(c->W, a.tq);
+            a.d_lo = 0;
+            a.d_hi = c->D;
+            a.vol = io[i].vol;
+            a.dstride = io[i].dstride;
+            a.d_out0 = 0;
+            a.vec = io[i].vol && (io[i].dstride % 4 == 0) &&
+                    ((uintptr_t)io[i].vol % (dtype == 0 ? 16 : 8) == 0) ? 1 : 0;
+            a.coef = c->coefH;
+            a.s2 = s2;
+            a.minb2 = c->row_minb2;
+            a.wta.disp = io[i].disp;
+            a.wta.first = 1;
+            a.wta.last = 1;
+            const int nthr = a.nch * a.tq;
+            const int nslices = (c->D + kG * a.tq - 1) / (kG * a.tq);
+            if (mode == kModeWta) a.spb = nslices;
+            else a.spb = c->row_spb > 0 ? std::min(c->row_spb, nslices) : slices_per_block(nslices, c->H);
+            while (a.spb > 1 && zncc_row_smem_bytes(r, mode, a, nthr) > (size_t)lc->smem_max) --a.spb;
+            const size_t sm = zncc_row_smem_bytes(r, mode, a, nthr);
+            if (sm > (size_t)lc->smem_max)
+                return fail(lc, ZNCC_EUNSUPPORTED, "the cost kernel's row band does not fit in shared memory");
+            a.item0 = b.total_items;
+            a.nitems = c->H * ((nslices + a.spb - 1) / a.spb);
+            b.total_items += a.nitems;
+            threads = std::max(threads, nthr);
+            smem = std::max(smem, sm);
+            minb2 = minb2 && a.minb2;
+        }
+        int bps = 0;
+        ZNCC_CUDA(lc, zncc_row_occupancy(r, mode, dtype, threads, smem, minb2, &bps), "occupancy query");
+        b.grid = std::max(1, std::min(b.total_items, lc->num_sms * std::max(1, bps)));
+        ZNCC_LAUNCH(lc, kind, launch_zncc_row(r, b, threads, smem, mode, dtype, lc->cur), what);
     }
     return ZNCC_OK;
 }
 
-// One DT pass pair along rows (horiz) or columns of a [H][W][dstride] volume.
+// One DT pass pair along rows (horiz) or columns of a pair's [H][W][dstride] volume.
 struct LinePass {
     void* vol = nullptr;           // output (and input unless src / ones)
     const void* src = nullptr;
@@ -259,41 +317,38 @@ struct LinePass {
     uint16_t* disp = nullptr;
     float s2 = 1.0f;
     int force_tq = 0;
-    bool ahat = false;             // a pass of the A_hat chain (profiled separately)
 };
 
-// The launch shape: among lane counts per chunk (8, 4, 2, or the forced one) and lines per
-// block that fit in shared memory, prefer whole 64-byte segments per chunk, then streaming
-// through shared memory (async), then at least two resident blocks per SM, then the most
-// resident warps. The grid is the resident blocks (persistent), each taking an equal run of
-// items.
+// The block shape of a pair's pass: among lane counts per chunk (8, 4, 2, or the forced
+// one) and lines per block that fit in shared memory, prefer whole 64-byte segments per
+// chunk, then streaming through shared memory (async), then at least two resident blocks
+// per SM, then the most resident warps. Chosen once per context and pass signature.
 zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
+    const int forced = p.force_tq ? p.force_tq : (p.horiz ? c->h_tq : c->v_tq);
     const long long key = ((((long long)p.horiz * 2 + p.mode) * 2 + p.dtype) * 2 + (a.vec ? 1 : 0)) * 16 +
-                          p.force_tq + ((long long)p.dcount << 20) + ((long long)(p.horiz ? c->h_tq : c->v_tq) << 40);
+                          forced + ((long long)p.dcount << 20);
     for (const LinePlan& pl : c->plans)
         if (pl.key == key) {
-            a.tq = pl.tq; a.lpc = pl.lpc; a.nch = pl.nch; a.async = pl.async; a.per_block = pl.per_block;
+            a.tq = pl.tq; a.lpc = pl.lpc; a.nch = pl.nch; a.async = pl.async;
             return ZNCC_OK;
         }
     LinePlan best{key, 0, 0, 0, 0, 0, 0};
     long long best_score = -1;
     const int tqs[4] = {8, 4, 2, 1};
-    const int forced = p.force_tq ? p.force_tq : (p.horiz ? c->h_tq : c->v_tq);
     for (int ti = 0; ti < 4; ++ti) {
         const int tq = tqs[ti];
         if (forced ? tq != forced : tq == 1) continue;
         const int nch = padded_chunks(a.n, tq);
         const int per_line = nch * tq;
         if (per_line > 512) continue;
-        // a chunk's lanes read tq * 4 contiguous entries per position: shapes whose segments
-        // are whole 64-byte DRAM bursts come first
         const bool whole_bursts = tq * 4 * (p.dtype == 0 ? 4 : 2) >= 64;
         for (int async = a.vec ? 1 : 0; async >= 0; --async) {
             for (int lpc = std::max(1, std::min(8, 256 / per_line)); lpc >= 1; --lpc) {
                 a.tq = tq; a.nch = nch; a.lpc = lpc; a.async = async;
-                if (line_pair_smem_bytes(p.mode, p.dtype, a) > (size_t)c->smem_max) continue;
+                const size_t smem = line_pair_smem_bytes(p.mode, p.dtype, a);
+                if (smem > (size_t)c->smem_max) continue;
                 int bps = 0;
-                ZNCC_CUDA(c, line_pair_occupancy(a, p.mode, p.dtype, &bps), "occupancy query");
+                ZNCC_CUDA(c, line_pair_occupancy(p.mode, p.dtype, lpc * per_line, smem, &bps), "occupancy query");
                 if (bps < 1) continue;
                 const long long warps = (long long)bps * lpc * per_line / 32;
                 const long long score = (whole_bursts ? 10000000LL : 0) + async * 1000000LL +
@@ -308,111 +363,163 @@ zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
     }
     if (best_score < 0) return fail(c, ZNCC_EUNSUPPORTED, "line too long for the DT kernel's shared memory");
     a.tq = best.tq; a.lpc = best.lpc; a.nch = best.nch; a.async = best.async;
-    const int nslices = (p.dcount + kG * a.tq - 1) / (kG * a.tq);
-    const int ngroups = (a.nlines + a.lpc - 1) / a.lpc;
-    const int grid_max = std::max(1, c->num_sms * best.blocks);
-    if (p.mode == kLineWta) {
-        const int gpb = (ngroups + grid_max - 1) / grid_max;
-        a.per_block = gpb * nslices;
-    } else {
-        const int total = ngroups * nslices;
-        a.per_block = (total + grid_max - 1) / grid_max;
-    }
-    best.per_block = a.per_block;
     c->plans.push_back(best);
     return ZNCC_OK;
 }
 
-zncc_status run_line_pair(zncc_ctx* c, const LinePass& p) {
-    LineArgs a;
-    memset(&a, 0, sizeof(a));
-    const int n = p.horiz ? c->W : c->H;
-    a.vol = p.vol;
-    a.src = p.src;
-    a.src_ones = p.ones ? 1 : 0;
-    a.elem_stride = p.horiz ? p.dstride : (long long)c->W * p.dstride;
-    a.line_stride = p.horiz ? (long long)c->W * p.dstride : p.dstride;
-    a.n = n;
-    a.nlines = p.horiz ? c->H : c->W;
-    a.dcount = p.dcount;
-    a.d_base = 0;
-    a.ahat_in = p.ahat_in;
-    a.ahat_out = p.ahat_out;
-    a.coef = p.horiz ? c->coefH : c->coefV;
-    a.coef_line_stride = p.horiz ? c->W : c->H;
-    a.s2 = p.s2;
-    const void* in = p.src ? p.src : p.vol;
-    a.vec = (p.dstride % 4 == 0) && ((uintptr_t)p.vol % (p.dtype == 0 ? 16 : 8) == 0) &&
-                    ((uintptr_t)in % (p.dtype == 0 ? 16 : 8) == 0) ? 1 : 0;
-    a.wta.disp = p.disp;
-    a.wta.first = 1;
-    a.wta.last = 1;
-    a.pix_line = p.horiz ? c->W : 1;
-    a.pix_pos = p.horiz ? 1 : c->W;
-    ZNCC_TRY(plan_line_pass(c, a, p));
-    const int kind = p.ahat ? K_AHAT
-                     : (p.horiz ? K_DT_HPAIR : (p.mode == kLineWta ? K_DT_VPAIR_WTA : K_DT_VPAIR));
-    ZNCC_LAUNCH(c, kind, launch_line_pair(a, p.mode, p.dtype, c->cur), p.horiz ? "DT horizontal pair" : "DT vertical pair");
+// One line-pair launch over the passes of several pairs (the same mode and storage).
+zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passes, int n, int kind) {
+    LineBatch b;
+    memset(&b, 0, sizeof(b));
+    const int mode = passes[0].mode, dtype = passes[0].dtype;
+    int threads = 0;
+    size_t stage = 0, rest = 0;
+    for (int i = 0; i < n; ++i) {
+        zncc_ctx* c = ctxs[i];
+        const LinePass& p = passes[i];
+        LineArgs& a = b.p[b.npairs++];
+        a.vol = p.vol;
+        a.src = p.src;
+        a.src_ones = p.ones ? 1 : 0;
+        a.elem_stride = p.horiz ? p.dstride : (long long)c->W * p.dstride;
+        a.line_stride = p.horiz ? (long long)c->W * p.dstride : p.dstride;
+        a.n = p.horiz ? c->W : c->H;
+        a.nlines = p.horiz ? c->H : c->W;
+        a.dcount = p.dcount;
+        a.d_base = 0;
+        a.ahat_in = p.ahat_in;
+        a.ahat_out = p.ahat_out;
+        a.coef = p.horiz ? c->coefH : c->coefV;
+        a.coef_line_stride = p.horiz ? c->W : c->H;
+        a.s2 = p.s2;
+        const void* in = p.src ? p.src : p.vol;
+        const size_t al = p.dtype == 0 ? 16 : 8;
+        a.vec = (p.dstride % 4 == 0) && ((uintptr_t)p.vol % al == 0) && ((uintptr_t)in % al == 0) ? 1 : 0;
+        a.wta.disp = p.disp;
+        a.wta.first = 1;
+        a.wta.last = 1;
+        a.pix_line = p.horiz ? c->W : 1;
+        a.pix_pos = p.horiz ? 1 : c->W;
+        if (plan_line_pass(c, a, p) != ZNCC_OK) return fail(lc, ZNCC_EUNSUPPORTED, c->err);
+        const int nslices = (a.dcount + kG * a.tq - 1) / (kG * a.tq);
+        const int ngroups = (a.nlines + a.lpc - 1) / a.lpc;
+        a.step0 = b.total_steps;
+        a.nsteps = ngroups * nslices;
+        a.item0 = b.total_items;
+        a.nitems = mode == kLineWta ? ngroups : a.nsteps;
+        b.total_steps += a.nsteps;
+        b.total_items += a.nitems;
+        threads = std::max(threads, a.lpc * a.nch * a.tq);
+        const size_t st = line_stage_bytes(dtype, a);
+        stage = std::max(stage, st);
+        rest = std::max(rest, line_pair_smem_bytes(mode, dtype, a) - st);
+    }
+    b.stage_bytes = (long long)stage;
+    const size_t smem = stage + rest;
+    if (smem > (size_t)lc->smem_max) return fail(lc, ZNCC_EUNSUPPORTED, "batched DT pass exceeds shared memory");
+    int bps = 0;
+    ZNCC_CUDA(lc, line_pair_occupancy(mode, dtype, threads, smem, &bps), "occupancy query");
+    b.grid = std::max(1, std::min(b.total_items, lc->num_sms * std::max(1, bps)));
+    ZNCC_LAUNCH(lc, kind, launch_line_batch(b, threads, smem, mode, dtype, lc->cur), "DT pass pair");
     return ZNCC_OK;
 }
 
-// The scaled DT responses of an all-ones plane after pairs 1 .. n (A_hat, Eqs. (3)-(6) on a
-// constant input), one [H][W] map each: the per-pixel bound of |aggregated cost|.
-zncc_status run_ahat_chain(zncc_ctx* c, int n, float s2) {
-    const size_t npix = (size_t)c->W * c->H;
-    if (c->nahat < n) {
-        free_dev_f(c->ahat);
-        c->nahat = 0;
-        cudaError_t e = cudaMalloc(&c->ahat, npix * n * sizeof(float));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(c, ZNCC_ENOMEM, std::string("A_hat maps: ") + cudaGetErrorString(e));
-        }
-        c->nahat = n;
-    }
-    for (int p = 1; p <= n; ++p) {
-        LinePass lp;
-        lp.vol = c->ahat + (size_t)(p - 1) * npix;
-        lp.src = p == 1 ? nullptr : c->ahat + (size_t)(p - 2) * npix;
-        lp.ones = p == 1;
-        lp.dstride = 1;
-        lp.dcount = 1;
-        lp.dtype = 0;
-        lp.horiz = (p % 2) == 1;
-        lp.s2 = s2;
-        lp.force_tq = 1;
-        lp.ahat = true;
-        ZNCC_TRY(run_line_pair(c, lp));
-    }
-    return ZNCC_OK;
-}
-
-template <typename T>
-void free_dev(T*& p) {
-    if (p) cudaFree(p);
-    p = nullptr;
-}
-
-void release(zncc_ctx* c) {
-    free_dev(c->coefH);
-    free_dev(c->coefV);
+zncc_status ensure_volume(zncc_ctx* c, int dtype, long long dstride) {
+    const size_t need = (size_t)c->W * c->H * (size_t)dstride * (dtype == 0 ? 4 : 2);
+    if (c->vol_bytes >= need) return ZNCC_OK;
     free_dev(c->vol);
-    free_dev(c->bestv);
-    free_dev(c->bestd);
-    free_dev(c->ahat);
+    c->vol_bytes = 0;
+    ZNCC_TRY(alloc_dev(c, &c->vol, need, "cost volume"));
+    c->vol_bytes = need;
+    return ZNCC_OK;
+}
+
+zncc_status ensure_ahat(zncc_ctx* c, int n) {
+    if (c->nahat >= n) return ZNCC_OK;
+    free_dev_f(c->ahat);
     c->nahat = 0;
-    c->plans.clear();
-    free_dev(c->img);
-    free_dev(c->disp);
-    if (c->side) cudaStreamDestroy(c->side);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
-    c->side = nullptr;
-    c->ev_fork = c->ev_join = nullptr;
-    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
-    c->events.clear();
-    c->records.clear();
-    c->events_used = 0;
+    ZNCC_TRY(alloc_dev(c, (void**)&c->ahat, (size_t)c->W * c->H * n * sizeof(float), "A_hat maps"));
+    c->nahat = n;
+    return ZNCC_OK;
+}
+
+// The fused path over n pairs that share the DT parameters and the storage type: the
+// coefficients, the cost kernel with the first horizontal pair, the remaining pairs, and
+// WTA in the last vertical pair; every step is one launch for all pairs (one per window
+// radius for the cost kernel).
+zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigma_r, int iters,
+                      int storage) {
+    if (iters == 0) return run_rows(lc, io, n, kModeWta, 0, 0.0f, K_ZNCC_WTA, "ZNCC + WTA");
+    const int dt = storage == ZNCC_F32 ? 0 : 1;
+    zncc_ctx* ctxs[kMaxBatch];
+    for (int i = 0; i < n; ++i) {
+        ctxs[i] = io[i].c;
+        io[i].dstride = (io[i].c->D + 3) / 4 * 4;     // padded so that every access is vectorised
+        if (ensure_volume(io[i].c, dt, io[i].dstride) != ZNCC_OK) return fail(lc, ZNCC_ENOMEM, io[i].c->err);
+        io[i].vol = io[i].c->vol;
+    }
+    ZNCC_TRY(run_coef(lc, io, n, sigma_s, sigma_r));
+    const float s2 = scale_s2(sigma_s);
+    const int npairs = 2 * iters;
+    // Half storage keeps each stored pair p >= 2 divided by A_hat_p (the per-pixel bound of
+    // |cost|), so that it stays inside the half range wherever the guide isolates a pixel;
+    // the next pair multiplies it back. The factor is the same for every d of a pixel. The
+    // A_hat maps depend only on the guide: they are computed on a second stream,
+    // concurrently with the cost kernel, and joined before the first stored pair is read.
+    const bool norm = dt == 1 && npairs > 2;
+    if (norm) {
+        for (int i = 0; i < n; ++i)
+            if (ensure_ahat(io[i].c, npairs - 1) != ZNCC_OK) return fail(lc, ZNCC_ENOMEM, io[i].c->err);
+        if (!lc->side) {
+            ZNCC_CUDA(lc, cudaStreamCreateWithFlags(&lc->side, cudaStreamNonBlocking), "side stream");
+            ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_fork, cudaEventDisableTiming), "fork event");
+            ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_join, cudaEventDisableTiming), "join event");
+        }
+        ZNCC_CUDA(lc, cudaEventRecord(lc->ev_fork, lc->stream), "fork");
+        ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->side, lc->ev_fork, 0), "fork");
+        lc->cur = lc->side;
+        zncc_status st = ZNCC_OK;
+        for (int p = 1; p <= npairs - 1 && st == ZNCC_OK; ++p) {
+            LinePass lp[kMaxBatch];
+            for (int i = 0; i < n; ++i) {
+                const size_t npix = (size_t)io[i].c->W * io[i].c->H;
+                lp[i].vol = io[i].c->ahat + (size_t)(p - 1) * npix;
+                lp[i].src = p == 1 ? nullptr : io[i].c->ahat + (size_t)(p - 2) * npix;
+                lp[i].ones = p == 1;
+                lp[i].dstride = 1;
+                lp[i].dcount = 1;
+                lp[i].dtype = 0;
+                lp[i].horiz = (p % 2) == 1;
+                lp[i].s2 = s2;
+                lp[i].force_tq = 1;
+            }
+            st = run_lines(lc, ctxs, lp, n, K_AHAT);
+        }
+        lc->cur = lc->stream;
+        ZNCC_TRY(st);
+        ZNCC_CUDA(lc, cudaEventRecord(lc->ev_join, lc->side), "join");
+    }
+    ZNCC_TRY(run_rows(lc, io, n, kModeHPair, dt, s2, K_ZNCC_HPAIR, "ZNCC + horizontal DT pair"));
+    if (norm) ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_join, 0), "join of the A_hat stream");
+    for (int pair = 2; pair <= npairs; ++pair) {    // pair 1 is the cost kernel's
+        LinePass lp[kMaxBatch];
+        for (int i = 0; i < n; ++i) {
+            const size_t npix = (size_t)io[i].c->W * io[i].c->H;
+            lp[i].vol = io[i].vol;
+            lp[i].dstride = io[i].dstride;
+            lp[i].dcount = io[i].c->D;
+            lp[i].dtype = dt;
+            lp[i].s2 = s2;
+            lp[i].horiz = (pair % 2) == 1;
+            lp[i].mode = pair == npairs ? kLineWta : kLineStore;
+            lp[i].disp = pair == npairs ? io[i].disp : nullptr;
+            lp[i].ahat_in = norm && pair - 1 >= 2 ? io[i].c->ahat + (size_t)(pair - 2) * npix : nullptr;
+            lp[i].ahat_out = norm && pair < npairs ? io[i].c->ahat + (size_t)(pair - 1) * npix : nullptr;
+        }
+        const int kind = pair % 2 ? K_DT_HPAIR : (pair == npairs ? K_DT_VPAIR_WTA : K_DT_VPAIR);
+        ZNCC_TRY(run_lines(lc, ctxs, lp, n, kind));
+    }
+    return ZNCC_OK;
 }
 
 }  // namespace
@@ -494,7 +601,8 @@ zncc_status zncc_cost_volume(zncc_ctx* c, const uint8_t* left, const uint8_t* ri
     ZNCC_TRY(check_images(c, left, right, pitch));
     if (!cost) return fail(c, ZNCC_EINVAL, "cost pointer is NULL");
     if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
-    return run_rows(c, left, right, pitch, kModeRaw, dtype, cost, c->D, 0.0f, nullptr, K_ZNCC_RAW, "ZNCC cost");
+    PairIO io{c, left, right, pitch, nullptr, cost, c->D};
+    return run_rows(c, &io, 1, kModeRaw, dtype, 0.0f, K_ZNCC_RAW, "ZNCC cost");
 }
 
 zncc_status dt_aggregate(zncc_ctx* c, const uint8_t* guide, int pitch, void* cost, zncc_dtype dtype,
@@ -507,19 +615,19 @@ zncc_status dt_aggregate(zncc_ctx* c, const uint8_t* guide, int pitch, void* cos
     if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
     ZNCC_TRY(check_dt(c, sigma_s, sigma_r, iters));
     if (iters == 0) return ZNCC_OK;
-    ZNCC_TRY(run_coef(c, guide, pitch, sigma_s, sigma_r));
-    const float s2 = scale_s2(sigma_s);
+    PairIO io{c, guide, guide, pitch, nullptr, cost, c->D};
+    ZNCC_TRY(run_coef(c, &io, 1, sigma_s, sigma_r));
     LinePass lp;
     lp.vol = cost;
     lp.dstride = c->D;
     lp.dcount = c->D;
     lp.dtype = dtype;
-    lp.s2 = s2;
+    lp.s2 = scale_s2(sigma_s);
     for (int it = 0; it < iters; ++it) {
         lp.horiz = true;
-        ZNCC_TRY(run_line_pair(c, lp));
+        ZNCC_TRY(run_lines(c, &c, &lp, 1, K_DT_HPAIR));
         lp.horiz = false;
-        ZNCC_TRY(run_line_pair(c, lp));
+        ZNCC_TRY(run_lines(c, &c, &lp, 1, K_DT_VPAIR));
     }
     return ZNCC_OK;
 }
@@ -541,67 +649,32 @@ zncc_status zncc_run(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int
     if (!disp) return fail(c, ZNCC_EINVAL, "disp pointer is NULL");
     if (storage != ZNCC_F32 && storage != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
     ZNCC_TRY(check_dt(c, sigma_s, sigma_r, iters));
-    const size_t npix = (size_t)c->W * c->H;
+    PairIO io{c, left, right, pitch, disp, nullptr, 0};
+    return run_fused(c, &io, 1, sigma_s, sigma_r, iters, storage);
+}
 
-    if (iters == 0) return run_rows(c, left, right, pitch, kModeWta, 0, nullptr, 0, 0.0f, disp, K_ZNCC_WTA, "ZNCC + WTA");
-    const int dt = storage == ZNCC_F32 ? 0 : 1;
-    const long long dstride = (c->D + 3) / 4 * 4;   // padded so every access is vectorised
-    const size_t need = npix * (size_t)dstride * (dt == 0 ? 4 : 2);
-    if (c->vol_bytes < need) {
-        free_dev(c->vol);
-        c->vol_bytes = 0;
-        cudaError_t e = cudaMalloc(&c->vol, need);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(c, e == cudaErrorMemoryAllocation ? ZNCC_ENOMEM : ZNCC_ECUDA,
-                        std::string("cost volume allocation: ") + cudaGetErrorString(e));
-        }
-        c->vol_bytes = need;
+zncc_status zncc_run_batch(zncc_ctx* const* ctxs, const uint8_t* const* lefts, const uint8_t* const* rights,
+                           const int* pitches, uint16_t* const* disps, int n, float sigma_s, float sigma_r,
+                           int iters, zncc_dtype storage) {
+    if (!ctxs || !ctxs[0] || n < 1) return ZNCC_EINVAL;
+    zncc_ctx* lc = ctxs[0];
+    lc->err.clear();
+    if (n > kMaxBatch) return fail(lc, ZNCC_EINVAL, "at most 32 pairs per batch");
+    if (!lefts || !rights || !pitches || !disps) return fail(lc, ZNCC_EINVAL, "a batch array is NULL");
+    if (storage != ZNCC_F32 && storage != ZNCC_F16) return fail(lc, ZNCC_EINVAL, "unknown dtype");
+    ZNCC_TRY(check_dt(lc, sigma_s, sigma_r, iters));
+    PairIO io[kMaxBatch];
+    for (int i = 0; i < n; ++i) {
+        zncc_ctx* c = ctxs[i];
+        if (!c) return fail(lc, ZNCC_EINVAL, "a context is NULL");
+        if (c->device != lc->device) return fail(lc, ZNCC_EINVAL, "the contexts of a batch share one device");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return fail(lc, ZNCC_EINVAL, "a context appears twice in the batch");
+        if (check_images(c, lefts[i], rights[i], pitches[i]) != ZNCC_OK) return fail(lc, ZNCC_EINVAL, c->err);
+        if (!disps[i]) return fail(lc, ZNCC_EINVAL, "disp pointer is NULL");
+        io[i] = PairIO{c, lefts[i], rights[i], pitches[i], disps[i], nullptr, 0};
     }
-    ZNCC_TRY(run_coef(c, left, pitch, sigma_s, sigma_r));
-    const float s2 = scale_s2(sigma_s);
-    if (dt == 1 && iters > 1) {
-        // the A_hat maps of half storage depend only on the guide: computed on a second stream,
-        // concurrently with the cost kernel, and joined before the first stored pair is read
-        if (!c->side) {
-            ZNCC_CUDA(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
-            ZNCC_CUDA(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "fork event");
-            ZNCC_CUDA(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "join event");
-        }
-        ZNCC_CUDA(c, cudaEventRecord(c->ev_fork, c->stream), "fork");
-        ZNCC_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork");
-        c->cur = c->side;
-        const zncc_status st = run_ahat_chain(c, 2 * iters - 1, s2);
-        c->cur = c->stream;
-        ZNCC_TRY(st);
-        ZNCC_CUDA(c, cudaEventRecord(c->ev_join, c->side), "join");
-    }
-    ZNCC_TRY(run_rows(c, left, right, pitch, kModeHPair, dt, c->vol, dstride, s2, nullptr, K_ZNCC_HPAIR,
-                      "ZNCC + horizontal DT pair"));
-    // Half storage keeps each stored pair p >= 2 divided by A_hat_p (the per-pixel bound of
-    // |cost|), so that it stays inside the half range wherever the guide isolates a pixel;
-    // the next pair multiplies it back. The factor is the same for every d of a pixel.
-    const bool norm = dt == 1;
-    const int npairs = 2 * iters;
-    const size_t ahat_sz = npix;
-    const bool fork = norm && npairs > 2;
-    if (fork) ZNCC_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join of the A_hat stream");
-    (void)ahat_sz;
-    LinePass lp;
-    lp.vol = c->vol;
-    lp.dstride = dstride;
-    lp.dcount = c->D;
-    lp.dtype = dt;
-    lp.s2 = s2;
-    for (int pair = 2; pair <= npairs; ++pair) {    // pair 1 is the cost kernel's
-        lp.horiz = (pair % 2) == 1;
-        lp.mode = pair == npairs ? kLineWta : kLineStore;
-        lp.disp = pair == npairs ? disp : nullptr;
-        lp.ahat_in = norm && pair - 1 >= 2 ? c->ahat + (size_t)(pair - 2) * ahat_sz : nullptr;
-        lp.ahat_out = norm && pair < npairs ? c->ahat + (size_t)(pair - 1) * ahat_sz : nullptr;
-        ZNCC_TRY(run_line_pair(c, lp));
-    }
-    return ZNCC_OK;
+    return run_fused(lc, io, n, sigma_s, sigma_r, iters, storage);
 }
 
 zncc_status zncc_run_host(zncc_ctx* c, const uint8_t* left_host, const uint8_t* right_host, int pitch,

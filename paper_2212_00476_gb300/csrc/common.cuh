@@ -137,7 +137,7 @@ __device__ __forceinline__ void lds4(const __half* p, float (&o)[4]) {
 // warps per line. The result is scaled by s2 = (1-K)^2, or per position by mul[p].y when
 // mul (cidx layout) is given. after_forward() runs once the forward sweep has consumed the
 // input values (the caller may then overwrite where they came from). Synchronizes the
-// block twice.
+// block twice; threads with active == false (whole warps) only take part in the barriers.
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
@@ -147,117 +147,126 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
                                         int plane, int k, int tq, int dq, int lane, int wl,
                                         int nwl, float* sa, float4* sb, float s2,
                                         const float2* __restrict__ mul = nullptr,
-                                        Hook after_forward = Hook()) {
+                                        Hook after_forward = Hook(), bool active = true) {
     const int start = k * kL;
-    // forward sweep of the chunk, zero carry-in
-    float u[4] = {0.f, 0.f, 0.f, 0.f};
+    float A = 0.f, Ae = 1.f;
+    float B[4], Be[4], F[4], G[4];
 #pragma unroll
-    for (int i = 0; i < kL; ++i) {
-        const float w = co[cidx(start + i, plane)].x;
+    for (int j = 0; j < 4; ++j) B[j] = Be[j] = F[j] = G[j] = 0.f;
+
+    // ---- phase 1: forward sweep of the chunk with zero carry-in, warp scan of its map ----
+    if (active) {
+        float u[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            u[j] = fmaf(w, u[j], v[i][j]);
-            v[i][j] = u[j];
+        for (int i = 0; i < kL; ++i) {
+            const float w = co[cidx(start + i, plane)].x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                u[j] = fmaf(w, u[j], v[i][j]);
+                v[i][j] = u[j];
+            }
         }
     }
     after_forward();
-    // forward carries: inclusive scan of (A, B) over the warp's chunks, then the warps before
-    float A = co[cidx(start + kL - 1, plane)].y;
-    float B[4] = {u[0], u[1], u[2], u[3]};
-    for (int off = tq; off < 32; off <<= 1) {
-        const float A2 = __shfl_up_sync(kFull, A, off);
-        float B2[4];
+    if (active) {
+        A = co[cidx(start + kL - 1, plane)].y;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) B2[j] = __shfl_up_sync(kFull, B[j], off);
-        if (lane >= off) {
+        for (int j = 0; j < 4; ++j) B[j] = v[kL - 1][j];
+        for (int off = tq; off < 32; off <<= 1) {
+            const float A2 = __shfl_up_sync(kFull, A, off);
+            float B2[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) B[j] = fmaf(A, B2[j], B[j]);
-            A *= A2;
+            for (int j = 0; j < 4; ++j) B2[j] = __shfl_up_sync(kFull, B[j], off);
+            if (lane >= off) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) B[j] = fmaf(A, B2[j], B[j]);
+                A *= A2;
+            }
         }
-    }
-    float Ae = __shfl_up_sync(kFull, A, tq);
-    float Be[4];
+        Ae = __shfl_up_sync(kFull, A, tq);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) Be[j] = __shfl_up_sync(kFull, B[j], tq);
-    if (lane < tq) {
-        Ae = 1.0f;
-        Be[0] = Be[1] = Be[2] = Be[3] = 0.0f;
-    }
-    if (lane >= 32 - tq) {
-        sa[wl * tq + dq] = A;
-        sb[wl * tq + dq] = make_float4(B[0], B[1], B[2], B[3]);
+        for (int j = 0; j < 4; ++j) Be[j] = __shfl_up_sync(kFull, B[j], tq);
+        if (lane < tq) {
+            Ae = 1.0f;
+            Be[0] = Be[1] = Be[2] = Be[3] = 0.0f;
+        }
+        if (lane >= 32 - tq) {
+            sa[wl * tq + dq] = A;
+            sb[wl * tq + dq] = make_float4(B[0], B[1], B[2], B[3]);
+        }
     }
     __syncthreads();
-    float F[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int w2 = 0; w2 < wl; ++w2) {
-        const float a2 = sa[w2 * tq + dq];
-        const float4 b2 = sb[w2 * tq + dq];
-        F[0] = fmaf(a2, F[0], b2.x);
-        F[1] = fmaf(a2, F[1], b2.y);
-        F[2] = fmaf(a2, F[2], b2.z);
-        F[3] = fmaf(a2, F[3], b2.w);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) F[j] = fmaf(Ae, F[j], Be[j]);
 
-    // forward correction, then the backward sweep of the chunk with zero carry-in
-    float h[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int i = kL - 1; i >= 0; --i) {
-        const float4 c = co[cidx(start + i, plane)];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float ft = fmaf(c.y, F[j], v[i][j]);
-            h[j] = fmaf(c.z, h[j], ft);
-            v[i][j] = h[j];
+    // ---- phase 2: carry from the warps before, corrected forward values, backward sweep ----
+    if (active) {
+        for (int w2 = 0; w2 < wl; ++w2) {
+            const float a2 = sa[w2 * tq + dq];
+            const float4 b2 = sb[w2 * tq + dq];
+            F[0] = fmaf(a2, F[0], b2.x);
+            F[1] = fmaf(a2, F[1], b2.y);
+            F[2] = fmaf(a2, F[2], b2.z);
+            F[3] = fmaf(a2, F[3], b2.w);
         }
-    }
-    // backward carries: the same scan from the right
-    A = co[cidx(start, plane)].w;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) B[j] = h[j];
-    for (int off = tq; off < 32; off <<= 1) {
-        const float A2 = __shfl_down_sync(kFull, A, off);
-        float B2[4];
+        for (int j = 0; j < 4; ++j) F[j] = fmaf(Ae, F[j], Be[j]);
+        float h[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) B2[j] = __shfl_down_sync(kFull, B[j], off);
-        if (lane + off < 32) {
+        for (int i = kL - 1; i >= 0; --i) {
+            const float4 c = co[cidx(start + i, plane)];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) B[j] = fmaf(A, B2[j], B[j]);
-            A *= A2;
+            for (int j = 0; j < 4; ++j) {
+                const float ft = fmaf(c.y, F[j], v[i][j]);
+                h[j] = fmaf(c.z, h[j], ft);
+                v[i][j] = h[j];
+            }
         }
-    }
-    Ae = __shfl_down_sync(kFull, A, tq);
+        A = co[cidx(start, plane)].w;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) Be[j] = __shfl_down_sync(kFull, B[j], tq);
-    if (lane >= 32 - tq) {
-        Ae = 1.0f;
-        Be[0] = Be[1] = Be[2] = Be[3] = 0.0f;
-    }
-    if (lane < tq) {
-        sa[(nwl + wl) * tq + dq] = A;
-        sb[(nwl + wl) * tq + dq] = make_float4(B[0], B[1], B[2], B[3]);
+        for (int j = 0; j < 4; ++j) B[j] = h[j];
+        for (int off = tq; off < 32; off <<= 1) {
+            const float A2 = __shfl_down_sync(kFull, A, off);
+            float B2[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) B2[j] = __shfl_down_sync(kFull, B[j], off);
+            if (lane + off < 32) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) B[j] = fmaf(A, B2[j], B[j]);
+                A *= A2;
+            }
+        }
+        Ae = __shfl_down_sync(kFull, A, tq);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Be[j] = __shfl_down_sync(kFull, B[j], tq);
+        if (lane >= 32 - tq) {
+            Ae = 1.0f;
+            Be[0] = Be[1] = Be[2] = Be[3] = 0.0f;
+        }
+        if (lane < tq) {
+            sa[(nwl + wl) * tq + dq] = A;
+            sb[(nwl + wl) * tq + dq] = make_float4(B[0], B[1], B[2], B[3]);
+        }
     }
     __syncthreads();
-    float G[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int w2 = nwl - 1; w2 > wl; --w2) {
-        const float a2 = sa[(nwl + w2) * tq + dq];
-        const float4 b2 = sb[(nwl + w2) * tq + dq];
-        G[0] = fmaf(a2, G[0], b2.x);
-        G[1] = fmaf(a2, G[1], b2.y);
-        G[2] = fmaf(a2, G[2], b2.z);
-        G[3] = fmaf(a2, G[3], b2.w);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) G[j] = fmaf(Ae, G[j], Be[j]);
 
-    // backward correction and the s^2 of the scaled form (or the per-position multiplier)
+    // ---- phase 3: carry from the warps after, backward correction, scale ----
+    if (active) {
+        for (int w2 = nwl - 1; w2 > wl; --w2) {
+            const float a2 = sa[(nwl + w2) * tq + dq];
+            const float4 b2 = sb[(nwl + w2) * tq + dq];
+            G[0] = fmaf(a2, G[0], b2.x);
+            G[1] = fmaf(a2, G[1], b2.y);
+            G[2] = fmaf(a2, G[2], b2.z);
+            G[3] = fmaf(a2, G[3], b2.w);
+        }
 #pragma unroll
-    for (int i = 0; i < kL; ++i) {
-        const float b = co[cidx(start + i, plane)].w;
-        const float m = mul ? mul[cidx(start + i, plane)].y : s2;
+        for (int j = 0; j < 4; ++j) G[j] = fmaf(Ae, G[j], Be[j]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[i][j] = m * fmaf(b, G[j], v[i][j]);
+        for (int i = 0; i < kL; ++i) {
+            const float b = co[cidx(start + i, plane)].w;
+            const float m = mul ? mul[cidx(start + i, plane)].y : s2;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[i][j] = m * fmaf(b, G[j], v[i][j]);
+        }
     }
 }
 
@@ -295,20 +304,8 @@ struct WtaRegs {
     }
 };
 
-// ---- per-thread WTA running best over the slices a block visits -------------------------
-// Entry (i, k, dq) of a line's [kL][nch][tq] array of (value, d) pairs belongs to one thread;
-// a slice folds the thread's 4 disparities into it without any cross-lane traffic, and the
-// lanes of a pixel are reduced once, after the last slice.
-__device__ __forceinline__ void wta_fold_own(float2* rb, const float (&c)[4], int nvalid, int d_first) {
-    float best = rb->x;
-    int bd = __float_as_int(rb->y);
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (j < nvalid && c[j] > best) { best = c[j]; bd = d_first + j; }
-    *rb = make_float2(best, __int_as_float(bd));
-}
-
-// Reduces the tq lanes of a pixel (consecutive lanes of a warp); all lanes get the result.
+// Reduces the tq lanes of a pixel (consecutive lanes of a warp); all lanes get the result:
+// the largest value, and the smallest d among equal values.
 __device__ __forceinline__ void wta_reduce_lanes(float2 e, int tq, float& best, int& bd) {
     best = e.x;
     bd = __float_as_int(e.y);

@@ -66,24 +66,28 @@ cudaError_t launch_window_stats(const uint8_t* img, int pitch, int W, int H, int
 //   (w(p), prod_{j=c..p} w(j), w(p+1), prod_{j=p..c+15} w(j+1)),  c = chunk start (16 | c).
 // coefH is [H][W]; coefV is [W][H] (a column is contiguous). One thread per position; the
 // 16 positions of a chunk are 16 consecutive lanes, whose products are shuffle scans.
-__global__ void k_dt_coef(const uint8_t* __restrict__ g, int pitch, int W, int H, float K,
-                          float inv_sr255, float4* __restrict__ coefH, float4* __restrict__ coefV) {
+__global__ void k_dt_coef(const __grid_constant__ CoefBatch b) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int pi = 0;
+    while (pi + 1 < b.npairs && gid >= b.p[pi + 1].thread0) ++pi;
+    const CoefArgs& a = b.p[pi];
+    const int W = a.W, H = a.H;
     const int nchH = (W + kL - 1) / kL, nchV = (H + kL - 1) / kL;
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    int chunk = gid / kL;
-    const int i = gid & (kL - 1);
+    const long long local = gid - a.thread0;
+    int chunk = (int)(local / kL);
+    const int i = (int)(local & (kL - 1));
     const bool horiz = chunk < H * nchH;
     if (!horiz) chunk -= H * nchH;
-    const bool live = horiz || chunk < W * nchV;
+    const bool live = gid < b.total_threads && (horiz || chunk < W * nchV);
     const int n = horiz ? W : H;
     const int nchl = horiz ? nchH : nchV;
     const int line = live ? chunk / nchl : 0;
     const int p = (live ? chunk - line * nchl : 0) * kL + i;
     auto pix = [&](int q) -> int {
-        return horiz ? g[(size_t)line * pitch + q] : g[(size_t)q * pitch + line];
+        return horiz ? a.guide[(size_t)line * a.pitch + q] : a.guide[(size_t)q * a.pitch + line];
     };
     auto weight = [&](int q) -> float {    // the step q-1 -> q
-        return (live && q >= 1 && q < n) ? K * expf(-fabsf((float)(pix(q) - pix(q - 1))) * inv_sr255) : 0.0f;
+        return (live && q >= 1 && q < n) ? a.K * expf(-fabsf((float)(pix(q) - pix(q - 1))) * a.inv_sr255) : 0.0f;
     };
     const float w = weight(p);
     float wn = __shfl_down_sync(kFull, w, 1, kL);
@@ -97,15 +101,18 @@ __global__ void k_dt_coef(const uint8_t* __restrict__ g, int pitch, int W, int H
         if (i + off < kL) B *= b2;
     }
     if (live && p < n) {
-        float4* out = horiz ? coefH + (size_t)line * W : coefV + (size_t)line * H;
+        float4* out = horiz ? a.coefH + (size_t)line * W : a.coefV + (size_t)line * H;
         out[p] = make_float4(w, A, wn, B);
     }
 }
 
-cudaError_t launch_dt_coef(const uint8_t* guide, int pitch, int W, int H, float K, float inv_sr255,
-                           float4* coefH, float4* coefV, cudaStream_t st) {
-    const long long total = (long long)kL * (H * ((W + kL - 1) / kL) + W * ((H + kL - 1) / kL));
-    k_dt_coef<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(guide, pitch, W, H, K, inv_sr255, coefH, coefV);
+long long dt_coef_threads(int W, int H) {
+    return (long long)kL * ((long long)H * ((W + kL - 1) / kL) + (long long)W * ((H + kL - 1) / kL));
+}
+
+cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st) {
+    const long long blocks = (b.total_threads + 255) / 256;
+    k_dt_coef<<<(unsigned)blocks, 256, 0, st>>>(b);
     return cudaGetLastError();
 }
 
@@ -123,144 +130,175 @@ cudaError_t launch_dt_coef(const uint8_t* guide, int pitch, int W, int H, float 
 // cp.async while the current one is computed, across group boundaries: two staging buffers,
 // each refilled (two items ahead) as soon as the forward sweep has consumed it. In Wta mode
 // per_block is a multiple of nslices: a block sees every disparity of its lines.
-template <typename T>
-__host__ __device__ inline size_t line_stage_bytes(const LineArgs& a) {
-    return a.async ? 2ull * a.lpc * kL * a.nch * a.tq * (4 * sizeof(T)) : 0;
+size_t line_stage_bytes(int dtype, const LineArgs& a) {
+    return a.async ? 2ull * a.lpc * kL * a.nch * a.tq * (4 * (dtype == 0 ? 4 : 2)) : 0;
 }
 
-int line_pair_items(const LineArgs& a) {
-    const int nslices = (a.dcount + kG * a.tq - 1) / (kG * a.tq);
-    return ((a.nlines + a.lpc - 1) / a.lpc) * nslices;
-}
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
+__global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineBatch b) {
     extern __shared__ float4 smem4[];
-    const int tq = a.tq, nch = a.nch, ds = kG * tq;
-    const int per_line = nch * tq, nwl = per_line >> 5, span = nch * kL;
-    const int li = threadIdx.x / per_line;
-    const int tl = threadIdx.x - li * per_line;
-    const int k = tl / tq, dq = tl - k * tq;
-    const int lane = threadIdx.x & 31, wl = tl >> 5;
-    const int pX = plane_of(span);
-
-    T* stage = reinterpret_cast<T*>(smem4);                           // [2][lpc][kL][per_line] x 4
-    float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + line_stage_bytes<T>(a));
-    float2* mul_all = reinterpret_cast<float2*>(co_all + a.lpc * 4 * pX);   // [lpc][4 pX]
-    float4* sb_all = reinterpret_cast<float4*>(mul_all + a.lpc * 4 * pX);   // [lpc][2 nwl tq]
-    float* sa_all = reinterpret_cast<float*>(sb_all + a.lpc * 2 * nwl * tq);
-    const float4* co = co_all + li * 4 * pX;
-    const float2* mul = mul_all + li * 4 * pX;
-    float4* sb = sb_all + li * 2 * nwl * tq;
-    float* sa = sa_all + li * 2 * nwl * tq;
-
-    const int nslices = (a.dcount + ds - 1) / ds;
-    const int total = ((a.nlines + a.lpc - 1) / a.lpc) * nslices;
-    const int it0 = blockIdx.x * a.per_block;
-    const int it1 = min(total, it0 + a.per_block);
-    T* vol = reinterpret_cast<T*>(a.vol);
-    const T* src = a.src ? reinterpret_cast<const T*>(a.src) : vol;
-    const bool vec = a.vec != 0, async = a.async != 0, ones = a.src_ones != 0;
-    const bool scaled_in = a.ahat_in != nullptr;
-    const int npos = a.n - k * kL;                                     // positions of this chunk
-    auto elem0 = [&](int line, int sl) -> size_t {                   // the chunk's first group
-        return (size_t)line * a.line_stride + (size_t)(k * kL) * a.elem_stride + sl * ds + dq * kG;
+    const int lane = threadIdx.x & 31;
+    const int i0 = (int)((long long)blockIdx.x * b.total_items / b.grid);
+    const int i1 = (int)((long long)(blockIdx.x + 1) * b.total_items / b.grid);
+    // the block's steps: from the first step of item i0 to the first step of item i1
+    auto step_of_item = [&](int item) -> int {
+        if (item >= b.total_items) return b.total_steps;
+        int q = 0;
+        while (item >= b.p[q].item0 + b.p[q].nitems) ++q;
+        const int spi = b.p[q].nsteps / b.p[q].nitems;
+        return b.p[q].step0 + (item - b.p[q].item0) * spi;
     };
-    auto stage_at = [&](int buf, int i) -> T* {
-        return stage + ((size_t)((buf * a.lpc + li) * kL + i) * per_line + tl) * 4;
+    const int s0 = step_of_item(i0), s1 = step_of_item(i1);
+
+    // the pair of a step and the geometry of this thread within it
+    struct Geo {
+        int pi, tq, nch, per_line, nwl, span, pX, ds, nslices, li, tl, k, dq, wl, g, sl, line;
+        bool active, line_ok;
     };
-    // prefetch of item `it` into the stage buffer. With vec the entries per pixel are a
-    // multiple of 4, so a group with any valid disparity lies whole inside the volume; its
-    // entries past dcount are never stored or compared.
-    auto prefetch = [&](int it, int buf) {
-        if (it < it1) {
-            const int g = it / nslices, sl = it - g * nslices;
-            const int line = g * a.lpc + li;
-            const bool ok = line < a.nlines && sl * ds + dq * kG < a.dcount;
-            const T* p = src + (ok ? elem0(line, sl) : 0);
+    auto geo = [&](int s, int pi_hint) -> Geo {
+        Geo o;
+        o.pi = pi_hint;
+        while (s >= b.p[o.pi].step0 + b.p[o.pi].nsteps) ++o.pi;
+        const LineArgs& a = b.p[o.pi];
+        o.tq = a.tq;
+        o.nch = a.nch;
+        o.per_line = o.nch * o.tq;
+        o.nwl = o.per_line >> 5;
+        o.span = o.nch * kL;
+        o.pX = plane_of(o.span);
+        o.ds = kG * o.tq;
+        o.nslices = (a.dcount + o.ds - 1) / o.ds;
+        o.active = (int)threadIdx.x < a.lpc * o.per_line;
+        o.li = o.active ? threadIdx.x / o.per_line : 0;
+        o.tl = o.active ? threadIdx.x - o.li * o.per_line : 0;
+        o.k = o.tl / o.tq;
+        o.dq = o.tl - o.k * o.tq;
+        o.wl = o.tl >> 5;
+        const int ls = s - a.step0;
+        o.g = ls / o.nslices;
+        o.sl = ls - o.g * o.nslices;
+        o.line = o.g * a.lpc + o.li;
+        o.line_ok = o.active && o.line < a.nlines;
+        return o;
+    };
+    auto elem0 = [&](const LineArgs& a, const Geo& o) -> size_t {   // the chunk's first group
+        return (size_t)o.line * a.line_stride + (size_t)(o.k * kL) * a.elem_stride + o.sl * o.ds + o.dq * kG;
+    };
+    T* stage = reinterpret_cast<T*>(smem4);
+    // stage buffer buf of a step with geometry o: [2][lpc][kL][per_line] groups of 4 entries
+    auto stage_at = [&](const LineArgs& a, const Geo& o, int buf, int i) -> T* {
+        return stage + ((size_t)((buf * a.lpc + o.li) * kL + i) * o.per_line + o.tl) * 4;
+    };
+    // prefetch of step s into stage buffer buf. With vec the entries per pixel are a multiple
+    // of 4, so a group with any valid disparity lies whole inside the volume; its entries
+    // past dcount are never stored or compared.
+    int pf_pi = 0;
+    auto prefetch = [&](int s, int buf) {
+        if (s < s1) {
+            const Geo o = geo(s, pf_pi);
+            pf_pi = o.pi;
+            const LineArgs& a = b.p[o.pi];
+            if (a.async && o.active) {
+                const T* src = a.src ? reinterpret_cast<const T*>(a.src) : reinterpret_cast<const T*>(a.vol);
+                const bool ok = o.line_ok && o.sl * o.ds + o.dq * kG < a.dcount;
+                const T* q = src + (ok ? elem0(a, o) : 0);
+                const int npos = a.n - o.k * kL;
 #pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                const bool valid = ok && i < npos;
-                cp_async<4 * sizeof(T)>(stage_at(buf, i), valid ? p + (size_t)i * a.elem_stride : src, valid);
+                for (int i = 0; i < kL; ++i) {
+                    const bool valid = ok && i < npos;
+                    cp_async<4 * sizeof(T)>(stage_at(a, o, buf, i), valid ? q + (size_t)i * a.elem_stride : src, valid);
+                }
             }
         }
         cp_async_commit();
     };
-    if (async) {
-        prefetch(it0, 0);
-        prefetch(it0 + 1, 1);
-    }
+    prefetch(s0, 0);
+    prefetch(s0 + 1, 1);
 
     WtaRegs wr;
-    int cur_group = -1;
-    for (int it = it0, n_it = 0; it < it1; ++it, ++n_it) {
-        const int g = it / nslices, sl = it - g * nslices;
-        const int line = g * a.lpc + li;
-        const bool line_ok = line < a.nlines;
-        if (g != cur_group) {          // stage the coefficients and multipliers of group g
+    int cur_pi = -1, cur_g = -1, pi = 0;
+    for (int s = s0, n_s = 0; s < s1; ++s, ++n_s) {
+        const Geo o = geo(s, pi);
+        pi = o.pi;
+        const LineArgs& a = b.p[pi];
+        // shared memory of this pair: [stage][coefficients][multipliers][scan buffers]
+        float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + b.stage_bytes);
+        float2* mul_all = reinterpret_cast<float2*>(co_all + a.lpc * 4 * o.pX);
+        float4* sb_all = reinterpret_cast<float4*>(mul_all + a.lpc * 4 * o.pX);
+        float* sa_all = reinterpret_cast<float*>(sb_all + a.lpc * 2 * o.nwl * o.tq);
+        const float4* co = co_all + o.li * 4 * o.pX;
+        const float2* mul = mul_all + o.li * 4 * o.pX;
+        float4* sb = sb_all + o.li * 2 * o.nwl * o.tq;
+        float* sa = sa_all + o.li * 2 * o.nwl * o.tq;
+
+        if (pi != cur_pi || o.g != cur_g) {     // stage the coefficients and multipliers of the group
             __syncthreads();
             for (int l2 = 0; l2 < a.lpc; ++l2) {
-                const int ln = g * a.lpc + l2;
+                const int ln = o.g * a.lpc + l2;
                 const bool ok = ln < a.nlines;
-                for (int t = threadIdx.x; t < span; t += blockDim.x) {
+                for (int t = threadIdx.x; t < o.span; t += blockDim.x) {
                     const bool in = ok && t < a.n;
-                    co_all[l2 * 4 * pX + cidx(t, pX)] =
+                    co_all[l2 * 4 * o.pX + cidx(t, o.pX)] =
                         in ? __ldg(a.coef + (size_t)ln * a.coef_line_stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
                     const size_t pix = (size_t)ln * a.pix_line + (size_t)t * a.pix_pos;
                     const float mi = in && a.ahat_in ? __ldg(a.ahat_in + pix) : 1.0f;
                     const float mo = in && a.ahat_out ? a.s2 / __ldg(a.ahat_out + pix) : a.s2;
-                    mul_all[l2 * 4 * pX + cidx(t, pX)] = make_float2(mi, mo);
+                    mul_all[l2 * 4 * o.pX + cidx(t, o.pX)] = make_float2(mi, mo);
                 }
             }
             if constexpr (MODE == kLineWta) wr.reset();
             __syncthreads();
-            cur_group = g;
+            cur_pi = pi;
+            cur_g = o.g;
         }
-        const int dl = sl * ds + dq * kG;                              // entry of d_first
+        const int dl = o.sl * o.ds + o.dq * kG;                        // entry of d_first
         const int nvalid = max(0, min(4, a.dcount - dl));
-        const bool any = line_ok && nvalid > 0;
+        const bool any = o.line_ok && nvalid > 0;
+        const int npos = a.n - o.k * kL;
+        T* vol = reinterpret_cast<T*>(a.vol);
         float v[kL][4];
-        if (ones) {
+        cp_async_wait<1>();                                            // this step's copies landed
+        if (a.src_ones) {
 #pragma unroll
             for (int i = 0; i < kL; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v[i][j] = (any && i < npos && j < nvalid) ? 1.0f : 0.0f;
-        } else if (async) {
-            cp_async_wait<1>();                                        // this item's copies landed
+        } else if (a.async) {
 #pragma unroll
-            for (int i = 0; i < kL; ++i) lds4(stage_at(n_it & 1, i), v[i]);
+            for (int i = 0; i < kL; ++i) lds4(stage_at(a, o, n_s & 1, i), v[i]);
         } else {
-            const T* q = src + (line_ok ? elem0(line, sl) : 0);
+            const T* src = a.src ? reinterpret_cast<const T*>(a.src) : vol;
+            const T* q = src + (o.line_ok ? elem0(a, o) : 0);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
-                if (any && i < npos) ld4(q, nvalid, vec, v[i]);
+                if (any && i < npos) ld4(q, nvalid, a.vec != 0, v[i]);
                 else v[i][0] = v[i][1] = v[i][2] = v[i][3] = 0.0f;
                 q += a.elem_stride;
             }
         }
-        if (scaled_in) {
+        if (a.ahat_in && o.active) {
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
-                const float m = mul[cidx(k * kL + i, pX)].x;
+                const float m = mul[cidx(o.k * kL + i, o.pX)].x;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v[i][j] *= m;
             }
         }
         // the staging buffer is free once the forward sweep has read it: refill it two ahead
-        dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2, mul, [&]() {
-            if (async) prefetch(it + 2, n_it & 1);
-        });
+        dt_pair(v, co, o.pX, o.k, o.tq, o.dq, lane, o.wl, o.nwl, sa, sb, a.s2, mul,
+                [&]() { prefetch(s + 2, n_s & 1); }, o.active);
         if constexpr (MODE == kLineWta) {
-            wr.fold(v, nvalid, a.d_base + dl);
-            if (sl == nslices - 1) {                                   // the group's last slice
+            if (o.active) wr.fold(v, nvalid, a.d_base + dl);
+            if (o.sl == o.nslices - 1 && o.active) {                    // the group's last slice
 #pragma unroll
                 for (int i = 0; i < kL; ++i) {
                     float best;
                     int bd;
-                    wta_reduce_lanes(wr.entry(i), tq, best, bd);
-                    const int pos = k * kL + i;
-                    if (dq == 0 && line_ok && pos < a.n) {
-                        const size_t pix = (size_t)line * a.pix_line + (size_t)pos * a.pix_pos;
+                    wta_reduce_lanes(wr.entry(i), o.tq, best, bd);
+                    const int pos = o.k * kL + i;
+                    if (o.dq == 0 && o.line_ok && pos < a.n) {
+                        const size_t pix = (size_t)o.line * a.pix_line + (size_t)pos * a.pix_pos;
                         if (!a.wta.first) {                            // earlier launches: smaller d
                             const float pb = a.wta.bestv[pix];
                             if (!(best > pb)) { best = pb; bd = a.wta.bestd[pix]; }
@@ -274,47 +312,43 @@ __global__ void __launch_bounds__(512) k_line_pair(LineArgs a) {
                 }
             }
         } else {
-            T* q = vol + (line_ok ? elem0(line, sl) : 0);
+            T* q = vol + (o.line_ok ? elem0(a, o) : 0);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
-                if (any && i < npos) st4(q, nvalid, vec, v[i]);
+                if (any && i < npos) st4(q, nvalid, a.vec != 0, v[i]);
                 q += a.elem_stride;
             }
         }
     }
-    if (async) cp_async_wait<0>();
+    cp_async_wait<0>();
 }
 
 size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a) {
     const int pX = plane_of(a.nch * kL);
     const int nwl = a.nch * a.tq / 32;
-    size_t b = dtype == 0 ? line_stage_bytes<float>(a) : line_stage_bytes<__half>(a);
-    b += (size_t)a.lpc * ((16ull + 8ull) * 4 * pX + dt_scan_bytes(nwl, a.tq));
-    return b;
+    (void)mode;
+    return line_stage_bytes(dtype, a) + (size_t)a.lpc * ((16ull + 8ull) * 4 * pX + dt_scan_bytes(nwl, a.tq));
 }
 
-static void (*line_pair_fn(int mode, int dtype))(LineArgs) {
+static void (*line_pair_fn(int mode, int dtype))(LineBatch) {
     if (mode == kLineStore) return dtype == 0 ? k_line_pair<float, kLineStore> : k_line_pair<__half, kLineStore>;
     return dtype == 0 ? k_line_pair<float, kLineWta> : k_line_pair<__half, kLineWta>;
 }
 
-cudaError_t line_pair_occupancy(const LineArgs& a, int mode, int dtype, int* blocks_per_sm) {
-    void (*fn)(LineArgs) = line_pair_fn(mode, dtype);
-    const size_t smem = line_pair_smem_bytes(mode, dtype, a);
+cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, int* blocks_per_sm) {
+    void (*fn)(LineBatch) = line_pair_fn(mode, dtype);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, a.lpc * a.nch * a.tq, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
 }
 
-cudaError_t launch_line_pair(const LineArgs& a, int mode, int dtype, cudaStream_t st) {
-    const int total = line_pair_items(a);
-    dim3 grid((total + a.per_block - 1) / a.per_block);
-    dim3 block(a.lpc * a.nch * a.tq);
-    const size_t smem = line_pair_smem_bytes(mode, dtype, a);
-    void (*fn)(LineArgs) = line_pair_fn(mode, dtype);
+cudaError_t launch_line_batch(const LineBatch& b, int threads, size_t smem, int mode, int dtype,
+                              cudaStream_t st) {
+    dim3 grid(b.grid);
+    void (*fn)(LineBatch) = line_pair_fn(mode, dtype);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<grid, block, smem, st>>>(a);
+    fn<<<grid, threads, smem, st>>>(b);
     return cudaGetLastError();
 }
 
@@ -354,15 +388,30 @@ size_t zncc_row_smem_bytes(int R, int mode, const RowArgs& a, int nthreads) {
     return zncc_row_smem(R, mode, a, nthreads);
 }
 
-cudaError_t launch_zncc_row(int R, const RowArgs& a, int mode, int dtype, cudaStream_t st) {
+cudaError_t launch_zncc_row(int R, const RowBatch& b, int threads, size_t smem, int mode, int dtype,
+                            cudaStream_t st) {
     switch (R) {
-        case 1: return launch_zncc_row_r1(a, mode, dtype, st);
-        case 2: return launch_zncc_row_r2(a, mode, dtype, st);
-        case 3: return launch_zncc_row_r3(a, mode, dtype, st);
-        case 4: return launch_zncc_row_r4(a, mode, dtype, st);
-        case 5: return launch_zncc_row_r5(a, mode, dtype, st);
-        case 6: return launch_zncc_row_r6(a, mode, dtype, st);
-        case 7: return launch_zncc_row_r7(a, mode, dtype, st);
+        case 1: return launch_zncc_row_r1(b, threads, smem, mode, dtype, st);
+        case 2: return launch_zncc_row_r2(b, threads, smem, mode, dtype, st);
+        case 3: return launch_zncc_row_r3(b, threads, smem, mode, dtype, st);
+        case 4: return launch_zncc_row_r4(b, threads, smem, mode, dtype, st);
+        case 5: return launch_zncc_row_r5(b, threads, smem, mode, dtype, st);
+        case 6: return launch_zncc_row_r6(b, threads, smem, mode, dtype, st);
+        case 7: return launch_zncc_row_r7(b, threads, smem, mode, dtype, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t zncc_row_occupancy(int R, int mode, int dtype, int threads, size_t smem, bool minb2,
+                               int* blocks_per_sm) {
+    switch (R) {
+        case 1: return zncc_row_occupancy_r1(mode, dtype, threads, smem, minb2, blocks_per_sm);
+        case 2: return zncc_row_occupancy_r2(mode, dtype, threads, smem, minb2, blocks_per_sm);
+        case 3: return zncc_row_occupancy_r3(mode, dtype, threads, smem, minb2, blocks_per_sm);
+        case 4: return zncc_row_occupancy_r4(mode, dtype, threads, smem, minb2, blocks_per_sm);
+        case 5: return zncc_row_occupancy_r5(mode, dtype, threads, smem, minb2, blocks_per_sm);
+        case 6: return zncc_row_occupancy_r6(mode, dtype, threads, smem, minb2, blocks_per_sm);
+        case 7: return zncc_row_occupancy_r7(mode, dtype, threads, smem, minb2, blocks_per_sm);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -8,6 +8,7 @@ namespace zncc {
 
 enum { kModeRaw = 0, kModeHPair = 1, kModeWta = 2 };   // k_zncc_row variants
 enum { kLineStore = 0, kLineWta = 1 };                  // k_line_pair variants
+constexpr int kMaxBatch = 32;                           // pairs per batched launch
 
 // WTA output of a launch: a running best (value, d) per pixel that persists across launches
 // which split the disparity range, and the disparity map written by the last one.
@@ -33,6 +34,14 @@ struct RowArgs {
     float s2;                 // (1 - K)^2
     WtaOut wta;               // (Wta)
     int minb2;                // use the two-blocks-per-SM variant where the block allows
+    int item0, nitems;        // this pair's items (row, run of spb slices) in a batched launch
+};
+
+// One cost-kernel launch over up to kMaxBatch pairs of the same window radius, passed by
+// value. Of G blocks, block b takes the items [b * total / G, (b+1) * total / G), in order.
+struct RowBatch {
+    int npairs, total_items, grid, mode;
+    RowArgs p[kMaxBatch];
 };
 
 struct LineArgs {
@@ -55,26 +64,56 @@ struct LineArgs {
     int async;                // vec, and the next slices are streamed through shared memory
     WtaOut wta;               // (Wta)
     long long pix_line, pix_pos;  // pixel of (line, pos) is line * pix_line + pos * pix_pos
+    // position of this pair in a batched launch: items and steps (line group, slice) are
+    // numbered pair by pair; an item is one step (Store) or every slice of a group (Wta)
+    int item0, nitems, step0, nsteps;
+};
+
+// One line-pair launch over up to kMaxBatch pairs, passed by value. Of G blocks, block b
+// takes the items [b * total / G, (b+1) * total / G) of all pairs, in order.
+struct LineBatch {
+    int npairs, total_items, total_steps, grid;
+    long long stage_bytes;    // staging region (the largest pair's), before the other arrays
+    LineArgs p[kMaxBatch];
 };
 
 size_t zncc_row_smem_bytes(int R, int mode, const RowArgs& a, int nthreads);
 size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a);
+cudaError_t launch_line_batch(const LineBatch& b, int threads, size_t smem, int mode, int dtype,
+                              cudaStream_t st);
 
-cudaError_t launch_zncc_row(int R, const RowArgs& a, int mode, int dtype, cudaStream_t st);
-cudaError_t launch_line_pair(const LineArgs& a, int mode, int dtype, cudaStream_t st);
-int line_pair_items(const LineArgs& a);
-cudaError_t line_pair_occupancy(const LineArgs& a, int mode, int dtype, int* blocks_per_sm);
+cudaError_t launch_zncc_row(int R, const RowBatch& b, int threads, size_t smem, int mode, int dtype,
+                            cudaStream_t st);
+cudaError_t zncc_row_occupancy(int R, int mode, int dtype, int threads, size_t smem, bool minb2,
+                               int* blocks_per_sm);
+size_t line_stage_bytes(int dtype, const LineArgs& a);
+cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, int* blocks_per_sm);
 cudaError_t launch_window_stats(const uint8_t* img, int pitch, int W, int H, int r, int x_begin,
                                 int nx, int* S, int* Q, float* isig, int2* packed,
                                 cudaStream_t st);
-cudaError_t launch_dt_coef(const uint8_t* guide, int pitch, int W, int H, float K,
-                           float inv_sr255, float4* coefH, float4* coefV, cudaStream_t st);
+struct CoefArgs {
+    const uint8_t* guide;
+    int pitch, W, H;
+    float K, inv_sr255;       // exp(-1/sigma_s), 1/(255 sigma_r)
+    float4* coefH;            // [H][W]
+    float4* coefV;            // [W][H]
+    long long thread0;        // first thread of this pair in the launch
+};
+struct CoefBatch {
+    int npairs;
+    long long total_threads;
+    CoefArgs p[kMaxBatch];
+};
+cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st);
+long long dt_coef_threads(int W, int H);
 cudaError_t launch_wta_volume(const void* cost, int dtype, int W, int H, int D, uint16_t* disp,
                               cudaStream_t st);
 
 // per-radius launchers, one translation unit each
-#define ZNCC_DECLARE_ROW(R) \
-    cudaError_t launch_zncc_row_r##R(const RowArgs& a, int mode, int dtype, cudaStream_t st);
+#define ZNCC_DECLARE_ROW(R)                                                                     \
+    cudaError_t launch_zncc_row_r##R(const RowBatch& b, int threads, size_t smem, int mode, int dtype, \
+                                     cudaStream_t st);                                             \
+    cudaError_t zncc_row_occupancy_r##R(int mode, int dtype, int threads, size_t smem, bool minb2, int* bps);
 ZNCC_DECLARE_ROW(1)
 ZNCC_DECLARE_ROW(2)
 ZNCC_DECLARE_ROW(3)

@@ -32,20 +32,21 @@ namespace zncc {
 // block and serve all of its disparity slices; the window statistics of both images
 // (Sec. IV-B-1, Eq. (sum1)) come from the same packed columns: a column's pixel sum is
 // __dp4a(word, 0x01010101) and its sum of squares __dp4a(word, word), slid like P.
-template <int R, typename T, int MODE, int MINB>
-__global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(RowArgs a) {
+// One item of the cost kernel: row y of one pair, disparity slices [run*spb, run*spb+spb).
+// Threads beyond the pair's nch * tq (whole warps) only take part in the barriers.
+template <int R, typename T, int MODE>
+__device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int run, uint4* smem_u4) {
     constexpr int l = 2 * R + 1;
     constexpr int NW = (l + 3) / 4;     // packed words per column
-    extern __shared__ uint4 smem_u4[];
-
-    const int y = blockIdx.x;
     const int tq = a.tq, ds = kG * tq, nch = a.nch, span = nch * kL;
     const int W = a.W, H = a.H;
     const int tid = threadIdx.x;
-    const int k = tid / tq, dq = tid - k * tq;
-    const int lane = tid & 31, wl = tid >> 5, nwl = blockDim.x >> 5;
+    const int nthr = nch * tq;
+    const bool active = tid < nthr;
+    const int k = active ? tid / tq : 0, dq = active ? tid - (tid / tq) * tq : 0;
+    const int lane = tid & 31, wl = tid >> 5, nwl = nthr >> 5;
     const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
-    const int s_begin = blockIdx.y * a.spb;
+    const int s_begin = run * a.spb;
     const int s_end = min(nslices, s_begin + a.spb);
     // every lane's disparities lie in [blk_lo, blk_hi)
     const int blk_lo = a.d_lo + s_begin * ds, blk_hi = a.d_lo + s_end * ds;
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(RowArg
     float4* sb = co + 4 * pX;
     float* sa = reinterpret_cast<float*>(sb + 2 * nwl * tq);
 
-    // ---- stage the packed bands (and the DT coefficients / the running best) ----
+    // ---- stage the packed bands (and the DT coefficients) ----
     for (int t = tid; t < NLP + NRP; t += blockDim.x) {
         const bool is_left = t < NLP;
         const int ix = is_left ? t : t - NLP;
@@ -131,70 +132,71 @@ __global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(RowArg
     for (int sl = s_begin; sl < s_end; ++sl) {
         const int d_first = a.d_lo + sl * ds + dq * kG;
         const int nvalid = max(0, min(4, a.d_hi - d_first));
-
-        // ---- window sums of products P for 16 pixels x 4 disparities ----
-        int P[kL][4];
-#pragma unroll
-        for (int i = 0; i < kL; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) P[i][j] = 0;
-        // RP index of column x' - d_first - j at step t (x' = x0 - R + t) is rbase + t - j
-        const int rbase = x0 - R - d_first - xr0;      // >= 3: d_first + 3 < blk_hi
-        uint4 rp[4];
-        rp[1] = RP[p4(rbase - 1, pRP)];
-        rp[2] = RP[p4(rbase - 2, pRP)];
-        rp[3] = RP[p4(rbase - 3, pRP)];
-        unsigned pre[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int t = 0; t < kL + 2 * R; ++t) {
-            const uint4 lp = LP[p4(x0 + t, pLP)];
-            rp[0] = RP[p4(rbase + t, pRP)];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                pre[j] = __dp4a(lp.x, rp[j].x, pre[j]);
-                if (NW > 1) pre[j] = __dp4a(lp.y, rp[j].y, pre[j]);
-                if (NW > 2) pre[j] = __dp4a(lp.z, rp[j].z, pre[j]);
-                if (NW > 3) pre[j] = __dp4a(lp.w, rp[j].w, pre[j]);
-                if (t - 2 * R >= 0 && t - 2 * R < kL) P[t - 2 * R][j] += (int)pre[j];
-                if (t + 1 < kL) P[t + 1][j] -= (int)pre[j];
-            }
-            rp[3] = rp[2];
-            rp[2] = rp[1];
-            rp[1] = rp[0];
-        }
-
-        // ---- normalization, Eq. (2); the target statistics slide like the columns ----
-        const int cb = x0 - d_first - c0;               // SR index of (i, j) is cb + i - j >= 3
-        int2 sr[4];
-        sr[1] = SR[p4(cb - 1, pSR)];
-        sr[2] = SR[p4(cb - 2, pSR)];
-        sr[3] = SR[p4(cb - 3, pSR)];
         float v[kL][4];
+        if (active) {
+            // ---- window sums of products P for 16 pixels x 4 disparities ----
+            int P[kL][4];
 #pragma unroll
-        for (int i = 0; i < kL; ++i) {
-            const int x = x0 + i;
-            const int2 st = at4(SL, x0, i, pX);
-            sr[0] = SR[p4(cb + i, pSR)];
-            const float isl = __int_as_float(st.y);
+            for (int i = 0; i < kL; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const unsigned num = n * (unsigned)P[i][j] - (unsigned)st.x * (unsigned)sr[j].x;
-                const bool ok = x < W && j < nvalid;
-                v[i][j] = ok ? (float)(int)num * isl * __int_as_float(sr[j].y) : 0.0f;
+                for (int j = 0; j < 4; ++j) P[i][j] = 0;
+            // RP index of column x' - d_first - j at step t (x' = x0 - R + t) is rbase + t - j
+            const int rbase = x0 - R - d_first - xr0;      // >= 3: d_first + 3 < blk_hi
+            uint4 rp[4];
+            rp[1] = RP[p4(rbase - 1, pRP)];
+            rp[2] = RP[p4(rbase - 2, pRP)];
+            rp[3] = RP[p4(rbase - 3, pRP)];
+            unsigned pre[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int t = 0; t < kL + 2 * R; ++t) {
+                const uint4 lp = LP[p4(x0 + t, pLP)];
+                rp[0] = RP[p4(rbase + t, pRP)];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    pre[j] = __dp4a(lp.x, rp[j].x, pre[j]);
+                    if (NW > 1) pre[j] = __dp4a(lp.y, rp[j].y, pre[j]);
+                    if (NW > 2) pre[j] = __dp4a(lp.z, rp[j].z, pre[j]);
+                    if (NW > 3) pre[j] = __dp4a(lp.w, rp[j].w, pre[j]);
+                    if (t - 2 * R >= 0 && t - 2 * R < kL) P[t - 2 * R][j] += (int)pre[j];
+                    if (t + 1 < kL) P[t + 1][j] -= (int)pre[j];
+                }
+                rp[3] = rp[2];
+                rp[2] = rp[1];
+                rp[1] = rp[0];
             }
-            sr[3] = sr[2];
-            sr[2] = sr[1];
-            sr[1] = sr[0];
+
+            // ---- normalization, Eq. (2); the target statistics slide like the columns ----
+            const int cb = x0 - d_first - c0;               // SR index of (i, j) is cb + i - j >= 3
+            int2 sr[4];
+            sr[1] = SR[p4(cb - 1, pSR)];
+            sr[2] = SR[p4(cb - 2, pSR)];
+            sr[3] = SR[p4(cb - 3, pSR)];
+#pragma unroll
+            for (int i = 0; i < kL; ++i) {
+                const int x = x0 + i;
+                const int2 st = at4(SL, x0, i, pX);
+                sr[0] = SR[p4(cb + i, pSR)];
+                const float isl = __int_as_float(st.y);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned num = n * (unsigned)P[i][j] - (unsigned)st.x * (unsigned)sr[j].x;
+                    const bool ok = x < W && j < nvalid;
+                    v[i][j] = ok ? (float)(int)num * isl * __int_as_float(sr[j].y) : 0.0f;
+                }
+                sr[3] = sr[2];
+                sr[2] = sr[1];
+                sr[1] = sr[0];
+            }
         }
 
         if constexpr (MODE == kModeWta) {
-            wr.fold(v, nvalid, d_first);
+            if (active) wr.fold(v, nvalid, d_first);
             continue;
         }
-        if constexpr (MODE == kModeHPair) dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2);
+        if constexpr (MODE == kModeHPair) dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2, nullptr, NoHook(), active);
 
         // ---- store [H][W][dstride] ----
-        if (nvalid > 0) {
+        if (active && nvalid > 0) {
             T* q = out + ((size_t)y * W + x0) * a.dstride + (d_first - a.d_out0);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
@@ -205,29 +207,50 @@ __global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(RowArg
     }
 
     if constexpr (MODE == kModeWta) {
+        if (active) {
 #pragma unroll
-        for (int i = 0; i < kL; ++i) {
-            float best;
-            int bd;
-            wta_reduce_lanes(wr.entry(i), tq, best, bd);
-            const int x = x0 + i;
-            if (dq == 0 && x < W) {
-                const size_t o = (size_t)y * W + x;
-                if (!a.wta.first) {                                    // earlier launches: smaller d
-                    const float pb = a.wta.bestv[o];
-                    if (!(best > pb)) { best = pb; bd = a.wta.bestd[o]; }
-                }
-                if (a.wta.last) a.wta.disp[o] = (uint16_t)bd;
-                else {
-                    a.wta.bestv[o] = best;
-                    a.wta.bestd[o] = bd;
+            for (int i = 0; i < kL; ++i) {
+                float best;
+                int bd;
+                wta_reduce_lanes(wr.entry(i), tq, best, bd);
+                const int x = x0 + i;
+                if (dq == 0 && x < W) {
+                    const size_t o = (size_t)y * W + x;
+                    if (!a.wta.first) {                                // earlier launches: smaller d
+                        const float pb = a.wta.bestv[o];
+                        if (!(best > pb)) { best = pb; bd = a.wta.bestd[o]; }
+                    }
+                    if (a.wta.last) a.wta.disp[o] = (uint16_t)bd;
+                    else {
+                        a.wta.bestv[o] = best;
+                        a.wta.bestd[o] = bd;
+                    }
                 }
             }
         }
     }
 }
 
-// Shared-memory bytes of one block of k_zncc_row.
+template <int R, typename T, int MODE, int MINB>
+__global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(const __grid_constant__ RowBatch b) {
+    extern __shared__ uint4 smem_u4[];
+    const int i0 = (int)((long long)blockIdx.x * b.total_items / b.grid);
+    const int i1 = (int)((long long)(blockIdx.x + 1) * b.total_items / b.grid);
+    int pi = 0;
+    for (int item = i0; item < i1; ++item) {
+        while (item >= b.p[pi].item0 + b.p[pi].nitems) ++pi;
+        const RowArgs& a = b.p[pi];
+        const int ds = kG * a.tq;
+        const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
+        const int nruns = (nslices + a.spb - 1) / a.spb;
+        const int local = item - a.item0;
+        const int y = local / nruns;
+        zncc_row_item<R, T, MODE>(a, y, local - y * nruns, smem_u4);
+        __syncthreads();                                 // the next item restages shared memory
+    }
+}
+
+// Shared-memory bytes of one item of k_zncc_row.
 inline size_t zncc_row_smem(int R, int mode, const RowArgs& a, int nthreads) {
     const int ds = kG * a.tq, span = a.nch * kL;
     const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
@@ -240,27 +263,36 @@ inline size_t zncc_row_smem(int R, int mode, const RowArgs& a, int nthreads) {
 }
 
 template <int R>
-cudaError_t launch_zncc_row_impl(const RowArgs& a, int mode, int dtype, cudaStream_t st) {
-    const int ds = kG * a.tq;
-    const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
-    dim3 grid(a.H, (nslices + a.spb - 1) / a.spb);
-    dim3 block(a.nch * a.tq);
-    const size_t smem = zncc_row_smem(R, mode, a, (int)block.x);
-    // blocks of up to 320 threads use the variant limited to 96 registers (two resident
-    // blocks per SM); larger blocks the 128-register one
-    void (*fn)(RowArgs) = nullptr;
-    if (block.x <= 320 && a.minb2) {
-        if (mode == kModeRaw) fn = dtype == 0 ? k_zncc_row<R, float, kModeRaw, 2> : k_zncc_row<R, __half, kModeRaw, 2>;
-        else if (mode == kModeHPair) fn = dtype == 0 ? k_zncc_row<R, float, kModeHPair, 2> : k_zncc_row<R, __half, kModeHPair, 2>;
-        else fn = k_zncc_row<R, float, kModeWta, 2>;
-    } else {
-        if (mode == kModeRaw) fn = dtype == 0 ? k_zncc_row<R, float, kModeRaw, 1> : k_zncc_row<R, __half, kModeRaw, 1>;
-        else if (mode == kModeHPair) fn = dtype == 0 ? k_zncc_row<R, float, kModeHPair, 1> : k_zncc_row<R, __half, kModeHPair, 1>;
-        else fn = k_zncc_row<R, float, kModeWta, 1>;
+static void (*row_fn(int mode, int dtype, bool minb2))(RowBatch) {
+    if (minb2) {
+        if (mode == kModeRaw) return dtype == 0 ? k_zncc_row<R, float, kModeRaw, 2> : k_zncc_row<R, __half, kModeRaw, 2>;
+        if (mode == kModeHPair) return dtype == 0 ? k_zncc_row<R, float, kModeHPair, 2> : k_zncc_row<R, __half, kModeHPair, 2>;
+        return k_zncc_row<R, float, kModeWta, 2>;
     }
+    if (mode == kModeRaw) return dtype == 0 ? k_zncc_row<R, float, kModeRaw, 1> : k_zncc_row<R, __half, kModeRaw, 1>;
+    if (mode == kModeHPair) return dtype == 0 ? k_zncc_row<R, float, kModeHPair, 1> : k_zncc_row<R, __half, kModeHPair, 1>;
+    return k_zncc_row<R, float, kModeWta, 1>;
+}
+
+// The variant limited to 96 registers (two resident blocks per SM) serves blocks of up to
+// 320 threads when minb2 is set; larger blocks use the 128-register one.
+template <int R>
+cudaError_t zncc_row_occupancy_impl(int mode, int dtype, int threads, size_t smem, bool minb2, int* bps) {
+    void (*fn)(RowBatch) = row_fn<R>(mode, dtype, minb2 && threads <= 320);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<grid, block, smem, st>>>(a);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, threads, smem);
+}
+
+template <int R>
+cudaError_t launch_zncc_row_impl(const RowBatch& b, int threads, size_t smem, int mode, int dtype,
+                                 cudaStream_t st) {
+    bool minb2 = true;
+    for (int i = 0; i < b.npairs; ++i) minb2 = minb2 && b.p[i].minb2;
+    void (*fn)(RowBatch) = row_fn<R>(mode, dtype, minb2 && threads <= 320);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<b.grid, threads, smem, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,8 @@ loaded, every call raises.
 The methods of ZnccContext carry the names of the C calls they wrap:
 
     zncc_window_stats, zncc_cost_volume, dt_aggregate, wta_disparity, zncc_run, zncc_run_host
+
+and the module-level zncc_run_batch wraps the batched call.
 """
 
 from __future__ import annotations
@@ -40,6 +42,7 @@ SIGNATURES = [
     ("wta_disparity", _i, [_vp, _vp, _i, _vp]),
     ("zncc_run", _i, [_vp, _vp, _vp, _i, _f, _f, _i, _i, _vp]),
     ("zncc_run_host", _i, [_vp, _vp, _vp, _i, _f, _f, _i, _i, _vp]),
+    ("zncc_run_batch", _i, [_vp, _vp, _vp, _vp, _vp, _i, _f, _f, _i, _i]),
     ("zncc_last_error", ctypes.c_char_p, [_vp]),
     ("zncc_status_string", ctypes.c_char_p, [_i]),
     ("zncc_kernel_launch_count", ctypes.c_uint64, []),
@@ -87,6 +90,20 @@ def _ptr(t) -> int:
 
 def launch_count() -> int:
     return int(lib().zncc_kernel_launch_count())
+
+
+def zncc_run_batch(ctxs, lefts, rights, disps, sigma_s, sigma_r, iters, storage=ZNCC_F32):
+    """One batched fused run over several pairs (each with its own ZnccContext; the first
+    context's stream carries the launches)."""
+    n = len(ctxs)
+    VP = ctypes.c_void_p * n
+    st = lib().zncc_run_batch(VP(*[c._h.value for c in ctxs]), VP(*[_ptr(t) for t in lefts]),
+                              VP(*[_ptr(t) for t in rights]),
+                              (ctypes.c_int * n)(*[t.stride(0) for t in lefts]),
+                              VP(*[_ptr(t) for t in disps]), n, float(sigma_s), float(sigma_r),
+                              int(iters), int(storage))
+    if st != ZNCC_OK:
+        raise ZnccError(st, lib().zncc_last_error(ctxs[0]._h).decode())
 
 
 class ZnccContext:
