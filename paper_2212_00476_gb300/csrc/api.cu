@@ -243,10 +243,13 @@ zncc_status run_coef(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, float
 // disparity of its row.
 zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype, float s2, int kind,
                      const char* what) {
+    // pairs share a launch when they share the window radius and the block shape
+    auto tq_of = [](int W) { return W <= 1024 ? 8 : (W <= 2048 ? 4 : 2); };
     bool done[kMaxBatch] = {false};
     for (int first = 0; first < n; ++first) {
         if (done[first]) continue;
         const int r = io[first].c->r;
+        const int tq0 = tq_of(io[first].c->W), nch0 = padded_chunks(io[first].c->W, tq0);
         RowBatch b;
         memset(&b, 0, sizeof(b));
         b.mode = mode;
@@ -254,7 +257,8 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
         size_t smem = 0;
         bool minb2 = true;
         for (int i = first; i < n; ++i) {
-            if (done[i] || io[i].c->r != r) continue;
+            if (done[i] || io[i].c->r != r || tq_of(io[i].c->W) != tq0 || padded_chunks(io[i].c->W, tq0) != nch0)
+                continue;
             done[i] = true;
             zncc_ctx* c = io[i].c;
             RowArgs& a = b.p[b.npairs++];
@@ -264,8 +268,8 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
             a.W = c->W;
             a.H = c->H;
             a.D = c->D;
-            a.tq = c->W <= 1024 ? 8 : (c->W <= 2048 ? 4 : 2);
-            a.nch = padded_chunks(c->W, a.tq);
+            a.tq = tq0;
+            a.nch = nch0;
             a.d_lo = 0;
             a.d_hi = c->D;
             a.vol = io[i].vol;
@@ -367,17 +371,16 @@ zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
     return ZNCC_OK;
 }
 
-// One line-pair launch over the passes of several pairs (the same mode and storage).
+// Line-pair launches over the passes of several pairs (the same mode and storage): pairs
+// whose passes have the same block shape share one launch.
 zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passes, int n, int kind) {
-    LineBatch b;
-    memset(&b, 0, sizeof(b));
     const int mode = passes[0].mode, dtype = passes[0].dtype;
-    int threads = 0;
-    size_t stage = 0, rest = 0;
+    LineArgs args[kMaxBatch];
     for (int i = 0; i < n; ++i) {
         zncc_ctx* c = ctxs[i];
         const LinePass& p = passes[i];
-        LineArgs& a = b.p[b.npairs++];
+        LineArgs& a = args[i];
+        memset(&a, 0, sizeof(a));
         a.vol = p.vol;
         a.src = p.src;
         a.src_ones = p.ones ? 1 : 0;
@@ -401,26 +404,43 @@ zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passe
         a.pix_line = p.horiz ? c->W : 1;
         a.pix_pos = p.horiz ? 1 : c->W;
         if (plan_line_pass(c, a, p) != ZNCC_OK) return fail(lc, ZNCC_EUNSUPPORTED, c->err);
-        const int nslices = (a.dcount + kG * a.tq - 1) / (kG * a.tq);
-        const int ngroups = (a.nlines + a.lpc - 1) / a.lpc;
-        a.step0 = b.total_steps;
-        a.nsteps = ngroups * nslices;
-        a.item0 = b.total_items;
-        a.nitems = mode == kLineWta ? ngroups : a.nsteps;
-        b.total_steps += a.nsteps;
-        b.total_items += a.nitems;
-        threads = std::max(threads, a.lpc * a.nch * a.tq);
-        const size_t st = line_stage_bytes(dtype, a);
-        stage = std::max(stage, st);
-        rest = std::max(rest, line_pair_smem_bytes(mode, dtype, a) - st);
     }
-    b.stage_bytes = (long long)stage;
-    const size_t smem = stage + rest;
-    if (smem > (size_t)lc->smem_max) return fail(lc, ZNCC_EUNSUPPORTED, "batched DT pass exceeds shared memory");
-    int bps = 0;
-    ZNCC_CUDA(lc, line_pair_occupancy(mode, dtype, threads, smem, &bps), "occupancy query");
-    b.grid = std::max(1, std::min(b.total_items, lc->num_sms * std::max(1, bps)));
-    ZNCC_LAUNCH(lc, kind, launch_line_batch(b, threads, smem, mode, dtype, lc->cur), "DT pass pair");
+    bool done[kMaxBatch] = {false};
+    for (int first = 0; first < n; ++first) {
+        if (done[first]) continue;
+        const LineArgs& a0 = args[first];
+        LineBatch b;
+        memset(&b, 0, sizeof(b));
+        int threads = 0;
+        size_t stage = 0, rest = 0;
+        for (int i = first; i < n; ++i) {
+            const LineArgs& ai = args[i];
+            if (done[i] || ai.tq != a0.tq || ai.nch != a0.nch || ai.lpc != a0.lpc || ai.async != a0.async)
+                continue;
+            done[i] = true;
+            LineArgs& a = b.p[b.npairs++];
+            a = ai;
+            const int nslices = (a.dcount + kG * a.tq - 1) / (kG * a.tq);
+            const int ngroups = (a.nlines + a.lpc - 1) / a.lpc;
+            a.step0 = b.total_steps;
+            a.nsteps = ngroups * nslices;
+            a.item0 = b.total_items;
+            a.nitems = mode == kLineWta ? ngroups : a.nsteps;
+            b.total_steps += a.nsteps;
+            b.total_items += a.nitems;
+            threads = std::max(threads, a.lpc * a.nch * a.tq);
+            const size_t st = line_stage_bytes(dtype, a);
+            stage = std::max(stage, st);
+            rest = std::max(rest, line_pair_smem_bytes(mode, dtype, a) - st);
+        }
+        b.stage_bytes = (long long)stage;
+        const size_t smem = stage + rest;
+        if (smem > (size_t)lc->smem_max) return fail(lc, ZNCC_EUNSUPPORTED, "DT pass exceeds shared memory");
+        int bps = 0;
+        ZNCC_CUDA(lc, line_pair_occupancy(mode, dtype, threads, smem, &bps), "occupancy query");
+        b.grid = std::max(1, std::min(b.total_items, lc->num_sms * std::max(1, bps)));
+        ZNCC_LAUNCH(lc, kind, launch_line_batch(b, threads, smem, mode, dtype, lc->cur), "DT pass pair");
+    }
     return ZNCC_OK;
 }
 

@@ -151,77 +151,98 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     };
     const int s0 = step_of_item(i0), s1 = step_of_item(i1);
 
-    // the pair of a step and the geometry of this thread within it
-    struct Geo {
-        int pi, tq, nch, per_line, nwl, span, pX, ds, nslices, li, tl, k, dq, wl, g, sl, line;
-        bool active, line_ok;
+    // A cursor over steps: the pair, the line group and the slice of a step, advanced one
+    // step at a time, and this thread's place in the pair's block shape (recomputed only
+    // when the pair changes).
+    struct Cursor {
+        int s, pi, g, sl;
+        int tq, nch, per_line, nwl, span, pX, ds, nslices, ngroups;
+        int li, tl, k, dq, wl;
+        bool active;
     };
-    auto geo = [&](int s, int pi_hint) -> Geo {
-        Geo o;
-        o.pi = pi_hint;
-        while (s >= b.p[o.pi].step0 + b.p[o.pi].nsteps) ++o.pi;
-        const LineArgs& a = b.p[o.pi];
-        o.tq = a.tq;
-        o.nch = a.nch;
-        o.per_line = o.nch * o.tq;
-        o.nwl = o.per_line >> 5;
-        o.span = o.nch * kL;
-        o.pX = plane_of(o.span);
-        o.ds = kG * o.tq;
-        o.nslices = (a.dcount + o.ds - 1) / o.ds;
-        o.active = (int)threadIdx.x < a.lpc * o.per_line;
-        o.li = o.active ? threadIdx.x / o.per_line : 0;
-        o.tl = o.active ? threadIdx.x - o.li * o.per_line : 0;
-        o.k = o.tl / o.tq;
-        o.dq = o.tl - o.k * o.tq;
-        o.wl = o.tl >> 5;
-        const int ls = s - a.step0;
-        o.g = ls / o.nslices;
-        o.sl = ls - o.g * o.nslices;
-        o.line = o.g * a.lpc + o.li;
-        o.line_ok = o.active && o.line < a.nlines;
-        return o;
+    auto set_pair = [&](Cursor& c) {
+        const LineArgs& a = b.p[c.pi];
+        c.tq = a.tq;
+        c.nch = a.nch;
+        c.per_line = c.nch * c.tq;
+        c.nwl = c.per_line >> 5;
+        c.span = c.nch * kL;
+        c.pX = plane_of(c.span);
+        c.ds = kG * c.tq;
+        c.nslices = (a.dcount + c.ds - 1) / c.ds;
+        c.ngroups = a.nsteps / c.nslices;
+        c.active = (int)threadIdx.x < a.lpc * c.per_line;
+        c.li = c.active ? threadIdx.x / c.per_line : 0;
+        c.tl = c.active ? threadIdx.x - c.li * c.per_line : 0;
+        c.k = c.tl / c.tq;
+        c.dq = c.tl - c.k * c.tq;
+        c.wl = c.tl >> 5;
     };
-    auto elem0 = [&](const LineArgs& a, const Geo& o) -> size_t {   // the chunk's first group
-        return (size_t)o.line * a.line_stride + (size_t)(o.k * kL) * a.elem_stride + o.sl * o.ds + o.dq * kG;
+    auto seek = [&](int s) -> Cursor {          // once per block
+        Cursor c;
+        c.s = s;
+        c.pi = 0;
+        while (c.pi + 1 < b.npairs && s >= b.p[c.pi].step0 + b.p[c.pi].nsteps) ++c.pi;
+        set_pair(c);
+        const int ls = s - b.p[c.pi].step0;
+        c.g = ls / c.nslices;
+        c.sl = ls - c.g * c.nslices;
+        return c;
+    };
+    auto advance = [&](Cursor& c) {
+        ++c.s;
+        if (++c.sl == c.nslices) {
+            c.sl = 0;
+            if (++c.g == c.ngroups && c.pi + 1 < b.npairs) {
+                c.g = 0;
+                ++c.pi;
+                set_pair(c);
+            }
+        }
+    };
+    auto line_of = [&](const Cursor& c) { return c.g * b.p[c.pi].lpc + c.li; };
+    auto elem0 = [&](const LineArgs& a, const Cursor& c) -> size_t {   // the chunk's first group
+        return (size_t)line_of(c) * a.line_stride + (size_t)(c.k * kL) * a.elem_stride + c.sl * c.ds + c.dq * kG;
     };
     T* stage = reinterpret_cast<T*>(smem4);
-    // stage buffer buf of a step with geometry o: [2][lpc][kL][per_line] groups of 4 entries
-    auto stage_at = [&](const LineArgs& a, const Geo& o, int buf, int i) -> T* {
-        return stage + ((size_t)((buf * a.lpc + o.li) * kL + i) * o.per_line + o.tl) * 4;
+    // stage buffer buf of a step: [2][lpc][kL][per_line] groups of 4 entries
+    auto stage_at = [&](const LineArgs& a, const Cursor& c, int buf, int i) -> T* {
+        return stage + ((size_t)((buf * a.lpc + c.li) * kL + i) * c.per_line + c.tl) * 4;
     };
-    // prefetch of step s into stage buffer buf. With vec the entries per pixel are a multiple
-    // of 4, so a group with any valid disparity lies whole inside the volume; its entries
-    // past dcount are never stored or compared.
-    int pf_pi = 0;
-    auto prefetch = [&](int s, int buf) {
-        if (s < s1) {
-            const Geo o = geo(s, pf_pi);
-            pf_pi = o.pi;
-            const LineArgs& a = b.p[o.pi];
-            if (a.async && o.active) {
+    // prefetch of the step at cursor pc into stage buffer buf. With vec the entries per pixel
+    // are a multiple of 4, so a group with any valid disparity lies whole inside the volume;
+    // its entries past dcount are never stored or compared.
+    auto prefetch = [&](const Cursor& pc, int buf) {
+        if (pc.s < s1) {
+            const LineArgs& a = b.p[pc.pi];
+            if (a.async && pc.active) {
                 const T* src = a.src ? reinterpret_cast<const T*>(a.src) : reinterpret_cast<const T*>(a.vol);
-                const bool ok = o.line_ok && o.sl * o.ds + o.dq * kG < a.dcount;
-                const T* q = src + (ok ? elem0(a, o) : 0);
-                const int npos = a.n - o.k * kL;
+                const bool ok = line_of(pc) < a.nlines && pc.sl * pc.ds + pc.dq * kG < a.dcount;
+                const T* q = src + (ok ? elem0(a, pc) : 0);
+                const int npos = a.n - pc.k * kL;
 #pragma unroll
                 for (int i = 0; i < kL; ++i) {
                     const bool valid = ok && i < npos;
-                    cp_async<4 * sizeof(T)>(stage_at(a, o, buf, i), valid ? q + (size_t)i * a.elem_stride : src, valid);
+                    cp_async<4 * sizeof(T)>(stage_at(a, pc, buf, i), valid ? q + (size_t)i * a.elem_stride : src, valid);
                 }
             }
         }
         cp_async_commit();
     };
-    prefetch(s0, 0);
-    prefetch(s0 + 1, 1);
+    Cursor o = seek(s0);
+    Cursor pf = o;                              // two steps ahead of o
+    prefetch(pf, 0);
+    advance(pf);
+    prefetch(pf, 1);
+    advance(pf);
 
     WtaRegs wr;
-    int cur_pi = -1, cur_g = -1, pi = 0;
-    for (int s = s0, n_s = 0; s < s1; ++s, ++n_s) {
-        const Geo o = geo(s, pi);
-        pi = o.pi;
+    int cur_pi = -1, cur_g = -1;
+    for (int n_s = 0; o.s < s1; advance(o), ++n_s) {
+        const int pi = o.pi;
         const LineArgs& a = b.p[pi];
+        const int line = line_of(o);
+        const bool line_ok = o.active && line < a.nlines;
         // shared memory of this pair: [stage][coefficients][multipliers][scan buffers]
         float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + b.stage_bytes);
         float2* mul_all = reinterpret_cast<float2*>(co_all + a.lpc * 4 * o.pX);
@@ -254,7 +275,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
         }
         const int dl = o.sl * o.ds + o.dq * kG;                        // entry of d_first
         const int nvalid = max(0, min(4, a.dcount - dl));
-        const bool any = o.line_ok && nvalid > 0;
+        const bool any = line_ok && nvalid > 0;
         const int npos = a.n - o.k * kL;
         T* vol = reinterpret_cast<T*>(a.vol);
         float v[kL][4];
@@ -269,7 +290,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
             for (int i = 0; i < kL; ++i) lds4(stage_at(a, o, n_s & 1, i), v[i]);
         } else {
             const T* src = a.src ? reinterpret_cast<const T*>(a.src) : vol;
-            const T* q = src + (o.line_ok ? elem0(a, o) : 0);
+            const T* q = src + (line_ok ? elem0(a, o) : 0);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 if (any && i < npos) ld4(q, nvalid, a.vec != 0, v[i]);
@@ -287,7 +308,10 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
         }
         // the staging buffer is free once the forward sweep has read it: refill it two ahead
         dt_pair(v, co, o.pX, o.k, o.tq, o.dq, lane, o.wl, o.nwl, sa, sb, a.s2, mul,
-                [&]() { prefetch(s + 2, n_s & 1); }, o.active);
+                [&]() {
+                    prefetch(pf, n_s & 1);
+                    advance(pf);
+                }, o.active);
         if constexpr (MODE == kLineWta) {
             if (o.active) wr.fold(v, nvalid, a.d_base + dl);
             if (o.sl == o.nslices - 1 && o.active) {                    // the group's last slice
@@ -297,8 +321,8 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                     int bd;
                     wta_reduce_lanes(wr.entry(i), o.tq, best, bd);
                     const int pos = o.k * kL + i;
-                    if (o.dq == 0 && o.line_ok && pos < a.n) {
-                        const size_t pix = (size_t)o.line * a.pix_line + (size_t)pos * a.pix_pos;
+                    if (o.dq == 0 && line_ok && pos < a.n) {
+                        const size_t pix = (size_t)line * a.pix_line + (size_t)pos * a.pix_pos;
                         if (!a.wta.first) {                            // earlier launches: smaller d
                             const float pb = a.wta.bestv[pix];
                             if (!(best > pb)) { best = pb; bd = a.wta.bestd[pix]; }
@@ -312,7 +336,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                 }
             }
         } else {
-            T* q = vol + (o.line_ok ? elem0(a, o) : 0);
+            T* q = vol + (line_ok ? elem0(a, o) : 0);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 if (any && i < npos) st4(q, nvalid, a.vec != 0, v[i]);
