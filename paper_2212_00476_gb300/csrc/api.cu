@@ -299,7 +299,8 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
             minb2 = minb2 && a.minb2;
         }
         int bps = 0;
-        ZNCC_CUDA(lc, zncc_row_occupancy(r, mode, dtype, threads, smem, minb2, &bps), "occupancy query");
+        ZNCC_CUDA(lc, zncc_row_occupancy(r, mode, dtype, threads, smem, minb2, b.npairs == 1, &bps),
+                  "occupancy query");
         b.grid = std::max(1, std::min(b.total_items, lc->num_sms * std::max(1, bps)));
         ZNCC_LAUNCH(lc, kind, launch_zncc_row(r, b, threads, smem, mode, dtype, lc->cur), what);
     }
@@ -326,17 +327,11 @@ struct LinePass {
 // The block shape of a pair's pass: among lane counts per chunk (8, 4, 2, or the forced
 // one) and lines per block that fit in shared memory, prefer whole 64-byte segments per
 // chunk, then streaming through shared memory (async), then at least two resident blocks
-// per SM, then the most resident warps. Chosen once per context and pass signature.
-zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
-    const int forced = p.force_tq ? p.force_tq : (p.horiz ? c->h_tq : c->v_tq);
-    const long long key = ((((long long)p.horiz * 2 + p.mode) * 2 + p.dtype) * 2 + (a.vec ? 1 : 0)) * 16 +
-                          forced + ((long long)p.dcount << 20);
-    for (const LinePlan& pl : c->plans)
-        if (pl.key == key) {
-            a.tq = pl.tq; a.lpc = pl.lpc; a.nch = pl.nch; a.async = pl.async;
-            return ZNCC_OK;
-        }
-    LinePlan best{key, 0, 0, 0, 0, 0, 0};
+// per SM, then the most resident warps. `found` is false when no shape fits; on success
+// the shape is also left in a.
+cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePass& p, LinePlan& best,
+                             bool& found) {
+    found = false;
     long long best_score = -1;
     const int tqs[4] = {8, 4, 2, 1};
     for (int ti = 0; ti < 4; ++ti) {
@@ -350,9 +345,10 @@ zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
             for (int lpc = std::max(1, std::min(8, 256 / per_line)); lpc >= 1; --lpc) {
                 a.tq = tq; a.nch = nch; a.lpc = lpc; a.async = async;
                 const size_t smem = line_pair_smem_bytes(p.mode, p.dtype, a);
-                if (smem > (size_t)c->smem_max) continue;
+                if (smem > (size_t)smem_max) continue;
                 int bps = 0;
-                ZNCC_CUDA(c, line_pair_occupancy(p.mode, p.dtype, lpc * per_line, smem, &bps), "occupancy query");
+                cudaError_t e = line_pair_occupancy(p.mode, p.dtype, lpc * per_line, smem, true, &bps);
+                if (e != cudaSuccess) return e;
                 if (bps < 1) continue;
                 const long long warps = (long long)bps * lpc * per_line / 32;
                 const long long score = (whole_bursts ? 10000000LL : 0) + async * 1000000LL +
@@ -365,10 +361,76 @@ zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
             }
         }
     }
-    if (best_score < 0) return fail(c, ZNCC_EUNSUPPORTED, "line too long for the DT kernel's shared memory");
+    if (best_score < 0) return cudaSuccess;
+    found = true;
     a.tq = best.tq; a.lpc = best.lpc; a.nch = best.nch; a.async = best.async;
+    return cudaSuccess;
+}
+
+// The block shape of a pair's pass (choose_line_plan), chosen once per context and pass
+// signature.
+zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
+    const int forced = p.force_tq ? p.force_tq : (p.horiz ? c->h_tq : c->v_tq);
+    const long long key = ((((long long)p.horiz * 2 + p.mode) * 2 + p.dtype) * 2 + (a.vec ? 1 : 0)) * 16 +
+                          forced + ((long long)p.dcount << 20);
+    for (const LinePlan& pl : c->plans)
+        if (pl.key == key) {
+            a.tq = pl.tq; a.lpc = pl.lpc; a.nch = pl.nch; a.async = pl.async;
+            return ZNCC_OK;
+        }
+    LinePlan best{key, 0, 0, 0, 0, 0, 0};
+    bool found = false;
+    ZNCC_CUDA(c, choose_line_plan(c->smem_max, forced, a, p, best, found), "occupancy query");
+    if (!found) return fail(c, ZNCC_EUNSUPPORTED, "line too long for the DT kernel's shared memory");
     c->plans.push_back(best);
     return ZNCC_OK;
+}
+
+// The arguments of one pair's pass, before its block shape is chosen.
+void fill_line_args(LineArgs& a, const LinePass& p, int W, int H, const float4* coefH, const float4* coefV) {
+    memset(&a, 0, sizeof(a));
+    a.vol = p.vol;
+    a.src = p.src;
+    a.src_ones = p.ones ? 1 : 0;
+    a.elem_stride = p.horiz ? p.dstride : (long long)W * p.dstride;
+    a.line_stride = p.horiz ? (long long)W * p.dstride : p.dstride;
+    a.n = p.horiz ? W : H;
+    a.nlines = p.horiz ? H : W;
+    a.dcount = p.dcount;
+    a.d_base = 0;
+    a.ahat_in = p.ahat_in;
+    a.ahat_out = p.ahat_out;
+    a.coef = p.horiz ? coefH : coefV;
+    a.coef_line_stride = p.horiz ? W : H;
+    a.s2 = p.s2;
+    const void* in = p.src ? p.src : p.vol;
+    const size_t al = p.dtype == 0 ? 16 : 8;
+    a.vec = (p.dstride % 4 == 0) && ((uintptr_t)p.vol % al == 0) && ((uintptr_t)in % al == 0) ? 1 : 0;
+    a.wta.disp = p.disp;
+    a.wta.first = 1;
+    a.wta.last = 1;
+    a.pix_line = p.horiz ? W : 1;
+    a.pix_pos = p.horiz ? 1 : W;
+}
+
+// Appends a pair (its block shape chosen) to a launch: its items and steps, and the block's
+// thread count and shared memory (staging region and the rest) grown to cover it.
+void add_line_pair(LineBatch& b, const LineArgs& ai, int mode, int dtype, int& threads, size_t& stage,
+                   size_t& rest) {
+    LineArgs& a = b.p[b.npairs++];
+    a = ai;
+    const int nslices = (a.dcount + kG * a.tq - 1) / (kG * a.tq);
+    const int ngroups = (a.nlines + a.lpc - 1) / a.lpc;
+    a.step0 = b.total_steps;
+    a.nsteps = ngroups * nslices;
+    a.item0 = b.total_items;
+    a.nitems = mode == kLineWta ? ngroups : a.nsteps;
+    b.total_steps += a.nsteps;
+    b.total_items += a.nitems;
+    threads = std::max(threads, a.lpc * a.nch * a.tq);
+    const size_t st = line_stage_bytes(dtype, a);
+    stage = std::max(stage, st);
+    rest = std::max(rest, line_pair_smem_bytes(mode, dtype, a) - st);
 }
 
 // Line-pair launches over the passes of several pairs (the same mode and storage): pairs
@@ -380,29 +442,7 @@ zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passe
         zncc_ctx* c = ctxs[i];
         const LinePass& p = passes[i];
         LineArgs& a = args[i];
-        memset(&a, 0, sizeof(a));
-        a.vol = p.vol;
-        a.src = p.src;
-        a.src_ones = p.ones ? 1 : 0;
-        a.elem_stride = p.horiz ? p.dstride : (long long)c->W * p.dstride;
-        a.line_stride = p.horiz ? (long long)c->W * p.dstride : p.dstride;
-        a.n = p.horiz ? c->W : c->H;
-        a.nlines = p.horiz ? c->H : c->W;
-        a.dcount = p.dcount;
-        a.d_base = 0;
-        a.ahat_in = p.ahat_in;
-        a.ahat_out = p.ahat_out;
-        a.coef = p.horiz ? c->coefH : c->coefV;
-        a.coef_line_stride = p.horiz ? c->W : c->H;
-        a.s2 = p.s2;
-        const void* in = p.src ? p.src : p.vol;
-        const size_t al = p.dtype == 0 ? 16 : 8;
-        a.vec = (p.dstride % 4 == 0) && ((uintptr_t)p.vol % al == 0) && ((uintptr_t)in % al == 0) ? 1 : 0;
-        a.wta.disp = p.disp;
-        a.wta.first = 1;
-        a.wta.last = 1;
-        a.pix_line = p.horiz ? c->W : 1;
-        a.pix_pos = p.horiz ? 1 : c->W;
+        fill_line_args(a, p, c->W, c->H, c->coefH, c->coefV);
         if (plan_line_pass(c, a, p) != ZNCC_OK) return fail(lc, ZNCC_EUNSUPPORTED, c->err);
     }
     bool done[kMaxBatch] = {false};
@@ -418,26 +458,13 @@ zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passe
             if (done[i] || ai.tq != a0.tq || ai.nch != a0.nch || ai.lpc != a0.lpc || ai.async != a0.async)
                 continue;
             done[i] = true;
-            LineArgs& a = b.p[b.npairs++];
-            a = ai;
-            const int nslices = (a.dcount + kG * a.tq - 1) / (kG * a.tq);
-            const int ngroups = (a.nlines + a.lpc - 1) / a.lpc;
-            a.step0 = b.total_steps;
-            a.nsteps = ngroups * nslices;
-            a.item0 = b.total_items;
-            a.nitems = mode == kLineWta ? ngroups : a.nsteps;
-            b.total_steps += a.nsteps;
-            b.total_items += a.nitems;
-            threads = std::max(threads, a.lpc * a.nch * a.tq);
-            const size_t st = line_stage_bytes(dtype, a);
-            stage = std::max(stage, st);
-            rest = std::max(rest, line_pair_smem_bytes(mode, dtype, a) - st);
+            add_line_pair(b, ai, mode, dtype, threads, stage, rest);
         }
         b.stage_bytes = (long long)stage;
         const size_t smem = stage + rest;
         if (smem > (size_t)lc->smem_max) return fail(lc, ZNCC_EUNSUPPORTED, "DT pass exceeds shared memory");
         int bps = 0;
-        ZNCC_CUDA(lc, line_pair_occupancy(mode, dtype, threads, smem, &bps), "occupancy query");
+        ZNCC_CUDA(lc, line_pair_occupancy(mode, dtype, threads, smem, b.npairs == 1, &bps), "occupancy query");
         b.grid = std::max(1, std::min(b.total_items, lc->num_sms * std::max(1, bps)));
         ZNCC_LAUNCH(lc, kind, launch_line_batch(b, threads, smem, mode, dtype, lc->cur), "DT pass pair");
     }

@@ -135,9 +135,15 @@ size_t line_stage_bytes(int dtype, const LineArgs& a) {
 }
 
 
-template <typename T, int MODE>
+// Every pair of a launch has the same block shape (tq, nch, lpc, async): the launcher groups
+// pairs that way, so the shape and this thread's place in it are read from pair 0 at
+// constant offsets of the parameter block; only extents, strides and pointers differ between
+// pairs. SINGLE: the launch holds one pair, whose arguments are then all read at constant
+// offsets instead of through a dynamic index.
+template <typename T, int MODE, bool SINGLE>
 __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineBatch b) {
     extern __shared__ float4 smem4[];
+    auto P = [&](int pi) -> const LineArgs& { return b.p[SINGLE ? 0 : pi]; };
     const int lane = threadIdx.x & 31;
     const int i0 = (int)((long long)blockIdx.x * b.total_items / b.grid);
     const int i1 = (int)((long long)(blockIdx.x + 1) * b.total_items / b.grid);
@@ -145,46 +151,41 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     auto step_of_item = [&](int item) -> int {
         if (item >= b.total_items) return b.total_steps;
         int q = 0;
-        while (item >= b.p[q].item0 + b.p[q].nitems) ++q;
-        const int spi = b.p[q].nsteps / b.p[q].nitems;
-        return b.p[q].step0 + (item - b.p[q].item0) * spi;
+        if (!SINGLE)
+            while (item >= b.p[q].item0 + b.p[q].nitems) ++q;
+        const LineArgs& a = P(q);
+        const int spi = a.nsteps / a.nitems;
+        return a.step0 + (item - a.item0) * spi;
     };
     const int s0 = step_of_item(i0), s1 = step_of_item(i1);
 
+    // block shape (shared by the launch's pairs) and this thread's place in it
+    const int tq = b.p[0].tq, nch = b.p[0].nch, lpc = b.p[0].lpc;
+    const bool async = b.p[0].async != 0;
+    const int per_line = nch * tq, nwl = per_line >> 5, pX = plane_of(nch * kL), ds = kG * tq;
+    const bool active = (int)threadIdx.x < lpc * per_line;
+    const int li = active ? threadIdx.x / per_line : 0;
+    const int tl = active ? threadIdx.x - li * per_line : 0;
+    const int k = tl / tq, dq = tl - k * tq, wl = tl >> 5;
+
     // A cursor over steps: the pair, the line group and the slice of a step, advanced one
-    // step at a time, and this thread's place in the pair's block shape (recomputed only
-    // when the pair changes).
+    // step at a time.
     struct Cursor {
-        int s, pi, g, sl;
-        int tq, nch, per_line, nwl, span, pX, ds, nslices, ngroups;
-        int li, tl, k, dq, wl;
-        bool active;
+        int s, pi, g, sl, nslices, ngroups;
     };
     auto set_pair = [&](Cursor& c) {
-        const LineArgs& a = b.p[c.pi];
-        c.tq = a.tq;
-        c.nch = a.nch;
-        c.per_line = c.nch * c.tq;
-        c.nwl = c.per_line >> 5;
-        c.span = c.nch * kL;
-        c.pX = plane_of(c.span);
-        c.ds = kG * c.tq;
-        c.nslices = (a.dcount + c.ds - 1) / c.ds;
+        const LineArgs& a = P(c.pi);
+        c.nslices = (a.dcount + ds - 1) / ds;
         c.ngroups = a.nsteps / c.nslices;
-        c.active = (int)threadIdx.x < a.lpc * c.per_line;
-        c.li = c.active ? threadIdx.x / c.per_line : 0;
-        c.tl = c.active ? threadIdx.x - c.li * c.per_line : 0;
-        c.k = c.tl / c.tq;
-        c.dq = c.tl - c.k * c.tq;
-        c.wl = c.tl >> 5;
     };
     auto seek = [&](int s) -> Cursor {          // once per block
         Cursor c;
         c.s = s;
         c.pi = 0;
-        while (c.pi + 1 < b.npairs && s >= b.p[c.pi].step0 + b.p[c.pi].nsteps) ++c.pi;
+        if (!SINGLE)
+            while (c.pi + 1 < b.npairs && s >= b.p[c.pi].step0 + b.p[c.pi].nsteps) ++c.pi;
         set_pair(c);
-        const int ls = s - b.p[c.pi].step0;
+        const int ls = s - P(c.pi).step0;
         c.g = ls / c.nslices;
         c.sl = ls - c.g * c.nslices;
         return c;
@@ -193,38 +194,37 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
         ++c.s;
         if (++c.sl == c.nslices) {
             c.sl = 0;
-            if (++c.g == c.ngroups && c.pi + 1 < b.npairs) {
+            if (++c.g == c.ngroups && !SINGLE && c.pi + 1 < b.npairs) {
                 c.g = 0;
                 ++c.pi;
                 set_pair(c);
             }
         }
     };
-    auto line_of = [&](const Cursor& c) { return c.g * b.p[c.pi].lpc + c.li; };
+    auto line_of = [&](const Cursor& c) { return c.g * lpc + li; };
     auto elem0 = [&](const LineArgs& a, const Cursor& c) -> size_t {   // the chunk's first group
-        return (size_t)line_of(c) * a.line_stride + (size_t)(c.k * kL) * a.elem_stride + c.sl * c.ds + c.dq * kG;
+        return (size_t)line_of(c) * a.line_stride + (size_t)(k * kL) * a.elem_stride + c.sl * ds + dq * kG;
     };
     T* stage = reinterpret_cast<T*>(smem4);
     // stage buffer buf of a step: [2][lpc][kL][per_line] groups of 4 entries
-    auto stage_at = [&](const LineArgs& a, const Cursor& c, int buf, int i) -> T* {
-        return stage + ((size_t)((buf * a.lpc + c.li) * kL + i) * c.per_line + c.tl) * 4;
+    auto stage_at = [&](int buf, int i) -> T* {
+        return stage + ((size_t)((buf * lpc + li) * kL + i) * per_line + tl) * 4;
     };
     // prefetch of the step at cursor pc into stage buffer buf. With vec the entries per pixel
     // are a multiple of 4, so a group with any valid disparity lies whole inside the volume;
     // its entries past dcount are never stored or compared.
     auto prefetch = [&](const Cursor& pc, int buf) {
-        if (pc.s < s1) {
-            const LineArgs& a = b.p[pc.pi];
-            if (a.async && pc.active) {
-                const T* src = a.src ? reinterpret_cast<const T*>(a.src) : reinterpret_cast<const T*>(a.vol);
-                const bool ok = line_of(pc) < a.nlines && pc.sl * pc.ds + pc.dq * kG < a.dcount;
-                const T* q = src + (ok ? elem0(a, pc) : 0);
-                const int npos = a.n - pc.k * kL;
+        if (async && pc.s < s1 && active) {
+            const LineArgs& a = P(pc.pi);
+            const T* src = a.src ? reinterpret_cast<const T*>(a.src) : reinterpret_cast<const T*>(a.vol);
+            const bool ok = line_of(pc) < a.nlines && pc.sl * ds + dq * kG < a.dcount;
+            const T* q = src + (ok ? elem0(a, pc) : 0);
+            const long long es = a.elem_stride;
+            const int npos = a.n - k * kL;
 #pragma unroll
-                for (int i = 0; i < kL; ++i) {
-                    const bool valid = ok && i < npos;
-                    cp_async<4 * sizeof(T)>(stage_at(a, pc, buf, i), valid ? q + (size_t)i * a.elem_stride : src, valid);
-                }
+            for (int i = 0; i < kL; ++i) {
+                const bool valid = ok && i < npos;
+                cp_async<4 * sizeof(T)>(stage_at(buf, i), valid ? q + (size_t)i * es : src, valid);
             }
         }
         cp_async_commit();
@@ -236,36 +236,37 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     prefetch(pf, 1);
     advance(pf);
 
+    // shared memory: [stage][coefficients][multipliers][scan buffers]
+    float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + b.stage_bytes);
+    float2* mul_all = reinterpret_cast<float2*>(co_all + lpc * 4 * pX);
+    float4* sb_all = reinterpret_cast<float4*>(mul_all + lpc * 4 * pX);
+    float* sa_all = reinterpret_cast<float*>(sb_all + lpc * 2 * nwl * tq);
+    const float4* co = co_all + li * 4 * pX;
+    const float2* mul = mul_all + li * 4 * pX;
+    float4* sb = sb_all + li * 2 * nwl * tq;
+    float* sa = sa_all + li * 2 * nwl * tq;
+
     WtaRegs wr;
     int cur_pi = -1, cur_g = -1;
     for (int n_s = 0; o.s < s1; advance(o), ++n_s) {
         const int pi = o.pi;
-        const LineArgs& a = b.p[pi];
+        const LineArgs& a = P(pi);
         const int line = line_of(o);
-        const bool line_ok = o.active && line < a.nlines;
-        // shared memory of this pair: [stage][coefficients][multipliers][scan buffers]
-        float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + b.stage_bytes);
-        float2* mul_all = reinterpret_cast<float2*>(co_all + a.lpc * 4 * o.pX);
-        float4* sb_all = reinterpret_cast<float4*>(mul_all + a.lpc * 4 * o.pX);
-        float* sa_all = reinterpret_cast<float*>(sb_all + a.lpc * 2 * o.nwl * o.tq);
-        const float4* co = co_all + o.li * 4 * o.pX;
-        const float2* mul = mul_all + o.li * 4 * o.pX;
-        float4* sb = sb_all + o.li * 2 * o.nwl * o.tq;
-        float* sa = sa_all + o.li * 2 * o.nwl * o.tq;
+        const bool line_ok = active && line < a.nlines;
 
         if (pi != cur_pi || o.g != cur_g) {     // stage the coefficients and multipliers of the group
             __syncthreads();
-            for (int l2 = 0; l2 < a.lpc; ++l2) {
-                const int ln = o.g * a.lpc + l2;
+            for (int l2 = 0; l2 < lpc; ++l2) {
+                const int ln = o.g * lpc + l2;
                 const bool ok = ln < a.nlines;
-                for (int t = threadIdx.x; t < o.span; t += blockDim.x) {
+                for (int t = threadIdx.x; t < nch * kL; t += blockDim.x) {
                     const bool in = ok && t < a.n;
-                    co_all[l2 * 4 * o.pX + cidx(t, o.pX)] =
+                    co_all[l2 * 4 * pX + cidx(t, pX)] =
                         in ? __ldg(a.coef + (size_t)ln * a.coef_line_stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
                     const size_t pix = (size_t)ln * a.pix_line + (size_t)t * a.pix_pos;
                     const float mi = in && a.ahat_in ? __ldg(a.ahat_in + pix) : 1.0f;
                     const float mo = in && a.ahat_out ? a.s2 / __ldg(a.ahat_out + pix) : a.s2;
-                    mul_all[l2 * 4 * o.pX + cidx(t, o.pX)] = make_float2(mi, mo);
+                    mul_all[l2 * 4 * pX + cidx(t, pX)] = make_float2(mi, mo);
                 }
             }
             if constexpr (MODE == kLineWta) wr.reset();
@@ -273,10 +274,10 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
             cur_pi = pi;
             cur_g = o.g;
         }
-        const int dl = o.sl * o.ds + o.dq * kG;                        // entry of d_first
+        const int dl = o.sl * ds + dq * kG;                        // entry of d_first
         const int nvalid = max(0, min(4, a.dcount - dl));
         const bool any = line_ok && nvalid > 0;
-        const int npos = a.n - o.k * kL;
+        const int npos = a.n - k * kL;
         T* vol = reinterpret_cast<T*>(a.vol);
         float v[kL][4];
         cp_async_wait<1>();                                            // this step's copies landed
@@ -285,9 +286,9 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
             for (int i = 0; i < kL; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v[i][j] = (any && i < npos && j < nvalid) ? 1.0f : 0.0f;
-        } else if (a.async) {
+        } else if (async) {
 #pragma unroll
-            for (int i = 0; i < kL; ++i) lds4(stage_at(a, o, n_s & 1, i), v[i]);
+            for (int i = 0; i < kL; ++i) lds4(stage_at(n_s & 1, i), v[i]);
         } else {
             const T* src = a.src ? reinterpret_cast<const T*>(a.src) : vol;
             const T* q = src + (line_ok ? elem0(a, o) : 0);
@@ -298,30 +299,30 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                 q += a.elem_stride;
             }
         }
-        if (a.ahat_in && o.active) {
+        if (a.ahat_in && active) {
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
-                const float m = mul[cidx(o.k * kL + i, o.pX)].x;
+                const float m = mul[cidx(k * kL + i, pX)].x;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v[i][j] *= m;
             }
         }
         // the staging buffer is free once the forward sweep has read it: refill it two ahead
-        dt_pair(v, co, o.pX, o.k, o.tq, o.dq, lane, o.wl, o.nwl, sa, sb, a.s2, mul,
+        dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2, mul,
                 [&]() {
                     prefetch(pf, n_s & 1);
                     advance(pf);
-                }, o.active);
+                }, active);
         if constexpr (MODE == kLineWta) {
-            if (o.active) wr.fold(v, nvalid, a.d_base + dl);
-            if (o.sl == o.nslices - 1 && o.active) {                    // the group's last slice
+            if (active) wr.fold(v, nvalid, a.d_base + dl);
+            if (o.sl == o.nslices - 1 && active) {                    // the group's last slice
 #pragma unroll
                 for (int i = 0; i < kL; ++i) {
                     float best;
                     int bd;
-                    wta_reduce_lanes(wr.entry(i), o.tq, best, bd);
-                    const int pos = o.k * kL + i;
-                    if (o.dq == 0 && line_ok && pos < a.n) {
+                    wta_reduce_lanes(wr.entry(i), tq, best, bd);
+                    const int pos = k * kL + i;
+                    if (dq == 0 && line_ok && pos < a.n) {
                         const size_t pix = (size_t)line * a.pix_line + (size_t)pos * a.pix_pos;
                         if (!a.wta.first) {                            // earlier launches: smaller d
                             const float pb = a.wta.bestv[pix];
@@ -354,13 +355,19 @@ size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a) {
     return line_stage_bytes(dtype, a) + (size_t)a.lpc * ((16ull + 8ull) * 4 * pX + dt_scan_bytes(nwl, a.tq));
 }
 
-static void (*line_pair_fn(int mode, int dtype))(LineBatch) {
-    if (mode == kLineStore) return dtype == 0 ? k_line_pair<float, kLineStore> : k_line_pair<__half, kLineStore>;
-    return dtype == 0 ? k_line_pair<float, kLineWta> : k_line_pair<__half, kLineWta>;
+template <bool SINGLE>
+static void (*line_pair_fn_t(int mode, int dtype))(LineBatch) {
+    if (mode == kLineStore)
+        return dtype == 0 ? k_line_pair<float, kLineStore, SINGLE> : k_line_pair<__half, kLineStore, SINGLE>;
+    return dtype == 0 ? k_line_pair<float, kLineWta, SINGLE> : k_line_pair<__half, kLineWta, SINGLE>;
 }
 
-cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, int* blocks_per_sm) {
-    void (*fn)(LineBatch) = line_pair_fn(mode, dtype);
+static void (*line_pair_fn(int mode, int dtype, bool single))(LineBatch) {
+    return single ? line_pair_fn_t<true>(mode, dtype) : line_pair_fn_t<false>(mode, dtype);
+}
+
+cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, bool single, int* blocks_per_sm) {
+    void (*fn)(LineBatch) = line_pair_fn(mode, dtype, single);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
@@ -369,7 +376,7 @@ cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, i
 cudaError_t launch_line_batch(const LineBatch& b, int threads, size_t smem, int mode, int dtype,
                               cudaStream_t st) {
     dim3 grid(b.grid);
-    void (*fn)(LineBatch) = line_pair_fn(mode, dtype);
+    void (*fn)(LineBatch) = line_pair_fn(mode, dtype, b.npairs == 1);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, threads, smem, st>>>(b);
@@ -427,15 +434,15 @@ cudaError_t launch_zncc_row(int R, const RowBatch& b, int threads, size_t smem, 
 }
 
 cudaError_t zncc_row_occupancy(int R, int mode, int dtype, int threads, size_t smem, bool minb2,
-                               int* blocks_per_sm) {
+                               bool single, int* blocks_per_sm) {
     switch (R) {
-        case 1: return zncc_row_occupancy_r1(mode, dtype, threads, smem, minb2, blocks_per_sm);
-        case 2: return zncc_row_occupancy_r2(mode, dtype, threads, smem, minb2, blocks_per_sm);
-        case 3: return zncc_row_occupancy_r3(mode, dtype, threads, smem, minb2, blocks_per_sm);
-        case 4: return zncc_row_occupancy_r4(mode, dtype, threads, smem, minb2, blocks_per_sm);
-        case 5: return zncc_row_occupancy_r5(mode, dtype, threads, smem, minb2, blocks_per_sm);
-        case 6: return zncc_row_occupancy_r6(mode, dtype, threads, smem, minb2, blocks_per_sm);
-        case 7: return zncc_row_occupancy_r7(mode, dtype, threads, smem, minb2, blocks_per_sm);
+        case 1: return zncc_row_occupancy_r1(mode, dtype, threads, smem, minb2, single, blocks_per_sm);
+        case 2: return zncc_row_occupancy_r2(mode, dtype, threads, smem, minb2, single, blocks_per_sm);
+        case 3: return zncc_row_occupancy_r3(mode, dtype, threads, smem, minb2, single, blocks_per_sm);
+        case 4: return zncc_row_occupancy_r4(mode, dtype, threads, smem, minb2, single, blocks_per_sm);
+        case 5: return zncc_row_occupancy_r5(mode, dtype, threads, smem, minb2, single, blocks_per_sm);
+        case 6: return zncc_row_occupancy_r6(mode, dtype, threads, smem, minb2, single, blocks_per_sm);
+        case 7: return zncc_row_occupancy_r7(mode, dtype, threads, smem, minb2, single, blocks_per_sm);
         default: return cudaErrorInvalidValue;
     }
 }

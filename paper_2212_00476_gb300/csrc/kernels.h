@@ -85,9 +85,10 @@ cudaError_t launch_line_batch(const LineBatch& b, int threads, size_t smem, int 
 cudaError_t launch_zncc_row(int R, const RowBatch& b, int threads, size_t smem, int mode, int dtype,
                             cudaStream_t st);
 cudaError_t zncc_row_occupancy(int R, int mode, int dtype, int threads, size_t smem, bool minb2,
-                               int* blocks_per_sm);
+                               bool single, int* blocks_per_sm);
 size_t line_stage_bytes(int dtype, const LineArgs& a);
-cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, int* blocks_per_sm);
+// single: the variant for launches of one pair (npairs == 1), which the launchers pick
+cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, bool single, int* blocks_per_sm);
 cudaError_t launch_window_stats(const uint8_t* img, int pitch, int W, int H, int r, int x_begin,
                                 int nx, int* S, int* Q, float* isig, int2* packed,
                                 cudaStream_t st);
@@ -113,7 +114,8 @@ cudaError_t launch_wta_volume(const void* cost, int dtype, int W, int H, int D, 
 #define ZNCC_DECLARE_ROW(R)                                                                     \
     cudaError_t launch_zncc_row_r##R(const RowBatch& b, int threads, size_t smem, int mode, int dtype, \
                                      cudaStream_t st);                                             \
-    cudaError_t zncc_row_occupancy_r##R(int mode, int dtype, int threads, size_t smem, bool minb2, int* bps);
+    cudaError_t zncc_row_occupancy_r##R(int mode, int dtype, int threads, size_t smem, bool minb2, bool single, \
+                                        int* bps);
 ZNCC_DECLARE_ROW(1)
 ZNCC_DECLARE_ROW(2)
 ZNCC_DECLARE_ROW(3)

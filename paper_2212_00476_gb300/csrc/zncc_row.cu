@@ -15,7 +15,7 @@ cudaError_t ZNCC_CAT(launch_zncc_row_r, ZNCC_R)(const RowBatch& b, int threads, 
     return launch_zncc_row_impl<ZNCC_R>(b, threads, smem, mode, dtype, st);
 }
 cudaError_t ZNCC_CAT(zncc_row_occupancy_r, ZNCC_R)(int mode, int dtype, int threads, size_t smem, bool minb2,
-                                                   int* bps) {
-    return zncc_row_occupancy_impl<ZNCC_R>(mode, dtype, threads, smem, minb2, bps);
+                                                   bool single, int* bps) {
+    return zncc_row_occupancy_impl<ZNCC_R>(mode, dtype, threads, smem, minb2, single, bps);
 }
 }  // namespace zncc

@@ -231,15 +231,18 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int run, 
     }
 }
 
-template <int R, typename T, int MODE, int MINB>
+// SINGLE: the launch holds one pair, whose arguments are then read at constant offsets of
+// the parameter block instead of through a dynamic index.
+template <int R, typename T, int MODE, int MINB, bool SINGLE>
 __global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(const __grid_constant__ RowBatch b) {
     extern __shared__ uint4 smem_u4[];
     const int i0 = (int)((long long)blockIdx.x * b.total_items / b.grid);
     const int i1 = (int)((long long)(blockIdx.x + 1) * b.total_items / b.grid);
     int pi = 0;
     for (int item = i0; item < i1; ++item) {
-        while (item >= b.p[pi].item0 + b.p[pi].nitems) ++pi;
-        const RowArgs& a = b.p[pi];
+        if (!SINGLE)
+            while (item >= b.p[pi].item0 + b.p[pi].nitems) ++pi;
+        const RowArgs& a = b.p[SINGLE ? 0 : pi];
         const int ds = kG * a.tq;
         const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
         const int nruns = (nslices + a.spb - 1) / a.spb;
@@ -262,23 +265,31 @@ inline size_t zncc_row_smem(int R, int mode, const RowArgs& a, int nthreads) {
     return b;
 }
 
+template <int R, int MINB, bool SINGLE>
+static void (*row_fn_t(int mode, int dtype))(RowBatch) {
+    if (mode == kModeRaw)
+        return dtype == 0 ? k_zncc_row<R, float, kModeRaw, MINB, SINGLE> : k_zncc_row<R, __half, kModeRaw, MINB, SINGLE>;
+    if (mode == kModeHPair)
+        return dtype == 0 ? k_zncc_row<R, float, kModeHPair, MINB, SINGLE> : k_zncc_row<R, __half, kModeHPair, MINB, SINGLE>;
+    return k_zncc_row<R, float, kModeWta, MINB, SINGLE>;
+}
+
+// Batched launches come from the fused path only (HPair, Wta); a batched Raw launch would
+// use the single-pair variant's arguments and is never made.
 template <int R>
-static void (*row_fn(int mode, int dtype, bool minb2))(RowBatch) {
-    if (minb2) {
-        if (mode == kModeRaw) return dtype == 0 ? k_zncc_row<R, float, kModeRaw, 2> : k_zncc_row<R, __half, kModeRaw, 2>;
-        if (mode == kModeHPair) return dtype == 0 ? k_zncc_row<R, float, kModeHPair, 2> : k_zncc_row<R, __half, kModeHPair, 2>;
-        return k_zncc_row<R, float, kModeWta, 2>;
-    }
-    if (mode == kModeRaw) return dtype == 0 ? k_zncc_row<R, float, kModeRaw, 1> : k_zncc_row<R, __half, kModeRaw, 1>;
-    if (mode == kModeHPair) return dtype == 0 ? k_zncc_row<R, float, kModeHPair, 1> : k_zncc_row<R, __half, kModeHPair, 1>;
-    return k_zncc_row<R, float, kModeWta, 1>;
+static void (*row_fn(int mode, int dtype, bool minb2, bool single))(RowBatch) {
+    if (single) return minb2 ? row_fn_t<R, 2, true>(mode, dtype) : row_fn_t<R, 1, true>(mode, dtype);
+    if (mode == kModeRaw) return nullptr;
+    return minb2 ? row_fn_t<R, 2, false>(mode, dtype) : row_fn_t<R, 1, false>(mode, dtype);
 }
 
 // The variant limited to 96 registers (two resident blocks per SM) serves blocks of up to
 // 320 threads when minb2 is set; larger blocks use the 128-register one.
 template <int R>
-cudaError_t zncc_row_occupancy_impl(int mode, int dtype, int threads, size_t smem, bool minb2, int* bps) {
-    void (*fn)(RowBatch) = row_fn<R>(mode, dtype, minb2 && threads <= 320);
+cudaError_t zncc_row_occupancy_impl(int mode, int dtype, int threads, size_t smem, bool minb2, bool single,
+                                    int* bps) {
+    void (*fn)(RowBatch) = row_fn<R>(mode, dtype, minb2 && threads <= 320, single);
+    if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, threads, smem);
@@ -289,7 +300,8 @@ cudaError_t launch_zncc_row_impl(const RowBatch& b, int threads, size_t smem, in
                                  cudaStream_t st) {
     bool minb2 = true;
     for (int i = 0; i < b.npairs; ++i) minb2 = minb2 && b.p[i].minb2;
-    void (*fn)(RowBatch) = row_fn<R>(mode, dtype, minb2 && threads <= 320);
+    void (*fn)(RowBatch) = row_fn<R>(mode, dtype, minb2 && threads <= 320, b.npairs == 1);
+    if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<b.grid, threads, smem, st>>>(b);
