@@ -93,6 +93,50 @@ zncc_status zncc_cost_volume(zncc_ctx* ctx, const uint8_t* left, const uint8_t* 
 zncc_status dt_aggregate(zncc_ctx* ctx, const uint8_t* guide_left, int pitch, void* cost,
                          zncc_dtype dtype, float sigma_s, float sigma_r, int iters);
 
+/* dt_aggregate without allocating anything. The paper has no counterpart: this entry point
+ * serves callers that must not allocate while they run, such as
+ *  - a server that has committed its device memory in full to its own pools, for which a
+ *    cudaMalloc would fail or evict,
+ *  - a loop with a fixed latency budget, which cannot absorb cudaMalloc, nor cudaFree (it
+ *    waits for every stream of the device), nor a host heap allocation,
+ *  - code that runs where the allocator must not be entered (inside a custom allocator's
+ *    own callbacks, or while another thread holds the allocator's lock).
+ * It computes what dt_aggregate computes (Sec. III-B, Eqs. (3)-(6), weights of Eq. (11)) on
+ * a width x height x max_disp volume, without a context: the DT coefficients go to a scratch
+ * array compiled into the library's device code (a static __device__ array of 64 MiB), which
+ * the CUDA driver reserves on a device when that code is loaded there, once per process. The
+ * call makes no cudaMalloc, cudaFree or host heap allocation, and keeps no pointer.
+ *
+ * Limit: width * height <= 2,097,152 pixels (32 bytes of scratch per pixel; 1920 x 1080
+ * fits), with width <= 3072, height <= 4096, max_disp <= 1024. A larger image returns
+ * ZNCC_EUNSUPPORTED before anything is queued, with the limit in zncc_last_error(NULL).
+ *
+ * Set-up: the first call on each device obtains the scratch's address (cudaGetSymbolAddress,
+ * which may load the library's device code) and the device's limits; the first call for each
+ * new line length, disparity count and storage type chooses its launch shapes (occupancy
+ * queries). Make these first calls once, at set-up, before any stream capture begins.
+ *
+ * Zero state: nothing in the scratch needs to start at zero. Each call writes every
+ * coefficient of its image before it reads any, so leftovers of an earlier call are never
+ * read.
+ *
+ * Overlapping calls race: there is one scratch per device, shared by every call in the
+ * process. Calls whose GPU work may overlap (on different streams with no ordering between
+ * them, or from several host threads) overwrite each other's coefficients and give wrong
+ * results. Issue them on one stream, or order them with events. The host-side state is
+ * guarded by a mutex, so concurrent calls are safe on the host; only their GPU work races.
+ *
+ * Arguments: guide_left is device uint8 [H][W] with row pitch `pitch` (>= width); cost is a
+ * device [H][W][max_disp] volume of `dtype`, aggregated in place, owned by the caller and
+ * valid until the queued work completes. sigma_s > 0, sigma_r > 0, iters in [0, 64]
+ * (0 returns at once). cuda_stream is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream); the work is queued on it asynchronously. Errors: ZNCC_EINVAL (a NULL
+ * pointer or an argument out of range), ZNCC_EUNSUPPORTED (the size limits above),
+ * ZNCC_ECUDA (a CUDA call failed); the text is in zncc_last_error(NULL) (per host thread). */
+zncc_status dt_aggregate_noalloc(const uint8_t* guide_left, int pitch, int width, int height,
+                                 int max_disp, void* cost, zncc_dtype dtype, float sigma_s,
+                                 float sigma_r, int iters, void* cuda_stream);
+
 /* WTA disparity (Sec. III-C, Eq. (WTA1)): for each pixel the smallest d with the largest
  * cost (argmin of 1 - C). cost: device [H][W][D]; disp: device uint16 [H][W]. */
 zncc_status wta_disparity(zncc_ctx* ctx, const void* cost, zncc_dtype dtype, uint16_t* disp);
@@ -131,7 +175,8 @@ zncc_status zncc_run_host(zncc_ctx* ctx, const uint8_t* left_host, const uint8_t
                           zncc_dtype storage, uint16_t* disp_host);
 
 /* Text of the last error recorded on this context ("" if none). Valid until the next call
- * on the context. ctx == NULL returns the last error of a failed zncc_create. */
+ * on the context. ctx == NULL returns the last error of a failed call without a context
+ * (zncc_create, dt_aggregate_noalloc) on the calling host thread. */
 const char* zncc_last_error(const zncc_ctx* ctx);
 
 /* Static text for a status code. */

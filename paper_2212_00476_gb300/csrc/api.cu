@@ -1,11 +1,13 @@
 // api.cu -- the C ABI of libzncc.so (declared in include/zncc.h): argument checks, the
 // context's device scratch, and the launch sequence of each call.
 #include <math.h>
+#include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -19,7 +21,16 @@ using namespace zncc;
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
-thread_local std::string g_create_error;
+// Error text of the last failed call without a context (zncc_create, dt_aggregate_noalloc)
+// on this thread: a fixed buffer, so that recording an error allocates nothing.
+thread_local char g_free_error[256];
+
+void set_free_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_free_error, sizeof(g_free_error), fmt, ap);
+    va_end(ap);
+}
 
 // Kernel kinds for per-kernel timing (zncc_profile_*).
 enum Kind {
@@ -76,7 +87,7 @@ namespace {
 
 zncc_status fail(zncc_ctx* c, zncc_status s, const std::string& msg) {
     if (c) c->err = msg;
-    else g_create_error = msg;
+    else set_free_error("%s", msg.c_str());
     return s;
 }
 
@@ -569,12 +580,80 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
     return ZNCC_OK;
 }
 
+// ---- dt_aggregate_noalloc: per-device state of the static scratch --------------------
+// Everything here has static storage: the scratch address and device limits, resolved once
+// per device, and a fixed-capacity cache of line-pass shapes. A mutex guards both.
+constexpr int kNoallocDevices = 64;
+constexpr int kNoallocPlans = 16;
+
+struct NoallocPlan {
+    bool used;
+    int n, dcount, horiz, dtype, vec;
+    LinePlan plan;
+};
+
+struct NoallocDevice {
+    bool ready;
+    unsigned char* scratch;
+    int smem_max, num_sms;
+    NoallocPlan plans[kNoallocPlans];
+    int next;                       // the cache slot replaced next when it is full
+};
+
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc[kNoallocDevices];
+
+zncc_status noalloc_cuda_fail(cudaError_t e, const char* what) {
+    set_free_error("dt_aggregate_noalloc: %s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return ZNCC_ECUDA;
+}
+
+// The device's state, set up on its first use (the caller holds g_noalloc_mu).
+zncc_status noalloc_device(int dev, NoallocDevice** out) {
+    NoallocDevice& d = g_noalloc[dev];
+    if (!d.ready) {
+        void* p = nullptr;
+        cudaError_t e = noalloc_scratch_address(&p);
+        if (e != cudaSuccess) return noalloc_cuda_fail(e, "scratch address (cudaGetSymbolAddress)");
+        e = cudaDeviceGetAttribute(&d.smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return noalloc_cuda_fail(e, "device attributes");
+        d.scratch = static_cast<unsigned char*>(p);
+        d.ready = true;
+    }
+    *out = &d;
+    return ZNCC_OK;
+}
+
+// The block shape of a pass (choose_line_plan), from the device's cache (the caller holds
+// g_noalloc_mu).
+zncc_status noalloc_plan(NoallocDevice& d, LineArgs& a, const LinePass& p) {
+    for (const NoallocPlan& c : d.plans)
+        if (c.used && c.n == a.n && c.dcount == p.dcount && c.horiz == (int)p.horiz && c.dtype == p.dtype &&
+            c.vec == a.vec) {
+            a.tq = c.plan.tq; a.lpc = c.plan.lpc; a.nch = c.plan.nch; a.async = c.plan.async;
+            return ZNCC_OK;
+        }
+    LinePlan best{0, 0, 0, 0, 0, 0, 0};
+    bool found = false;
+    cudaError_t e = choose_line_plan(d.smem_max, 0, a, p, best, found);
+    if (e != cudaSuccess) return noalloc_cuda_fail(e, "occupancy query");
+    if (!found) {
+        set_free_error("dt_aggregate_noalloc: a line of %d pixels does not fit the DT kernel's shared memory", a.n);
+        return ZNCC_EUNSUPPORTED;
+    }
+    NoallocPlan& slot = d.plans[d.next];
+    d.next = (d.next + 1) % kNoallocPlans;
+    slot = NoallocPlan{true, a.n, p.dcount, (int)p.horiz, p.dtype, a.vec, best};
+    return ZNCC_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 zncc_status zncc_create(int width, int height, int max_disp, int win, zncc_ctx** out) {
-    g_create_error.clear();
+    g_free_error[0] = '\0';
     if (!out) return fail(nullptr, ZNCC_EINVAL, "out is NULL");
     *out = nullptr;
     if (width < 1 || height < 1) return fail(nullptr, ZNCC_EINVAL, "width and height must be >= 1");
@@ -679,6 +758,99 @@ zncc_status dt_aggregate(zncc_ctx* c, const uint8_t* guide, int pitch, void* cos
     return ZNCC_OK;
 }
 
+zncc_status dt_aggregate_noalloc(const uint8_t* guide, int pitch, int width, int height, int max_disp,
+                                 void* cost, zncc_dtype dtype, float sigma_s, float sigma_r, int iters,
+                                 void* cuda_stream) {
+    g_free_error[0] = '\0';
+    if (!guide || !cost) {
+        set_free_error("dt_aggregate_noalloc: guide or cost pointer is NULL");
+        return ZNCC_EINVAL;
+    }
+    if (width < 1 || height < 1 || max_disp < 1 || pitch < width) {
+        set_free_error("dt_aggregate_noalloc: width, height and max_disp must be >= 1 and pitch >= width");
+        return ZNCC_EINVAL;
+    }
+    if (dtype != ZNCC_F32 && dtype != ZNCC_F16) {
+        set_free_error("dt_aggregate_noalloc: unknown dtype");
+        return ZNCC_EINVAL;
+    }
+    if (!(sigma_s > 0.0f) || !isfinite(sigma_s) || !(sigma_r > 0.0f) || !isfinite(sigma_r) || iters < 0 ||
+        iters > 64) {
+        set_free_error("dt_aggregate_noalloc: sigma_s and sigma_r must be > 0 and iters in [0, 64]");
+        return ZNCC_EINVAL;
+    }
+    if (width > 3072 || height > 4096 || max_disp > 1024) {
+        set_free_error("dt_aggregate_noalloc: width must be <= 3072, height <= 4096 and max_disp <= 1024");
+        return ZNCC_EUNSUPPORTED;
+    }
+    const long long npix = (long long)width * height;
+    if (npix > kNoallocMaxPixels) {
+        set_free_error("dt_aggregate_noalloc: %d x %d needs %lld bytes of scratch (32 per pixel); the static "
+                       "scratch holds %lld bytes, so width * height must be <= %lld",
+                       width, height, npix * 32, (long long)kNoallocScratchBytes, kNoallocMaxPixels);
+        return ZNCC_EUNSUPPORTED;
+    }
+    if (iters == 0) return ZNCC_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_cuda_fail(e, "current device");
+    if (dev < 0 || dev >= kNoallocDevices) {
+        set_free_error("dt_aggregate_noalloc: device ordinals above %d are not supported", kNoallocDevices - 1);
+        return ZNCC_EUNSUPPORTED;
+    }
+    const cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocDevice* d = nullptr;
+    ZNCC_TRY(noalloc_device(dev, &d));
+    float4* coefH = reinterpret_cast<float4*>(d->scratch);
+    float4* coefV = coefH + npix;
+
+    CoefBatch cb;
+    memset(&cb, 0, sizeof(cb));
+    cb.npairs = 1;
+    CoefArgs& ca = cb.p[0];
+    ca.guide = guide;
+    ca.pitch = pitch;
+    ca.W = width;
+    ca.H = height;
+    ca.K = (float)exp(-1.0 / (double)sigma_s);
+    ca.inv_sr255 = (float)(1.0 / (255.0 * (double)sigma_r));
+    ca.coefH = coefH;
+    ca.coefV = coefV;
+    cb.total_threads = dt_coef_threads(width, height);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    e = launch_dt_coef(cb, st);
+    if (e != cudaSuccess) return noalloc_cuda_fail(e, "DT coefficients");
+
+    LinePass lp;
+    lp.vol = cost;
+    lp.dstride = max_disp;
+    lp.dcount = max_disp;
+    lp.dtype = dtype;
+    lp.s2 = scale_s2(sigma_s);
+    for (int it = 0; it < 2 * iters; ++it) {
+        lp.horiz = (it % 2) == 0;
+        LineArgs a;
+        fill_line_args(a, lp, width, height, coefH, coefV);
+        ZNCC_TRY(noalloc_plan(*d, a, lp));
+        LineBatch b;
+        memset(&b, 0, sizeof(b));
+        int threads = 0;
+        size_t stage = 0, rest = 0;
+        add_line_pair(b, a, kLineStore, dtype, threads, stage, rest);
+        b.stage_bytes = (long long)stage;
+        const size_t smem = stage + rest;
+        int bps = 0;
+        e = line_pair_occupancy(kLineStore, dtype, threads, smem, true, &bps);
+        if (e != cudaSuccess) return noalloc_cuda_fail(e, "occupancy query");
+        b.grid = std::max(1, std::min(b.total_items, d->num_sms * std::max(1, bps)));
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        e = launch_line_batch(b, threads, smem, kLineStore, dtype, st);
+        if (e != cudaSuccess) return noalloc_cuda_fail(e, "DT pass pair");
+    }
+    return ZNCC_OK;
+}
+
 zncc_status wta_disparity(zncc_ctx* c, const void* cost, zncc_dtype dtype, uint16_t* disp) {
     if (!c) return ZNCC_EINVAL;
     c->err.clear();
@@ -753,7 +925,7 @@ zncc_status zncc_run_host(zncc_ctx* c, const uint8_t* left_host, const uint8_t* 
     return ZNCC_OK;
 }
 
-const char* zncc_last_error(const zncc_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+const char* zncc_last_error(const zncc_ctx* c) { return c ? c->err.c_str() : g_free_error; }
 
 const char* zncc_status_string(zncc_status s) {
     switch (s) {

@@ -110,6 +110,12 @@ long long dt_coef_threads(int W, int H);
 cudaError_t launch_wta_volume(const void* cost, int dtype, int W, int H, int D, uint16_t* disp,
                               cudaStream_t st);
 
+// Scratch of dt_aggregate_noalloc: the DT coefficients of one W x H image (two float4 per
+// pixel) in a static device array of this size; its address on the current device.
+constexpr size_t kNoallocScratchBytes = 64ull << 20;
+constexpr long long kNoallocMaxPixels = (long long)(kNoallocScratchBytes / (2 * sizeof(float4)));
+cudaError_t noalloc_scratch_address(void** p);
+
 // per-radius launchers, one translation unit each
 #define ZNCC_DECLARE_ROW(R)                                                                     \
     cudaError_t launch_zncc_row_r##R(const RowBatch& b, int threads, size_t smem, int mode, int dtype, \

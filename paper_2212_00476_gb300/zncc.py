@@ -8,7 +8,8 @@ The methods of ZnccContext carry the names of the C calls they wrap:
 
     zncc_window_stats, zncc_cost_volume, dt_aggregate, wta_disparity, zncc_run, zncc_run_host
 
-and the module-level zncc_run_batch wraps the batched call.
+and the module-level zncc_run_batch and dt_aggregate_noalloc wrap the batched call and the
+context-free aggregation that allocates nothing.
 """
 
 from __future__ import annotations
@@ -39,6 +40,7 @@ SIGNATURES = [
     ("zncc_window_stats", _i, [_vp, _vp, _i, _vp, _vp, _vp]),
     ("zncc_cost_volume", _i, [_vp, _vp, _vp, _i, _vp, _i]),
     ("dt_aggregate", _i, [_vp, _vp, _i, _vp, _i, _f, _f, _i]),
+    ("dt_aggregate_noalloc", _i, [_vp, _i, _i, _i, _i, _vp, _i, _f, _f, _i, _vp]),
     ("wta_disparity", _i, [_vp, _vp, _i, _vp]),
     ("zncc_run", _i, [_vp, _vp, _vp, _i, _f, _f, _i, _i, _vp]),
     ("zncc_run_host", _i, [_vp, _vp, _vp, _i, _f, _f, _i, _i, _vp]),
@@ -104,6 +106,20 @@ def zncc_run_batch(ctxs, lefts, rights, disps, sigma_s, sigma_r, iters, storage=
                               int(iters), int(storage))
     if st != ZNCC_OK:
         raise ZnccError(st, lib().zncc_last_error(ctxs[0]._h).decode())
+
+
+def dt_aggregate_noalloc(guide, cost, sigma_s, sigma_r, iters, dtype=ZNCC_F32, stream=None):
+    """DT aggregation of cost ([H][W][D] device tensor) in place, guided by guide ([H][W]
+    uint8), without a context and without any allocation: the coefficients go to the
+    library's static device scratch (W * H <= 2,097,152). stream: a torch.cuda.Stream or
+    None (legacy default stream). Calls whose GPU work overlaps race on the scratch."""
+    H, W = int(guide.shape[0]), int(guide.shape[1])
+    D = int(cost.shape[-1])
+    s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    st = lib().dt_aggregate_noalloc(_ptr(guide), guide.stride(0), W, H, D, _ptr(cost), int(dtype),
+                                    float(sigma_s), float(sigma_r), int(iters), s)
+    if st != ZNCC_OK:
+        raise ZnccError(st, lib().zncc_last_error(None).decode())
 
 
 class ZnccContext:
