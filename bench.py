@@ -234,7 +234,12 @@ def run_gb300(args):
         ctx.zncc_run(left, right, disp, SIG_S, SIG_R, iters, storage)
 
     tuned = None
-    if not args.no_autotune:
+    if args.tuning:                             # fixed launch shapes, e.g. for a profiler run
+        from paper_2212_00476_gb300 import autotune
+        settings = {k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))}
+        autotune.apply(ctx, settings)
+        tuned = {"settings": settings}
+    elif not args.no_autotune:
         from paper_2212_00476_gb300 import autotune
         with torch.cuda.stream(stream):
             tuned = autotune.tune(ctx, left, right, disp, SIG_S, SIG_R, iters, storage)
@@ -452,6 +457,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch_uneven16"], default="paper_1280x384")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default="", help="fixed launch shapes instead of autotuning, "
+                    "e.g. row_minb2=0,row_spb=8")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
