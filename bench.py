@@ -447,6 +447,168 @@ def run_batch(args):
     return 0
 
 
+def run_precision(args):
+    """FP32 vs FP16 volume storage at 1920x1080, D = 256, 11x11, 3 DT iterations against the
+    FP64 oracle: the largest |aggregated cost - oracle| / A_hat over the whole volume (the
+    unfused chain zncc_cost_volume + dt_aggregate, which rounds every stored pair to the
+    storage type), and the disparity maps of the fused path: the share of pixels that differ
+    from the oracle's map, all pixels and those whose oracle best-second gap is at least
+    1e-5 * A_hat. Also the fused path's time per pair for each storage type."""
+    import torch
+
+    import oracle
+    from paper_2212_00476_gb300 import zncc as Z
+    from synth import config_pair
+
+    wl = WORKLOADS["precision_1920x1080"]
+    H, W, D, win = wl["h"], wl["w"], wl["d"], wl["win"]
+    pair = config_pair("precision_1920x1080")
+    t0 = time.perf_counter()
+    ref, gap, cref = oracle.run(pair.left, pair.right, D, win // 2, SIG_S, SIG_R, ITERS, want_cost=True)
+    ahat = oracle.ones_response(pair.left, SIG_S, SIG_R, ITERS)
+    t_oracle = time.perf_counter() - t0
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctx = Z.ZnccContext(W, H, D, win)
+    left = torch.from_numpy(pair.left).to(dev)
+    right = torch.from_numpy(pair.right).to(dev)
+    disp = torch.empty((H, W), dtype=torch.int16, device=dev)
+    clear = gap >= 1e-5 * ahat
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    result = {}
+    for name, st, tdt in (("f32", Z.ZNCC_F32, torch.float32), ("f16", Z.ZNCC_F16, torch.float16)):
+        vol = torch.empty((H, W, D), dtype=tdt, device=dev)
+        ctx.zncc_cost_volume(left, right, vol, st)
+        ctx.dt_aggregate(left, vol, SIG_S, SIG_R, ITERS, st)
+        torch.cuda.synchronize()
+        worst, worst_normal = 0.0, 0.0
+        for y0 in range(0, H, 60):
+            g = vol[y0:y0 + 60].float().cpu().numpy().astype(np.float64)
+            a = ahat[y0:y0 + 60, :, None]
+            e = np.abs(g - cref[y0:y0 + 60]) / a
+            worst = max(worst, float(e.max()))
+            normal = np.broadcast_to(a >= 2.0 ** -14, e.shape)
+            if normal.any():
+                worst_normal = max(worst_normal, float(e[normal].max()))
+        del vol
+        ms = []
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.zncc_run(left, right, disp, SIG_S, SIG_R, ITERS, st)
+            b.record()
+            b.synchronize()
+            if i >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        got = disp.cpu().numpy().view(np.uint16)
+        diff = got != ref
+        result[name] = {"max_abs_err_over_ahat": worst,
+                        "max_abs_err_over_ahat_where_ahat_ge_2^-14": worst_normal,
+                        "map_mismatch_rate": round(float(diff.mean()), 6),
+                        "map_mismatch_rate_clear_pixels": round(float(diff[clear].mean()), 6),
+                        "fused_ms_per_pair": round(sum(ms) / len(ms), 4),
+                        "fused_gdisp_s": round(W * H * D / (sum(ms) / len(ms) * 1e-3) / 1e9, 3)}
+    ctx.close()
+    line = {
+        "metric": "precision: FP32 vs FP16 volume storage vs the FP64 oracle, 1920x1080 D=256 11x11",
+        "value": result["f16"]["map_mismatch_rate"], "unit": "share of pixels (F16 map vs oracle)",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32,f16", "data": "synthetic",
+        "config": {"workload": workload_desc("precision_1920x1080", "f32/f16"),
+                   "near_tie_pixels": round(float(1 - clear.mean()), 6),
+                   "pixels_with_ahat_below_2^-14": round(float((ahat < 2.0 ** -14).mean()), 6),
+                   "volume_error_path": "unfused zncc_cost_volume + dt_aggregate (each stored pair "
+                                        "rounded to the storage type, no A_hat normalisation)",
+                   "oracle_seconds": round(t_oracle, 2),
+                   "l2": "flushed before every timed pair (256 MB write outside the events)"},
+        "f32": result["f32"], "f16": result["f16"],
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_serving(args):
+    """Poisson arrivals (seed 5) of requests of size {640x192, 1280x384, 1920x1080} and D
+    {64, 128, 256}, 9x9, 3 DT iterations, through the serving calls with continuous batching
+    (max_slots 32) and one pair per launch (max_slots 1), under a 40 GB budget. Latency =
+    time from a request's scheduled arrival until serve_poll returns its map; one loop submits
+    on schedule and polls every outstanding ticket. The images of a (size, D) shape come from
+    one seeded pair (seed 500000 + shape index), reused by every request of that shape."""
+    import torch
+
+    from paper_2212_00476_gb300 import zncc as Z
+    from synth.stereo import SERVE_DISPS, SERVE_SIZES, make_pair, serving_requests
+
+    torch.cuda.set_device(0)
+    storage = Z.ZNCC_F32 if args.storage == "f32" else Z.ZNCC_F16
+    shapes = [(h, w, d) for (h, w) in SERVE_SIZES for d in SERVE_DISPS]
+    pool = {sh: make_pair(sh[0], sh[1], sh[2], 500000 + i, disp="planes", occlusion_frac=0.05)
+            for i, sh in enumerate(shapes)}
+    outs = {sh: np.zeros(sh[:2], np.uint16) for sh in shapes}
+    rates = [float(r) for r in args.rates.split(",")]
+    budget = 40 * 10**9
+
+    def serve(rate, max_slots, n):
+        reqs = serving_requests(n, rate, seed=5)
+        with Z.ZnccServer(budget, max_slots) as srv:
+            for sh in shapes:                                   # contexts exist before timing
+                p = pool[sh]
+                t = srv.submit(p.left, p.right, sh[2], 9, SIG_S, SIG_R, ITERS, storage)
+                assert srv.poll(t, outs[sh], 60_000_000) == Z.ZNCC_OK, srv.last_error()
+            lat, pending, i, units = [], {}, 0, 0
+            t0 = time.perf_counter()
+            while i < n or pending:
+                now = time.perf_counter() - t0
+                while i < n and reqs[i]["t"] <= now:
+                    r = reqs[i]
+                    sh = (r["h"], r["w"], r["max_disp"])
+                    p = pool[sh]
+                    pending[srv.submit(p.left, p.right, sh[2], 9, SIG_S, SIG_R, ITERS, storage)] = (sh, r["t"])
+                    units += sh[0] * sh[1] * sh[2]
+                    i += 1
+                done = []
+                for tk, (sh, ta) in pending.items():
+                    st = srv.poll(tk, outs[sh], 0)
+                    if st == Z.ZNCC_OK:
+                        lat.append(time.perf_counter() - t0 - ta)
+                        done.append(tk)
+                    elif st != Z.ZNCC_ENOTREADY:
+                        raise RuntimeError(f"request failed: {Z.STATUS_NAMES[st]} {srv.last_error()}")
+                for tk in done:
+                    del pending[tk]
+                if not done:
+                    time.sleep(2e-5)
+            span = time.perf_counter() - t0
+        lat.sort()
+        q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] * 1e3
+        return {"p50_ms": round(q(0.50), 3), "p99_ms": round(q(0.99), 3), "max_ms": round(lat[-1] * 1e3, 3),
+                "requests": n, "span_s": round(span, 3), "served_req_per_s": round(n / span, 1),
+                "served_gdisp_s": round(units / span / 1e9, 3)}
+
+    sweep = []
+    for rate in rates:
+        n = args.requests
+        sweep.append({"rate_req_per_s": rate, "batched": serve(rate, 32, n), "one_pair_per_launch": serve(rate, 1, n)})
+    head = sweep[0]
+    line = {
+        "metric": f"served p50/p99 latency at {rates[0]:g} req/s (continuous batching vs one pair per launch)",
+        "value": head["batched"]["p99_ms"], "unit": "ms (p99)", "n_gpus": 1, "steps": args.requests,
+        "warmup": len(shapes), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals seed 5; sizes 640x192/1280x384/1920x1080, "
+                               "D 64/128/256, 9x9, sigma_s 20, sigma_r 0.1, 3 iterations; 40 GB budget",
+                   "l2": "not flushed (a live request stream)"},
+        "p50_ms": head["batched"]["p50_ms"], "p99_ms": head["batched"]["p99_ms"],
+        "plain_p50_ms": head["one_pair_per_launch"]["p50_ms"],
+        "plain_p99_ms": head["one_pair_per_launch"]["p99_ms"],
+        "sweep": sweep,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -454,7 +616,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch_uneven16"], default="paper_1280x384")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch_uneven16", "serving", "precision_sweep"],
+                    default="paper_1280x384")
+    ap.add_argument("--rates", default="200,500,1000,2000", help="serving: arrival rates (req/s)")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: requests per rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default="", help="fixed launch shapes instead of autotuning, "
@@ -463,7 +628,15 @@ def main():
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
     if args.impl == "reference":
+        if args.workload not in WORKLOADS:
+            print(json.dumps({"impl": "reference", "unavailable": f"the reference arm times the oracle on "
+                              f"the single-pair workloads {sorted(WORKLOADS)} only"}))
+            return 0
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
+    if args.workload == "precision_sweep":
+        return run_precision(args)
     if args.workload == "batch_uneven16":
         return run_batch(args)
     return run_gb300(args)

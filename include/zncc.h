@@ -174,6 +174,56 @@ zncc_status zncc_run_host(zncc_ctx* ctx, const uint8_t* left_host, const uint8_t
                           int pitch, float sigma_s, float sigma_r, int iters,
                           zncc_dtype storage, uint16_t* disp_host);
 
+/* ---- Serving: continuous batching of independent pairs ---------------------------------
+ * A server owns a pool of contexts on the current device, a queue of requests and a scheduler
+ * thread. Requests come from host memory and may differ in size, disparity range, window,
+ * DT parameters and storage type. Whenever requests wait and slots are free, the scheduler
+ * admits them in submission order and launches those that share the DT parameters, the
+ * iteration count and the storage type as one batched fused run (zncc_run_batch, up to 32
+ * pairs), on one of two streams, so that a new batch starts while earlier ones still run.
+ * Results are identical to running each pair alone: the batched kernels compute every pair
+ * exactly as a single zncc_run does. Contexts are reused per request shape; the device memory
+ * they hold (cost volume, DT coefficients, A_hat maps, images and disparity map) is charged
+ * to `volume_budget_bytes`, and idle ones are freed, least recently used first, when a new
+ * shape needs room. The paper has no serving layer; the batched path serves its workload of
+ * many independent pairs. All server calls are thread-safe, except that no call may run
+ * concurrently with or after serve_destroy. */
+typedef struct zncc_server zncc_server;
+
+/* Create a server: volume_budget_bytes (> 0) bounds the device memory of its contexts;
+ * max_slots (>= 1) bounds the requests on the GPU at once (1 = one pair per launch, no
+ * batching). The scheduler thread binds the device current at this call. */
+zncc_status serve_create(size_t volume_budget_bytes, int max_slots, zncc_server** out);
+
+/* Queue one pair: left_host/right_host are uint8 [height][width] (row pitch = width), copied
+ * before the call returns (the caller may reuse them at once). The window, DT parameters,
+ * iteration count and storage have the meaning and limits of zncc_run. Returns at once with
+ * *ticket (> 0). Errors: ZNCC_EINVAL (bad arguments, or a request whose device memory alone
+ * exceeds the budget: it could never run), ZNCC_EUNSUPPORTED (sizes beyond the kernels'
+ * limits), ZNCC_EBUSY (the server is shutting down, or 65536 requests are outstanding),
+ * ZNCC_ENOMEM (host memory). A request that merely has to wait for room is queued. */
+zncc_status serve_submit(zncc_server* server, const uint8_t* left_host, const uint8_t* right_host,
+                         int width, int height, int max_disp, int win, float sigma_s,
+                         float sigma_r, int iters, zncc_dtype storage, uint64_t* ticket);
+
+/* Result of a request: waits up to timeout_us (>= 0) microseconds for it to finish. On
+ * completion copies its disparity map to disp_host (uint16 [height][width]), forgets the
+ * ticket and returns the request's status: ZNCC_OK, or the error that stopped it
+ * (ZNCC_ENOMEM / ZNCC_ECUDA from its context or launch, ZNCC_EBUSY if the server was
+ * destroyed before it started). Not finished: ZNCC_ENOTREADY when timeout_us == 0,
+ * ZNCC_ETIMEOUT otherwise (the ticket stays valid). Unknown ticket: ZNCC_EINVAL. */
+zncc_status serve_poll(zncc_server* server, uint64_t ticket, uint16_t* disp_host, int timeout_us);
+
+/* Stop the server: requests not yet started end with ZNCC_EBUSY, running batches are waited
+ * for (at most 30 s), then every context, buffer and stream is freed. If the running work
+ * does not finish in time, returns ZNCC_ETIMEOUT and leaves the server's memory allocated
+ * (freeing buffers the GPU may still use would be unsafe). */
+zncc_status serve_destroy(zncc_server* server);
+
+/* Text of the last error the server recorded ("" if none); valid until the server's next
+ * error. */
+const char* serve_last_error(const zncc_server* server);
+
 /* Text of the last error recorded on this context ("" if none). Valid until the next call
  * on the context. ctx == NULL returns the last error of a failed call without a context
  * (zncc_create, dt_aggregate_noalloc) on the calling host thread. */

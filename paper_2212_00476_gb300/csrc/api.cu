@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -31,6 +32,22 @@ void set_free_error(const char* fmt, ...) {
     vsnprintf(g_free_error, sizeof(g_free_error), fmt, ap);
     va_end(ap);
 }
+
+}  // namespace
+
+// Every device allocation of the library goes through here. Host-side fault injection for
+// tests: with the environment variable ZNCC_FAIL_DEVICE_ALLOC set to 1, each allocation
+// reports cudaErrorMemoryAllocation without calling the driver (no GPU fault is involved).
+cudaError_t zncc::device_alloc(void** p, size_t bytes) {
+    const char* f = getenv("ZNCC_FAIL_DEVICE_ALLOC");
+    if (f && f[0] == '1') {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+namespace {
 
 // Kernel kinds for per-kernel timing (zncc_profile_*).
 enum Kind {
@@ -199,7 +216,7 @@ void free_dev_f(float*& p) {
 }
 
 zncc_status alloc_dev(zncc_ctx* c, void** p, size_t bytes, const char* what) {
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = device_alloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -674,8 +691,8 @@ zncc_status zncc_create(int width, int height, int max_disp, int win, zncc_ctx**
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     const size_t npix = (size_t)width * height;
-    if (e == cudaSuccess) e = cudaMalloc(&c->coefH, npix * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMalloc(&c->coefV, npix * sizeof(float4));
+    if (e == cudaSuccess) e = device_alloc((void**)&c->coefH, npix * sizeof(float4));
+    if (e == cudaSuccess) e = device_alloc((void**)&c->coefV, npix * sizeof(float4));
     if (e != cudaSuccess) {
         zncc_status s = e == cudaErrorMemoryAllocation ? ZNCC_ENOMEM : ZNCC_ECUDA;
         std::string m = std::string("zncc_create: ") + cudaGetErrorString(e);
@@ -905,8 +922,8 @@ zncc_status zncc_run_host(zncc_ctx* c, const uint8_t* left_host, const uint8_t* 
     if (!disp_host) return fail(c, ZNCC_EINVAL, "disp_host pointer is NULL");
     const size_t npix = (size_t)c->W * c->H;
     if (!c->img) {
-        cudaError_t e = cudaMalloc(&c->img, 2 * npix);
-        if (e == cudaSuccess) e = cudaMalloc(&c->disp, npix * sizeof(uint16_t));
+        cudaError_t e = device_alloc((void**)&c->img, 2 * npix);
+        if (e == cudaSuccess) e = device_alloc((void**)&c->disp, npix * sizeof(uint16_t));
         if (e != cudaSuccess) {
             cudaGetLastError();
             free_dev(c->img);

@@ -110,6 +110,10 @@ long long dt_coef_threads(int W, int H);
 cudaError_t launch_wta_volume(const void* cost, int dtype, int W, int H, int D, uint16_t* disp,
                               cudaStream_t st);
 
+// Device allocation of the library (cudaMalloc, or an injected out-of-memory failure when the
+// environment variable ZNCC_FAIL_DEVICE_ALLOC is 1).
+cudaError_t device_alloc(void** p, size_t bytes);
+
 // Scratch of dt_aggregate_noalloc: the DT coefficients of one W x H image (two float4 per
 // pixel) in a static device array of this size; its address on the current device.
 constexpr size_t kNoallocScratchBytes = 64ull << 20;

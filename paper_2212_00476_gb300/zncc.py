@@ -9,7 +9,9 @@ The methods of ZnccContext carry the names of the C calls they wrap:
     zncc_window_stats, zncc_cost_volume, dt_aggregate, wta_disparity, zncc_run, zncc_run_host
 
 and the module-level zncc_run_batch and dt_aggregate_noalloc wrap the batched call and the
-context-free aggregation that allocates nothing.
+context-free aggregation that allocates nothing. serve_create, serve_submit, serve_poll and
+serve_destroy wrap the serving calls (a handle in, numpy arrays for the host images), and
+ZnccServer bundles them.
 """
 
 from __future__ import annotations
@@ -45,6 +47,12 @@ SIGNATURES = [
     ("zncc_run", _i, [_vp, _vp, _vp, _i, _f, _f, _i, _i, _vp]),
     ("zncc_run_host", _i, [_vp, _vp, _vp, _i, _f, _f, _i, _i, _vp]),
     ("zncc_run_batch", _i, [_vp, _vp, _vp, _vp, _vp, _i, _f, _f, _i, _i]),
+    ("serve_create", _i, [_sz, _i, ctypes.POINTER(_vp)]),
+    ("serve_submit", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _f, _f, _i, _i,
+                          ctypes.POINTER(ctypes.c_uint64)]),
+    ("serve_poll", _i, [_vp, ctypes.c_uint64, _vp, _i]),
+    ("serve_destroy", _i, [_vp]),
+    ("serve_last_error", ctypes.c_char_p, [_vp]),
     ("zncc_last_error", ctypes.c_char_p, [_vp]),
     ("zncc_status_string", ctypes.c_char_p, [_i]),
     ("zncc_kernel_launch_count", ctypes.c_uint64, []),
@@ -120,6 +128,70 @@ def dt_aggregate_noalloc(guide, cost, sigma_s, sigma_r, iters, dtype=ZNCC_F32, s
                                     float(sigma_s), float(sigma_r), int(iters), s)
     if st != ZNCC_OK:
         raise ZnccError(st, lib().zncc_last_error(None).decode())
+
+
+def serve_create(volume_budget_bytes: int, max_slots: int):
+    """A server handle (ctypes.c_void_p)."""
+    h = _vp()
+    st = lib().serve_create(int(volume_budget_bytes), int(max_slots), ctypes.byref(h))
+    if st != ZNCC_OK:
+        raise ZnccError(st, "serve_create")
+    return h
+
+
+def serve_submit(server, left: np.ndarray, right: np.ndarray, max_disp: int, win: int,
+                 sigma_s: float, sigma_r: float, iters: int, storage: int = ZNCC_F32) -> int:
+    """Queue one pair (uint8 [H][W] host arrays, copied before return); returns its ticket."""
+    assert left.dtype == np.uint8 and right.dtype == np.uint8 and left.shape == right.shape
+    left = np.ascontiguousarray(left)
+    right = np.ascontiguousarray(right)
+    t = ctypes.c_uint64()
+    st = lib().serve_submit(server, left.ctypes.data, right.ctypes.data, left.shape[1],
+                            left.shape[0], int(max_disp), int(win), float(sigma_s),
+                            float(sigma_r), int(iters), int(storage), ctypes.byref(t))
+    if st != ZNCC_OK:
+        raise ZnccError(st, lib().serve_last_error(server).decode() or "serve_submit")
+    return int(t.value)
+
+
+def serve_poll(server, ticket: int, disp: np.ndarray, timeout_us: int = 0) -> int:
+    """Status of a request (ZNCC_OK: its map is now in disp, uint16 [H][W]); ZNCC_ENOTREADY
+    and ZNCC_ETIMEOUT are returned, not raised, as are the request's own errors."""
+    assert disp.dtype == np.uint16 and disp.flags.c_contiguous
+    return int(lib().serve_poll(server, ctypes.c_uint64(ticket), disp.ctypes.data, int(timeout_us)))
+
+
+def serve_destroy(server) -> int:
+    return int(lib().serve_destroy(server))
+
+
+class ZnccServer:
+    """A libzncc server: queue pairs from host memory, poll their disparity maps."""
+
+    def __init__(self, volume_budget_bytes: int, max_slots: int = 32):
+        self._h = serve_create(volume_budget_bytes, max_slots)
+
+    def submit(self, left, right, max_disp, win, sigma_s, sigma_r, iters, storage=ZNCC_F32):
+        return serve_submit(self._h, left, right, max_disp, win, sigma_s, sigma_r, iters, storage)
+
+    def poll(self, ticket, disp, timeout_us=0):
+        return serve_poll(self._h, ticket, disp, timeout_us)
+
+    def last_error(self) -> str:
+        return lib().serve_last_error(self._h).decode()
+
+    def close(self) -> int:
+        st = ZNCC_OK
+        if getattr(self, "_h", None) is not None:
+            st = serve_destroy(self._h)
+            self._h = None
+        return st
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class ZnccContext:
