@@ -481,7 +481,7 @@ def run_precision(args):
         ctx.zncc_cost_volume(left, right, vol, st)
         ctx.dt_aggregate(left, vol, SIG_S, SIG_R, ITERS, st)
         torch.cuda.synchronize()
-        worst, worst_normal = 0.0, 0.0
+        worst, worst_normal = 0.0, None
         for y0 in range(0, H, 60):
             g = vol[y0:y0 + 60].float().cpu().numpy().astype(np.float64)
             a = ahat[y0:y0 + 60, :, None]
@@ -489,7 +489,7 @@ def run_precision(args):
             worst = max(worst, float(e.max()))
             normal = np.broadcast_to(a >= 2.0 ** -14, e.shape)
             if normal.any():
-                worst_normal = max(worst_normal, float(e[normal].max()))
+                worst_normal = max(worst_normal or 0.0, float(e[normal].max()))
         del vol
         ms = []
         for i in range(args.warmup + args.steps):

@@ -178,9 +178,10 @@ zncc_status zncc_run_host(zncc_ctx* ctx, const uint8_t* left_host, const uint8_t
  * A server owns a pool of contexts on the current device, a queue of requests and a scheduler
  * thread. Requests come from host memory and may differ in size, disparity range, window,
  * DT parameters and storage type. Whenever requests wait and slots are free, the scheduler
- * admits them in submission order and launches those that share the DT parameters, the
- * iteration count and the storage type as one batched fused run (zncc_run_batch, up to 32
- * pairs), on one of two streams, so that a new batch starts while earlier ones still run.
+ * admits them in submission order and launches the small ones (W*H*D < 2^25) that share the
+ * DT parameters, the iteration count and the storage type as one batched fused run
+ * (zncc_run_batch, up to 32 pairs) and a larger one, which fills the GPU by itself, alone; on
+ * one of two streams, so that a new launch starts while earlier ones still run.
  * Results are identical to running each pair alone: the batched kernels compute every pair
  * exactly as a single zncc_run does. Contexts are reused per request shape; the device memory
  * they hold (cost volume, DT coefficients, A_hat maps, images and disparity map) is charged

@@ -1,10 +1,10 @@
 // serve.cpp -- the serving layer of libzncc (serve_* in include/zncc.h): a queue of stereo
 // requests from host memory, admitted under a device-memory budget onto a pool of contexts
 // and run by continuous batching: whenever requests wait and slots are free, the scheduler
-// thread launches the waiting ones that share DT parameters as one zncc_run_batch (up to 32
-// pairs of uneven sizes), on one of two streams, so that a new batch starts while earlier ones
-// are still on the GPU. Completion is signalled by a host function queued behind each
-// batch's result copies.
+// thread launches the waiting small ones that share DT parameters as one zncc_run_batch (up
+// to 32 pairs of uneven sizes), and a pair large enough to fill the GPU by itself alone, on
+// one of two streams, so that a new launch starts while earlier ones are still on the GPU.
+// Completion is signalled by a host function queued behind each batch's result copies.
 //
 // Contexts (and their image, disparity and volume buffers) are kept per request shape and
 // reused; idle ones are evicted, least recently used first, when a new shape needs room.
@@ -33,6 +33,11 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr size_t kMaxQueued = 1 << 16;     // requests waiting or running at once
 constexpr double kDrainSeconds = 30.0;     // serve_destroy's bound on in-flight work
+// A pair of at least this many volume elements fills the GPU by itself: it runs alone, with
+// the single-pair kernels; smaller ones are batched together.
+constexpr long long kAloneElements = 1LL << 25;
+
+bool runs_alone(int W, int H, int D) { return (long long)W * H * D >= kAloneElements; }
 
 struct ShapeKey {
     int W, H, D, win, storage, iters;
@@ -326,6 +331,8 @@ void worker_main(zncc_server* s) {
         while (idx < s->queue.size() && (int)b->reqs.size() < zncc::kMaxBatch &&
                s->inflight + (int)b->reqs.size() < s->max_slots) {
             Request* r = s->queue[idx];
+            const bool alone = runs_alone(r->key.W, r->key.H, r->key.D);
+            if (head && alone) break;                           // a large pair starts its own launch
             if (head && (r->sigma_s != head->sigma_s || r->sigma_r != head->sigma_r ||
                          r->key.iters != head->key.iters || r->key.storage != head->key.storage)) {
                 ++idx;
@@ -359,6 +366,7 @@ void worker_main(zncc_server* s) {
             r->state = Request::RUNNING;
             b->reqs.push_back(r);
             if (!head) head = r;
+            if (alone) break;
         }
         if (b->reqs.empty()) {
             delete b;
