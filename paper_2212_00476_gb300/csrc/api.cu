@@ -65,7 +65,7 @@ struct ProfRecord {
 // Launch shape of one kind of line pass, chosen once per context and pass signature.
 struct LinePlan {
     long long key;
-    int tq, lpc, nch, async, per_block, blocks;
+    int tq, lpc, nch, async, per_block, blocks, cs;
 };
 
 constexpr int kTargetBlocks = 1216;   // about eight blocks per SM on a 152-SM GB300
@@ -365,25 +365,39 @@ cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePa
     for (int ti = 0; ti < 4; ++ti) {
         const int tq = tqs[ti];
         if (forced ? tq != forced : tq == 1) continue;
-        const int nch = padded_chunks(a.n, tq);
+        // chunks per CTA: the line in one block, or split over a cluster of 2 or 4 CTAs
+        const int per_warp = 32 / tq, nch_line = padded_chunks(a.n, tq);
+        int cs = 1, nch = nch_line;
+        while (nch * tq > 512 && cs < 4) {
+            cs *= 2;
+            nch = ((nch_line + cs - 1) / cs + per_warp - 1) / per_warp * per_warp;
+        }
         const int per_line = nch * tq;
         if (per_line > 512) continue;
-        const bool whole_bursts = tq * 4 * (p.dtype == 0 ? 4 : 2) >= 64;
+        const int seg = tq * 4 * (p.dtype == 0 ? 4 : 2);      // bytes per chunk position
+        const bool whole_bursts = seg >= 64;
         for (int async = a.vec ? 1 : 0; async >= 0; --async) {
-            for (int lpc = std::max(1, std::min(8, 256 / per_line)); lpc >= 1; --lpc) {
-                a.tq = tq; a.nch = nch; a.lpc = lpc; a.async = async;
+            for (int lpc = cs > 1 ? 1 : std::max(1, std::min(8, 256 / per_line)); lpc >= 1; --lpc) {
+                a.tq = tq; a.nch = nch; a.lpc = lpc; a.async = async; a.cs = cs;
                 const size_t smem = line_pair_smem_bytes(p.mode, p.dtype, a);
                 if (smem > (size_t)smem_max) continue;
                 int bps = 0;
-                cudaError_t e = line_pair_occupancy(p.mode, p.dtype, lpc * per_line, smem, true, &bps);
+                cudaError_t e = line_pair_occupancy(p.mode, p.dtype, lpc * per_line, smem, true, cs > 1, &bps);
                 if (e != cudaSuccess) return e;
                 if (bps < 1) continue;
+                if (cs > 1) {
+                    int ncl = 0;
+                    e = line_pair_max_clusters(p.mode, p.dtype, per_line, smem, true, cs, &ncl);
+                    if (e != cudaSuccess) return e;
+                    if (ncl < 1) continue;
+                }
                 const long long warps = (long long)bps * lpc * per_line / 32;
                 const long long score = (whole_bursts ? 10000000LL : 0) + async * 1000000LL +
-                                        (bps >= 2 ? 100000LL : 0) + warps * 100 + tq;
+                                        (bps >= 2 ? 100000LL : 0) + warps * 100 + (cs == 1 ? 50 : 0) + tq;
                 if (score > best_score) {
                     best_score = score;
                     best.tq = tq; best.lpc = lpc; best.nch = nch; best.async = async; best.blocks = bps;
+                    best.cs = cs;
                 }
                 break;                      // fewer lines per block only when this did not fit
             }
@@ -391,8 +405,24 @@ cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePa
     }
     if (best_score < 0) return cudaSuccess;
     found = true;
-    a.tq = best.tq; a.lpc = best.lpc; a.nch = best.nch; a.async = best.async;
+    a.tq = best.tq; a.lpc = best.lpc; a.nch = best.nch; a.async = best.async; a.cs = best.cs;
     return cudaSuccess;
+}
+
+// Grid of a line-pair launch: the resident blocks (or clusters of cs CTAs), at most one per item.
+cudaError_t size_line_grid(LineBatch& b, int threads, size_t smem, int mode, int dtype, int num_sms) {
+    const int cs = b.p[0].cs;
+    cudaError_t e;
+    if (cs > 1) {
+        int ncl = 0;
+        e = line_pair_max_clusters(mode, dtype, threads, smem, b.npairs == 1, cs, &ncl);
+        b.grid = cs * std::max(1, std::min(b.total_items, ncl));
+    } else {
+        int bps = 0;
+        e = line_pair_occupancy(mode, dtype, threads, smem, b.npairs == 1, false, &bps);
+        b.grid = std::max(1, std::min(b.total_items, num_sms * std::max(1, bps)));
+    }
+    return e;
 }
 
 // The block shape of a pair's pass (choose_line_plan), chosen once per context and pass
@@ -403,10 +433,10 @@ zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
                           forced + ((long long)p.dcount << 20);
     for (const LinePlan& pl : c->plans)
         if (pl.key == key) {
-            a.tq = pl.tq; a.lpc = pl.lpc; a.nch = pl.nch; a.async = pl.async;
+            a.tq = pl.tq; a.lpc = pl.lpc; a.nch = pl.nch; a.async = pl.async; a.cs = pl.cs;
             return ZNCC_OK;
         }
-    LinePlan best{key, 0, 0, 0, 0, 0, 0};
+    LinePlan best{key, 0, 0, 0, 0, 0, 0, 1};
     bool found = false;
     ZNCC_CUDA(c, choose_line_plan(c->smem_max, forced, a, p, best, found), "occupancy query");
     if (!found) return fail(c, ZNCC_EUNSUPPORTED, "line too long for the DT kernel's shared memory");
@@ -439,6 +469,7 @@ void fill_line_args(LineArgs& a, const LinePass& p, int W, int H, const float4* 
     a.wta.last = 1;
     a.pix_line = p.horiz ? W : 1;
     a.pix_pos = p.horiz ? 1 : W;
+    a.cs = 1;
 }
 
 // Appends a pair (its block shape chosen) to a launch: its items and steps, and the block's
@@ -483,7 +514,8 @@ zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passe
         size_t stage = 0, rest = 0;
         for (int i = first; i < n; ++i) {
             const LineArgs& ai = args[i];
-            if (done[i] || ai.tq != a0.tq || ai.nch != a0.nch || ai.lpc != a0.lpc || ai.async != a0.async)
+            if (done[i] || ai.tq != a0.tq || ai.nch != a0.nch || ai.lpc != a0.lpc || ai.async != a0.async ||
+                ai.cs != a0.cs)
                 continue;
             done[i] = true;
             add_line_pair(b, ai, mode, dtype, threads, stage, rest);
@@ -491,9 +523,7 @@ zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passe
         b.stage_bytes = (long long)stage;
         const size_t smem = stage + rest;
         if (smem > (size_t)lc->smem_max) return fail(lc, ZNCC_EUNSUPPORTED, "DT pass exceeds shared memory");
-        int bps = 0;
-        ZNCC_CUDA(lc, line_pair_occupancy(mode, dtype, threads, smem, b.npairs == 1, &bps), "occupancy query");
-        b.grid = std::max(1, std::min(b.total_items, lc->num_sms * std::max(1, bps)));
+        ZNCC_CUDA(lc, size_line_grid(b, threads, smem, mode, dtype, lc->num_sms), "occupancy query");
         ZNCC_LAUNCH(lc, kind, launch_line_batch(b, threads, smem, mode, dtype, lc->cur), "DT pass pair");
     }
     return ZNCC_OK;
@@ -648,10 +678,10 @@ zncc_status noalloc_plan(NoallocDevice& d, LineArgs& a, const LinePass& p) {
     for (const NoallocPlan& c : d.plans)
         if (c.used && c.n == a.n && c.dcount == p.dcount && c.horiz == (int)p.horiz && c.dtype == p.dtype &&
             c.vec == a.vec) {
-            a.tq = c.plan.tq; a.lpc = c.plan.lpc; a.nch = c.plan.nch; a.async = c.plan.async;
+            a.tq = c.plan.tq; a.lpc = c.plan.lpc; a.nch = c.plan.nch; a.async = c.plan.async; a.cs = c.plan.cs;
             return ZNCC_OK;
         }
-    LinePlan best{0, 0, 0, 0, 0, 0, 0};
+    LinePlan best{0, 0, 0, 0, 0, 0, 0, 1};
     bool found = false;
     cudaError_t e = choose_line_plan(d.smem_max, 0, a, p, best, found);
     if (e != cudaSuccess) return noalloc_cuda_fail(e, "occupancy query");
@@ -857,10 +887,8 @@ zncc_status dt_aggregate_noalloc(const uint8_t* guide, int pitch, int width, int
         add_line_pair(b, a, kLineStore, dtype, threads, stage, rest);
         b.stage_bytes = (long long)stage;
         const size_t smem = stage + rest;
-        int bps = 0;
-        e = line_pair_occupancy(kLineStore, dtype, threads, smem, true, &bps);
+        e = size_line_grid(b, threads, smem, kLineStore, dtype, d->num_sms);
         if (e != cudaSuccess) return noalloc_cuda_fail(e, "occupancy query");
-        b.grid = std::max(1, std::min(b.total_items, d->num_sms * std::max(1, bps)));
         g_launches.fetch_add(1, std::memory_order_relaxed);
         e = launch_line_batch(b, threads, smem, kLineStore, dtype, st);
         if (e != cudaSuccess) return noalloc_cuda_fail(e, "DT pass pair");

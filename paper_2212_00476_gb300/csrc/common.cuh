@@ -23,13 +23,12 @@ template <typename T>
 __device__ __forceinline__ T& at4(T* base, int start, int i, int plane) {
     return base[(i & 3) * plane + (start >> 2) + (i >> 2)];
 }
-// Coefficient arrays add an XOR swizzle inside the plane (bit 1 flipped where bit 3 is set),
-// which also separates the chunks of a warp when only two lanes share a chunk.
-__device__ __forceinline__ int cidx(int pos, int plane) {
-    int q = pos >> 2;
-    q ^= ((q >> 3) & 1) << 1;
-    return (pos & 3) * plane + q;
-}
+// Per-position arrays of a DT line (coefficients, multipliers) are chunk-major: the kL entries of a chunk are contiguous and chunks are kCS = kL + 1 entries
+// apart. A thread then reaches every entry of its chunk at a constant offset from one
+// pointer, and the lanes of a warp, which read the same position of consecutive chunks, fall
+// on distinct banks (the padding entry shifts each chunk by one 16-byte group).
+constexpr int kCS = kL + 1;
+__host__ __device__ __forceinline__ int cpos(int pos) { return (pos >> 4) * kCS + (pos & (kL - 1)); }
 
 // ---- cost-volume element access: 4 consecutive disparities per thread ----------------
 
@@ -112,6 +111,41 @@ __device__ __forceinline__ void lds4(const __half* p, float (&o)[4]) {
     o[0] = half_lo(t.x); o[1] = half_hi(t.x); o[2] = half_lo(t.y); o[3] = half_hi(t.y);
 }
 
+// ---- thread-block clusters: a DT line split across the CTAs of a cluster ---------------
+// The CTA's rank in its cluster (0 for a launch without clusters).
+__device__ __forceinline__ int cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+// Barrier over every thread of the cluster; shared-memory writes before it (local or to other
+// CTAs of the cluster) are visible to every thread of the cluster after it.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// The barrier between the phases of a line pair: the block's, or the cluster's when the line
+// spans cs > 1 CTAs.
+__device__ __forceinline__ void line_sync(int cs) {
+    if (cs > 1) cluster_sync_all();
+    else __syncthreads();
+}
+// Stores to the same shared-memory offset in the CTA of the given rank (distributed shared
+// memory).
+__device__ __forceinline__ unsigned cluster_addr(const void* p, int rank) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_rank(float* p, int rank, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cluster_addr(p, rank)), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_rank(float4* p, int rank, float4 v) {
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(cluster_addr(p, rank)), "f"(v.x),
+                 "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
 // ---- WTA (Eq. (WTA1)): the largest cost wins, ties go to the smallest d ----------------
 
 // ---- DT line pair: forward then backward recursive pass along a line ------------------
@@ -132,23 +166,24 @@ __device__ __forceinline__ void lds4(const __half* p, float (&o)[4]) {
 //   z = w(p+1), w = B(p) = prod_{j = p .. chunk end} w(j+1),
 // zero past the line end, so that padded chunks carry nothing.
 //
-// co: the line's coefficients in shared memory (cidx layout); sa/sb: the line's scan
-// buffers, 2 * nwl * tq entries each; wl / nwl: this thread's warp within the line and the
-// warps per line. The result is scaled by s2 = (1-K)^2, or per position by mul[p].y when
-// mul (cidx layout) is given. after_forward() runs once the forward sweep has consumed the
+// co: the kL coefficients of this thread's chunk in shared memory (co[i] for position i of
+// the chunk); sa/sb: the line's scan buffers, 2 * nwl * tq entries each; wl / nwl: this
+// thread's warp within the line and the warps per line. The result is scaled by s2 =
+// (1-K)^2, or per position by mul[i].y when mul (the chunk's multipliers) is given. after_forward() runs once the forward sweep has consumed the
 // input values (the caller may then overwrite where they came from). Synchronizes the
 // block twice; threads with active == false (whole warps) only take part in the barriers.
+// A line may span the cs CTAs of a thread-block cluster: wl / nwl then number the warps of
+// the whole line, each warp's chunk map is stored into the scan buffers of every CTA of the
+// cluster, and the two barriers are the cluster's.
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
 template <typename Hook = NoHook>
-__device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restrict__ co,
-                                        int plane, int k, int tq, int dq, int lane, int wl,
-                                        int nwl, float* sa, float4* sb, float s2,
+__device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restrict__ co, int tq, int dq,
+                                        int lane, int wl, int nwl, float* sa, float4* sb, float s2,
                                         const float2* __restrict__ mul = nullptr,
-                                        Hook after_forward = Hook(), bool active = true) {
-    const int start = k * kL;
+                                        Hook after_forward = Hook(), bool active = true, int cs = 1) {
     float A = 0.f, Ae = 1.f;
     float B[4], Be[4], F[4], G[4];
 #pragma unroll
@@ -159,7 +194,7 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
         float u[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < kL; ++i) {
-            const float w = co[cidx(start + i, plane)].x;
+            const float w = co[i].x;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 u[j] = fmaf(w, u[j], v[i][j]);
@@ -169,7 +204,7 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
     }
     after_forward();
     if (active) {
-        A = co[cidx(start + kL - 1, plane)].y;
+        A = co[kL - 1].y;
 #pragma unroll
         for (int j = 0; j < 4; ++j) B[j] = v[kL - 1][j];
         for (int off = tq; off < 32; off <<= 1) {
@@ -191,11 +226,19 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
             Be[0] = Be[1] = Be[2] = Be[3] = 0.0f;
         }
         if (lane >= 32 - tq) {
-            sa[wl * tq + dq] = A;
-            sb[wl * tq + dq] = make_float4(B[0], B[1], B[2], B[3]);
+            const float4 b4 = make_float4(B[0], B[1], B[2], B[3]);
+            if (cs == 1) {
+                sa[wl * tq + dq] = A;
+                sb[wl * tq + dq] = b4;
+            } else {
+                for (int r = 0; r < cs; ++r) {
+                    st_rank(sa + wl * tq + dq, r, A);
+                    st_rank(sb + wl * tq + dq, r, b4);
+                }
+            }
         }
     }
-    __syncthreads();
+    line_sync(cs);
 
     // ---- phase 2: carry from the warps before, corrected forward values, backward sweep ----
     if (active) {
@@ -212,7 +255,7 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
         float h[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = kL - 1; i >= 0; --i) {
-            const float4 c = co[cidx(start + i, plane)];
+            const float4 c = co[i];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float ft = fmaf(c.y, F[j], v[i][j]);
@@ -220,7 +263,7 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
                 v[i][j] = h[j];
             }
         }
-        A = co[cidx(start, plane)].w;
+        A = co[0].w;
 #pragma unroll
         for (int j = 0; j < 4; ++j) B[j] = h[j];
         for (int off = tq; off < 32; off <<= 1) {
@@ -242,11 +285,19 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
             Be[0] = Be[1] = Be[2] = Be[3] = 0.0f;
         }
         if (lane < tq) {
-            sa[(nwl + wl) * tq + dq] = A;
-            sb[(nwl + wl) * tq + dq] = make_float4(B[0], B[1], B[2], B[3]);
+            const float4 b4 = make_float4(B[0], B[1], B[2], B[3]);
+            if (cs == 1) {
+                sa[(nwl + wl) * tq + dq] = A;
+                sb[(nwl + wl) * tq + dq] = b4;
+            } else {
+                for (int r = 0; r < cs; ++r) {
+                    st_rank(sa + (nwl + wl) * tq + dq, r, A);
+                    st_rank(sb + (nwl + wl) * tq + dq, r, b4);
+                }
+            }
         }
     }
-    __syncthreads();
+    line_sync(cs);
 
     // ---- phase 3: carry from the warps after, backward correction, scale ----
     if (active) {
@@ -262,8 +313,8 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
         for (int j = 0; j < 4; ++j) G[j] = fmaf(Ae, G[j], Be[j]);
 #pragma unroll
         for (int i = 0; i < kL; ++i) {
-            const float b = co[cidx(start + i, plane)].w;
-            const float m = mul ? mul[cidx(start + i, plane)].y : s2;
+            const float b = co[i].w;
+            const float m = mul ? mul[i].y : s2;
 #pragma unroll
             for (int j = 0; j < 4; ++j) v[i][j] = m * fmaf(b, G[j], v[i][j]);
         }

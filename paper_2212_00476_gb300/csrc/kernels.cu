@@ -125,13 +125,15 @@ cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st) {
 // Work: lines in groups of lpc, each group with nslices disparity slices of 4*tq
 // disparities; an item is (group, slice), numbered group-major. The grid is sized to the
 // resident blocks (persistent); block b processes the items [b*per_block, (b+1)*per_block)
-// in order, restaging the coefficients when the group changes. With aligned 4-disparity
+// in order, restaging the coefficients when the group changes. A line longer than one block
+// can hold at the chosen lanes per chunk spans the CTAs of a thread-block cluster (one line
+// per cluster), which exchange their warps' chunk maps through distributed shared memory. With aligned 4-disparity
 // groups (async) each thread streams its elements of the next item into shared memory with
 // cp.async while the current one is computed, across group boundaries: two staging buffers,
 // each refilled (two items ahead) as soon as the forward sweep has consumed it. In Wta mode
 // per_block is a multiple of nslices: a block sees every disparity of its lines.
 size_t line_stage_bytes(int dtype, const LineArgs& a) {
-    return a.async ? 2ull * a.lpc * kL * a.nch * a.tq * (4 * (dtype == 0 ? 4 : 2)) : 0;
+    return a.async ? 2ull * a.lpc * a.nch * a.tq * kL * (4 * (dtype == 0 ? 4 : 2)) : 0;
 }
 
 
@@ -139,14 +141,19 @@ size_t line_stage_bytes(int dtype, const LineArgs& a) {
 // pairs that way, so the shape and this thread's place in it are read from pair 0 at
 // constant offsets of the parameter block; only extents, strides and pointers differ between
 // pairs. SINGLE: the launch holds one pair, whose arguments are then all read at constant
-// offsets instead of through a dynamic index.
-template <typename T, int MODE, bool SINGLE>
+// offsets instead of through a dynamic index. CLUSTER: lines span the CTAs of a cluster.
+template <typename T, int MODE, bool SINGLE, bool CLUSTER>
 __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineBatch b) {
     extern __shared__ float4 smem4[];
     auto P = [&](int pi) -> const LineArgs& { return b.p[SINGLE ? 0 : pi]; };
     const int lane = threadIdx.x & 31;
-    const int i0 = (int)((long long)blockIdx.x * b.total_items / b.grid);
-    const int i1 = (int)((long long)(blockIdx.x + 1) * b.total_items / b.grid);
+    // A line spans the cs CTAs of a cluster (consecutive blocks), CTA `rank` holding chunks
+    // [rank * nch, rank * nch + nch); the cluster's CTAs take the same items in lock step.
+    const int cs = CLUSTER ? b.p[0].cs : 1;
+    const int rank = CLUSTER ? cluster_rank() : 0;
+    const int cid = blockIdx.x / cs, ncl = b.grid / cs;
+    const int i0 = (int)((long long)cid * b.total_items / ncl);
+    const int i1 = (int)((long long)(cid + 1) * b.total_items / ncl);
     // the block's steps: from the first step of item i0 to the first step of item i1
     auto step_of_item = [&](int item) -> int {
         if (item >= b.total_items) return b.total_steps;
@@ -162,11 +169,14 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     // block shape (shared by the launch's pairs) and this thread's place in it
     const int tq = b.p[0].tq, nch = b.p[0].nch, lpc = b.p[0].lpc;
     const bool async = b.p[0].async != 0;
-    const int per_line = nch * tq, nwl = per_line >> 5, pX = plane_of(nch * kL), ds = kG * tq;
+    const int per_line = nch * tq, nwl = per_line >> 5, ds = kG * tq;
+    const int nwl_all = cs * nwl;                   // warps of a whole line
     const bool active = (int)threadIdx.x < lpc * per_line;
     const int li = active ? threadIdx.x / per_line : 0;
     const int tl = active ? threadIdx.x - li * per_line : 0;
     const int k = tl / tq, dq = tl - k * tq, wl = tl >> 5;
+    const int kg = rank * nch + k;                  // chunk within the whole line
+    const int pos0 = rank * nch * kL;               // first line position of this CTA
 
     // A cursor over steps: the pair, the line group and the slice of a step, advanced one
     // step at a time.
@@ -203,13 +213,14 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     };
     auto line_of = [&](const Cursor& c) { return c.g * lpc + li; };
     auto elem0 = [&](const LineArgs& a, const Cursor& c) -> size_t {   // the chunk's first group
-        return (size_t)line_of(c) * a.line_stride + (size_t)(k * kL) * a.elem_stride + c.sl * ds + dq * kG;
+        return (size_t)line_of(c) * a.line_stride + (size_t)(kg * kL) * a.elem_stride + c.sl * ds + dq * kG;
     };
-    T* stage = reinterpret_cast<T*>(smem4);
-    // stage buffer buf of a step: [2][lpc][kL][per_line] groups of 4 entries
-    auto stage_at = [&](int buf, int i) -> T* {
-        return stage + ((size_t)((buf * lpc + li) * kL + i) * per_line + tl) * 4;
-    };
+    // staging buffers: [2][kL][threads] groups of 4 entries: position i of this thread's
+    // chunk at stage_at(buf) + i * sstride (consecutive threads, consecutive groups)
+    const int nthr = lpc * per_line;
+    const int sstride = nthr * 4;
+    T* const stage0 = reinterpret_cast<T*>(smem4) + (size_t)threadIdx.x * 4;
+    auto stage_at = [&](int buf) -> T* { return stage0 + (size_t)buf * kL * sstride; };
     // prefetch of the step at cursor pc into stage buffer buf. With vec the entries per pixel
     // are a multiple of 4, so a group with any valid disparity lies whole inside the volume;
     // its entries past dcount are never stored or compared.
@@ -220,11 +231,17 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
             const bool ok = line_of(pc) < a.nlines && pc.sl * ds + dq * kG < a.dcount;
             const T* q = src + (ok ? elem0(a, pc) : 0);
             const long long es = a.elem_stride;
-            const int npos = a.n - k * kL;
+            const int npos = a.n - kg * kL;
+            T* st = stage_at(buf);
+            if (ok && npos >= kL) {                 // a whole chunk: no per-position test
 #pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                const bool valid = ok && i < npos;
-                cp_async<4 * sizeof(T)>(stage_at(buf, i), valid ? q + (size_t)i * es : src, valid);
+                for (int i = 0; i < kL; ++i) cp_async<4 * sizeof(T)>(st + i * sstride, q + (size_t)i * es, true);
+            } else {
+#pragma unroll
+                for (int i = 0; i < kL; ++i) {
+                    const bool valid = ok && i < npos;
+                    cp_async<4 * sizeof(T)>(st + i * sstride, valid ? q + (size_t)i * es : src, valid);
+                }
             }
         }
         cp_async_commit();
@@ -237,14 +254,16 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     advance(pf);
 
     // shared memory: [stage][coefficients][multipliers][scan buffers]
+    // coefficients and multipliers: [lpc][nch][kCS], chunk-major
     float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + b.stage_bytes);
-    float2* mul_all = reinterpret_cast<float2*>(co_all + lpc * 4 * pX);
-    float4* sb_all = reinterpret_cast<float4*>(mul_all + lpc * 4 * pX);
-    float* sa_all = reinterpret_cast<float*>(sb_all + lpc * 2 * nwl * tq);
-    const float4* co = co_all + li * 4 * pX;
-    const float2* mul = mul_all + li * 4 * pX;
-    float4* sb = sb_all + li * 2 * nwl * tq;
-    float* sa = sa_all + li * 2 * nwl * tq;
+    float2* mul_all = reinterpret_cast<float2*>(co_all + lpc * nch * kCS);
+    float4* sb_all = reinterpret_cast<float4*>(mul_all + lpc * nch * kCS);
+    float* sa_all = reinterpret_cast<float*>(sb_all + lpc * 2 * nwl_all * tq);
+    const float4* co = co_all + (li * nch + k) * kCS;            // this thread's chunk
+    const float2* mul = mul_all + (li * nch + k) * kCS;
+    float4* sb = sb_all + li * 2 * nwl_all * tq;
+    float* sa = sa_all + li * 2 * nwl_all * tq;
+    if (cs > 1) cluster_sync_all();                 // every CTA of the cluster has started
 
     WtaRegs wr;
     int cur_pi = -1, cur_g = -1;
@@ -260,13 +279,14 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                 const int ln = o.g * lpc + l2;
                 const bool ok = ln < a.nlines;
                 for (int t = threadIdx.x; t < nch * kL; t += blockDim.x) {
-                    const bool in = ok && t < a.n;
-                    co_all[l2 * 4 * pX + cidx(t, pX)] =
-                        in ? __ldg(a.coef + (size_t)ln * a.coef_line_stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const size_t pix = (size_t)ln * a.pix_line + (size_t)t * a.pix_pos;
+                    const int gp = pos0 + t;
+                    const bool in = ok && gp < a.n;
+                    co_all[l2 * nch * kCS + cpos(t)] =
+                        in ? __ldg(a.coef + (size_t)ln * a.coef_line_stride + gp) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const size_t pix = (size_t)ln * a.pix_line + (size_t)gp * a.pix_pos;
                     const float mi = in && a.ahat_in ? __ldg(a.ahat_in + pix) : 1.0f;
                     const float mo = in && a.ahat_out ? a.s2 / __ldg(a.ahat_out + pix) : a.s2;
-                    mul_all[l2 * 4 * pX + cidx(t, pX)] = make_float2(mi, mo);
+                    mul_all[l2 * nch * kCS + cpos(t)] = make_float2(mi, mo);
                 }
             }
             if constexpr (MODE == kLineWta) wr.reset();
@@ -277,7 +297,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
         const int dl = o.sl * ds + dq * kG;                        // entry of d_first
         const int nvalid = max(0, min(4, a.dcount - dl));
         const bool any = line_ok && nvalid > 0;
-        const int npos = a.n - k * kL;
+        const int npos = a.n - kg * kL;
         T* vol = reinterpret_cast<T*>(a.vol);
         float v[kL][4];
         cp_async_wait<1>();                                            // this step's copies landed
@@ -287,8 +307,9 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v[i][j] = (any && i < npos && j < nvalid) ? 1.0f : 0.0f;
         } else if (async) {
+            const T* st = stage_at(n_s & 1);
 #pragma unroll
-            for (int i = 0; i < kL; ++i) lds4(stage_at(n_s & 1, i), v[i]);
+            for (int i = 0; i < kL; ++i) lds4(st + i * sstride, v[i]);
         } else {
             const T* src = a.src ? reinterpret_cast<const T*>(a.src) : vol;
             const T* q = src + (line_ok ? elem0(a, o) : 0);
@@ -302,17 +323,17 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
         if (a.ahat_in && active) {
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
-                const float m = mul[cidx(k * kL + i, pX)].x;
+                const float m = mul[i].x;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v[i][j] *= m;
             }
         }
         // the staging buffer is free once the forward sweep has read it: refill it two ahead
-        dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2, mul,
+        dt_pair(v, co, tq, dq, lane, rank * nwl + wl, nwl_all, sa, sb, a.s2, mul,
                 [&]() {
                     prefetch(pf, n_s & 1);
                     advance(pf);
-                }, active);
+                }, active, cs);
         if constexpr (MODE == kLineWta) {
             if (active) wr.fold(v, nvalid, a.d_base + dl);
             if (o.sl == o.nslices - 1 && active) {                    // the group's last slice
@@ -321,7 +342,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                     float best;
                     int bd;
                     wta_reduce_lanes(wr.entry(i), tq, best, bd);
-                    const int pos = k * kL + i;
+                    const int pos = kg * kL + i;
                     if (dq == 0 && line_ok && pos < a.n) {
                         const size_t pix = (size_t)line * a.pix_line + (size_t)pos * a.pix_pos;
                         if (!a.wta.first) {                            // earlier launches: smaller d
@@ -338,49 +359,90 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
             }
         } else {
             T* q = vol + (line_ok ? elem0(a, o) : 0);
+            const long long es = a.elem_stride;
+            if (any && npos >= kL && nvalid == 4 && a.vec) {     // a whole chunk of whole groups
 #pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                if (any && i < npos) st4(q, nvalid, a.vec != 0, v[i]);
-                q += a.elem_stride;
+                for (int i = 0; i < kL; ++i) st4(q + (size_t)i * es, 4, true, v[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < kL; ++i)
+                    if (any && i < npos) st4(q + (size_t)i * es, nvalid, a.vec != 0, v[i]);
             }
         }
     }
     cp_async_wait<0>();
+    if (cs > 1) cluster_sync_all();                 // no CTA leaves while others may store to it
 }
 
 size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a) {
-    const int pX = plane_of(a.nch * kL);
-    const int nwl = a.nch * a.tq / 32;
+    const int nwl_all = a.cs * a.nch * a.tq / 32;
     (void)mode;
-    return line_stage_bytes(dtype, a) + (size_t)a.lpc * ((16ull + 8ull) * 4 * pX + dt_scan_bytes(nwl, a.tq));
+    return line_stage_bytes(dtype, a) + (size_t)a.lpc * ((16ull + 8ull) * a.nch * kCS + dt_scan_bytes(nwl_all, a.tq));
 }
 
-template <bool SINGLE>
+template <bool SINGLE, bool CLUSTER>
 static void (*line_pair_fn_t(int mode, int dtype))(LineBatch) {
     if (mode == kLineStore)
-        return dtype == 0 ? k_line_pair<float, kLineStore, SINGLE> : k_line_pair<__half, kLineStore, SINGLE>;
-    return dtype == 0 ? k_line_pair<float, kLineWta, SINGLE> : k_line_pair<__half, kLineWta, SINGLE>;
+        return dtype == 0 ? k_line_pair<float, kLineStore, SINGLE, CLUSTER>
+                          : k_line_pair<__half, kLineStore, SINGLE, CLUSTER>;
+    return dtype == 0 ? k_line_pair<float, kLineWta, SINGLE, CLUSTER> : k_line_pair<__half, kLineWta, SINGLE, CLUSTER>;
 }
 
-static void (*line_pair_fn(int mode, int dtype, bool single))(LineBatch) {
-    return single ? line_pair_fn_t<true>(mode, dtype) : line_pair_fn_t<false>(mode, dtype);
+static void (*line_pair_fn(int mode, int dtype, bool single, bool cluster))(LineBatch) {
+    if (cluster) return single ? line_pair_fn_t<true, true>(mode, dtype) : line_pair_fn_t<false, true>(mode, dtype);
+    return single ? line_pair_fn_t<true, false>(mode, dtype) : line_pair_fn_t<false, false>(mode, dtype);
 }
 
-cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, bool single, int* blocks_per_sm) {
-    void (*fn)(LineBatch) = line_pair_fn(mode, dtype, single);
+cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, bool single, bool cluster,
+                                int* blocks_per_sm) {
+    void (*fn)(LineBatch) = line_pair_fn(mode, dtype, single, cluster);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
 }
 
-cudaError_t launch_line_batch(const LineBatch& b, int threads, size_t smem, int mode, int dtype,
-                              cudaStream_t st) {
-    dim3 grid(b.grid);
-    void (*fn)(LineBatch) = line_pair_fn(mode, dtype, b.npairs == 1);
+cudaError_t line_pair_max_clusters(int mode, int dtype, int threads, size_t smem, bool single, int cs,
+                                   int* clusters) {
+    void (*fn)(LineBatch) = line_pair_fn(mode, dtype, single, true);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<grid, threads, smem, st>>>(b);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(clusters, fn, &cfg);
+}
+
+cudaError_t launch_line_batch(const LineBatch& b, int threads, size_t smem, int mode, int dtype,
+                              cudaStream_t st) {
+    const int cs = b.p[0].cs;
+    void (*fn)(LineBatch) = line_pair_fn(mode, dtype, b.npairs == 1, cs > 1);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (cs <= 1) {
+        fn<<<dim3(b.grid), threads, smem, st>>>(b);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b.grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, b);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -53,7 +53,8 @@ struct LineArgs {
     int n, nlines;            // line length, number of lines
     int dcount;               // valid disparity entries per pixel
     int d_base;               // disparity of entry 0 (WTA)
-    int tq, lpc, nch;         // lanes per chunk, lines per block, chunks per line
+    int tq, lpc, nch;         // lanes per chunk, lines per block, chunks per line and CTA
+    int cs;                   // CTAs per line (a thread-block cluster; 1 = none, then lpc >= 1)
     int per_block;            // work items (line group, disparity slice) per block
     const float* ahat_in;     // per-pixel multiplier of the input (NULL: 1)
     const float* ahat_out;    // per-pixel divisor of the output (NULL: 1)
@@ -88,7 +89,11 @@ cudaError_t zncc_row_occupancy(int R, int mode, int dtype, int threads, size_t s
                                bool single, int* blocks_per_sm);
 size_t line_stage_bytes(int dtype, const LineArgs& a);
 // single: the variant for launches of one pair (npairs == 1), which the launchers pick
-cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, bool single, int* blocks_per_sm);
+cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, bool single, bool cluster,
+                                int* blocks_per_sm);
+// clusters of cs CTAs that can be resident at once on the device
+cudaError_t line_pair_max_clusters(int mode, int dtype, int threads, size_t smem, bool single, int cs,
+                                   int* clusters);
 cudaError_t launch_window_stats(const uint8_t* img, int pitch, int W, int H, int r, int x_begin,
                                 int nx, int* S, int* Q, float* isig, int2* packed,
                                 cudaStream_t st);

@@ -62,8 +62,8 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int run, 
     uint4* RP = LP + 4 * pLP;
     int2* SL = reinterpret_cast<int2*>(RP + 4 * pRP);               // (S, 1/sigma bits) per x
     int2* SR = SL + 4 * pX;                                          // per right centre
-    float4* co = reinterpret_cast<float4*>(SR + 4 * pSR);            // HPair
-    float4* sb = co + 4 * pX;
+    float4* co = reinterpret_cast<float4*>(SR + 4 * pSR);            // HPair, chunk-major
+    float4* sb = co + nch * kCS;
     float* sa = reinterpret_cast<float*>(sb + 2 * nwl * tq);
 
     // ---- stage the packed bands (and the DT coefficients) ----
@@ -84,7 +84,7 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int run, 
     }
     if constexpr (MODE == kModeHPair) {
         for (int t = tid; t < span; t += blockDim.x)
-            co[cidx(t, pX)] = t < W ? __ldg(a.coef + (size_t)y * W + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+            co[cpos(t)] = t < W ? __ldg(a.coef + (size_t)y * W + t) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
 
@@ -193,7 +193,8 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int run, 
             if (active) wr.fold(v, nvalid, d_first);
             continue;
         }
-        if constexpr (MODE == kModeHPair) dt_pair(v, co, pX, k, tq, dq, lane, wl, nwl, sa, sb, a.s2, nullptr, NoHook(), active);
+        if constexpr (MODE == kModeHPair)
+            dt_pair(v, co + k * kCS, tq, dq, lane, wl, nwl, sa, sb, a.s2, nullptr, NoHook(), active);
 
         // ---- store [H][W][dstride] ----
         if (active && nvalid > 0) {
@@ -261,7 +262,7 @@ inline size_t zncc_row_smem(int R, int mode, const RowArgs& a, int nthreads) {
     size_t b = 16ull * 4 * (plane_of(span + 2 * R) + plane_of(span + 2 * R + drange - 1));
     const int pX = plane_of(span);
     b += 8ull * 4 * (pX + plane_of(span + drange - 1));
-    if (mode == kModeHPair) b += 16ull * 4 * pX + dt_scan_bytes(nthreads / 32, a.tq);
+    if (mode == kModeHPair) b += 16ull * a.nch * kCS + dt_scan_bytes(nthreads / 32, a.tq);
     return b;
 }
 
