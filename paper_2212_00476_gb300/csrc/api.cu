@@ -52,11 +52,11 @@ namespace {
 // Kernel kinds for per-kernel timing (zncc_profile_*).
 enum Kind {
     K_STATS = 0, K_COEF, K_ZNCC_RAW, K_ZNCC_HPAIR, K_ZNCC_WTA, K_DT_HPAIR, K_DT_VPAIR,
-    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_AHAT, K_NKINDS
+    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_AHAT, K_WTA_FINISH, K_NKINDS
 };
 const char* const kKindNames[K_NKINDS] = {
     "window_stats", "dt_coef", "zncc_cost", "zncc_cost_hpair", "zncc_cost_wta",
-    "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume", "ahat_pair"};
+    "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume", "ahat_pair", "wta_finish"};
 
 struct ProfRecord {
     int kind, ev0, ev1;
@@ -82,6 +82,7 @@ struct zncc_ctx {
     std::string err;
     float4* coefH = nullptr;      // [H][W]       horizontal DT coefficients
     float4* coefV = nullptr;      // [W][H]       vertical DT coefficients
+    unsigned long long* keys = nullptr;   // [H][W] fused-WTA keys, zero between runs
     void* vol = nullptr;          // the fused path's intermediate volume (on first use)
     size_t vol_bytes = 0;
     float* ahat = nullptr;        // [nahat][H][W] DT responses of an all-ones plane (F16 storage)
@@ -174,6 +175,7 @@ void free_dev(T*& p) {
 void release(zncc_ctx* c) {
     free_dev(c->coefH);
     free_dev(c->coefV);
+    free_dev(c->keys);
     free_dev(c->vol);
     c->vol_bytes = 0;
     free_dev(c->ahat);
@@ -347,7 +349,7 @@ struct LinePass {
     int mode = kLineStore;
     const float* ahat_in = nullptr;
     const float* ahat_out = nullptr;
-    uint16_t* disp = nullptr;
+    unsigned long long* keys = nullptr;   // (Wta)
     float s2 = 1.0f;
     int force_tq = 0;
 };
@@ -464,9 +466,7 @@ void fill_line_args(LineArgs& a, const LinePass& p, int W, int H, const float4* 
     const void* in = p.src ? p.src : p.vol;
     const size_t al = p.dtype == 0 ? 16 : 8;
     a.vec = (p.dstride % 4 == 0) && ((uintptr_t)p.vol % al == 0) && ((uintptr_t)in % al == 0) ? 1 : 0;
-    a.wta.disp = p.disp;
-    a.wta.first = 1;
-    a.wta.last = 1;
+    a.keys = p.keys;
     a.pix_line = p.horiz ? W : 1;
     a.pix_pos = p.horiz ? 1 : W;
     a.cs = 1;
@@ -483,7 +483,8 @@ void add_line_pair(LineBatch& b, const LineArgs& ai, int mode, int dtype, int& t
     a.step0 = b.total_steps;
     a.nsteps = ngroups * nslices;
     a.item0 = b.total_items;
-    a.nitems = mode == kLineWta ? ngroups : a.nsteps;
+    a.nitems = a.nsteps;
+    (void)mode;
     b.total_steps += a.nsteps;
     b.total_items += a.nitems;
     threads = std::max(threads, a.lpc * a.nch * a.tq);
@@ -617,13 +618,24 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
             lp[i].s2 = s2;
             lp[i].horiz = (pair % 2) == 1;
             lp[i].mode = pair == npairs ? kLineWta : kLineStore;
-            lp[i].disp = pair == npairs ? io[i].disp : nullptr;
+            lp[i].keys = pair == npairs ? io[i].c->keys : nullptr;
             lp[i].ahat_in = norm && pair - 1 >= 2 ? io[i].c->ahat + (size_t)(pair - 2) * npix : nullptr;
             lp[i].ahat_out = norm && pair < npairs ? io[i].c->ahat + (size_t)(pair - 1) * npix : nullptr;
         }
         const int kind = pair % 2 ? K_DT_HPAIR : (pair == npairs ? K_DT_VPAIR_WTA : K_DT_VPAIR);
         ZNCC_TRY(run_lines(lc, ctxs, lp, n, kind));
     }
+    WtaFinishBatch fb;                              // keys -> disparities, keys zeroed
+    memset(&fb, 0, sizeof(fb));
+    fb.npairs = n;
+    for (int i = 0; i < n; ++i) {
+        fb.p[i].keys = io[i].c->keys;
+        fb.p[i].disp = io[i].disp;
+        fb.p[i].npix = (long long)io[i].c->W * io[i].c->H;
+        fb.p[i].thread0 = fb.total_threads;
+        fb.total_threads += fb.p[i].npix;
+    }
+    ZNCC_LAUNCH(lc, K_WTA_FINISH, launch_wta_finish(fb, lc->cur), "WTA finish");
     return ZNCC_OK;
 }
 
@@ -723,6 +735,8 @@ zncc_status zncc_create(int width, int height, int max_disp, int win, zncc_ctx**
     const size_t npix = (size_t)width * height;
     if (e == cudaSuccess) e = device_alloc((void**)&c->coefH, npix * sizeof(float4));
     if (e == cudaSuccess) e = device_alloc((void**)&c->coefV, npix * sizeof(float4));
+    if (e == cudaSuccess) e = device_alloc((void**)&c->keys, npix * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->keys, 0, npix * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         zncc_status s = e == cudaErrorMemoryAllocation ? ZNCC_ENOMEM : ZNCC_ECUDA;
         std::string m = std::string("zncc_create: ") + cudaGetErrorString(e);

@@ -355,6 +355,17 @@ struct WtaRegs {
     }
 };
 
+// A (value, d) pair as a 64-bit key whose unsigned order is the WTA order: larger values
+// first, then smaller d. High word: the float's bits made order-preserving; low word: ~d.
+__device__ __forceinline__ unsigned long long wta_key(float v, int d) {
+    const unsigned u = __float_as_uint(v);
+    const unsigned hi = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)hi << 32) | (unsigned)(~(unsigned)d);
+}
+__device__ __forceinline__ uint16_t wta_key_disparity(unsigned long long key) {
+    return (uint16_t)(~(unsigned)key);
+}
+
 // Reduces the tq lanes of a pixel (consecutive lanes of a warp); all lanes get the result:
 // the largest value, and the smallest d among equal values.
 __device__ __forceinline__ void wta_reduce_lanes(float2 e, int tq, float& best, int& bd) {

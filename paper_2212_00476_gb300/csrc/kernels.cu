@@ -130,8 +130,9 @@ cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st) {
 // per cluster), which exchange their warps' chunk maps through distributed shared memory. With aligned 4-disparity
 // groups (async) each thread streams its elements of the next item into shared memory with
 // cp.async while the current one is computed, across group boundaries: two staging buffers,
-// each refilled (two items ahead) as soon as the forward sweep has consumed it. In Wta mode
-// per_block is a multiple of nslices: a block sees every disparity of its lines.
+// each refilled (two items ahead) as soon as the forward sweep has consumed it. In Wta mode a
+// block keeps a running best over the slices it sees of a line group and merges it into the
+// per-pixel keys (atomicMax) when the group or its range ends.
 size_t line_stage_bytes(int dtype, const LineArgs& a) {
     return a.async ? 2ull * a.lpc * a.nch * a.tq * kL * (4 * (dtype == 0 ? 4 : 2)) : 0;
 }
@@ -336,7 +337,8 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                 }, active, cs);
         if constexpr (MODE == kLineWta) {
             if (active) wr.fold(v, nvalid, a.d_base + dl);
-            if (o.sl == o.nslices - 1 && active) {                    // the group's last slice
+            // at the group's last slice, or the block's last step, merge this block's best
+            if ((o.sl == o.nslices - 1 || o.s + 1 == s1) && active) {
 #pragma unroll
                 for (int i = 0; i < kL; ++i) {
                     float best;
@@ -345,15 +347,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                     const int pos = kg * kL + i;
                     if (dq == 0 && line_ok && pos < a.n) {
                         const size_t pix = (size_t)line * a.pix_line + (size_t)pos * a.pix_pos;
-                        if (!a.wta.first) {                            // earlier launches: smaller d
-                            const float pb = a.wta.bestv[pix];
-                            if (!(best > pb)) { best = pb; bd = a.wta.bestd[pix]; }
-                        }
-                        if (a.wta.last) a.wta.disp[pix] = (uint16_t)bd;
-                        else {
-                            a.wta.bestv[pix] = best;
-                            a.wta.bestd[pix] = bd;
-                        }
+                        atomicMax(a.keys + pix, wta_key(best, bd));
                     }
                 }
             }
@@ -443,6 +437,26 @@ cudaError_t launch_line_batch(const LineBatch& b, int threads, size_t smem, int 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, fn, b);
+}
+
+// ---------------------------------------------------------------------------------------
+// End of the fused WTA: key -> disparity, key -> 0 (ready for the next run).
+__global__ void k_wta_finish(const __grid_constant__ WtaFinishBatch b) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int pi = 0;
+    while (pi + 1 < b.npairs && gid >= b.p[pi + 1].thread0) ++pi;
+    const WtaFinishArgs& a = b.p[pi];
+    const long long i = gid - a.thread0;
+    if (i < a.npix) {
+        a.disp[i] = wta_key_disparity(a.keys[i]);
+        a.keys[i] = 0ull;
+    }
+}
+
+cudaError_t launch_wta_finish(const WtaFinishBatch& b, cudaStream_t st) {
+    const long long blocks = (b.total_threads + 255) / 256;
+    k_wta_finish<<<(unsigned)blocks, 256, 0, st>>>(b);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------

@@ -63,15 +63,19 @@ struct LineArgs {
     float s2;
     int vec;                  // 16-byte (float) / 8-byte (half) accesses allowed
     int async;                // vec, and the next slices are streamed through shared memory
-    WtaOut wta;               // (Wta)
+    // (Wta) per-pixel keys (ordered value << 32 | ~d), merged with atomicMax by every block that
+    // saw part of a pixel's disparities; zero before the launch, turned into disparities (and
+    // zeroed again) by k_wta_finish
+    unsigned long long* keys;
     long long pix_line, pix_pos;  // pixel of (line, pos) is line * pix_line + pos * pix_pos
     // position of this pair in a batched launch: items and steps (line group, slice) are
-    // numbered pair by pair; an item is one step (Store) or every slice of a group (Wta)
+    // numbered pair by pair
     int item0, nitems, step0, nsteps;
 };
 
-// One line-pair launch over up to kMaxBatch pairs, passed by value. Of G blocks, block b
-// takes the items [b * total / G, (b+1) * total / G) of all pairs, in order.
+// One line-pair launch over up to kMaxBatch pairs, passed by value. Of G blocks (or clusters),
+// block b takes the items [b * total / G, (b+1) * total / G) of all pairs, in order; an item is
+// one step (line group, disparity slice) in both modes.
 struct LineBatch {
     int npairs, total_items, total_steps, grid;
     long long stage_bytes;    // staging region (the largest pair's), before the other arrays
@@ -114,6 +118,19 @@ cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st);
 long long dt_coef_threads(int W, int H);
 cudaError_t launch_wta_volume(const void* cost, int dtype, int W, int H, int D, uint16_t* disp,
                               cudaStream_t st);
+
+// The end of a fused WTA: each pixel's key becomes its disparity, and the key is zeroed.
+struct WtaFinishArgs {
+    unsigned long long* keys;
+    uint16_t* disp;
+    long long npix, thread0;
+};
+struct WtaFinishBatch {
+    int npairs;
+    long long total_threads;
+    WtaFinishArgs p[kMaxBatch];
+};
+cudaError_t launch_wta_finish(const WtaFinishBatch& b, cudaStream_t st);
 
 // Device allocation of the library (cudaMalloc, or an injected out-of-memory failure when the
 // environment variable ZNCC_FAIL_DEVICE_ALLOC is 1).
