@@ -82,7 +82,7 @@ def _time(ctx, run, reps):
     return times[len(times) // 2]
 
 
-def tune(ctx, left, right, disp, sigma_s, sigma_r, iters, storage=Z.ZNCC_F32, reps=7,
+def tune(ctx, left, right, disp, sigma_s, sigma_r, iters, storage=Z.ZNCC_F32, reps=15,
          rounds=2, cache=DEFAULT_CACHE, force=False, log=None):
     """Best knob settings for this shape (cached); leaves them applied to ctx."""
     key = shape_key(ctx, iters, storage)
@@ -111,7 +111,7 @@ def tune(ctx, left, right, disp, sigma_s, sigma_r, iters, storage=Z.ZNCC_F32, re
                 ms = _time(ctx, run, reps)
                 if log:
                     log(f"{NAMES[k]}={v}: {ms}")
-                if ms is not None and ms < best_ms * 0.99:
+                if ms is not None and ms < best_ms * 0.985:
                     best_ms, settings, changed = ms, trial, True
             apply(ctx, settings)
         if not changed:

@@ -68,7 +68,6 @@ struct LinePlan {
     int tq, lpc, nch, async, per_block, blocks, cs;
 };
 
-constexpr int kTargetBlocks = 1216;   // about eight blocks per SM on a 152-SM GB300
 
 }  // namespace
 
@@ -157,13 +156,6 @@ int padded_chunks(int n, int tq) {
     const int per_warp = 32 / tq;
     const int nch = (n + kL - 1) / kL;
     return (nch + per_warp - 1) / per_warp * per_warp;
-}
-
-// Disparity slices per block: about kTargetBlocks blocks in all, equal runs per block.
-int slices_per_block(int nslices, int blocks_x) {
-    const int per = std::max(1, blocks_x * nslices / kTargetBlocks);
-    const int groups = std::max(1, (nslices + per - 1) / per);
-    return (nslices + groups - 1) / groups;
 }
 
 template <typename T>
@@ -316,13 +308,13 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
             const int nthr = a.nch * a.tq;
             const int nslices = (c->D + kG * a.tq - 1) / (kG * a.tq);
             if (mode == kModeWta) a.spb = nslices;
-            else a.spb = c->row_spb > 0 ? std::min(c->row_spb, nslices) : slices_per_block(nslices, c->H);
+            else a.spb = c->row_spb > 0 ? std::min(c->row_spb, nslices) : nslices;
             while (a.spb > 1 && zncc_row_smem_bytes(r, mode, a, nthr) > (size_t)lc->smem_max) --a.spb;
             const size_t sm = zncc_row_smem_bytes(r, mode, a, nthr);
             if (sm > (size_t)lc->smem_max)
                 return fail(lc, ZNCC_EUNSUPPORTED, "the cost kernel's row band does not fit in shared memory");
             a.item0 = b.total_items;
-            a.nitems = c->H * ((nslices + a.spb - 1) / a.spb);
+            a.nitems = mode == kModeWta ? c->H : c->H * nslices;       // units: rows, or (row, slice)
             b.total_items += a.nitems;
             threads = std::max(threads, nthr);
             smem = std::max(smem, sm);

@@ -25,7 +25,7 @@ struct RowArgs {
     int pitch, W, H, D;
     int nch, tq;              // chunks per row (padded to whole warps), lanes per chunk
     int d_lo, d_hi;           // disparity range of this launch (d_lo a multiple of 4)
-    int spb;                  // disparity slices (4 * tq each) per block
+    int spb;                  // disparity slices (4 * tq each) per visit of a row
     void* vol;                // output [H][W][dstride] of float or half (Raw / HPair)
     long long dstride;        // entries per pixel in the output
     int d_out0;               // disparity stored at entry 0 of a pixel
@@ -34,11 +34,11 @@ struct RowArgs {
     float s2;                 // (1 - K)^2
     WtaOut wta;               // (Wta)
     int minb2;                // use the two-blocks-per-SM variant where the block allows
-    int item0, nitems;        // this pair's items (row, run of spb slices) in a batched launch
+    int item0, nitems;        // this pair's units (row, slice), or rows (Wta), in a batched launch
 };
 
 // One cost-kernel launch over up to kMaxBatch pairs of the same window radius, passed by
-// value. Of G blocks, block b takes the items [b * total / G, (b+1) * total / G), in order.
+// value. Of G blocks, block b takes the units [b * total / G, (b+1) * total / G), in order.
 struct RowBatch {
     int npairs, total_items, grid, mode;
     RowArgs p[kMaxBatch];

@@ -32,10 +32,11 @@ namespace zncc {
 // block and serve all of its disparity slices; the window statistics of both images
 // (Sec. IV-B-1, Eq. (sum1)) come from the same packed columns: a column's pixel sum is
 // __dp4a(word, 0x01010101) and its sum of squares __dp4a(word, word), slid like P.
-// One item of the cost kernel: row y of one pair, disparity slices [run*spb, run*spb+spb).
+// One visit of the cost kernel: row y of one pair, disparity slices [s_begin, s_end).
 // Threads beyond the pair's nch * tq (whole warps) only take part in the barriers.
 template <int R, typename T, int MODE>
-__device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int run, uint4* smem_u4) {
+__device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_begin, int s_end,
+                                              uint4* smem_u4) {
     constexpr int l = 2 * R + 1;
     constexpr int NW = (l + 3) / 4;     // packed words per column
     const int tq = a.tq, ds = kG * tq, nch = a.nch, span = nch * kL;
@@ -45,9 +46,6 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int run, 
     const bool active = tid < nthr;
     const int k = active ? tid / tq : 0, dq = active ? tid - (tid / tq) * tq : 0;
     const int lane = tid & 31, wl = tid >> 5, nwl = nthr >> 5;
-    const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
-    const int s_begin = run * a.spb;
-    const int s_end = min(nslices, s_begin + a.spb);
     // every lane's disparities lie in [blk_lo, blk_hi)
     const int blk_lo = a.d_lo + s_begin * ds, blk_hi = a.d_lo + s_end * ds;
 
@@ -234,23 +232,38 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int run, 
 
 // SINGLE: the launch holds one pair, whose arguments are then read at constant offsets of
 // the parameter block instead of through a dynamic index.
+// Work units: (row, disparity slice) in row-major order, pair by pair (Wta: whole rows, since
+// a row's running best stays in registers). Block b takes the units [b*total/G, (b+1)*total/G)
+// and visits them row by row, at most spb slices per visit, so that the band of a row is
+// staged once per visit and every block gets the same work within one unit.
 template <int R, typename T, int MODE, int MINB, bool SINGLE>
 __global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(const __grid_constant__ RowBatch b) {
     extern __shared__ uint4 smem_u4[];
     const int i0 = (int)((long long)blockIdx.x * b.total_items / b.grid);
     const int i1 = (int)((long long)(blockIdx.x + 1) * b.total_items / b.grid);
     int pi = 0;
-    for (int item = i0; item < i1; ++item) {
+    for (int u = i0; u < i1;) {
         if (!SINGLE)
-            while (item >= b.p[pi].item0 + b.p[pi].nitems) ++pi;
+            while (u >= b.p[pi].item0 + b.p[pi].nitems) ++pi;
         const RowArgs& a = b.p[SINGLE ? 0 : pi];
         const int ds = kG * a.tq;
         const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
-        const int nruns = (nslices + a.spb - 1) / a.spb;
-        const int local = item - a.item0;
-        const int y = local / nruns;
-        zncc_row_item<R, T, MODE>(a, y, local - y * nruns, smem_u4);
-        __syncthreads();                                 // the next item restages shared memory
+        const int local = u - a.item0;
+        int y, s_begin, s_end;
+        if constexpr (MODE == kModeWta) {
+            y = local;
+            s_begin = 0;
+            s_end = nslices;
+            u += 1;
+        } else {
+            y = local / nslices;
+            s_begin = local - y * nslices;
+            const int last = min(i1, a.item0 + (y + 1) * nslices);      // this block, this row
+            s_end = min(s_begin + a.spb, s_begin + (last - u));
+            u += s_end - s_begin;
+        }
+        zncc_row_item<R, T, MODE>(a, y, s_begin, s_end, smem_u4);
+        __syncthreads();                                 // the next visit restages shared memory
     }
 }
 
