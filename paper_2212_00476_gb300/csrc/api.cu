@@ -263,7 +263,8 @@ zncc_status run_coef(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, float
 // one row and a run of disparity slices (the band of a block spans its slices, so the run
 // shrinks until the block fits in shared memory); in Wta mode a block covers every
 // disparity of its row.
-zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype, float s2, int kind,
+zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype, float s2, float K,
+                     float inv_sr255, int kind,
                      const char* what) {
     // pairs share a launch when they share the window radius and the block shape
     auto tq_of = [](int W) { return W <= 1024 ? 8 : (W <= 2048 ? 4 : 2); };
@@ -299,7 +300,8 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
             a.d_out0 = 0;
             a.vec = io[i].vol && (io[i].dstride % 4 == 0) &&
                     ((uintptr_t)io[i].vol % (dtype == 0 ? 16 : 8) == 0) ? 1 : 0;
-            a.coef = c->coefH;
+            a.K = K;
+            a.inv_sr255 = inv_sr255;
             a.s2 = s2;
             a.minb2 = c->row_minb2;
             a.wta.disp = io[i].disp;
@@ -547,7 +549,7 @@ zncc_status ensure_ahat(zncc_ctx* c, int n) {
 // radius for the cost kernel).
 zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigma_r, int iters,
                       int storage) {
-    if (iters == 0) return run_rows(lc, io, n, kModeWta, 0, 0.0f, K_ZNCC_WTA, "ZNCC + WTA");
+    if (iters == 0) return run_rows(lc, io, n, kModeWta, 0, 0.0f, 0.0f, 0.0f, K_ZNCC_WTA, "ZNCC + WTA");
     const int dt = storage == ZNCC_F32 ? 0 : 1;
     zncc_ctx* ctxs[kMaxBatch];
     for (int i = 0; i < n; ++i) {
@@ -556,49 +558,50 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
         if (ensure_volume(io[i].c, dt, io[i].dstride) != ZNCC_OK) return fail(lc, ZNCC_ENOMEM, io[i].c->err);
         io[i].vol = io[i].c->vol;
     }
-    ZNCC_TRY(run_coef(lc, io, n, sigma_s, sigma_r));
     const float s2 = scale_s2(sigma_s);
+    const float K = (float)exp(-1.0 / (double)sigma_s);
+    const float inv_sr255 = (float)(1.0 / (255.0 * (double)sigma_r));
     const int npairs = 2 * iters;
+    // The DT weights of the line pairs (and, with half storage, the A_hat maps) depend only on
+    // the guide: they are computed on a second stream, concurrently with the cost kernel
+    // (which computes the weights of its own rows), and joined before the first line pair.
     // Half storage keeps each stored pair p >= 2 divided by A_hat_p (the per-pixel bound of
     // |cost|), so that it stays inside the half range wherever the guide isolates a pixel;
-    // the next pair multiplies it back. The factor is the same for every d of a pixel. The
-    // A_hat maps depend only on the guide: they are computed on a second stream,
-    // concurrently with the cost kernel, and joined before the first stored pair is read.
+    // the next pair multiplies it back. The factor is the same for every d of a pixel.
     const bool norm = dt == 1 && npairs > 2;
-    if (norm) {
+    if (norm)
         for (int i = 0; i < n; ++i)
             if (ensure_ahat(io[i].c, npairs - 1) != ZNCC_OK) return fail(lc, ZNCC_ENOMEM, io[i].c->err);
-        if (!lc->side) {
-            ZNCC_CUDA(lc, cudaStreamCreateWithFlags(&lc->side, cudaStreamNonBlocking), "side stream");
-            ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_fork, cudaEventDisableTiming), "fork event");
-            ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_join, cudaEventDisableTiming), "join event");
-        }
-        ZNCC_CUDA(lc, cudaEventRecord(lc->ev_fork, lc->stream), "fork");
-        ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->side, lc->ev_fork, 0), "fork");
-        lc->cur = lc->side;
-        zncc_status st = ZNCC_OK;
-        for (int p = 1; p <= npairs - 1 && st == ZNCC_OK; ++p) {
-            LinePass lp[kMaxBatch];
-            for (int i = 0; i < n; ++i) {
-                const size_t npix = (size_t)io[i].c->W * io[i].c->H;
-                lp[i].vol = io[i].c->ahat + (size_t)(p - 1) * npix;
-                lp[i].src = p == 1 ? nullptr : io[i].c->ahat + (size_t)(p - 2) * npix;
-                lp[i].ones = p == 1;
-                lp[i].dstride = 1;
-                lp[i].dcount = 1;
-                lp[i].dtype = 0;
-                lp[i].horiz = (p % 2) == 1;
-                lp[i].s2 = s2;
-                lp[i].force_tq = 1;
-            }
-            st = run_lines(lc, ctxs, lp, n, K_AHAT);
-        }
-        lc->cur = lc->stream;
-        ZNCC_TRY(st);
-        ZNCC_CUDA(lc, cudaEventRecord(lc->ev_join, lc->side), "join");
+    if (!lc->side) {
+        ZNCC_CUDA(lc, cudaStreamCreateWithFlags(&lc->side, cudaStreamNonBlocking), "side stream");
+        ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_fork, cudaEventDisableTiming), "fork event");
+        ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_join, cudaEventDisableTiming), "join event");
     }
-    ZNCC_TRY(run_rows(lc, io, n, kModeHPair, dt, s2, K_ZNCC_HPAIR, "ZNCC + horizontal DT pair"));
-    if (norm) ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_join, 0), "join of the A_hat stream");
+    ZNCC_CUDA(lc, cudaEventRecord(lc->ev_fork, lc->stream), "fork");
+    ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->side, lc->ev_fork, 0), "fork");
+    lc->cur = lc->side;
+    zncc_status st = run_coef(lc, io, n, sigma_s, sigma_r);
+    for (int p = 1; norm && p <= npairs - 1 && st == ZNCC_OK; ++p) {
+        LinePass lp[kMaxBatch];
+        for (int i = 0; i < n; ++i) {
+            const size_t npix = (size_t)io[i].c->W * io[i].c->H;
+            lp[i].vol = io[i].c->ahat + (size_t)(p - 1) * npix;
+            lp[i].src = p == 1 ? nullptr : io[i].c->ahat + (size_t)(p - 2) * npix;
+            lp[i].ones = p == 1;
+            lp[i].dstride = 1;
+            lp[i].dcount = 1;
+            lp[i].dtype = 0;
+            lp[i].horiz = (p % 2) == 1;
+            lp[i].s2 = s2;
+            lp[i].force_tq = 1;
+        }
+        st = run_lines(lc, ctxs, lp, n, K_AHAT);
+    }
+    lc->cur = lc->stream;
+    ZNCC_TRY(st);
+    ZNCC_CUDA(lc, cudaEventRecord(lc->ev_join, lc->side), "join");
+    ZNCC_TRY(run_rows(lc, io, n, kModeHPair, dt, s2, K, inv_sr255, K_ZNCC_HPAIR, "ZNCC + horizontal DT pair"));
+    ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_join, 0), "join of the weights stream");
     for (int pair = 2; pair <= npairs; ++pair) {    // pair 1 is the cost kernel's
         LinePass lp[kMaxBatch];
         for (int i = 0; i < n; ++i) {
@@ -781,7 +784,7 @@ zncc_status zncc_cost_volume(zncc_ctx* c, const uint8_t* left, const uint8_t* ri
     if (!cost) return fail(c, ZNCC_EINVAL, "cost pointer is NULL");
     if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
     PairIO io{c, left, right, pitch, nullptr, cost, c->D};
-    return run_rows(c, &io, 1, kModeRaw, dtype, 0.0f, K_ZNCC_RAW, "ZNCC cost");
+    return run_rows(c, &io, 1, kModeRaw, dtype, 0.0f, 0.0f, 0.0f, K_ZNCC_RAW, "ZNCC cost");
 }
 
 zncc_status dt_aggregate(zncc_ctx* c, const uint8_t* guide, int pitch, void* cost, zncc_dtype dtype,

@@ -111,6 +111,15 @@ __device__ __forceinline__ void lds4(const __half* p, float (&o)[4]) {
     o[0] = half_lo(t.x); o[1] = half_hi(t.x); o[2] = half_lo(t.y); o[3] = half_hi(t.y);
 }
 
+// ---- programmatic dependent launch -------------------------------------------------------
+// A kernel launched with programmatic stream serialization may start while the kernel before
+// it on the stream is finishing; griddep_wait() returns once that kernel has completed and its
+// memory is visible, so every kernel calls it before touching global memory. A kernel calls
+// griddep_launch_dependents() when its remaining work no longer needs the whole device, so
+// that the next kernel's launch overlaps its tail. Both are no-ops without the attribute.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 // ---- thread-block clusters: a DT line split across the CTAs of a cluster ---------------
 // The CTA's rank in its cluster (0 for a launch without clusters).
 __device__ __forceinline__ int cluster_rank() {

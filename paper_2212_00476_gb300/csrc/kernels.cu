@@ -7,6 +7,26 @@
 
 namespace zncc {
 
+void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, dim3 grid, dim3 block, size_t smem,
+                   cudaStream_t st, int cluster) {
+    cfg = cudaLaunchConfig_t{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.numAttrs = 1;
+    if (cluster > 1) {
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = cluster;
+        attr[1].val.clusterDim.y = 1;
+        attr[1].val.clusterDim.z = 1;
+        cfg.numAttrs = 2;
+    }
+    cfg.attrs = attr;
+}
+
 // ---------------------------------------------------------------------------------------
 // Window statistics (Sec. IV-B-1, Eq. (sum1), Method 1 made separable): block per row y;
 // column sums of the 2r+1 clamped rows for every column the row's windows touch, then the
@@ -67,6 +87,7 @@ cudaError_t launch_window_stats(const uint8_t* img, int pitch, int W, int H, int
 // coefH is [H][W]; coefV is [W][H] (a column is contiguous). One thread per position; the
 // 16 positions of a chunk are 16 consecutive lanes, whose products are shuffle scans.
 __global__ void k_dt_coef(const __grid_constant__ CoefBatch b) {
+    griddep_wait();
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int pi = 0;
     while (pi + 1 < b.npairs && gid >= b.p[pi + 1].thread0) ++pi;
@@ -112,8 +133,10 @@ long long dt_coef_threads(int W, int H) {
 
 cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st) {
     const long long blocks = (b.total_threads + 255) / 256;
-    k_dt_coef<<<(unsigned)blocks, 256, 0, st>>>(b);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    launch_config(cfg, attr, dim3((unsigned)blocks), dim3(256), 0, st, 1);
+    return cudaLaunchKernelEx(&cfg, k_dt_coef, b);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -146,6 +169,7 @@ size_t line_stage_bytes(int dtype, const LineArgs& a) {
 template <typename T, int MODE, bool SINGLE, bool CLUSTER>
 __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineBatch b) {
     extern __shared__ float4 smem4[];
+    griddep_wait();
     auto P = [&](int pi) -> const LineArgs& { return b.p[SINGLE ? 0 : pi]; };
     const int lane = threadIdx.x & 31;
     // A line spans the cs CTAs of a cluster (consecutive blocks), CTA `rank` holding chunks
@@ -273,6 +297,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
         const LineArgs& a = P(pi);
         const int line = line_of(o);
         const bool line_ok = active && line < a.nlines;
+        if (o.s + 1 == s1) griddep_launch_dependents();             // this block's last step
 
         if (pi != cur_pi || o.g != cur_g) {     // stage the coefficients and multipliers of the group
             __syncthreads();
@@ -420,28 +445,16 @@ cudaError_t launch_line_batch(const LineBatch& b, int threads, size_t smem, int 
     void (*fn)(LineBatch) = line_pair_fn(mode, dtype, b.npairs == 1, cs > 1);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (cs <= 1) {
-        fn<<<dim3(b.grid), threads, smem, st>>>(b);
-        return cudaGetLastError();
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(b.grid);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    launch_config(cfg, attr, dim3(b.grid), dim3(threads), smem, st, cs);
     return cudaLaunchKernelEx(&cfg, fn, b);
 }
 
 // ---------------------------------------------------------------------------------------
 // End of the fused WTA: key -> disparity, key -> 0 (ready for the next run).
 __global__ void k_wta_finish(const __grid_constant__ WtaFinishBatch b) {
+    griddep_wait();
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int pi = 0;
     while (pi + 1 < b.npairs && gid >= b.p[pi + 1].thread0) ++pi;
@@ -455,8 +468,10 @@ __global__ void k_wta_finish(const __grid_constant__ WtaFinishBatch b) {
 
 cudaError_t launch_wta_finish(const WtaFinishBatch& b, cudaStream_t st) {
     const long long blocks = (b.total_threads + 255) / 256;
-    k_wta_finish<<<(unsigned)blocks, 256, 0, st>>>(b);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    launch_config(cfg, attr, dim3((unsigned)blocks), dim3(256), 0, st, 1);
+    return cudaLaunchKernelEx(&cfg, k_wta_finish, b);
 }
 
 // ---------------------------------------------------------------------------------------

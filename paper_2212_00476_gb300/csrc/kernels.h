@@ -30,7 +30,7 @@ struct RowArgs {
     long long dstride;        // entries per pixel in the output
     int d_out0;               // disparity stored at entry 0 of a pixel
     int vec;                  // 16-byte (float) / 8-byte (half) accesses allowed
-    const float4* coef;       // [H][W] horizontal DT coefficients (HPair)
+    float K, inv_sr255;       // DT weights (HPair): exp(-1/sigma_s), 1/(255 sigma_r); guide = left
     float s2;                 // (1 - K)^2
     WtaOut wta;               // (Wta)
     int minb2;                // use the two-blocks-per-SM variant where the block allows
@@ -81,6 +81,12 @@ struct LineBatch {
     long long stage_bytes;    // staging region (the largest pair's), before the other arrays
     LineArgs p[kMaxBatch];
 };
+
+// Launch configuration with programmatic stream serialization (the kernel may start while
+// the previous kernel on the stream finishes; it waits for it in griddep_wait) and, for
+// cluster > 1, thread-block clusters of that many CTAs along x. attr must hold 2 entries.
+void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, dim3 grid, dim3 block, size_t smem,
+                   cudaStream_t st, int cluster);
 
 size_t zncc_row_smem_bytes(int R, int mode, const RowArgs& a, int nthreads);
 size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a);

@@ -81,8 +81,28 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
         else RP[p4(ix, pRP)] = pk;
     }
     if constexpr (MODE == kModeHPair) {
-        for (int t = tid; t < span; t += blockDim.x)
-            co[cpos(t)] = t < W ? __ldg(a.coef + (size_t)y * W + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        // the row's DT coefficients (w, chunk prefix product, next w, chunk suffix product),
+        // computed here from the guide (the left image) as k_dt_coef computes them: 16
+        // consecutive lanes hold one chunk (span and the block are whole warps)
+        const uint8_t* g = a.left + (size_t)y * a.pitch;
+        auto weight = [&](int q) -> float {      // the step q-1 -> q
+            return (q >= 1 && q < W) ? a.K * expf(-fabsf((float)(g[q] - g[q - 1])) * a.inv_sr255) : 0.0f;
+        };
+        for (int t = tid; t < span; t += blockDim.x) {
+            const int i = t & (kL - 1);
+            const float w = weight(t);
+            float wn = __shfl_down_sync(kFull, w, 1, kL);
+            if (i == kL - 1) wn = weight(t + 1);
+            float A = w, B = wn;
+#pragma unroll
+            for (int off = 1; off < kL; off <<= 1) {
+                const float a2 = __shfl_up_sync(kFull, A, off, kL);
+                const float b2 = __shfl_down_sync(kFull, B, off, kL);
+                if (i >= off) A *= a2;
+                if (i + off < kL) B *= b2;
+            }
+            co[cpos(t)] = t < W ? make_float4(w, A, wn, B) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
     __syncthreads();
 
@@ -239,6 +259,7 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
 template <int R, typename T, int MODE, int MINB, bool SINGLE>
 __global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(const __grid_constant__ RowBatch b) {
     extern __shared__ uint4 smem_u4[];
+    griddep_wait();
     const int i0 = (int)((long long)blockIdx.x * b.total_items / b.grid);
     const int i1 = (int)((long long)(blockIdx.x + 1) * b.total_items / b.grid);
     int pi = 0;
@@ -262,6 +283,7 @@ __global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(const 
             s_end = min(s_begin + a.spb, s_begin + (last - u));
             u += s_end - s_begin;
         }
+        if (u >= i1) griddep_launch_dependents();       // this block's last visit
         zncc_row_item<R, T, MODE>(a, y, s_begin, s_end, smem_u4);
         __syncthreads();                                 // the next visit restages shared memory
     }
@@ -318,8 +340,10 @@ cudaError_t launch_zncc_row_impl(const RowBatch& b, int threads, size_t smem, in
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<b.grid, threads, smem, st>>>(b);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    launch_config(cfg, attr, dim3(b.grid), dim3(threads), smem, st, 1);
+    return cudaLaunchKernelEx(&cfg, fn, b);
 }
 
 }  // namespace zncc
