@@ -375,7 +375,7 @@ cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePa
         for (int async = a.vec ? 1 : 0; async >= 0; --async) {
             for (int lpc = cs > 1 ? 1 : std::max(1, std::min(8, 256 / per_line)); lpc >= 1; --lpc) {
                 a.tq = tq; a.nch = nch; a.lpc = lpc; a.async = async; a.cs = cs;
-                const size_t smem = line_pair_smem_bytes(p.mode, p.dtype, a);
+                const size_t smem = line_pair_smem_bytes(p.mode, p.dtype, a, line_coef_async(a));
                 if (smem > (size_t)smem_max) continue;
                 int bps = 0;
                 cudaError_t e = line_pair_occupancy(p.mode, p.dtype, lpc * per_line, smem, true, cs > 1, &bps);
@@ -470,6 +470,7 @@ void fill_line_args(LineArgs& a, const LinePass& p, int W, int H, const float4* 
 // thread count and shared memory (staging region and the rest) grown to cover it.
 void add_line_pair(LineBatch& b, const LineArgs& ai, int mode, int dtype, int& threads, size_t& stage,
                    size_t& rest) {
+    b.co_async = (b.npairs == 0 || b.co_async) && line_coef_async(ai);
     LineArgs& a = b.p[b.npairs++];
     a = ai;
     const int nslices = (a.dcount + kG * a.tq - 1) / (kG * a.tq);
@@ -484,7 +485,7 @@ void add_line_pair(LineBatch& b, const LineArgs& ai, int mode, int dtype, int& t
     threads = std::max(threads, a.lpc * a.nch * a.tq);
     const size_t st = line_stage_bytes(dtype, a);
     stage = std::max(stage, st);
-    rest = std::max(rest, line_pair_smem_bytes(mode, dtype, a) - st);
+    rest = std::max(rest, line_pair_smem_bytes(mode, dtype, a, line_coef_async(a)) - st);
 }
 
 // Line-pair launches over the passes of several pairs (the same mode and storage): pairs

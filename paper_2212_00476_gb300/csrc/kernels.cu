@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     // step at a time.
     struct Cursor {
         int s, pi, g, sl, nslices, ngroups;
+        int gseq;                                   // line groups entered since the block's first step
     };
     auto set_pair = [&](Cursor& c) {
         const LineArgs& a = P(c.pi);
@@ -223,12 +224,14 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
         const int ls = s - P(c.pi).step0;
         c.g = ls / c.nslices;
         c.sl = ls - c.g * c.nslices;
+        c.gseq = 0;
         return c;
     };
     auto advance = [&](Cursor& c) {
         ++c.s;
         if (++c.sl == c.nslices) {
             c.sl = 0;
+            ++c.gseq;
             if (++c.g == c.ngroups && !SINGLE && c.pi + 1 < b.npairs) {
                 c.g = 0;
                 ++c.pi;
@@ -246,10 +249,42 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     const int sstride = nthr * 4;
     T* const stage0 = reinterpret_cast<T*>(smem4) + (size_t)threadIdx.x * 4;
     auto stage_at = [&](int buf) -> T* { return stage0 + (size_t)buf * kL * sstride; };
+    // shared memory: [stage][coefficients: 1 or 2 buffers][multipliers][scan buffers], the
+    // per-position arrays [lpc][nch][kCS], chunk-major. Without A_hat scaling (has_mul false)
+    // there are no multipliers; with co_async the coefficients of a line group are streamed
+    // into the second buffer by cp.async along with the volume of the group's first step.
+    const bool has_mul = b.p[0].ahat_in != nullptr || b.p[0].ahat_out != nullptr;
+    const bool co_async = b.co_async != 0;
+    const int arr = lpc * nch * kCS;
+    float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + b.stage_bytes);
+    float2* mul_all = reinterpret_cast<float2*>(co_all + (co_async ? 2 : 1) * arr);
+    float4* sb_all = reinterpret_cast<float4*>(mul_all + (has_mul ? arr : 0));
+    float* sa_all = reinterpret_cast<float*>(sb_all + lpc * 2 * nwl_all * tq);
+    const int cthr = (li * nch + k) * kCS;                         // this thread's chunk
+    const float2* mul = has_mul ? mul_all + cthr : nullptr;
+    float4* sb = sb_all + li * 2 * nwl_all * tq;
+    float* sa = sa_all + li * 2 * nwl_all * tq;
+
+    // the coefficients of the line group at cursor pc into coefficient buffer cbuf (the block's)
+    auto prefetch_coef = [&](const Cursor& pc, int cbuf) {
+        const LineArgs& a = P(pc.pi);
+        float4* dst = co_all + cbuf * arr;
+        for (int l2 = 0; l2 < lpc; ++l2) {
+            const int ln = pc.g * lpc + l2;
+            for (int t = threadIdx.x; t < nch * kL; t += blockDim.x) {
+                const int gp = pos0 + t;
+                const bool in = ln < a.nlines && gp < a.n;
+                cp_async<16>(dst + l2 * nch * kCS + cpos(t),
+                             in ? a.coef + (size_t)ln * a.coef_line_stride + gp : a.coef, in);
+            }
+        }
+    };
     // prefetch of the step at cursor pc into stage buffer buf. With vec the entries per pixel
     // are a multiple of 4, so a group with any valid disparity lies whole inside the volume;
-    // its entries past dcount are never stored or compared.
+    // its entries past dcount are never stored or compared. The first step of a line group
+    // also brings the group's coefficients (co_async).
     auto prefetch = [&](const Cursor& pc, int buf) {
+        if (co_async && pc.s < s1 && (pc.sl == 0 || pc.s == s0)) prefetch_coef(pc, pc.gseq & 1);
         if (async && pc.s < s1 && active) {
             const LineArgs& a = P(pc.pi);
             const T* src = a.src ? reinterpret_cast<const T*>(a.src) : reinterpret_cast<const T*>(a.vol);
@@ -278,16 +313,6 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     prefetch(pf, 1);
     advance(pf);
 
-    // shared memory: [stage][coefficients][multipliers][scan buffers]
-    // coefficients and multipliers: [lpc][nch][kCS], chunk-major
-    float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + b.stage_bytes);
-    float2* mul_all = reinterpret_cast<float2*>(co_all + lpc * nch * kCS);
-    float4* sb_all = reinterpret_cast<float4*>(mul_all + lpc * nch * kCS);
-    float* sa_all = reinterpret_cast<float*>(sb_all + lpc * 2 * nwl_all * tq);
-    const float4* co = co_all + (li * nch + k) * kCS;            // this thread's chunk
-    const float2* mul = mul_all + (li * nch + k) * kCS;
-    float4* sb = sb_all + li * 2 * nwl_all * tq;
-    float* sa = sa_all + li * 2 * nwl_all * tq;
     if (cs > 1) cluster_sync_all();                 // every CTA of the cluster has started
 
     WtaRegs wr;
@@ -299,20 +324,33 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
         const bool line_ok = active && line < a.nlines;
         if (o.s + 1 == s1) griddep_launch_dependents();             // this block's last step
 
-        if (pi != cur_pi || o.g != cur_g) {     // stage the coefficients and multipliers of the group
+        cp_async_wait<1>();                                            // this step's copies landed
+        if (pi != cur_pi || o.g != cur_g) {     // a new line group: its coefficients (and multipliers)
             __syncthreads();
-            for (int l2 = 0; l2 < lpc; ++l2) {
-                const int ln = o.g * lpc + l2;
-                const bool ok = ln < a.nlines;
-                for (int t = threadIdx.x; t < nch * kL; t += blockDim.x) {
-                    const int gp = pos0 + t;
-                    const bool in = ok && gp < a.n;
-                    co_all[l2 * nch * kCS + cpos(t)] =
-                        in ? __ldg(a.coef + (size_t)ln * a.coef_line_stride + gp) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const size_t pix = (size_t)ln * a.pix_line + (size_t)gp * a.pix_pos;
-                    const float mi = in && a.ahat_in ? __ldg(a.ahat_in + pix) : 1.0f;
-                    const float mo = in && a.ahat_out ? a.s2 / __ldg(a.ahat_out + pix) : a.s2;
-                    mul_all[l2 * nch * kCS + cpos(t)] = make_float2(mi, mo);
+            if (!co_async) {
+                for (int l2 = 0; l2 < lpc; ++l2) {
+                    const int ln = o.g * lpc + l2;
+                    const bool ok = ln < a.nlines;
+                    for (int t = threadIdx.x; t < nch * kL; t += blockDim.x) {
+                        const int gp = pos0 + t;
+                        const bool in = ok && gp < a.n;
+                        co_all[l2 * nch * kCS + cpos(t)] =
+                            in ? __ldg(a.coef + (size_t)ln * a.coef_line_stride + gp) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+            if (has_mul) {
+                for (int l2 = 0; l2 < lpc; ++l2) {
+                    const int ln = o.g * lpc + l2;
+                    const bool ok = ln < a.nlines;
+                    for (int t = threadIdx.x; t < nch * kL; t += blockDim.x) {
+                        const int gp = pos0 + t;
+                        const bool in = ok && gp < a.n;
+                        const size_t pix = (size_t)ln * a.pix_line + (size_t)gp * a.pix_pos;
+                        const float mi = in && a.ahat_in ? __ldg(a.ahat_in + pix) : 1.0f;
+                        const float mo = in && a.ahat_out ? a.s2 / __ldg(a.ahat_out + pix) : a.s2;
+                        mul_all[l2 * nch * kCS + cpos(t)] = make_float2(mi, mo);
+                    }
                 }
             }
             if constexpr (MODE == kLineWta) wr.reset();
@@ -320,13 +358,13 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
             cur_pi = pi;
             cur_g = o.g;
         }
+        const float4* co = co_all + (co_async ? (o.gseq & 1) * arr : 0) + cthr;   // this thread's chunk
         const int dl = o.sl * ds + dq * kG;                        // entry of d_first
         const int nvalid = max(0, min(4, a.dcount - dl));
         const bool any = line_ok && nvalid > 0;
         const int npos = a.n - kg * kL;
         T* vol = reinterpret_cast<T*>(a.vol);
         float v[kL][4];
-        cp_async_wait<1>();                                            // this step's copies landed
         if (a.src_ones) {
 #pragma unroll
             for (int i = 0; i < kL; ++i)
@@ -346,7 +384,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                 q += a.elem_stride;
             }
         }
-        if (a.ahat_in && active) {
+        if (has_mul && a.ahat_in && active) {
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 const float m = mul[i].x;
@@ -393,10 +431,18 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     if (cs > 1) cluster_sync_all();                 // no CTA leaves while others may store to it
 }
 
-size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a) {
+bool line_coef_async(const LineArgs& a) {
+    const int nslices = (a.dcount + kG * a.tq - 1) / (kG * a.tq);
+    return !a.ahat_in && !a.ahat_out && nslices >= 2;
+}
+
+size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a, bool co_async) {
     const int nwl_all = a.cs * a.nch * a.tq / 32;
+    const bool has_mul = a.ahat_in || a.ahat_out;
     (void)mode;
-    return line_stage_bytes(dtype, a) + (size_t)a.lpc * ((16ull + 8ull) * a.nch * kCS + dt_scan_bytes(nwl_all, a.tq));
+    return line_stage_bytes(dtype, a) +
+           (size_t)a.lpc * ((16ull * (co_async ? 2 : 1) + (has_mul ? 8ull : 0ull)) * a.nch * kCS +
+                            dt_scan_bytes(nwl_all, a.tq));
 }
 
 template <bool SINGLE, bool CLUSTER>

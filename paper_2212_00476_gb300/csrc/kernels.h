@@ -78,6 +78,7 @@ struct LineArgs {
 // one step (line group, disparity slice) in both modes.
 struct LineBatch {
     int npairs, total_items, total_steps, grid;
+    int co_async;             // coefficients streamed by cp.async (two buffers; line_coef_async)
     long long stage_bytes;    // staging region (the largest pair's), before the other arrays
     LineArgs p[kMaxBatch];
 };
@@ -89,7 +90,10 @@ void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, dim3 grid
                    cudaStream_t st, int cluster);
 
 size_t zncc_row_smem_bytes(int R, int mode, const RowArgs& a, int nthreads);
-size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a);
+// A pass whose coefficients can be streamed (no A_hat multipliers, at least two slices per
+// line group); the shared memory of a block with one or two coefficient buffers.
+bool line_coef_async(const LineArgs& a);
+size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a, bool co_async);
 cudaError_t launch_line_batch(const LineBatch& b, int threads, size_t smem, int mode, int dtype,
                               cudaStream_t st);
 
