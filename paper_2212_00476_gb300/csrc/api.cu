@@ -85,6 +85,7 @@ struct zncc_ctx {
     void* vol = nullptr;          // the fused path's intermediate volume (on first use)
     size_t vol_bytes = 0;
     float* ahat = nullptr;        // [nahat][H][W] DT responses of an all-ones plane (F16 storage)
+    float2* mulmap = nullptr;     // [nahat] maps of pairs 2.. : (A_hat_{p-1}, s2 / A_hat_p), line-major
     int nahat = 0;
     int smem_max = 0;             // opt-in shared memory per block of the device
     int row_minb2 = 1;            // cost kernel: two-blocks-per-SM variant where it applies
@@ -171,6 +172,7 @@ void release(zncc_ctx* c) {
     free_dev(c->vol);
     c->vol_bytes = 0;
     free_dev(c->ahat);
+    free_dev(c->mulmap);
     c->nahat = 0;
     free_dev(c->img);
     free_dev(c->disp);
@@ -341,8 +343,7 @@ struct LinePass {
     int dtype = 0;
     bool horiz = true;
     int mode = kLineStore;
-    const float* ahat_in = nullptr;
-    const float* ahat_out = nullptr;
+    const float2* mulmap = nullptr;   // per-position (input multiplier, output scale), line-major
     unsigned long long* keys = nullptr;   // (Wta)
     float s2 = 1.0f;
     int force_tq = 0;
@@ -426,7 +427,7 @@ cudaError_t size_line_grid(LineBatch& b, int threads, size_t smem, int mode, int
 zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
     const int forced = p.force_tq ? p.force_tq : (p.horiz ? c->h_tq : c->v_tq);
     const long long key = ((((long long)p.horiz * 2 + p.mode) * 2 + p.dtype) * 2 + (a.vec ? 1 : 0)) * 16 +
-                          forced + ((long long)p.dcount << 20);
+                          forced + ((long long)p.dcount << 20) + ((long long)(p.mulmap ? 1 : 0) << 40);
     for (const LinePlan& pl : c->plans)
         if (pl.key == key) {
             a.tq = pl.tq; a.lpc = pl.lpc; a.nch = pl.nch; a.async = pl.async; a.cs = pl.cs;
@@ -452,8 +453,7 @@ void fill_line_args(LineArgs& a, const LinePass& p, int W, int H, const float4* 
     a.nlines = p.horiz ? H : W;
     a.dcount = p.dcount;
     a.d_base = 0;
-    a.ahat_in = p.ahat_in;
-    a.ahat_out = p.ahat_out;
+    a.mulmap = p.mulmap;
     a.coef = p.horiz ? coefH : coefV;
     a.coef_line_stride = p.horiz ? W : H;
     a.s2 = p.s2;
@@ -539,7 +539,9 @@ zncc_status ensure_ahat(zncc_ctx* c, int n) {
     if (c->nahat >= n) return ZNCC_OK;
     free_dev_f(c->ahat);
     c->nahat = 0;
+    free_dev(c->mulmap);
     ZNCC_TRY(alloc_dev(c, (void**)&c->ahat, (size_t)c->W * c->H * n * sizeof(float), "A_hat maps"));
+    ZNCC_TRY(alloc_dev(c, (void**)&c->mulmap, (size_t)c->W * c->H * n * sizeof(float2), "A_hat multipliers"));
     c->nahat = n;
     return ZNCC_OK;
 }
@@ -598,6 +600,16 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
         }
         st = run_lines(lc, ctxs, lp, n, K_AHAT);
     }
+    for (int i = 0; norm && i < n && st == ZNCC_OK; ++i)     // multipliers of the stored pairs
+        for (int pair = 2; pair <= npairs && st == ZNCC_OK; ++pair) {
+            const int W = io[i].c->W, H = io[i].c->H;
+            const size_t npix = (size_t)W * H;
+            const float* ain = pair - 1 >= 2 ? io[i].c->ahat + (size_t)(pair - 2) * npix : nullptr;
+            const float* aout = pair < npairs ? io[i].c->ahat + (size_t)(pair - 1) * npix : nullptr;
+            cudaError_t e = launch_mulmap(ain, aout, s2, W, H, (pair % 2) == 1,
+                                          io[i].c->mulmap + (size_t)(pair - 2) * npix, lc->cur);
+            if (e != cudaSuccess) st = cuda_fail(lc, e, "A_hat multipliers");
+        }
     lc->cur = lc->stream;
     ZNCC_TRY(st);
     ZNCC_CUDA(lc, cudaEventRecord(lc->ev_join, lc->side), "join");
@@ -615,8 +627,7 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
             lp[i].horiz = (pair % 2) == 1;
             lp[i].mode = pair == npairs ? kLineWta : kLineStore;
             lp[i].keys = pair == npairs ? io[i].c->keys : nullptr;
-            lp[i].ahat_in = norm && pair - 1 >= 2 ? io[i].c->ahat + (size_t)(pair - 2) * npix : nullptr;
-            lp[i].ahat_out = norm && pair < npairs ? io[i].c->ahat + (size_t)(pair - 1) * npix : nullptr;
+            lp[i].mulmap = norm ? io[i].c->mulmap + (size_t)(pair - 2) * npix : nullptr;
         }
         const int kind = pair % 2 ? K_DT_HPAIR : (pair == npairs ? K_DT_VPAIR_WTA : K_DT_VPAIR);
         ZNCC_TRY(run_lines(lc, ctxs, lp, n, kind));

@@ -249,26 +249,27 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     const int sstride = nthr * 4;
     T* const stage0 = reinterpret_cast<T*>(smem4) + (size_t)threadIdx.x * 4;
     auto stage_at = [&](int buf) -> T* { return stage0 + (size_t)buf * kL * sstride; };
-    // shared memory: [stage][coefficients: 1 or 2 buffers][multipliers][scan buffers], the
-    // per-position arrays [lpc][nch][kCS], chunk-major. Without A_hat scaling (has_mul false)
-    // there are no multipliers; with co_async the coefficients of a line group are streamed
-    // into the second buffer by cp.async along with the volume of the group's first step.
-    const bool has_mul = b.p[0].ahat_in != nullptr || b.p[0].ahat_out != nullptr;
+    // shared memory: [stage][coefficients: 1 or 2 buffers][multipliers: as many][scan
+    // buffers], the per-position arrays [lpc][nch][kCS], chunk-major. Without A_hat scaling
+    // (has_mul false) there are no multipliers; with co_async the arrays of a line group are
+    // streamed into the other buffer by cp.async along with the volume of its first step.
+    const bool has_mul = b.p[0].mulmap != nullptr;
     const bool co_async = b.co_async != 0;
     const int arr = lpc * nch * kCS;
+    const int nbuf = co_async ? 2 : 1;
     float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + b.stage_bytes);
-    float2* mul_all = reinterpret_cast<float2*>(co_all + (co_async ? 2 : 1) * arr);
-    float4* sb_all = reinterpret_cast<float4*>(mul_all + (has_mul ? arr : 0));
+    float2* mul_all = reinterpret_cast<float2*>(co_all + nbuf * arr);
+    float4* sb_all = reinterpret_cast<float4*>(mul_all + (has_mul ? nbuf * arr : 0));
     float* sa_all = reinterpret_cast<float*>(sb_all + lpc * 2 * nwl_all * tq);
     const int cthr = (li * nch + k) * kCS;                         // this thread's chunk
-    const float2* mul = has_mul ? mul_all + cthr : nullptr;
     float4* sb = sb_all + li * 2 * nwl_all * tq;
     float* sa = sa_all + li * 2 * nwl_all * tq;
 
-    // the coefficients of the line group at cursor pc into coefficient buffer cbuf (the block's)
+    // the coefficients (and multipliers) of the line group at cursor pc into buffer cbuf
     auto prefetch_coef = [&](const Cursor& pc, int cbuf) {
         const LineArgs& a = P(pc.pi);
         float4* dst = co_all + cbuf * arr;
+        float2* mdst = mul_all + cbuf * arr;
         for (int l2 = 0; l2 < lpc; ++l2) {
             const int ln = pc.g * lpc + l2;
             for (int t = threadIdx.x; t < nch * kL; t += blockDim.x) {
@@ -276,6 +277,9 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                 const bool in = ln < a.nlines && gp < a.n;
                 cp_async<16>(dst + l2 * nch * kCS + cpos(t),
                              in ? a.coef + (size_t)ln * a.coef_line_stride + gp : a.coef, in);
+                if (has_mul)
+                    cp_async<8>(mdst + l2 * nch * kCS + cpos(t),
+                                in ? a.mulmap + (size_t)ln * a.n + gp : a.mulmap, in);
             }
         }
     };
@@ -339,17 +343,14 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                     }
                 }
             }
-            if (has_mul) {
+            if (has_mul && !co_async) {
                 for (int l2 = 0; l2 < lpc; ++l2) {
                     const int ln = o.g * lpc + l2;
                     const bool ok = ln < a.nlines;
                     for (int t = threadIdx.x; t < nch * kL; t += blockDim.x) {
                         const int gp = pos0 + t;
-                        const bool in = ok && gp < a.n;
-                        const size_t pix = (size_t)ln * a.pix_line + (size_t)gp * a.pix_pos;
-                        const float mi = in && a.ahat_in ? __ldg(a.ahat_in + pix) : 1.0f;
-                        const float mo = in && a.ahat_out ? a.s2 / __ldg(a.ahat_out + pix) : a.s2;
-                        mul_all[l2 * nch * kCS + cpos(t)] = make_float2(mi, mo);
+                        mul_all[l2 * nch * kCS + cpos(t)] =
+                            ok && gp < a.n ? __ldg(a.mulmap + (size_t)ln * a.n + gp) : make_float2(0.f, 0.f);
                     }
                 }
             }
@@ -358,7 +359,9 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
             cur_pi = pi;
             cur_g = o.g;
         }
-        const float4* co = co_all + (co_async ? (o.gseq & 1) * arr : 0) + cthr;   // this thread's chunk
+        const int cb = co_async ? (o.gseq & 1) * arr : 0;
+        const float4* co = co_all + cb + cthr;                       // this thread's chunk
+        const float2* mul = has_mul ? mul_all + cb + cthr : nullptr;
         const int dl = o.sl * ds + dq * kG;                        // entry of d_first
         const int nvalid = max(0, min(4, a.dcount - dl));
         const bool any = line_ok && nvalid > 0;
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                 q += a.elem_stride;
             }
         }
-        if (has_mul && a.ahat_in && active) {
+        if (has_mul && active) {
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 const float m = mul[i].x;
@@ -433,16 +436,31 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
 
 bool line_coef_async(const LineArgs& a) {
     const int nslices = (a.dcount + kG * a.tq - 1) / (kG * a.tq);
-    return !a.ahat_in && !a.ahat_out && nslices >= 2;
+    return nslices >= 2;
 }
 
 size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a, bool co_async) {
     const int nwl_all = a.cs * a.nch * a.tq / 32;
-    const bool has_mul = a.ahat_in || a.ahat_out;
+    const size_t per_pos = (16ull + (a.mulmap ? 8ull : 0ull)) * (co_async ? 2 : 1);
     (void)mode;
-    return line_stage_bytes(dtype, a) +
-           (size_t)a.lpc * ((16ull * (co_async ? 2 : 1) + (has_mul ? 8ull : 0ull)) * a.nch * kCS +
-                            dt_scan_bytes(nwl_all, a.tq));
+    return line_stage_bytes(dtype, a) + (size_t)a.lpc * (per_pos * a.nch * kCS + dt_scan_bytes(nwl_all, a.tq));
+}
+
+__global__ void k_mulmap(const float* __restrict__ ain, const float* __restrict__ aout, float s2, int W, int H,
+                         int horiz, float2* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)W * H) return;
+    const int n = horiz ? W : H;
+    const int line = (int)(i / n), pos = (int)(i - (long long)line * n);
+    const size_t pix = horiz ? (size_t)line * W + pos : (size_t)pos * W + line;
+    out[i] = make_float2(ain ? ain[pix] : 1.0f, aout ? s2 / aout[pix] : s2);
+}
+
+cudaError_t launch_mulmap(const float* ain, const float* aout, float s2, int W, int H, bool horiz, float2* out,
+                          cudaStream_t st) {
+    const long long n = (long long)W * H;
+    k_mulmap<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ain, aout, s2, W, H, horiz ? 1 : 0, out);
+    return cudaGetLastError();
 }
 
 template <bool SINGLE, bool CLUSTER>

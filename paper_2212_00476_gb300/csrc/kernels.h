@@ -56,8 +56,9 @@ struct LineArgs {
     int tq, lpc, nch;         // lanes per chunk, lines per block, chunks per line and CTA
     int cs;                   // CTAs per line (a thread-block cluster; 1 = none, then lpc >= 1)
     int per_block;            // work items (line group, disparity slice) per block
-    const float* ahat_in;     // per-pixel multiplier of the input (NULL: 1)
-    const float* ahat_out;    // per-pixel divisor of the output (NULL: 1)
+    // per position of each line ([nlines][n], the pass's own line-major order): the multiplier
+    // of the input and the scale of the output (NULL: 1 and s2)
+    const float2* mulmap;
     const float4* coef;       // coefficients: coef[line * coef_line_stride + pos]
     long long coef_line_stride;
     float s2;
@@ -90,8 +91,8 @@ void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, dim3 grid
                    cudaStream_t st, int cluster);
 
 size_t zncc_row_smem_bytes(int R, int mode, const RowArgs& a, int nthreads);
-// A pass whose coefficients can be streamed (no A_hat multipliers, at least two slices per
-// line group); the shared memory of a block with one or two coefficient buffers.
+// A pass whose coefficients (and multipliers) can be streamed (at least two slices per line
+// group); the shared memory of a block with one or two buffers of them.
 bool line_coef_async(const LineArgs& a);
 size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a, bool co_async);
 cudaError_t launch_line_batch(const LineBatch& b, int threads, size_t smem, int mode, int dtype,
@@ -141,6 +142,10 @@ struct WtaFinishBatch {
     WtaFinishArgs p[kMaxBatch];
 };
 cudaError_t launch_wta_finish(const WtaFinishBatch& b, cudaStream_t st);
+// The multiplier map of a pass along rows (horiz) or columns of a W x H image: for each
+// (line, position), (ain ? ain[pix] : 1, aout ? s2 / aout[pix] : s2), ain/aout [H][W].
+cudaError_t launch_mulmap(const float* ain, const float* aout, float s2, int W, int H, bool horiz, float2* out,
+                          cudaStream_t st);
 
 // Device allocation of the library (cudaMalloc, or an injected out-of-memory failure when the
 // environment variable ZNCC_FAIL_DEVICE_ALLOC is 1).

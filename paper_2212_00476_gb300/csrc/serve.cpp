@@ -47,14 +47,14 @@ struct ShapeKey {
 };
 
 // Device bytes a context of this shape holds: DT coefficients (two float4 per pixel), the
-// fused WTA's keys, the volume (pixel stride padded to 4 entries), the F16 path's A_hat maps,
-// the images and map.
+// fused WTA's keys, the volume (pixel stride padded to 4 entries), the F16 path's A_hat maps
+// and multipliers, the images and map.
 size_t shape_charge(const ShapeKey& k) {
     const size_t npix = (size_t)k.W * k.H;
     size_t b = 32 * npix + 8 * npix + 4 * npix;
     if (k.iters > 0) {
         b += npix * (size_t)((k.D + 3) / 4 * 4) * (k.storage == ZNCC_F32 ? 4 : 2);
-        if (k.storage == ZNCC_F16 && k.iters > 1) b += npix * 4 * (size_t)(2 * k.iters - 1);
+        if (k.storage == ZNCC_F16 && k.iters > 1) b += npix * 12 * (size_t)(2 * k.iters - 1);
     }
     return b;
 }
