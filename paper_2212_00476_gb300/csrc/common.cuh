@@ -178,9 +178,11 @@ __device__ __forceinline__ void st_rank(float4* p, int rank, float4 v) {
 // co: the kL coefficients of this thread's chunk in shared memory (co[i] for position i of
 // the chunk); sa/sb: the line's scan buffers, 2 * nwl * tq entries each; wl / nwl: this
 // thread's warp within the line and the warps per line. The result is scaled by s2 =
-// (1-K)^2, or per position by mul[i].y when mul (the chunk's multipliers) is given. after_forward() runs once the forward sweep has consumed the
-// input values (the caller may then overwrite where they came from). Synchronizes the
-// block twice; threads with active == false (whole warps) only take part in the barriers.
+// (1-K)^2, or per position by mul[i].y when mul (the chunk's multipliers) is given; SCALE
+// false leaves it unscaled (a positive factor per pixel, which a WTA that follows ignores).
+// after_forward() runs once the forward sweep has consumed the input values (the caller may
+// then overwrite where they came from). Synchronizes the block twice; threads with active ==
+// false (whole warps) only take part in the barriers.
 // A line may span the cs CTAs of a thread-block cluster: wl / nwl then number the warps of
 // the whole line, each warp's chunk map is stored into the scan buffers of every CTA of the
 // cluster, and the two barriers are the cluster's.
@@ -188,7 +190,7 @@ struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
-template <typename Hook = NoHook>
+template <bool SCALE = true, typename Hook = NoHook>
 __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restrict__ co, int tq, int dq,
                                         int lane, int wl, int nwl, float* sa, float4* sb, float s2,
                                         const float2* __restrict__ mul = nullptr,
@@ -323,9 +325,9 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
 #pragma unroll
         for (int i = 0; i < kL; ++i) {
             const float b = co[i].w;
-            const float m = mul ? mul[i].y : s2;
+            const float m = SCALE ? (mul ? mul[i].y : s2) : 1.0f;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[i][j] = m * fmaf(b, G[j], v[i][j]);
+            for (int j = 0; j < 4; ++j) v[i][j] = SCALE ? m * fmaf(b, G[j], v[i][j]) : fmaf(b, G[j], v[i][j]);
         }
     }
 }

@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
             }
         }
         // the staging buffer is free once the forward sweep has read it: refill it two ahead
-        dt_pair(v, co, tq, dq, lane, rank * nwl + wl, nwl_all, sa, sb, a.s2, mul,
+        dt_pair<MODE != kLineWta>(v, co, tq, dq, lane, rank * nwl + wl, nwl_all, sa, sb, a.s2, mul,
                 [&]() {
                     prefetch(pf, n_s & 1);
                     advance(pf);
