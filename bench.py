@@ -45,6 +45,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over the ranks of the process group (x itself without one): the step time
+    of a replica run is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job disparities per second (Gdisp/s) of `world` replicas that each processed
+    units_per_rank in `seconds` (the max over ranks)."""
+    return world * units_per_rank / seconds / 1e9
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -274,11 +292,7 @@ def run_gb300(args):
     if world > 1:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), dev)
     clocks = clk.summary()
 
     # ---- per-kernel durations: the same steps again, each kernel between CUDA events ----
@@ -318,14 +332,10 @@ def run_gb300(args):
         t0 = time.perf_counter()
         ctx.zncc_run_host(lh, rh, dh, SIG_S, SIG_R, iters, storage)
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_times) / len(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(sum(e2e_times) / len(e2e_times), dev)
 
     units = W * H * D
-    value = world * units / (ms * 1e-3) / 1e9
+    value = replica_throughput(units, world, ms * 1e-3)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gdisp/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -345,7 +355,7 @@ def run_gb300(args):
                      "algorithmic_bytes_per_launch": dom_bytes,
                      "launch_ms": round(dom_ms, 5)},
         "kernels_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in prof.items()},
-        "e2e": {"value": round(world * units / e2e_s / 1e9, 3), "unit": "Gdisp/s",
+        "e2e": {"value": round(replica_throughput(units, world, e2e_s), 3), "unit": "Gdisp/s",
                 "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 2 * W * H,
                 "ms_per_step": round(e2e_s * 1e3, 4)},
         "gpu_launches": int(launches),
