@@ -154,8 +154,9 @@ zncc_status zncc_run(zncc_ctx* ctx, const uint8_t* left, const uint8_t* right, i
 
 /* The fused path over a batch of n <= 32 pairs of uneven sizes (each with its own context,
  * created for its W, H, D and window): every step (the DT coefficients, the cost kernel,
- * each DT pass pair) is one persistent launch over all pairs (the cost kernel: one per
- * distinct window size), so that small pairs share the GPU instead of leaving it idle.
+ * each DT pass pair) is one persistent launch over the pairs that share a block shape (the
+ * cost kernel: a window size), so that small pairs share the GPU instead of leaving it idle;
+ * a pair that fills the GPU by itself (W*H*D >= 2^25) runs its own chain of launches.
  * All launches go to the stream of ctxs[0], on which errors and timings are recorded; the
  * contexts must be distinct and on one device. lefts[i]/rights[i]: device images of pair i
  * (row pitch pitches[i]); disps[i]: its device uint16 disparity map. The DT parameters,

@@ -201,6 +201,10 @@ zncc_status check_dt(zncc_ctx* c, float sigma_s, float sigma_r, int iters) {
     return ZNCC_OK;
 }
 
+// A pair whose volume alone fills the device: batching it with others only costs the batched
+// kernels' per-pair argument indexing, so it gets launches of its own.
+bool fills_device(const zncc_ctx* c) { return (long long)c->W * c->H * c->D >= (1LL << 25); }
+
 float scale_s2(float sigma_s) {
     const double s = 1.0 - exp(-1.0 / (double)sigma_s);
     return (float)(s * s);
@@ -268,13 +272,15 @@ zncc_status run_coef(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, float
 zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype, float s2, float K,
                      float inv_sr255, int kind,
                      const char* what) {
-    // pairs share a launch when they share the window radius and the block shape
+    // pairs share a launch when they share the window radius and the block shape; a pair large
+    // enough to fill the device by itself takes a launch of its own
     auto tq_of = [](int W) { return W <= 1024 ? 8 : (W <= 2048 ? 4 : 2); };
     bool done[kMaxBatch] = {false};
     for (int first = 0; first < n; ++first) {
         if (done[first]) continue;
         const int r = io[first].c->r;
         const int tq0 = tq_of(io[first].c->W), nch0 = padded_chunks(io[first].c->W, tq0);
+        const bool alone = fills_device(io[first].c);
         RowBatch b;
         memset(&b, 0, sizeof(b));
         b.mode = mode;
@@ -282,7 +288,8 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
         size_t smem = 0;
         bool minb2 = true;
         for (int i = first; i < n; ++i) {
-            if (done[i] || io[i].c->r != r || tq_of(io[i].c->W) != tq0 || padded_chunks(io[i].c->W, tq0) != nch0)
+            if (done[i] || io[i].c->r != r || tq_of(io[i].c->W) != tq0 || padded_chunks(io[i].c->W, tq0) != nch0 ||
+                (i != first && (alone || fills_device(io[i].c))))
                 continue;
             done[i] = true;
             zncc_ctx* c = io[i].c;
@@ -504,6 +511,7 @@ zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passe
     for (int first = 0; first < n; ++first) {
         if (done[first]) continue;
         const LineArgs& a0 = args[first];
+        const bool alone = fills_device(ctxs[first]);
         LineBatch b;
         memset(&b, 0, sizeof(b));
         int threads = 0;
@@ -511,7 +519,7 @@ zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passe
         for (int i = first; i < n; ++i) {
             const LineArgs& ai = args[i];
             if (done[i] || ai.tq != a0.tq || ai.nch != a0.nch || ai.lpc != a0.lpc || ai.async != a0.async ||
-                ai.cs != a0.cs)
+                ai.cs != a0.cs || (i != first && (alone || fills_device(ctxs[i]))))
                 continue;
             done[i] = true;
             add_line_pair(b, ai, mode, dtype, threads, stage, rest);
@@ -959,7 +967,14 @@ zncc_status zncc_run_batch(zncc_ctx* const* ctxs, const uint8_t* const* lefts, c
         if (!disps[i]) return fail(lc, ZNCC_EINVAL, "disp pointer is NULL");
         io[i] = PairIO{c, lefts[i], rights[i], pitches[i], disps[i], nullptr, 0};
     }
-    return run_fused(lc, io, n, sigma_s, sigma_r, iters, storage);
+    // a pair that fills the device by itself runs its own chain; the others share launches
+    PairIO small[kMaxBatch];
+    int nsmall = 0;
+    for (int i = 0; i < n; ++i) {
+        if (fills_device(io[i].c)) ZNCC_TRY(run_fused(lc, &io[i], 1, sigma_s, sigma_r, iters, storage));
+        else small[nsmall++] = io[i];
+    }
+    return nsmall ? run_fused(lc, small, nsmall, sigma_s, sigma_r, iters, storage) : ZNCC_OK;
 }
 
 zncc_status zncc_run_host(zncc_ctx* c, const uint8_t* left_host, const uint8_t* right_host, int pitch,
