@@ -13,6 +13,8 @@ this module compiles it with gcc on first use and wraps each entry point:
     dt_aggregate                          Sec. III-B, Eqs. (3)-(6)
     wta                                   Sec. III-C, Eq. (WTA1)
     run                                   the whole path on one pair
+    fastdt_encode / fastdt_decode         Sec. IV-C, the 8-bit code (6-bit value, 2-bit flag)
+    fastdt_store / run_fastdt             Sec. IV-C, near-zero-mean 16-bit storage and the code
 """
 
 from __future__ import annotations
@@ -67,6 +69,13 @@ def _bind(lib):
     lib.oracle_wta.argtypes = [f64p, c_int, c_int, c_int, u16p, f64p, f64p]
     lib.oracle_run.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_double, c_double,
                                c_int, c_int, u16p, f64p, f64p]
+    lib.oracle_fastdt_encode.argtypes = [ctypes.c_int16]
+    lib.oracle_fastdt_encode.restype = ctypes.c_uint8
+    lib.oracle_fastdt_decode.argtypes = [ctypes.c_uint8]
+    lib.oracle_fastdt_decode.restype = ctypes.c_int16
+    lib.oracle_fastdt_store.argtypes = [f64p, f64p, c_int, c_int, c_int, c_int, c_double]
+    lib.oracle_dt_aggregate_fastdt.argtypes = [f64p, u8p, c_int, c_int, c_int, c_double, c_double,
+                                               c_int, c_int, c_double, c_int]
     return lib
 
 
@@ -206,3 +215,45 @@ def run(left, right, max_disp, r, sigma_s=20.0, sigma_r=0.1, iters=3, nthreads=N
                           _p(disp, ctypes.c_uint16), _p(gap, ctypes.c_double),
                           None if C is None else _p(C, ctypes.c_double)), "run")
     return (disp, gap, C) if want_cost else (disp, gap)
+
+
+# FastDT storage (Sec. IV-C): d_arb = 0 (the paper's choice) and the 16-bit scale T of this
+# build (the per-pixel normalised costs lie in [-2, 2]).
+FASTDT_D_ARB = 0
+FASTDT_T = 16383.0
+
+
+def fastdt_encode(value: int, lib=None) -> int:
+    """The 8-bit code of a 16-bit two's-complement value."""
+    return int((lib or load()).oracle_fastdt_encode(int(value)))
+
+
+def fastdt_decode(code: int, lib=None) -> int:
+    """The 16-bit value an 8-bit code stands for."""
+    return int((lib or load()).oracle_fastdt_decode(int(code)))
+
+
+def fastdt_store(C, ahat, d_arb=FASTDT_D_ARB, T=FASTDT_T, lib=None):
+    """One FastDT store of a float64 [H][W][nd] volume (returns a new array)."""
+    lib = lib or load()
+    C = np.array(C, dtype=np.float64, copy=True, order="C")
+    H, W, nd = C.shape
+    a = np.ascontiguousarray(ahat, dtype=np.float64)
+    _check(lib.oracle_fastdt_store(_p(C, ctypes.c_double), _p(a, ctypes.c_double), W, H, nd, int(d_arb),
+                                   float(T)), "fastdt_store")
+    return C
+
+
+def run_fastdt(left, right, max_disp, r, sigma_s=20.0, sigma_r=0.1, iters=3, d_arb=FASTDT_D_ARB,
+               T=FASTDT_T, nthreads=None, lib=None):
+    """The whole path with FastDT storage between pass pairs: (disparity, gap)."""
+    lib = lib or load()
+    left, right = _img(left), _img(right)
+    nthreads = nthreads or default_threads()
+    C = zncc_volume(left, right, max_disp, r, nthreads=nthreads, lib=lib)
+    H, W, _ = C.shape
+    _check(lib.oracle_dt_aggregate_fastdt(_p(C, ctypes.c_double), _p(left, ctypes.c_uint8), W, H, max_disp,
+                                          float(sigma_s), float(sigma_r), int(iters), int(d_arb), float(T),
+                                          nthreads), "dt_aggregate_fastdt")
+    disp, _, gap = wta(C, lib=lib)
+    return disp, gap

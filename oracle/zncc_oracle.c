@@ -12,6 +12,7 @@
  *   - DT weights:       Sec. III-B, Eqs. (7)-(10) and the simplified Eq. (11)
  *   - DT aggregation:   Sec. III-B, Eqs. (3)-(6), boundary condition C_L(0,y,d) = C(0,y,d)
  *   - disparity (WTA):  Sec. III-C, Eq. (WTA1)
+ *   - FastDT storage:   Sec. IV-C (near-zero-mean normalization, 16-bit values, 8-bit code)
  *
  * Readings of passages the paper leaves open (each listed in the design doc):
  *   - reference image I_R = left, target I_T = right; I_R(x,y) is matched to I_T(x-d,y);
@@ -378,6 +379,93 @@ int oracle_wta(const double* C, int W, int H, int nd, uint16_t* disp, double* be
         if (gap) gap[p] = second - bcost;
     }
     return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* FastDT storage (Sec. IV-C): cost-value normalization with nearly zero mean, 16-bit      */
+/* integers, and the 8-bit code of a 6-bit value and a 2-bit position flag.                */
+/*                                                                                        */
+/* Encoding of a 16-bit two's-complement value: values >= 0 give the code 0. A negative    */
+/* value keeps six bits next to its leading ones: bits 14..9 with flag 01 unless bits     */
+/* 14..11 are all ones; else bits 10..5 with flag 10 unless bits 10..7 are all ones; else */
+/* bits 6..1 with flag 11. The code is (six bits << 2) | flag.                            */
+/* Decoding: code 0 gives 0; otherwise the six bits go back to their position, every bit   */
+/* above them is set to one and every bit below them to zero.                             */
+
+uint8_t oracle_fastdt_encode(int16_t value) {
+    if (value >= 0) return 0;
+    unsigned v = (unsigned)(uint16_t)value;
+    unsigned hi4 = (v >> 11) & 0xF, mid4 = (v >> 7) & 0xF;
+    if (hi4 != 0xF) return (uint8_t)((((v >> 9) & 0x3F) << 2) | 1u);
+    if (mid4 != 0xF) return (uint8_t)((((v >> 5) & 0x3F) << 2) | 2u);
+    return (uint8_t)((((v >> 1) & 0x3F) << 2) | 3u);
+}
+
+int16_t oracle_fastdt_decode(uint8_t code) {
+    if (code == 0) return 0;
+    unsigned flag = code & 3u, six = code >> 2;
+    int low = flag == 1 ? 9 : (flag == 2 ? 5 : 1);      /* position of the six bits */
+    if (flag == 0) low = 1;                              /* not produced by the encoder */
+    unsigned v = six << low;
+    for (int b = low + 6; b < 16; ++b) v |= 1u << b;      /* ones above, zeros below */
+    return (int16_t)(uint16_t)v;
+}
+
+/* One FastDT store of a [H][W][nd] volume in place, after a pass pair whose all-ones      */
+/* response is ahat [H][W] (the per-pixel bound of |C|): per pixel, the near-zero-mean     */
+/* normalization against disparity d_arb, e = (C(d_arb) - C(d)) / ahat (e < 0 where d does */
+/* better than d_arb under the argmax), the 16-bit value E = rint(T e) clamped to int16,   */
+/* its 8-bit code, and back: C(d) = -decode(code) / T * ahat. Values that do no better     */
+/* than d_arb come back as 0, like C(d_arb) itself.                                        */
+int oracle_fastdt_store(double* C, const double* ahat, int W, int H, int nd, int d_arb, double T) {
+    if (!C || !ahat || W < 1 || H < 1 || nd < 1 || d_arb < 0 || d_arb >= nd || !(T > 0)) return ORACLE_EINVAL;
+    for (long p = 0; p < (long)W * H; ++p) {
+        double* c = C + p * nd;
+        const double ref = c[d_arb], a = ahat[p];
+        for (int d = 0; d < nd; ++d) {
+            double e = rint(T * (ref - c[d]) / a);
+            if (e < -32768.0) e = -32768.0;
+            if (e > 32767.0) e = 32767.0;
+            const int16_t E = oracle_fastdt_decode(oracle_fastdt_encode((int16_t)e));
+            c[d] = -(double)E / T * a;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* The DT chain with FastDT storage between pass pairs: after every pass pair but the last */
+/* (the last feeds WTA directly) the volume goes through oracle_fastdt_store with the      */
+/* all-ones response after the same number of pairs.                                       */
+int oracle_dt_aggregate_fastdt(double* C, const uint8_t* guide, int W, int H, int nd, double sigma_s,
+                               double sigma_r, int iters, int d_arb, double T, int nthreads) {
+    if (!C || !guide || W < 1 || H < 1 || nd < 1 || iters < 0 || !(sigma_s > 0) || !(sigma_r > 0))
+        return ORACLE_EINVAL;
+    size_t n = (size_t)W * H;
+    double* w = (double*)malloc(sizeof(double) * n * 5);
+    if (!w) return ORACLE_ENOMEM;
+    double* ones = w + 4 * n;
+    int rc = oracle_dt_weights(guide, W, H, sigma_s, sigma_r, 0, w, w + n, w + 2 * n, w + 3 * n);
+    for (size_t i = 0; i < n; ++i) ones[i] = 1.0;
+    const double s = 1.0 - exp(-1.0 / sigma_s);
+    for (int pair = 1; rc == ORACLE_OK && pair <= 2 * iters; ++pair) {
+        const int horiz = pair % 2;
+        pass_job a = {C, W, H, nd, horiz ? w : w + 2 * n, s}, b = {C, W, H, nd, horiz ? w + n : w + 3 * n, s};
+        pass_job oa = {ones, W, H, 1, horiz ? w : w + 2 * n, s}, ob = {ones, W, H, 1, horiz ? w + n : w + 3 * n, s};
+        if (horiz) {
+            parallel_for(H, nthreads, pass_l2r, &a);
+            parallel_for(H, nthreads, pass_r2l, &b);
+            parallel_for(H, nthreads, pass_l2r, &oa);
+            parallel_for(H, nthreads, pass_r2l, &ob);
+        } else {
+            parallel_for(W, nthreads, pass_u2d, &a);
+            parallel_for(W, nthreads, pass_d2u, &b);
+            parallel_for(W, nthreads, pass_u2d, &oa);
+            parallel_for(W, nthreads, pass_d2u, &ob);
+        }
+        if (pair < 2 * iters) rc = oracle_fastdt_store(C, ones, W, H, nd, d_arb, T);
+    }
+    free(w);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------------------ */

@@ -391,6 +391,78 @@ def pin_end_to_end_recovery(lib):
     assert (d0[m] == gt[m]).mean() >= 0.95
 
 
+# ---------------------------------------------------------------------------------------
+# FastDT storage (Sec. IV-C): the 8-bit code and the near-zero-mean 16-bit store
+
+def pin_fastdt_codec_examples(lib):
+    """Codes worked out by hand from the encoding and decoding rules of Sec. IV-C: positive
+    values and zero give code 0; 0x8000 keeps bits 14..9 (flag 01); -2048 = 0xF800 has bits
+    14..11 all ones and keeps bits 10..5 (flag 10); -128 = 0xFF80 and -1 = 0xFFFF keep bits
+    6..1 (flag 11); -2049 = 0xF7FF keeps 111011 from bits 14..9 and decodes to 0xF600."""
+    enc = lambda v: oracle.fastdt_encode(v, lib=lib)
+    dec = lambda c: oracle.fastdt_decode(c, lib=lib)
+    for v in (0, 1, 100, 32767):
+        assert enc(v) == 0
+    assert dec(0) == 0
+    cases = [(-32768, 0x01, -32768), (-2048, 0x02, -2048), (-128, 0x03, -128), (-1, 0xFF, -2),
+             (-2, 0xFF, -2), (-2049, (0b111011 << 2) | 1, -2560), (-129, (0b111011 << 2) | 2, -160),
+             (-3000, (0b111010 << 2) | 1, -3072)]
+    for v, code, back in cases:
+        assert enc(v) == code, (v, hex(enc(v)), hex(code))
+        assert dec(code) == back, (hex(code), dec(code), back)
+
+
+def pin_fastdt_codec_properties(lib):
+    """Over every 16-bit value: the decoded value never exceeds the original (the dropped low
+    bits are zeroed, the kept bits and the leading ones are exact), its error is below the
+    weight of the lowest kept bit (2^9, 2^5 or 2^1 for flags 01, 10, 11), non-negative values
+    decode to 0, and encoding a decoded value gives its code back."""
+    for v in range(-32768, 32768):
+        c = oracle.fastdt_encode(v, lib=lib)
+        d = oracle.fastdt_decode(c, lib=lib)
+        if v >= 0:
+            assert c == 0 and d == 0
+            continue
+        low = {1: 9, 2: 5, 3: 1}[c & 3]
+        assert d <= v and v - d < (1 << low), (v, c, d)
+        assert oracle.fastdt_encode(d, lib=lib) == c
+
+
+def pin_fastdt_store(lib):
+    """One store: the reference disparity comes back as 0, every value no better than it (under
+    the argmax) as 0, and a better value as C(d) - C(d_arb) within the code's error (the
+    dropped bits plus half a unit of rounding, in units of ahat / T)."""
+    rng = _rng(91)
+    C = rng.uniform(-1, 1, (6, 7, 9))
+    ahat = rng.uniform(0.5, 1.5, (6, 7))
+    C *= ahat[:, :, None]
+    out = oracle.fastdt_store(C, ahat, lib=lib)
+    T = oracle.FASTDT_T
+    for y in range(6):
+        for x in range(7):
+            ref = C[y, x, 0]
+            for d in range(9):
+                if C[y, x, d] <= ref:
+                    assert out[y, x, d] == 0.0
+                else:
+                    exact = (C[y, x, d] - ref) / ahat[y, x] * T
+                    got = out[y, x, d] / ahat[y, x] * T
+                    assert got >= exact - 0.5 - 1e-9 and got - exact < 512 + 0.5, (got, exact)
+
+
+def pin_fastdt_chain_accuracy(lib):
+    """The chain with FastDT storage still recovers a constant disparity on textured noise
+    (>= 99% of interior pixels) and agrees with the exact chain on most pixels of a
+    slanted-plane pair."""
+    p = make_pair(48, 120, 16, seed=31, disp="const", const_disp=7, gain=1.0, offset=0.0, noise=0.0)
+    disp, _ = oracle.run_fastdt(p.left, p.right, 16, 4, SIG_S, SIG_R, 3, lib=lib)
+    assert (disp[4:-4, 16:-4] == 7).mean() >= 0.99
+    q = make_pair(64, 160, 24, seed=32, disp="planes", occlusion_frac=0.05)
+    d8, _ = oracle.run_fastdt(q.left, q.right, 24, 4, SIG_S, SIG_R, 3, lib=lib)
+    d64, _ = oracle.run(q.left, q.right, 24, 4, SIG_S, SIG_R, 3, lib=lib)
+    assert (d8 == d64).mean() >= 0.9
+
+
 ALL_PINS = [
     pin_window_sums_routes, pin_window_sums_constant,
     pin_zncc_eq2_exact, pin_zncc_identical_windows, pin_zncc_affine_invariance,
@@ -401,4 +473,5 @@ ALL_PINS = [
     pin_dt_edge_stop,
     pin_wta_bruteforce_and_ties,
     pin_end_to_end_recovery,
+    pin_fastdt_codec_examples, pin_fastdt_codec_properties, pin_fastdt_store, pin_fastdt_chain_accuracy,
 ]

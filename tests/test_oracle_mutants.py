@@ -40,6 +40,12 @@ MUTANTS = [
      "c[k] = y == 0 ? j->s * c[k] : j->s * c[k] + c[k - j->nd] * wgt;"),
     ("wta_tie_largest", "if (1.0 - c[d] < bcost) { bcost = 1.0 - c[d]; bd = d; }",
      "if (1.0 - c[d] <= bcost) { bcost = 1.0 - c[d]; bd = d; }"),
+    ("fastdt_zero_encoded", "if (value >= 0) return 0;", "if (value > 0) return 0;"),
+    ("fastdt_flag_swapped", "if (mid4 != 0xF) return (uint8_t)((((v >> 5) & 0x3F) << 2) | 2u);",
+     "if (mid4 != 0xF) return (uint8_t)((((v >> 5) & 0x3F) << 2) | 1u);"),
+    ("fastdt_fill_short", "for (int b = low + 6; b < 16; ++b) v |= 1u << b;",
+     "for (int b = low + 7; b < 16; ++b) v |= 1u << b;"),
+    ("fastdt_reference_sign", "double e = rint(T * (ref - c[d]) / a);", "double e = rint(T * (c[d] - ref) / a);"),
 ]
 
 RUNNER = r"""
