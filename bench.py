@@ -1,7 +1,7 @@
 """Benchmark of the fused ZNCC + DT + WTA path on the paper-shaped workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--storage f32|f16] [--workload paper_1280x384]
+                    [--storage f32|f16|i8] [--workload paper_1280x384]
 
 One step = one pass of the whole path (window statistics, ZNCC fused with the first
 horizontal DT pair, the remaining DT passes, WTA fused into the last vertical pair) over one
@@ -68,6 +68,14 @@ def host_cores() -> int:
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count() or 1
+
+
+# bytes per stored volume element of each storage type (I8: the FastDT code of Sec. IV-C)
+STORAGE_BYTES = {"f32": 4, "f16": 2, "i8": 1}
+
+
+def storage_code(Z, name):
+    return {"f32": Z.ZNCC_F32, "f16": Z.ZNCC_F16, "i8": Z.ZNCC_I8}[name]
 
 
 def workload_desc(name, storage):
@@ -238,8 +246,8 @@ def run_gb300(args):
     dev = torch.device("cuda", local)
     wl = WORKLOADS[args.workload]
     iters = ITERS if args.workload != "plain_320x96" else 0
-    storage = Z.ZNCC_F32 if args.storage == "f32" else Z.ZNCC_F16
-    elt_bytes = 4 if storage == Z.ZNCC_F32 else 2
+    storage = storage_code(Z, args.storage)
+    elt_bytes = STORAGE_BYTES[args.storage]
     pair = config_pair(args.workload)
     H, W, D = wl["h"], wl["w"], wl["d"]
 
@@ -340,7 +348,7 @@ def run_gb300(args):
         "metric": METRIC, "value": round(value, 3), "unit": "Gdisp/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "fps": round(world * 1e3 / ms, 2), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32", "storage": args.storage, "data": "synthetic",
         "config": {"workload": workload_desc(args.workload, args.storage),
                    "l2": "flushed before every timed step (256 MB write outside the step events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -399,7 +407,7 @@ def run_batch(args):
         R.append(torch.from_numpy(p.right).to(dev))
         D.append(torch.empty((sp["h"], sp["w"]), dtype=torch.int16, device=dev))
         units += sp["w"] * sp["h"] * sp["max_disp"]
-    storage = Z.ZNCC_F32 if args.storage == "f32" else Z.ZNCC_F16
+    storage = storage_code(Z, args.storage)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def batched():
@@ -469,12 +477,14 @@ def run_batch(args):
 
 
 def run_precision(args):
-    """FP32 vs FP16 volume storage at 1920x1080, D = 256, 11x11, 3 DT iterations against the
-    FP64 oracle: the largest |aggregated cost - oracle| / A_hat over the whole volume (the
-    unfused chain zncc_cost_volume + dt_aggregate, which rounds every stored pair to the
-    storage type), and the disparity maps of the fused path: the share of pixels that differ
-    from the oracle's map, all pixels and those whose oracle best-second gap is at least
-    1e-5 * A_hat. Also the fused path's time per pair for each storage type."""
+    """FP32 vs FP16 vs FastDT (I8) volume storage at 1920x1080, D = 256, 11x11, 3 DT
+    iterations against the FP64 oracle: the largest |aggregated cost - oracle| / A_hat over the
+    whole volume (F32, F16: the unfused chain zncc_cost_volume + dt_aggregate, which rounds
+    every stored pair to the storage type), and the disparity maps of the fused path: the
+    share of pixels that differ from the oracle's map, all pixels and those whose oracle
+    best-second gap is at least 1e-5 * A_hat (I8 also against the oracle's FastDT chain), and
+    the share of valid pixels within one disparity of the ground truth, next to the oracle's.
+    Also the fused path's time per pair for each storage type."""
     import torch
 
     import oracle
@@ -487,7 +497,11 @@ def run_precision(args):
     t0 = time.perf_counter()
     ref, gap, cref = oracle.run(pair.left, pair.right, D, win // 2, SIG_S, SIG_R, ITERS, want_cost=True)
     ahat = oracle.ones_response(pair.left, SIG_S, SIG_R, ITERS)
+    ref_fast, _ = oracle.run_fastdt(pair.left, pair.right, D, win // 2, SIG_S, SIG_R, ITERS)
     t_oracle = time.perf_counter() - t0
+
+    def gt_accuracy(m):
+        return round(float((np.abs(m.astype(np.int64) - pair.gt) <= 1)[pair.valid].mean()), 6)
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     ctx = Z.ZnccContext(W, H, D, win)
@@ -497,7 +511,8 @@ def run_precision(args):
     clear = gap >= 1e-5 * ahat
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     result = {}
-    for name, st, tdt in (("f32", Z.ZNCC_F32, torch.float32), ("f16", Z.ZNCC_F16, torch.float16)):
+
+    def volume_error(tdt, st):
         vol = torch.empty((H, W, D), dtype=tdt, device=dev)
         ctx.zncc_cost_volume(left, right, vol, st)
         ctx.dt_aggregate(left, vol, SIG_S, SIG_R, ITERS, st)
@@ -511,7 +526,13 @@ def run_precision(args):
             normal = np.broadcast_to(a >= 2.0 ** -14, e.shape)
             if normal.any():
                 worst_normal = max(worst_normal or 0.0, float(e[normal].max()))
-        del vol
+        return worst, worst_normal
+
+    for name, st, tdt in (("f32", Z.ZNCC_F32, torch.float32), ("f16", Z.ZNCC_F16, torch.float16),
+                          ("i8", Z.ZNCC_I8, None)):
+        worst, worst_normal = None, None
+        if tdt is not None:                 # the FastDT codes exist only inside the fused path
+            worst, worst_normal = volume_error(tdt, st)
         ms = []
         for i in range(args.warmup + args.steps):
             flush.zero_()
@@ -529,22 +550,27 @@ def run_precision(args):
                         "max_abs_err_over_ahat_where_ahat_ge_2^-14": worst_normal,
                         "map_mismatch_rate": round(float(diff.mean()), 6),
                         "map_mismatch_rate_clear_pixels": round(float(diff[clear].mean()), 6),
+                        "gt_within_1px": gt_accuracy(got),
                         "fused_ms_per_pair": round(sum(ms) / len(ms), 4),
                         "fused_gdisp_s": round(W * H * D / (sum(ms) / len(ms) * 1e-3) / 1e9, 3)}
+        if name == "i8":
+            result[name]["map_mismatch_rate_vs_oracle_fastdt"] = round(float((got != ref_fast).mean()), 6)
     ctx.close()
     line = {
-        "metric": "precision: FP32 vs FP16 volume storage vs the FP64 oracle, 1920x1080 D=256 11x11",
+        "metric": "precision: FP32 vs FP16 vs FastDT 8-bit volume storage vs the FP64 oracle, "
+                  "1920x1080 D=256 11x11",
         "value": result["f16"]["map_mismatch_rate"], "unit": "share of pixels (F16 map vs oracle)",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32,f16", "data": "synthetic",
-        "config": {"workload": workload_desc("precision_1920x1080", "f32/f16"),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc("precision_1920x1080", "f32/f16/i8"),
+                   "oracle_gt_within_1px": {"f64": gt_accuracy(ref), "fastdt": gt_accuracy(ref_fast)},
                    "near_tie_pixels": round(float(1 - clear.mean()), 6),
                    "pixels_with_ahat_below_2^-14": round(float((ahat < 2.0 ** -14).mean()), 6),
                    "volume_error_path": "unfused zncc_cost_volume + dt_aggregate (each stored pair "
                                         "rounded to the storage type, no A_hat normalisation)",
                    "oracle_seconds": round(t_oracle, 2),
                    "l2": "flushed before every timed pair (256 MB write outside the events)"},
-        "f32": result["f32"], "f16": result["f16"],
+        "f32": result["f32"], "f16": result["f16"], "i8": result["i8"],
     }
     print(json.dumps(line))
     return 0
@@ -563,7 +589,7 @@ def run_serving(args):
     from synth.stereo import SERVE_DISPS, SERVE_SIZES, make_pair, serving_requests
 
     torch.cuda.set_device(0)
-    storage = Z.ZNCC_F32 if args.storage == "f32" else Z.ZNCC_F16
+    storage = storage_code(Z, args.storage)
     shapes = [(h, w, d) for (h, w) in SERVE_SIZES for d in SERVE_DISPS]
     pool = {sh: make_pair(sh[0], sh[1], sh[2], 500000 + i, disp="planes", occlusion_frac=0.05)
             for i, sh in enumerate(shapes)}
@@ -617,7 +643,7 @@ def run_serving(args):
         "metric": f"served p50/p99 latency at {rates[0]:g} req/s (continuous batching vs one pair per launch)",
         "value": head["batched"]["p99_ms"], "unit": "ms (p99)", "n_gpus": 1, "steps": args.requests,
         "warmup": len(shapes), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": args.storage, "data": "synthetic",
+        "dtype": "f32", "storage": args.storage, "data": "synthetic",
         "config": {"workload": "serving: Poisson arrivals seed 5; sizes 640x192/1280x384/1920x1080, "
                                "D 64/128/256, 9x9, sigma_s 20, sigma_r 0.1, 3 iterations; 40 GB budget",
                    "l2": "not flushed (a live request stream)"},
@@ -636,7 +662,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
+    ap.add_argument("--storage", choices=["f32", "f16", "i8"], default="f32")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch_uneven16", "serving", "precision_sweep"],
                     default="paper_1280x384")
     ap.add_argument("--rates", default="200,500,1000,2000", help="serving: arrival rates (req/s)")

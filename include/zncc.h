@@ -48,7 +48,16 @@ typedef enum {
     ZNCC_EUNSUPPORTED = 7   /* a size the kernels do not handle                          */
 } zncc_status;
 
-typedef enum { ZNCC_F32 = 0, ZNCC_F16 = 1 } zncc_dtype;
+/* Storage types. ZNCC_I8 is the FastDT storage of Sec. IV-C, for the intermediate volume of
+ * the fused path only (zncc_run, zncc_run_batch, zncc_run_host, serve_submit): after every DT
+ * pass pair but the last, the values v(d) of a pixel, divided by A_hat (the same pass pairs
+ * applied to an all-ones plane, the per-pixel bound of |v|), are stored as
+ * E = rint(16383 * (v(0) - v(d)) / A_hat), clamped to int16 and cut to an 8-bit code (the six
+ * bits next to the leading ones of the two's-complement value and a 2-bit flag naming their
+ * position; values >= 0, which do no better than d = 0, are code 0); the next pair reads the
+ * code back as -E / 16383 * A_hat. One byte per element; the calls that take a caller-owned
+ * cost volume reject it with ZNCC_EINVAL. */
+typedef enum { ZNCC_F32 = 0, ZNCC_F16 = 1, ZNCC_I8 = 2 } zncc_dtype;
 
 typedef struct zncc_ctx zncc_ctx;
 
@@ -141,11 +150,20 @@ zncc_status dt_aggregate_noalloc(const uint8_t* guide_left, int pitch, int width
  * cost (argmin of 1 - C). cost: device [H][W][D]; disp: device uint16 [H][W]. */
 zncc_status wta_disparity(zncc_ctx* ctx, const void* cost, zncc_dtype dtype, uint16_t* disp);
 
+/* The FastDT code (Sec. IV-C) on the device, as the fused path's ZNCC_I8 storage applies it:
+ * for i < n, codes[i] = the 8-bit code of the 16-bit value values[i] and decoded[i] = the
+ * 16-bit value that code stands for (the six kept bits in place, every bit above them one,
+ * every bit below zero; code 0 is 0). values, codes, decoded: device arrays of n elements
+ * (codes or decoded may be NULL). Runs on `cuda_stream` (NULL: the legacy default stream);
+ * ZNCC_EINVAL for n < 0, or values NULL with n > 0 (n == 0 launches nothing); the text of an error is in zncc_last_error(NULL). */
+zncc_status fastdt_codec(const int16_t* values, int n, uint8_t* codes, int16_t* decoded, void* cuda_stream);
+
 /* The fused path: window statistics, ZNCC fused with the first horizontal DT pass pair,
  * the remaining DT passes, and WTA fused into the last vertical pass pair, so that the
  * volume is written once per horizontal/vertical hand-over and never read back for WTA.
  * iters == 0 computes ZNCC and WTA in one kernel without storing any volume.
- * `storage` is the type of the context-owned intermediate volume (F16 halves its traffic).
+ * `storage` is the type of the context-owned intermediate volume (F16 halves its traffic,
+ * I8 quarters it at some loss of accuracy: the FastDT storage above).
  * left/right: device images; disp: device uint16 [H][W]. Sec. V-C fuses ZNCC with L2R and
  * WTA with D2U in the same way. */
 zncc_status zncc_run(zncc_ctx* ctx, const uint8_t* left, const uint8_t* right, int pitch,

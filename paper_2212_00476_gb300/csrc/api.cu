@@ -77,16 +77,16 @@ struct zncc_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t cur = nullptr;       // the stream launches go to (stream, or side)
     cudaStream_t side = nullptr;      // second stream for work independent of the cost kernel
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_first = nullptr;
     std::string err;
     float4* coefH = nullptr;      // [H][W]       horizontal DT coefficients
     float4* coefV = nullptr;      // [W][H]       vertical DT coefficients
     unsigned long long* keys = nullptr;   // [H][W] fused-WTA keys, zero between runs
     void* vol = nullptr;          // the fused path's intermediate volume (on first use)
     size_t vol_bytes = 0;
-    float* ahat = nullptr;        // [nahat][H][W] DT responses of an all-ones plane (F16 storage)
-    float2* mulmap = nullptr;     // [nahat] maps of pairs 2.. : (A_hat_{p-1}, s2 / A_hat_p), line-major
-    int nahat = 0;
+    float* ahat = nullptr;        // [nahat][H][W] DT responses of an all-ones plane (F16, I8 storage)
+    float2* mulmap = nullptr;     // [nmul] maps of the pairs from 2 (F16) or 1 (I8) on:
+    int nahat = 0, nmul = 0;      //        (A_hat_{p-1}, s2 / A_hat_p), line-major
     int smem_max = 0;             // opt-in shared memory per block of the device
     int row_minb2 = 1;            // cost kernel: two-blocks-per-SM variant where it applies
     int row_spb = 0;              // cost kernel: slices per block (0 = automatic)
@@ -173,14 +173,15 @@ void release(zncc_ctx* c) {
     c->vol_bytes = 0;
     free_dev(c->ahat);
     free_dev(c->mulmap);
-    c->nahat = 0;
+    c->nahat = c->nmul = 0;
     free_dev(c->img);
     free_dev(c->disp);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_first) cudaEventDestroy(c->ev_first);
     c->side = nullptr;
-    c->ev_fork = c->ev_join = nullptr;
+    c->ev_fork = c->ev_join = c->ev_first = nullptr;
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     c->records.clear();
@@ -237,6 +238,7 @@ struct PairIO {
     uint16_t* disp;
     void* vol;              // the pair's cost volume [H][W][dstride]
     long long dstride;
+    const float2* mulmap1 = nullptr;     // (FastDT) the multipliers of the cost kernel's pass pair
 };
 
 // DT coefficients of every pair (guide = left image), one launch.
@@ -308,7 +310,8 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
             a.dstride = io[i].dstride;
             a.d_out0 = 0;
             a.vec = io[i].vol && (io[i].dstride % 4 == 0) &&
-                    ((uintptr_t)io[i].vol % (dtype == 0 ? 16 : 8) == 0) ? 1 : 0;
+                    ((uintptr_t)io[i].vol % (dtype == 0 ? 16 : (dtype == 1 ? 8 : 4)) == 0) ? 1 : 0;
+            a.mulmap = io[i].mulmap1;
             a.K = K;
             a.inv_sr255 = inv_sr255;
             a.s2 = s2;
@@ -318,14 +321,18 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
             a.wta.last = 1;
             const int nthr = a.nch * a.tq;
             const int nslices = (c->D + kG * a.tq - 1) / (kG * a.tq);
-            if (mode == kModeWta) a.spb = nslices;
+            // WTA keeps a row's running best in registers, FastDT codes each slice against the
+            // row's d = 0: a block then visits whole rows
+            const bool whole_rows = mode == kModeWta || dtype == 2;
+            if (whole_rows) a.spb = nslices;
             else a.spb = c->row_spb > 0 ? std::min(c->row_spb, nslices) : nslices;
-            while (a.spb > 1 && zncc_row_smem_bytes(r, mode, a, nthr) > (size_t)lc->smem_max) --a.spb;
-            const size_t sm = zncc_row_smem_bytes(r, mode, a, nthr);
+            while (!whole_rows && a.spb > 1 && zncc_row_smem_bytes(r, mode, dtype, a, nthr) > (size_t)lc->smem_max)
+                --a.spb;
+            const size_t sm = zncc_row_smem_bytes(r, mode, dtype, a, nthr);
             if (sm > (size_t)lc->smem_max)
                 return fail(lc, ZNCC_EUNSUPPORTED, "the cost kernel's row band does not fit in shared memory");
             a.item0 = b.total_items;
-            a.nitems = mode == kModeWta ? c->H : c->H * nslices;       // units: rows, or (row, slice)
+            a.nitems = whole_rows ? c->H : c->H * nslices;       // units: rows, or (row, slice)
             b.total_items += a.nitems;
             threads = std::max(threads, nthr);
             smem = std::max(smem, sm);
@@ -378,7 +385,7 @@ cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePa
         }
         const int per_line = nch * tq;
         if (per_line > 512) continue;
-        const int seg = tq * 4 * (p.dtype == 0 ? 4 : 2);      // bytes per chunk position
+        const int seg = tq * 4 * (p.dtype == 0 ? 4 : (p.dtype == 1 ? 2 : 1));   // bytes per chunk position
         const bool whole_bursts = seg >= 64;
         for (int async = a.vec ? 1 : 0; async >= 0; --async) {
             for (int lpc = cs > 1 ? 1 : std::max(1, std::min(8, 256 / per_line)); lpc >= 1; --lpc) {
@@ -465,7 +472,7 @@ void fill_line_args(LineArgs& a, const LinePass& p, int W, int H, const float4* 
     a.coef_line_stride = p.horiz ? W : H;
     a.s2 = p.s2;
     const void* in = p.src ? p.src : p.vol;
-    const size_t al = p.dtype == 0 ? 16 : 8;
+    const size_t al = p.dtype == 0 ? 16 : (p.dtype == 1 ? 8 : 4);
     a.vec = (p.dstride % 4 == 0) && ((uintptr_t)p.vol % al == 0) && ((uintptr_t)in % al == 0) ? 1 : 0;
     a.keys = p.keys;
     a.pix_line = p.horiz ? W : 1;
@@ -485,8 +492,9 @@ void add_line_pair(LineBatch& b, const LineArgs& ai, int mode, int dtype, int& t
     a.step0 = b.total_steps;
     a.nsteps = ngroups * nslices;
     a.item0 = b.total_items;
-    a.nitems = a.nsteps;
-    (void)mode;
+    // FastDT stores code each slice against the line group's d = 0, which the group's first
+    // slice computes: a block then takes whole line groups
+    a.nitems = dtype == 2 && mode == kLineStore ? ngroups : a.nsteps;
     b.total_steps += a.nsteps;
     b.total_items += a.nitems;
     threads = std::max(threads, a.lpc * a.nch * a.tq);
@@ -534,7 +542,7 @@ zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passe
 }
 
 zncc_status ensure_volume(zncc_ctx* c, int dtype, long long dstride) {
-    const size_t need = (size_t)c->W * c->H * (size_t)dstride * (dtype == 0 ? 4 : 2);
+    const size_t need = (size_t)c->W * c->H * (size_t)dstride * (dtype == 0 ? 4 : (dtype == 1 ? 2 : 1));
     if (c->vol_bytes >= need) return ZNCC_OK;
     free_dev(c->vol);
     c->vol_bytes = 0;
@@ -543,14 +551,15 @@ zncc_status ensure_volume(zncc_ctx* c, int dtype, long long dstride) {
     return ZNCC_OK;
 }
 
-zncc_status ensure_ahat(zncc_ctx* c, int n) {
-    if (c->nahat >= n) return ZNCC_OK;
+zncc_status ensure_ahat(zncc_ctx* c, int nahat, int nmul) {
+    if (c->nahat >= nahat && c->nmul >= nmul) return ZNCC_OK;
     free_dev_f(c->ahat);
-    c->nahat = 0;
     free_dev(c->mulmap);
-    ZNCC_TRY(alloc_dev(c, (void**)&c->ahat, (size_t)c->W * c->H * n * sizeof(float), "A_hat maps"));
-    ZNCC_TRY(alloc_dev(c, (void**)&c->mulmap, (size_t)c->W * c->H * n * sizeof(float2), "A_hat multipliers"));
-    c->nahat = n;
+    c->nahat = c->nmul = 0;
+    ZNCC_TRY(alloc_dev(c, (void**)&c->ahat, (size_t)c->W * c->H * nahat * sizeof(float), "A_hat maps"));
+    ZNCC_TRY(alloc_dev(c, (void**)&c->mulmap, (size_t)c->W * c->H * nmul * sizeof(float2), "A_hat multipliers"));
+    c->nahat = nahat;
+    c->nmul = nmul;
     return ZNCC_OK;
 }
 
@@ -561,7 +570,7 @@ zncc_status ensure_ahat(zncc_ctx* c, int n) {
 zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigma_r, int iters,
                       int storage) {
     if (iters == 0) return run_rows(lc, io, n, kModeWta, 0, 0.0f, 0.0f, 0.0f, K_ZNCC_WTA, "ZNCC + WTA");
-    const int dt = storage == ZNCC_F32 ? 0 : 1;
+    const int dt = storage;                         // 0 float, 1 half, 2 FastDT codes
     zncc_ctx* ctxs[kMaxBatch];
     for (int i = 0; i < n; ++i) {
         ctxs[i] = io[i].c;
@@ -573,25 +582,44 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
     const float K = (float)exp(-1.0 / (double)sigma_s);
     const float inv_sr255 = (float)(1.0 / (255.0 * (double)sigma_r));
     const int npairs = 2 * iters;
-    // The DT weights of the line pairs (and, with half storage, the A_hat maps) depend only on
-    // the guide: they are computed on a second stream, concurrently with the cost kernel
-    // (which computes the weights of its own rows), and joined before the first line pair.
+    // The DT weights of the line pairs (and the A_hat maps) depend only on the guide: they are
+    // computed on a second stream, concurrently with the cost kernel (which computes the
+    // weights of its own rows), and joined before the first line pair.
     // Half storage keeps each stored pair p >= 2 divided by A_hat_p (the per-pixel bound of
     // |cost|), so that it stays inside the half range wherever the guide isolates a pixel;
     // the next pair multiplies it back. The factor is the same for every d of a pixel.
-    const bool norm = dt == 1 && npairs > 2;
+    // FastDT codes (Sec. IV-C) are normalised that way from the cost kernel's pair on, so the
+    // cost kernel waits for the first map (ev_first) instead of running beside the chain.
+    const bool norm = (dt == 1 && npairs > 2) || dt == 2;
+    const int pfirst = dt == 2 ? 1 : 2;             // the first pair with a multiplier map
     if (norm)
         for (int i = 0; i < n; ++i)
-            if (ensure_ahat(io[i].c, npairs - 1) != ZNCC_OK) return fail(lc, ZNCC_ENOMEM, io[i].c->err);
+            if (ensure_ahat(io[i].c, npairs - 1, npairs - pfirst + 1) != ZNCC_OK)
+                return fail(lc, ZNCC_ENOMEM, io[i].c->err);
     if (!lc->side) {
         ZNCC_CUDA(lc, cudaStreamCreateWithFlags(&lc->side, cudaStreamNonBlocking), "side stream");
         ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_fork, cudaEventDisableTiming), "fork event");
         ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_join, cudaEventDisableTiming), "join event");
+        ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_first, cudaEventDisableTiming), "first map event");
     }
     ZNCC_CUDA(lc, cudaEventRecord(lc->ev_fork, lc->stream), "fork");
     ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->side, lc->ev_fork, 0), "fork");
     lc->cur = lc->side;
     zncc_status st = run_coef(lc, io, n, sigma_s, sigma_r);
+    // the multipliers of pair p: (A_hat_{p-1}, or 1 for the raw cost of p = 1 and for the
+    // half volume of p = 2; s2 / A_hat_p, or s2 for the last pair, which is not stored)
+    auto mulmaps = [&](int p0, int p1) {
+        for (int i = 0; i < n && st == ZNCC_OK; ++i)
+            for (int pair = p0; pair <= p1 && st == ZNCC_OK; ++pair) {
+                const int W = io[i].c->W, H = io[i].c->H;
+                const size_t npix = (size_t)W * H;
+                const float* ain = pair - 1 >= pfirst ? io[i].c->ahat + (size_t)(pair - 2) * npix : nullptr;
+                const float* aout = pair < npairs ? io[i].c->ahat + (size_t)(pair - 1) * npix : nullptr;
+                cudaError_t e = launch_mulmap(ain, aout, s2, W, H, (pair % 2) == 1,
+                                              io[i].c->mulmap + (size_t)(pair - pfirst) * npix, lc->cur);
+                if (e != cudaSuccess) st = cuda_fail(lc, e, "A_hat multipliers");
+            }
+    };
     for (int p = 1; norm && p <= npairs - 1 && st == ZNCC_OK; ++p) {
         LinePass lp[kMaxBatch];
         for (int i = 0; i < n; ++i) {
@@ -607,20 +635,20 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
             lp[i].force_tq = 1;
         }
         st = run_lines(lc, ctxs, lp, n, K_AHAT);
-    }
-    for (int i = 0; norm && i < n && st == ZNCC_OK; ++i)     // multipliers of the stored pairs
-        for (int pair = 2; pair <= npairs && st == ZNCC_OK; ++pair) {
-            const int W = io[i].c->W, H = io[i].c->H;
-            const size_t npix = (size_t)W * H;
-            const float* ain = pair - 1 >= 2 ? io[i].c->ahat + (size_t)(pair - 2) * npix : nullptr;
-            const float* aout = pair < npairs ? io[i].c->ahat + (size_t)(pair - 1) * npix : nullptr;
-            cudaError_t e = launch_mulmap(ain, aout, s2, W, H, (pair % 2) == 1,
-                                          io[i].c->mulmap + (size_t)(pair - 2) * npix, lc->cur);
-            if (e != cudaSuccess) st = cuda_fail(lc, e, "A_hat multipliers");
+        if (dt == 2 && p == 1 && st == ZNCC_OK) {
+            mulmaps(1, 1);
+            const cudaError_t e = st == ZNCC_OK ? cudaEventRecord(lc->ev_first, lc->side) : cudaSuccess;
+            if (e != cudaSuccess) st = cuda_fail(lc, e, "first map");
         }
+    }
+    if (norm && st == ZNCC_OK) mulmaps(dt == 2 ? 2 : pfirst, npairs);
     lc->cur = lc->stream;
     ZNCC_TRY(st);
     ZNCC_CUDA(lc, cudaEventRecord(lc->ev_join, lc->side), "join");
+    if (dt == 2) {
+        ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_first, 0), "first map");
+        for (int i = 0; i < n; ++i) io[i].mulmap1 = io[i].c->mulmap;
+    }
     ZNCC_TRY(run_rows(lc, io, n, kModeHPair, dt, s2, K, inv_sr255, K_ZNCC_HPAIR, "ZNCC + horizontal DT pair"));
     ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_join, 0), "join of the weights stream");
     for (int pair = 2; pair <= npairs; ++pair) {    // pair 1 is the cost kernel's
@@ -635,7 +663,7 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
             lp[i].horiz = (pair % 2) == 1;
             lp[i].mode = pair == npairs ? kLineWta : kLineStore;
             lp[i].keys = pair == npairs ? io[i].c->keys : nullptr;
-            lp[i].mulmap = norm ? io[i].c->mulmap + (size_t)(pair - 2) * npix : nullptr;
+            lp[i].mulmap = norm ? io[i].c->mulmap + (size_t)(pair - pfirst) * npix : nullptr;
         }
         const int kind = pair % 2 ? K_DT_HPAIR : (pair == npairs ? K_DT_VPAIR_WTA : K_DT_VPAIR);
         ZNCC_TRY(run_lines(lc, ctxs, lp, n, kind));
@@ -934,13 +962,28 @@ zncc_status wta_disparity(zncc_ctx* c, const void* cost, zncc_dtype dtype, uint1
     return ZNCC_OK;
 }
 
+zncc_status fastdt_codec(const int16_t* values, int n, uint8_t* codes, int16_t* decoded, void* cuda_stream) {
+    g_free_error[0] = '\0';
+    if (n < 0 || (!values && n > 0)) {
+        set_free_error("fastdt_codec: n < 0, or values is NULL and n > 0");
+        return ZNCC_EINVAL;
+    }
+    g_launches.fetch_add(n > 0 ? 1 : 0, std::memory_order_relaxed);
+    const cudaError_t e = launch_fastdt_codec(values, n, codes, decoded, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) {
+        set_free_error("fastdt_codec: %s (%s)", cudaGetErrorName(e), cudaGetErrorString(e));
+        return ZNCC_ECUDA;
+    }
+    return ZNCC_OK;
+}
+
 zncc_status zncc_run(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch, float sigma_s,
                      float sigma_r, int iters, zncc_dtype storage, uint16_t* disp) {
     if (!c) return ZNCC_EINVAL;
     c->err.clear();
     ZNCC_TRY(check_images(c, left, right, pitch));
     if (!disp) return fail(c, ZNCC_EINVAL, "disp pointer is NULL");
-    if (storage != ZNCC_F32 && storage != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
+    if (storage != ZNCC_F32 && storage != ZNCC_F16 && storage != ZNCC_I8) return fail(c, ZNCC_EINVAL, "unknown dtype");
     ZNCC_TRY(check_dt(c, sigma_s, sigma_r, iters));
     PairIO io{c, left, right, pitch, disp, nullptr, 0};
     return run_fused(c, &io, 1, sigma_s, sigma_r, iters, storage);
@@ -954,7 +997,8 @@ zncc_status zncc_run_batch(zncc_ctx* const* ctxs, const uint8_t* const* lefts, c
     lc->err.clear();
     if (n > kMaxBatch) return fail(lc, ZNCC_EINVAL, "at most 32 pairs per batch");
     if (!lefts || !rights || !pitches || !disps) return fail(lc, ZNCC_EINVAL, "a batch array is NULL");
-    if (storage != ZNCC_F32 && storage != ZNCC_F16) return fail(lc, ZNCC_EINVAL, "unknown dtype");
+    if (storage != ZNCC_F32 && storage != ZNCC_F16 && storage != ZNCC_I8)
+        return fail(lc, ZNCC_EINVAL, "unknown dtype");
     ZNCC_TRY(check_dt(lc, sigma_s, sigma_r, iters));
     PairIO io[kMaxBatch];
     for (int i = 0; i < n; ++i) {

@@ -32,6 +32,8 @@ __host__ __device__ __forceinline__ int cpos(int pos) { return (pos >> 4) * kCS 
 
 // ---- cost-volume element access: 4 consecutive disparities per thread ----------------
 
+__device__ __forceinline__ void fastdt_unpack(unsigned word, float (&o)[4]);
+
 __device__ __forceinline__ void ld4(const float* p, int nvalid, bool vec, float (&o)[4]) {
     if (vec && nvalid == 4) {
         float4 t = *reinterpret_cast<const float4*>(p);
@@ -60,6 +62,13 @@ __device__ __forceinline__ void ld4(const __half* p, int nvalid, bool vec, float
     }
 }
 
+// FastDT codes: four per 32-bit word (4-byte aligned groups of a padded pixel stride)
+__device__ __forceinline__ void ld4(const uint8_t* p, int nvalid, bool vec, float (&o)[4]) {
+    (void)nvalid;
+    (void)vec;
+    fastdt_unpack(*reinterpret_cast<const unsigned*>(p), o);
+}
+
 __device__ __forceinline__ void st4(float* p, int nvalid, bool vec, const float (&o)[4]) {
     if (vec && nvalid == 4) {
         *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
@@ -78,6 +87,53 @@ __device__ __forceinline__ void st4(__half* p, int nvalid, bool vec, const float
         for (int j = 0; j < 4; ++j)
             if (j < nvalid) p[j] = __float2half_rn(o[j]);
     }
+}
+
+// ---- FastDT storage (Sec. IV-C): 8-bit codes of near-zero-mean 16-bit costs -------------
+// A stored value is e = (v(d_arb) - v(d)) / A_hat scaled by kFastT and rounded to a 16-bit
+// integer (values that do no better than d_arb are 0); its code keeps the six bits next to
+// the leading ones of the two's-complement value (bits 14..9, 10..5 or 6..1) and a 2-bit flag
+// for the position. Four codes (four consecutive disparities) share a 32-bit word.
+constexpr float kFastT = 16383.0f;
+
+__device__ __forceinline__ unsigned fastdt_encode(int value) {
+    if (value >= 0) return 0u;
+    const unsigned v = (unsigned)value & 0xFFFFu;
+    if (((v >> 11) & 0xFu) != 0xFu) return (((v >> 9) & 0x3Fu) << 2) | 1u;
+    if (((v >> 7) & 0xFu) != 0xFu) return (((v >> 5) & 0x3Fu) << 2) | 2u;
+    return (((v >> 1) & 0x3Fu) << 2) | 3u;
+}
+
+__device__ __forceinline__ int fastdt_decode(unsigned code) {
+    if (code == 0u) return 0;
+    const unsigned flag = code & 3u;
+    const int low = flag == 1u ? 9 : (flag == 2u ? 5 : 1);
+    const unsigned v = ((code >> 2) << low) | (0xFFFFu << (low + 6));   // ones above, zeros below
+    return (int)(short)(v & 0xFFFFu);
+}
+
+// the 16-bit value of e (clamped to the int16 range)
+__device__ __forceinline__ int fastdt_quantize(float e) {
+    return max(-32768, min(32767, __float2int_rn(kFastT * e)));
+}
+
+// four codes from a word -> the normalised values -E / kFastT (larger is better)
+__device__ __forceinline__ void fastdt_unpack(unsigned word, float (&o)[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = -(float)fastdt_decode((word >> (8 * j)) & 0xFFu) * (1.0f / kFastT);
+}
+
+// four normalised values and the reference -> a word of four codes
+__device__ __forceinline__ unsigned fastdt_pack(const float (&v)[4], float ref, int nvalid) {
+    unsigned w = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (j < nvalid) w |= fastdt_encode(fastdt_quantize(ref - v[j])) << (8 * j);
+    return w;
+}
+
+__device__ __forceinline__ void lds4(const uint8_t* p, float (&o)[4]) {
+    fastdt_unpack(*reinterpret_cast<const unsigned*>(p), o);
 }
 
 // ---- asynchronous global -> shared copies (cp.async) ------------------------------------

@@ -1,5 +1,6 @@
 // kernels.cu -- window statistics, DT coefficients, DT line pairs and WTA kernels.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -156,8 +157,10 @@ cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st) {
 // each refilled (two items ahead) as soon as the forward sweep has consumed it. In Wta mode a
 // block keeps a running best over the slices it sees of a line group and merges it into the
 // per-pixel keys (atomicMax) when the group or its range ends.
+static size_t elem_bytes(int dtype) { return dtype == 0 ? 4 : (dtype == 1 ? 2 : 1); }
+
 size_t line_stage_bytes(int dtype, const LineArgs& a) {
-    return a.async ? 2ull * a.lpc * a.nch * a.tq * kL * (4 * (dtype == 0 ? 4 : 2)) : 0;
+    return a.async ? 2ull * a.lpc * a.nch * a.tq * kL * (4 * elem_bytes(dtype)) : 0;
 }
 
 
@@ -257,9 +260,12 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     const bool co_async = b.co_async != 0;
     const int arr = lpc * nch * kCS;
     const int nbuf = co_async ? 2 : 1;
+    constexpr bool kFast = std::is_same<T, uint8_t>::value;          // FastDT codes
     float4* co_all = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + b.stage_bytes);
     float2* mul_all = reinterpret_cast<float2*>(co_all + nbuf * arr);
-    float4* sb_all = reinterpret_cast<float4*>(mul_all + (has_mul ? nbuf * arr : 0));
+    // (FastDT store) the reference value v(d_arb = 0) of each position of the group's lines
+    float* ref_all = reinterpret_cast<float*>(mul_all + (has_mul ? nbuf * arr : 0));
+    float4* sb_all = reinterpret_cast<float4*>(ref_all + (kFast && MODE == kLineStore ? arr : 0));
     float* sa_all = reinterpret_cast<float*>(sb_all + lpc * 2 * nwl_all * tq);
     const int cthr = (li * nch + k) * kCS;                         // this thread's chunk
     float4* sb = sb_all + li * 2 * nwl_all * tq;
@@ -417,6 +423,21 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                     }
                 }
             }
+        } else if constexpr (kFast) {
+            // near-zero-mean codes against d_arb = 0, held by lane dq 0 in the group's first
+            // slice (a block processes whole line groups, slices in order)
+            if (o.sl == 0) {
+                if (dq == 0 && active)
+#pragma unroll
+                    for (int i = 0; i < kL; ++i) ref_all[cthr + i] = v[i][0];
+                __syncthreads();
+            }
+            T* q = vol + (line_ok ? elem0(a, o) : 0);
+            const long long es = a.elem_stride;
+#pragma unroll
+            for (int i = 0; i < kL; ++i)
+                if (any && i < npos)
+                    *reinterpret_cast<unsigned*>(q + (size_t)i * es) = fastdt_pack(v[i], ref_all[cthr + i], nvalid);
         } else {
             T* q = vol + (line_ok ? elem0(a, o) : 0);
             const long long es = a.elem_stride;
@@ -441,8 +462,8 @@ bool line_coef_async(const LineArgs& a) {
 
 size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a, bool co_async) {
     const int nwl_all = a.cs * a.nch * a.tq / 32;
-    const size_t per_pos = (16ull + (a.mulmap ? 8ull : 0ull)) * (co_async ? 2 : 1);
-    (void)mode;
+    const size_t per_pos = (16ull + (a.mulmap ? 8ull : 0ull)) * (co_async ? 2 : 1) +
+                           (dtype == 2 && mode == kLineStore ? 4ull : 0ull);
     return line_stage_bytes(dtype, a) + (size_t)a.lpc * (per_pos * a.nch * kCS + dt_scan_bytes(nwl_all, a.tq));
 }
 
@@ -463,12 +484,31 @@ cudaError_t launch_mulmap(const float* ain, const float* aout, float s2, int W, 
     return cudaGetLastError();
 }
 
+// The FastDT code of each 16-bit value and the value it decodes to (Sec. IV-C).
+__global__ void k_fastdt_codec(const int16_t* __restrict__ values, int n, uint8_t* __restrict__ codes,
+                               int16_t* __restrict__ decoded) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned c = fastdt_encode((int)values[i]);
+    if (codes) codes[i] = (uint8_t)c;
+    if (decoded) decoded[i] = (int16_t)fastdt_decode(c);
+}
+
+cudaError_t launch_fastdt_codec(const int16_t* values, int n, uint8_t* codes, int16_t* decoded, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_fastdt_codec<<<(n + 255) / 256, 256, 0, st>>>(values, n, codes, decoded);
+    return cudaGetLastError();
+}
+
 template <bool SINGLE, bool CLUSTER>
 static void (*line_pair_fn_t(int mode, int dtype))(LineBatch) {
     if (mode == kLineStore)
         return dtype == 0 ? k_line_pair<float, kLineStore, SINGLE, CLUSTER>
-                          : k_line_pair<__half, kLineStore, SINGLE, CLUSTER>;
-    return dtype == 0 ? k_line_pair<float, kLineWta, SINGLE, CLUSTER> : k_line_pair<__half, kLineWta, SINGLE, CLUSTER>;
+                          : dtype == 1 ? k_line_pair<__half, kLineStore, SINGLE, CLUSTER>
+                                       : k_line_pair<uint8_t, kLineStore, SINGLE, CLUSTER>;
+    return dtype == 0 ? k_line_pair<float, kLineWta, SINGLE, CLUSTER>
+                      : dtype == 1 ? k_line_pair<__half, kLineWta, SINGLE, CLUSTER>
+                                   : k_line_pair<uint8_t, kLineWta, SINGLE, CLUSTER>;
 }
 
 static void (*line_pair_fn(int mode, int dtype, bool single, bool cluster))(LineBatch) {
@@ -570,8 +610,8 @@ cudaError_t launch_wta_volume(const void* cost, int dtype, int W, int H, int D, 
     return cudaGetLastError();
 }
 
-size_t zncc_row_smem_bytes(int R, int mode, const RowArgs& a, int nthreads) {
-    return zncc_row_smem(R, mode, a, nthreads);
+size_t zncc_row_smem_bytes(int R, int mode, int dtype, const RowArgs& a, int nthreads) {
+    return zncc_row_smem(R, mode, dtype, a, nthreads);
 }
 
 cudaError_t launch_zncc_row(int R, const RowBatch& b, int threads, size_t smem, int mode, int dtype,

@@ -31,6 +31,7 @@ struct RowArgs {
     int d_out0;               // disparity stored at entry 0 of a pixel
     int vec;                  // 16-byte (float) / 8-byte (half) accesses allowed
     float K, inv_sr255;       // DT weights (HPair): exp(-1/sigma_s), 1/(255 sigma_r); guide = left
+    const float2* mulmap;     // (HPair, FastDT codes) [H][W]: (unused, output scale (1-K)^2/A_hat_1)
     float s2;                 // (1 - K)^2
     WtaOut wta;               // (Wta)
     int minb2;                // use the two-blocks-per-SM variant where the block allows
@@ -90,7 +91,7 @@ struct LineBatch {
 void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, dim3 grid, dim3 block, size_t smem,
                    cudaStream_t st, int cluster);
 
-size_t zncc_row_smem_bytes(int R, int mode, const RowArgs& a, int nthreads);
+size_t zncc_row_smem_bytes(int R, int mode, int dtype, const RowArgs& a, int nthreads);
 // A pass whose coefficients (and multipliers) can be streamed (at least two slices per line
 // group); the shared memory of a block with one or two buffers of them.
 bool line_coef_async(const LineArgs& a);
@@ -146,6 +147,7 @@ cudaError_t launch_wta_finish(const WtaFinishBatch& b, cudaStream_t st);
 // (line, position), (ain ? ain[pix] : 1, aout ? s2 / aout[pix] : s2), ain/aout [H][W].
 cudaError_t launch_mulmap(const float* ain, const float* aout, float s2, int W, int H, bool horiz, float2* out,
                           cudaStream_t st);
+cudaError_t launch_fastdt_codec(const int16_t* values, int n, uint8_t* codes, int16_t* decoded, cudaStream_t st);
 
 // Device allocation of the library (cudaMalloc, or an injected out-of-memory failure when the
 // environment variable ZNCC_FAIL_DEVICE_ALLOC is 1).

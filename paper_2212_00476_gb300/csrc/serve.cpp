@@ -47,14 +47,15 @@ struct ShapeKey {
 };
 
 // Device bytes a context of this shape holds: DT coefficients (two float4 per pixel), the
-// fused WTA's keys, the volume (pixel stride padded to 4 entries), the F16 path's A_hat maps
-// and multipliers, the images and map.
+// fused WTA's keys, the volume (pixel stride padded to 4 entries), the A_hat maps and
+// multipliers of the F16 and I8 paths, the images and map.
 size_t shape_charge(const ShapeKey& k) {
     const size_t npix = (size_t)k.W * k.H;
     size_t b = 32 * npix + 8 * npix + 4 * npix;
     if (k.iters > 0) {
-        b += npix * (size_t)((k.D + 3) / 4 * 4) * (k.storage == ZNCC_F32 ? 4 : 2);
+        b += npix * (size_t)((k.D + 3) / 4 * 4) * (k.storage == ZNCC_F32 ? 4 : (k.storage == ZNCC_F16 ? 2 : 1));
         if (k.storage == ZNCC_F16 && k.iters > 1) b += npix * 12 * (size_t)(2 * k.iters - 1);
+        if (k.storage == ZNCC_I8) b += npix * (4 * (size_t)(2 * k.iters - 1) + 8 * (size_t)(2 * k.iters));
     }
     return b;
 }
@@ -386,7 +387,7 @@ void worker_main(zncc_server* s) {
 zncc_status check_request(int W, int H, int D, int win, float ss, float sr, int iters, int storage) {
     if (W < 1 || H < 1 || D < 1 || win < 3 || win > 15 || win % 2 == 0) return ZNCC_EINVAL;
     if (!(ss > 0.0f) || !(sr > 0.0f) || iters < 0 || iters > 64) return ZNCC_EINVAL;
-    if (storage != ZNCC_F32 && storage != ZNCC_F16) return ZNCC_EINVAL;
+    if (storage != ZNCC_F32 && storage != ZNCC_F16 && storage != ZNCC_I8) return ZNCC_EINVAL;
     if (W > 3072 || H > 4096 || D > 1024) return ZNCC_EUNSUPPORTED;
     return ZNCC_OK;
 }

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -63,6 +64,10 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
     float4* co = reinterpret_cast<float4*>(SR + 4 * pSR);            // HPair, chunk-major
     float4* sb = co + nch * kCS;
     float* sa = reinterpret_cast<float*>(sb + 2 * nwl * tq);
+    // FastDT codes (HPair): the row's output scales and the reference values v(d_arb = 0)
+    constexpr bool kFast = std::is_same<T, uint8_t>::value;
+    float2* mrow = reinterpret_cast<float2*>(sa + 2 * nwl * tq);     // chunk-major (kCS)
+    float* ref = reinterpret_cast<float*>(mrow + nch * kCS);
 
     // ---- stage the packed bands (and the DT coefficients) ----
     for (int t = tid; t < NLP + NRP; t += blockDim.x) {
@@ -102,6 +107,8 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
                 if (i + off < kL) B *= b2;
             }
             co[cpos(t)] = t < W ? make_float4(w, A, wn, B) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (kFast)
+                mrow[cpos(t)] = t < W ? __ldg(a.mulmap + (size_t)y * W + t) : make_float2(0.f, 0.f);
         }
     }
     __syncthreads();
@@ -212,10 +219,28 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
             continue;
         }
         if constexpr (MODE == kModeHPair)
-            dt_pair(v, co + k * kCS, tq, dq, lane, wl, nwl, sa, sb, a.s2, nullptr, NoHook(), active);
+            dt_pair(v, co + k * kCS, tq, dq, lane, wl, nwl, sa, sb, a.s2, kFast ? mrow + k * kCS : nullptr,
+                    NoHook(), active);
 
-        // ---- store [H][W][dstride] ----
-        if (active && nvalid > 0) {
+        if constexpr (kFast) {
+            // near-zero-mean codes against d_arb = 0, held by lane dq 0 in slice 0 (a visit covers
+            // every slice of its row, in order)
+            if (sl == 0) {
+                if (dq == 0 && active)
+#pragma unroll
+                    for (int i = 0; i < kL; ++i) ref[k * kCS + i] = v[i][0];
+                __syncthreads();
+            }
+            if (active && nvalid > 0) {
+                T* q = out + ((size_t)y * W + x0) * a.dstride + (d_first - a.d_out0);
+#pragma unroll
+                for (int i = 0; i < kL; ++i) {
+                    if (x0 + i < W) *reinterpret_cast<unsigned*>(q) = fastdt_pack(v[i], ref[k * kCS + i], nvalid);
+                    q += a.dstride;
+                }
+            }
+        } else if (active && nvalid > 0) {
+            // ---- store [H][W][dstride] ----
             T* q = out + ((size_t)y * W + x0) * a.dstride + (d_first - a.d_out0);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
@@ -271,7 +296,7 @@ __global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(const 
         const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
         const int local = u - a.item0;
         int y, s_begin, s_end;
-        if constexpr (MODE == kModeWta) {
+        if constexpr (MODE == kModeWta || std::is_same<T, uint8_t>::value) {     // whole rows
             y = local;
             s_begin = 0;
             s_end = nslices;
@@ -290,7 +315,7 @@ __global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(const 
 }
 
 // Shared-memory bytes of one item of k_zncc_row.
-inline size_t zncc_row_smem(int R, int mode, const RowArgs& a, int nthreads) {
+inline size_t zncc_row_smem(int R, int mode, int dtype, const RowArgs& a, int nthreads) {
     const int ds = kG * a.tq, span = a.nch * kL;
     const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
     const int drange = std::min(a.spb, nslices) * ds;
@@ -298,6 +323,7 @@ inline size_t zncc_row_smem(int R, int mode, const RowArgs& a, int nthreads) {
     const int pX = plane_of(span);
     b += 8ull * 4 * (pX + plane_of(span + drange - 1));
     if (mode == kModeHPair) b += 16ull * a.nch * kCS + dt_scan_bytes(nthreads / 32, a.tq);
+    if (mode == kModeHPair && dtype == 2) b += 12ull * a.nch * kCS;      // FastDT: scales, references
     return b;
 }
 
@@ -306,7 +332,9 @@ static void (*row_fn_t(int mode, int dtype))(RowBatch) {
     if (mode == kModeRaw)
         return dtype == 0 ? k_zncc_row<R, float, kModeRaw, MINB, SINGLE> : k_zncc_row<R, __half, kModeRaw, MINB, SINGLE>;
     if (mode == kModeHPair)
-        return dtype == 0 ? k_zncc_row<R, float, kModeHPair, MINB, SINGLE> : k_zncc_row<R, __half, kModeHPair, MINB, SINGLE>;
+        return dtype == 0 ? k_zncc_row<R, float, kModeHPair, MINB, SINGLE>
+                          : dtype == 1 ? k_zncc_row<R, __half, kModeHPair, MINB, SINGLE>
+                                       : k_zncc_row<R, uint8_t, kModeHPair, MINB, SINGLE>;
     return k_zncc_row<R, float, kModeWta, MINB, SINGLE>;
 }
 

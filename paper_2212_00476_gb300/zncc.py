@@ -8,8 +8,8 @@ The methods of ZnccContext carry the names of the C calls they wrap:
 
     zncc_window_stats, zncc_cost_volume, dt_aggregate, wta_disparity, zncc_run, zncc_run_host
 
-and the module-level zncc_run_batch and dt_aggregate_noalloc wrap the batched call and the
-context-free aggregation that allocates nothing. serve_create, serve_submit, serve_poll and
+and the module-level zncc_run_batch, dt_aggregate_noalloc and fastdt_codec wrap the batched
+call, the context-free aggregation that allocates nothing and the FastDT code on the device. serve_create, serve_submit, serve_poll and
 serve_destroy wrap the serving calls (a handle in, numpy arrays for the host images), and
 ZnccServer bundles them.
 """
@@ -27,7 +27,7 @@ LIB_PATH = os.path.join(_PKG, "libzncc.so")
 
 ZNCC_OK, ZNCC_EINVAL, ZNCC_ENOMEM, ZNCC_ECUDA, ZNCC_EBUSY, ZNCC_ENOTREADY, ZNCC_ETIMEOUT, \
     ZNCC_EUNSUPPORTED = range(8)
-ZNCC_F32, ZNCC_F16 = 0, 1
+ZNCC_F32, ZNCC_F16, ZNCC_I8 = 0, 1, 2
 ZNCC_TUNE_ROW_MINB2, ZNCC_TUNE_ROW_SPB, ZNCC_TUNE_H_TQ, ZNCC_TUNE_V_TQ = 1, 2, 3, 4
 STATUS_NAMES = ["ZNCC_OK", "ZNCC_EINVAL", "ZNCC_ENOMEM", "ZNCC_ECUDA", "ZNCC_EBUSY",
                 "ZNCC_ENOTREADY", "ZNCC_ETIMEOUT", "ZNCC_EUNSUPPORTED"]
@@ -44,6 +44,7 @@ SIGNATURES = [
     ("dt_aggregate", _i, [_vp, _vp, _i, _vp, _i, _f, _f, _i]),
     ("dt_aggregate_noalloc", _i, [_vp, _i, _i, _i, _i, _vp, _i, _f, _f, _i, _vp]),
     ("wta_disparity", _i, [_vp, _vp, _i, _vp]),
+    ("fastdt_codec", _i, [_vp, _i, _vp, _vp, _vp]),
     ("zncc_run", _i, [_vp, _vp, _vp, _i, _f, _f, _i, _i, _vp]),
     ("zncc_run_host", _i, [_vp, _vp, _vp, _i, _f, _f, _i, _i, _vp]),
     ("zncc_run_batch", _i, [_vp, _vp, _vp, _vp, _vp, _i, _f, _f, _i, _i]),
@@ -126,6 +127,17 @@ def dt_aggregate_noalloc(guide, cost, sigma_s, sigma_r, iters, dtype=ZNCC_F32, s
     s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
     st = lib().dt_aggregate_noalloc(_ptr(guide), guide.stride(0), W, H, D, _ptr(cost), int(dtype),
                                     float(sigma_s), float(sigma_r), int(iters), s)
+    if st != ZNCC_OK:
+        raise ZnccError(st, lib().zncc_last_error(None).decode())
+
+
+def fastdt_codec(values, codes=None, decoded=None, stream=None):
+    """The FastDT codes (uint8 device tensor) of int16 device values and the values they
+    decode to (int16), on the device (Sec. IV-C)."""
+    n = int(values.numel())
+    s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    st = lib().fastdt_codec(_ptr(values), n, None if codes is None else _ptr(codes),
+                            None if decoded is None else _ptr(decoded), s)
     if st != ZNCC_OK:
         raise ZnccError(st, lib().zncc_last_error(None).decode())
 
