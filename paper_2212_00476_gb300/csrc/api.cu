@@ -75,9 +75,7 @@ struct zncc_ctx {
     int W = 0, H = 0, D = 0, win = 0, r = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t cur = nullptr;       // the stream launches go to (stream, or side)
-    cudaStream_t side = nullptr;      // second stream for work independent of the cost kernel
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_first = nullptr;
+    cudaStream_t cur = nullptr;       // the stream launches go to
     std::string err;
     float4* coefH = nullptr;      // [H][W]       horizontal DT coefficients
     float4* coefV = nullptr;      // [W][H]       vertical DT coefficients
@@ -176,12 +174,6 @@ void release(zncc_ctx* c) {
     c->nahat = c->nmul = 0;
     free_dev(c->img);
     free_dev(c->disp);
-    if (c->side) cudaStreamDestroy(c->side);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
-    if (c->ev_first) cudaEventDestroy(c->ev_first);
-    c->side = nullptr;
-    c->ev_fork = c->ev_join = c->ev_first = nullptr;
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     c->records.clear();
@@ -563,6 +555,40 @@ zncc_status ensure_ahat(zncc_ctx* c, int nahat, int nmul) {
     return ZNCC_OK;
 }
 
+// Pass pair p of the A_hat chain (A_hat_p from A_hat_{p-1}, or from ones for p = 1) for every
+// pair of the batch, one launch, with the multipliers of pair p when it has a map (p >= pfirst).
+zncc_status run_ahat(zncc_ctx* lc, const PairIO* io, int n, int p, int pfirst, int npairs, float K,
+                     float inv_sr255, float s2, bool fast) {
+    AhatBatch b;
+    memset(&b, 0, sizeof(b));
+    b.npairs = n;
+    b.horiz = (p % 2) == 1;
+    b.K = K;
+    b.inv_sr255 = inv_sr255;
+    b.s2 = s2;
+    // FastDT passes read -E (times A_hat / T) and write values scaled by T, ready to round
+    b.xscale = fast ? 1.0f / kFastT : 1.0f;
+    b.yscale = fast ? s2 * kFastT : s2;
+    for (int i = 0; i < n; ++i) {
+        zncc_ctx* c = io[i].c;
+        const size_t npix = (size_t)c->W * c->H;
+        AhatArgs& a = b.p[i];
+        a.guide = io[i].left;
+        a.pitch = io[i].pitch;
+        a.W = c->W;
+        a.H = c->H;
+        a.ain = p == 1 ? nullptr : c->ahat + (size_t)(p - 2) * npix;
+        a.aout = c->ahat + (size_t)(p - 1) * npix;
+        a.mulmap = p >= pfirst && p <= npairs ? c->mulmap + (size_t)(p - pfirst) * npix : nullptr;
+        a.in_mul = p - 1 >= pfirst ? 1 : 0;
+        a.line0 = b.total_lines;
+        b.total_lines += b.horiz ? c->H : c->W;
+        b.nmax = std::max(b.nmax, b.horiz ? c->W : c->H);
+    }
+    ZNCC_LAUNCH(lc, K_AHAT, launch_ahat_pair(b, lc->cur), "A_hat pass pair");
+    return ZNCC_OK;
+}
+
 // The fused path over n pairs that share the DT parameters and the storage type: the
 // coefficients, the cost kernel with the first horizontal pair, the remaining pairs, and
 // WTA in the last vertical pair; every step is one launch for all pairs (one per window
@@ -582,75 +608,36 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
     const float K = (float)exp(-1.0 / (double)sigma_s);
     const float inv_sr255 = (float)(1.0 / (255.0 * (double)sigma_r));
     const int npairs = 2 * iters;
-    // The DT weights of the line pairs (and the A_hat maps) depend only on the guide: they are
-    // computed on a second stream, concurrently with the cost kernel (which computes the
-    // weights of its own rows), and joined before the first line pair.
+    // The DT weights of the line pairs (and the A_hat maps) depend only on the guide; they are
+    // computed first, on the same stream: the persistent cost kernel fills every SM, so work
+    // on a second stream would only run after it anyway (the cost kernel computes the weights
+    // of its own rows).
     // Half storage keeps each stored pair p >= 2 divided by A_hat_p (the per-pixel bound of
     // |cost|), so that it stays inside the half range wherever the guide isolates a pixel;
     // the next pair multiplies it back. The factor is the same for every d of a pixel.
-    // FastDT codes (Sec. IV-C) are normalised that way from the cost kernel's pair on, so the
-    // cost kernel waits for the first map (ev_first) instead of running beside the chain.
+    // FastDT codes (Sec. IV-C) are normalised that way from the cost kernel's pair on.
     const bool norm = (dt == 1 && npairs > 2) || dt == 2;
     const int pfirst = dt == 2 ? 1 : 2;             // the first pair with a multiplier map
     if (norm)
         for (int i = 0; i < n; ++i)
             if (ensure_ahat(io[i].c, npairs - 1, npairs - pfirst + 1) != ZNCC_OK)
                 return fail(lc, ZNCC_ENOMEM, io[i].c->err);
-    if (!lc->side) {
-        ZNCC_CUDA(lc, cudaStreamCreateWithFlags(&lc->side, cudaStreamNonBlocking), "side stream");
-        ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_fork, cudaEventDisableTiming), "fork event");
-        ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_join, cudaEventDisableTiming), "join event");
-        ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_first, cudaEventDisableTiming), "first map event");
+    ZNCC_TRY(run_coef(lc, io, n, sigma_s, sigma_r));
+    for (int p = 1; norm && p <= npairs - 1; ++p)
+        ZNCC_TRY(run_ahat(lc, io, n, p, pfirst, npairs, K, inv_sr255, s2, dt == 2));
+    // the last pair's multipliers (A_hat_{npairs-1}, s2): its result is not stored
+    for (int i = 0; norm && i < n; ++i) {
+        const int W = io[i].c->W, H = io[i].c->H;
+        const size_t npix = (size_t)W * H;
+        const float* ain = npairs - 1 >= pfirst ? io[i].c->ahat + (size_t)(npairs - 2) * npix : nullptr;
+        ZNCC_LAUNCH(lc, K_AHAT,
+                    launch_mulmap(ain, dt == 2 ? 1.0f / kFastT : 1.0f, s2, W, H, (npairs % 2) == 1,
+                                  io[i].c->mulmap + (size_t)(npairs - pfirst) * npix, lc->cur),
+                    "A_hat multipliers");
     }
-    ZNCC_CUDA(lc, cudaEventRecord(lc->ev_fork, lc->stream), "fork");
-    ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->side, lc->ev_fork, 0), "fork");
-    lc->cur = lc->side;
-    zncc_status st = run_coef(lc, io, n, sigma_s, sigma_r);
-    // the multipliers of pair p: (A_hat_{p-1}, or 1 for the raw cost of p = 1 and for the
-    // half volume of p = 2; s2 / A_hat_p, or s2 for the last pair, which is not stored)
-    auto mulmaps = [&](int p0, int p1) {
-        for (int i = 0; i < n && st == ZNCC_OK; ++i)
-            for (int pair = p0; pair <= p1 && st == ZNCC_OK; ++pair) {
-                const int W = io[i].c->W, H = io[i].c->H;
-                const size_t npix = (size_t)W * H;
-                const float* ain = pair - 1 >= pfirst ? io[i].c->ahat + (size_t)(pair - 2) * npix : nullptr;
-                const float* aout = pair < npairs ? io[i].c->ahat + (size_t)(pair - 1) * npix : nullptr;
-                cudaError_t e = launch_mulmap(ain, aout, s2, W, H, (pair % 2) == 1,
-                                              io[i].c->mulmap + (size_t)(pair - pfirst) * npix, lc->cur);
-                if (e != cudaSuccess) st = cuda_fail(lc, e, "A_hat multipliers");
-            }
-    };
-    for (int p = 1; norm && p <= npairs - 1 && st == ZNCC_OK; ++p) {
-        LinePass lp[kMaxBatch];
-        for (int i = 0; i < n; ++i) {
-            const size_t npix = (size_t)io[i].c->W * io[i].c->H;
-            lp[i].vol = io[i].c->ahat + (size_t)(p - 1) * npix;
-            lp[i].src = p == 1 ? nullptr : io[i].c->ahat + (size_t)(p - 2) * npix;
-            lp[i].ones = p == 1;
-            lp[i].dstride = 1;
-            lp[i].dcount = 1;
-            lp[i].dtype = 0;
-            lp[i].horiz = (p % 2) == 1;
-            lp[i].s2 = s2;
-            lp[i].force_tq = 1;
-        }
-        st = run_lines(lc, ctxs, lp, n, K_AHAT);
-        if (dt == 2 && p == 1 && st == ZNCC_OK) {
-            mulmaps(1, 1);
-            const cudaError_t e = st == ZNCC_OK ? cudaEventRecord(lc->ev_first, lc->side) : cudaSuccess;
-            if (e != cudaSuccess) st = cuda_fail(lc, e, "first map");
-        }
-    }
-    if (norm && st == ZNCC_OK) mulmaps(dt == 2 ? 2 : pfirst, npairs);
-    lc->cur = lc->stream;
-    ZNCC_TRY(st);
-    ZNCC_CUDA(lc, cudaEventRecord(lc->ev_join, lc->side), "join");
-    if (dt == 2) {
-        ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_first, 0), "first map");
+    if (dt == 2)
         for (int i = 0; i < n; ++i) io[i].mulmap1 = io[i].c->mulmap;
-    }
     ZNCC_TRY(run_rows(lc, io, n, kModeHPair, dt, s2, K, inv_sr255, K_ZNCC_HPAIR, "ZNCC + horizontal DT pair"));
-    ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_join, 0), "join of the weights stream");
     for (int pair = 2; pair <= npairs; ++pair) {    // pair 1 is the cost kernel's
         LinePass lp[kMaxBatch];
         for (int i = 0; i < n; ++i) {

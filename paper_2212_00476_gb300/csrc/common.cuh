@@ -62,7 +62,8 @@ __device__ __forceinline__ void ld4(const __half* p, int nvalid, bool vec, float
     }
 }
 
-// FastDT codes: four per 32-bit word (4-byte aligned groups of a padded pixel stride)
+// FastDT codes: four per 32-bit word (4-byte aligned groups of a padded pixel stride), read
+// as -E (the caller scales by A_hat / kFastT)
 __device__ __forceinline__ void ld4(const uint8_t* p, int nvalid, bool vec, float (&o)[4]) {
     (void)nvalid;
     (void)vec;
@@ -90,46 +91,60 @@ __device__ __forceinline__ void st4(__half* p, int nvalid, bool vec, const float
 }
 
 // ---- FastDT storage (Sec. IV-C): 8-bit codes of near-zero-mean 16-bit costs -------------
-// A stored value is e = (v(d_arb) - v(d)) / A_hat scaled by kFastT and rounded to a 16-bit
-// integer (values that do no better than d_arb are 0); its code keeps the six bits next to
+// A stored value is E = rint(kFastT * (v(d_arb) - v(d)) / A_hat) as a 16-bit integer
+// (values that do no better than d_arb, E >= 0, are 0); its code keeps the six bits next to
 // the leading ones of the two's-complement value (bits 14..9, 10..5 or 6..1) and a 2-bit flag
-// for the position. Four codes (four consecutive disparities) share a 32-bit word.
+// for the position (01, 10, 11). Four codes (four consecutive disparities) share a 32-bit
+// word, the lowest disparity in the lowest byte. The code, branch-free: E < -2048 keeps bits
+// 14..9, E < -128 bits 10..5, else bits 6..1.
 constexpr float kFastT = 16383.0f;
 
 __device__ __forceinline__ unsigned fastdt_encode(int value) {
-    if (value >= 0) return 0u;
-    const unsigned v = (unsigned)value & 0xFFFFu;
-    if (((v >> 11) & 0xFu) != 0xFu) return (((v >> 9) & 0x3Fu) << 2) | 1u;
-    if (((v >> 7) & 0xFu) != 0xFu) return (((v >> 5) & 0x3Fu) << 2) | 2u;
-    return (((v >> 1) & 0x3Fu) << 2) | 3u;
+    const int t = (value < -2048) + (value < -128);          // 2, 1, 0
+    const int low = 1 + 4 * t;                                // lowest kept bit: 9, 5, 1
+    const unsigned code = (((unsigned)(value >> low) & 0x3Fu) << 2) | (unsigned)(3 - t);
+    return value < 0 ? code : 0u;
 }
 
-__device__ __forceinline__ int fastdt_decode(unsigned code) {
-    if (code == 0u) return 0;
-    const unsigned flag = code & 3u;
-    const int low = flag == 1u ? 9 : (flag == 2u ? 5 : 1);
-    const unsigned v = ((code >> 2) << low) | (0xFFFFu << (low + 6));   // ones above, zeros below
-    return (int)(short)(v & 0xFFFFu);
+// E from the values, normalised and scaled by kFastT (at least -32768): ref - v rounded to the
+// nearest integer, ties to even, by adding 1.5 * 2^23 (exact for |E| < 2^22; larger E is
+// positive and codes to 0 either way).
+__device__ __forceinline__ int fastdt_quantize(float ref, float v) {
+    const float y = fmaxf(ref - v, -32768.0f);
+    return __float_as_int(y + 12582912.0f) - 0x4B400000;
 }
 
-// the 16-bit value of e (clamped to the int16 range)
-__device__ __forceinline__ int fastdt_quantize(float e) {
-    return max(-32768, min(32767, __float2int_rn(kFastT * e)));
-}
-
-// four codes from a word -> the normalised values -E / kFastT (larger is better)
-__device__ __forceinline__ void fastdt_unpack(unsigned word, float (&o)[4]) {
+// four values of E -> a word of four codes (entries j >= nvalid code 0)
+__device__ __forceinline__ unsigned fastdt_pack_codes(const int (&E)[4], int nvalid) {
+    unsigned c[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) o[j] = -(float)fastdt_decode((word >> (8 * j)) & 0xFFu) * (1.0f / kFastT);
+    for (int j = 0; j < 4; ++j) c[j] = j < nvalid ? fastdt_encode(E[j]) : 0u;
+    return __byte_perm(__byte_perm(c[0], c[1], 0x0040), __byte_perm(c[2], c[3], 0x0040), 0x5410);
 }
 
-// four normalised values and the reference -> a word of four codes
+// four values and the reference (normalised, scaled by kFastT) -> a word of four codes
 __device__ __forceinline__ unsigned fastdt_pack(const float (&v)[4], float ref, int nvalid) {
-    unsigned w = 0u;
+    int E[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (j < nvalid) w |= fastdt_encode(fastdt_quantize(ref - v[j])) << (8 * j);
-    return w;
+    for (int j = 0; j < 4; ++j) E[j] = fastdt_quantize(ref, v[j]);
+    return fastdt_pack_codes(E, nvalid);
+}
+
+// A word of four codes -> -E of each as an exact float (code 0 -> 0; larger is better). A code
+// with six bits s and flag f stands for E = (s - 64) * 2^low, low = 9, 5, 1 for f = 1, 2, 3:
+// the six bits in place, ones above them, zeros below. Per byte, 64 - s becomes a float by
+// placing it in the mantissa of 2^23, and 2^low comes from a four-entry table of exponent
+// bytes indexed by f (2^9, 2^5, 2^1, and 0 for f = 0).
+__device__ __forceinline__ void fastdt_unpack(unsigned word, float (&o)[4]) {
+    const unsigned F = word & 0x03030303u;
+    const unsigned M = 0x40404040u - ((word >> 2) & 0x3F3F3F3Fu);
+    const unsigned sel[4] = {((F << 12) & 0x3000u) | 0x444u, ((F << 4) & 0x3000u) | 0x444u,
+                             ((F >> 4) & 0x3000u) | 0x444u, ((F >> 12) & 0x3000u) | 0x444u};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float m = __int_as_float(__byte_perm(M, 0x4B000000u, 0x7440u | j)) - 8388608.0f;
+        o[j] = m * __int_as_float(__byte_perm(0x40424400u, 0u, sel[j]));
+    }
 }
 
 __device__ __forceinline__ void lds4(const uint8_t* p, float (&o)[4]) {

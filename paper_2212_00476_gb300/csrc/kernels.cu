@@ -128,6 +128,128 @@ __global__ void k_dt_coef(const __grid_constant__ CoefBatch b) {
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// A_hat pass pair: the scaled pair of Eqs. (3)-(6) on one plane, one warp per line. The warp
+// first stages the line's weights and inputs in shared memory, 16 positions a lane per
+// round with every load of the round in flight at once; then lane l takes positions
+// [l*seg, (l+1)*seg) (seg odd, so that the lanes' sweeps fall on distinct banks): a sweep
+// with zero carry gives the lane's affine map x -> P x + u (P the product of its weights), a
+// warp scan composes the maps, and a second sweep from the true carry computes the values;
+// the backward pass likewise from the right.
+constexpr int kAhatWarps = 4;
+constexpr int kAhatArrays = 3;      // per line: weights, inputs, values
+
+__global__ void __launch_bounds__(32 * kAhatWarps) k_ahat_pair(const __grid_constant__ AhatBatch b) {
+    extern __shared__ float ahat_smem[];
+    griddep_wait();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gline = blockIdx.x * kAhatWarps + wib;
+    if (gline >= b.total_lines) return;
+    int pi = 0;
+    while (pi + 1 < b.npairs && gline >= b.p[pi + 1].line0) ++pi;
+    const AhatArgs& a = b.p[pi];
+    const int line = gline - a.line0;
+    const bool horiz = b.horiz != 0;
+    const int W = a.W, n = horiz ? a.W : a.H;
+    const uint8_t* g = a.guide + (horiz ? (size_t)line * a.pitch : (size_t)line);
+    const size_t gstep = horiz ? 1 : (size_t)a.pitch;             // guide step along the line
+    const float* ain = a.ain ? a.ain + (horiz ? (size_t)line * W : (size_t)line) : nullptr;
+    const size_t astep = horiz ? 1 : (size_t)W;                   // plane step along the line
+    float* ws = ahat_smem + (size_t)wib * kAhatArrays * b.nmax;   // w(q): the step q-1 -> q
+    float* xs = ws + b.nmax;                                      // input
+    float* fs = xs + b.nmax;                                      // forward values, then A_hat
+    constexpr int kR = 16;
+    for (int base = 0; base < n; base += 32 * kR) {
+        int gc[kR], gp[kR];
+        float in[kR];
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+            const int q = base + k * 32 + lane;
+            const bool ok = q < n;
+            gc[k] = ok ? g[(size_t)q * gstep] : 0;
+            gp[k] = ok && q >= 1 ? g[(size_t)(q - 1) * gstep] : 0;
+            in[k] = ok && ain ? ain[(size_t)q * astep] : 1.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+            const int q = base + k * 32 + lane;
+            if (q < n) {    // the expression of k_dt_coef
+                ws[q] = q >= 1 ? b.K * expf(-fabsf((float)(gc[k] - gp[k])) * b.inv_sr255) : 0.0f;
+                xs[q] = in[k];
+            }
+        }
+    }
+    __syncwarp();
+    const int seg = ((n + 31) / 32) | 1;
+    const int p0 = min(n, lane * seg), p1 = min(n, p0 + seg);
+
+    // forward: f(p) = c(p) + w(p) f(p-1)
+    float P = 1.0f, u = 0.0f;
+#pragma unroll 4
+    for (int q = p0; q < p1; ++q) {
+        const float w = ws[q];
+        u = fmaf(w, u, xs[q]);
+        P *= w;
+    }
+    for (int off = 1; off < 32; off <<= 1) {
+        const float P2 = __shfl_up_sync(kFull, P, off), u2 = __shfl_up_sync(kFull, u, off);
+        if (lane >= off) {
+            u = fmaf(P, u2, u);
+            P *= P2;
+        }
+    }
+    float x = __shfl_up_sync(kFull, u, 1);
+    if (lane == 0) x = 0.0f;
+#pragma unroll 4
+    for (int q = p0; q < p1; ++q) {
+        x = fmaf(ws[q], x, xs[q]);
+        fs[q] = x;
+    }
+    // backward: h(p) = f(p) + w(p+1) h(p+1); w(n) = 0 (the weights are never written again)
+    P = 1.0f;
+    u = 0.0f;
+#pragma unroll 4
+    for (int q = p1 - 1; q >= p0; --q) {
+        const float w = q + 1 < n ? ws[q + 1] : 0.0f;
+        u = fmaf(w, u, fs[q]);
+        P *= w;
+    }
+    for (int off = 1; off < 32; off <<= 1) {
+        const float P2 = __shfl_down_sync(kFull, P, off), u2 = __shfl_down_sync(kFull, u, off);
+        if (lane + off < 32) {
+            u = fmaf(P, u2, u);
+            P *= P2;
+        }
+    }
+    x = __shfl_down_sync(kFull, u, 1);
+    if (lane == 31) x = 0.0f;
+#pragma unroll 4
+    for (int q = p1 - 1; q >= p0; --q) {
+        x = fmaf(q + 1 < n ? ws[q + 1] : 0.0f, x, fs[q]);
+        fs[q] = b.s2 * x;
+    }
+    __syncwarp();
+    float* aout = a.aout + (horiz ? (size_t)line * W : (size_t)line);
+    float2* mm = a.mulmap ? a.mulmap + (size_t)line * n : nullptr;
+#pragma unroll 8
+    for (int q = lane; q < n; q += 32) {
+        const float A = fs[q];
+        aout[(size_t)q * astep] = A;
+        if (mm) mm[q] = make_float2(a.in_mul ? b.xscale * xs[q] : 1.0f, b.yscale / A);
+    }
+    griddep_launch_dependents();
+}
+
+cudaError_t launch_ahat_pair(const AhatBatch& b, cudaStream_t st) {
+    const size_t smem = (size_t)kAhatWarps * kAhatArrays * b.nmax * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_ahat_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    launch_config(cfg, attr, dim3((b.total_lines + kAhatWarps - 1) / kAhatWarps), dim3(32 * kAhatWarps), smem, st, 1);
+    return cudaLaunchKernelEx(&cfg, k_ahat_pair, b);
+}
+
 long long dt_coef_threads(int W, int H) {
     return (long long)kL * ((long long)H * ((W + kL - 1) / kL) + (long long)W * ((H + kL - 1) / kL));
 }
@@ -393,7 +515,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
                 q += a.elem_stride;
             }
         }
-        if (has_mul && active) {
+        if (has_mul && active) {         // (FastDT codes always have multipliers)
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 const float m = mul[i].x;
@@ -467,36 +589,49 @@ size_t line_pair_smem_bytes(int mode, int dtype, const LineArgs& a, bool co_asyn
     return line_stage_bytes(dtype, a) + (size_t)a.lpc * (per_pos * a.nch * kCS + dt_scan_bytes(nwl_all, a.tq));
 }
 
-__global__ void k_mulmap(const float* __restrict__ ain, const float* __restrict__ aout, float s2, int W, int H,
-                         int horiz, float2* __restrict__ out) {
+// The multipliers of the last pass pair (its result is not stored): (xscale * ain, or 1; s2).
+__global__ void k_mulmap(const float* __restrict__ ain, float xscale, float s2, int W, int H, int horiz,
+                         float2* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)W * H) return;
     const int n = horiz ? W : H;
     const int line = (int)(i / n), pos = (int)(i - (long long)line * n);
     const size_t pix = horiz ? (size_t)line * W + pos : (size_t)pos * W + line;
-    out[i] = make_float2(ain ? ain[pix] : 1.0f, aout ? s2 / aout[pix] : s2);
+    out[i] = make_float2(ain ? xscale * ain[pix] : 1.0f, s2);
 }
 
-cudaError_t launch_mulmap(const float* ain, const float* aout, float s2, int W, int H, bool horiz, float2* out,
+cudaError_t launch_mulmap(const float* ain, float xscale, float s2, int W, int H, bool horiz, float2* out,
                           cudaStream_t st) {
     const long long n = (long long)W * H;
-    k_mulmap<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ain, aout, s2, W, H, horiz ? 1 : 0, out);
+    k_mulmap<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ain, xscale, s2, W, H, horiz ? 1 : 0, out);
     return cudaGetLastError();
 }
 
-// The FastDT code of each 16-bit value and the value it decodes to (Sec. IV-C).
+// The FastDT code of each 16-bit value and the value it decodes to (Sec. IV-C), four values a
+// thread through the packing and unpacking of the DT kernels.
 __global__ void k_fastdt_codec(const int16_t* __restrict__ values, int n, uint8_t* __restrict__ codes,
                                int16_t* __restrict__ decoded) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const unsigned c = fastdt_encode((int)values[i]);
-    if (codes) codes[i] = (uint8_t)c;
-    if (decoded) decoded[i] = (int16_t)fastdt_decode(c);
+    const long long i0 = 4ll * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 >= n) return;
+    const int nvalid = (int)min(4ll, n - i0);
+    int E[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) E[j] = j < nvalid ? (int)values[i0 + j] : 0;
+    const unsigned word = fastdt_pack_codes(E, nvalid);
+    float o[4];
+    fastdt_unpack(word, o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (j < nvalid) {
+            if (codes) codes[i0 + j] = (uint8_t)(word >> (8 * j));
+            if (decoded) decoded[i0 + j] = (int16_t)(-(int)o[j]);
+        }
 }
 
 cudaError_t launch_fastdt_codec(const int16_t* values, int n, uint8_t* codes, int16_t* decoded, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    k_fastdt_codec<<<(n + 255) / 256, 256, 0, st>>>(values, n, codes, decoded);
+    const int threads = (n + 3) / 4;
+    k_fastdt_codec<<<(threads + 255) / 256, 256, 0, st>>>(values, n, codes, decoded);
     return cudaGetLastError();
 }
 

@@ -127,6 +127,26 @@ struct CoefBatch {
     CoefArgs p[kMaxBatch];
 };
 cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st);
+
+// One DT pass pair over an A_hat plane (the response of an all-ones plane, Sec. IV-C), a
+// line per warp, the weights from the guide: aout = pair(ain, or ones), and the pass's
+// multipliers (in_mul ? xscale * ain : 1, yscale / aout) in its line order.
+struct AhatArgs {
+    const uint8_t* guide;
+    int pitch, W, H;
+    const float* ain;         // [H][W], or nullptr for an all-ones input
+    float* aout;              // [H][W]
+    float2* mulmap;           // [nlines][n] or nullptr
+    int in_mul;               // mulmap.x = ain (1) or 1 (0)
+    int line0;                // first line of this pair in the launch
+};
+struct AhatBatch {
+    int npairs, total_lines, horiz, nmax;
+    float K, inv_sr255, s2;
+    float xscale, yscale;     // multiplier factors: 1 and s2, or 1/T and s2 T for FastDT codes
+    AhatArgs p[kMaxBatch];
+};
+cudaError_t launch_ahat_pair(const AhatBatch& b, cudaStream_t st);
 long long dt_coef_threads(int W, int H);
 cudaError_t launch_wta_volume(const void* cost, int dtype, int W, int H, int D, uint16_t* disp,
                               cudaStream_t st);
@@ -145,7 +165,7 @@ struct WtaFinishBatch {
 cudaError_t launch_wta_finish(const WtaFinishBatch& b, cudaStream_t st);
 // The multiplier map of a pass along rows (horiz) or columns of a W x H image: for each
 // (line, position), (ain ? ain[pix] : 1, aout ? s2 / aout[pix] : s2), ain/aout [H][W].
-cudaError_t launch_mulmap(const float* ain, const float* aout, float s2, int W, int H, bool horiz, float2* out,
+cudaError_t launch_mulmap(const float* ain, float xscale, float s2, int W, int H, bool horiz, float2* out,
                           cudaStream_t st);
 cudaError_t launch_fastdt_codec(const int16_t* values, int n, uint8_t* codes, int16_t* decoded, cudaStream_t st);
 
