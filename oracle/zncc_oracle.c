@@ -23,7 +23,14 @@
  *   - "scaled" form: each pass multiplies its input term by (1-K), K = exp(-1/sigma_s).
  *     It equals the literal chain times (1-K)^(4*iters) and keeps |C| <= 1;
  *   - iterations repeat the 4-pass chain (L2R, R2L, U2D, D2U) with the same sigmas;
- *   - WTA returns the smallest d reaching the maximum aggregated value (argmin of 1-C).
+ *   - WTA returns the smallest d reaching the maximum aggregated value (argmin of 1-C);
+ *   - FastDT: d_arb = 0 (the paper's choice); the store happens after every pass pair but
+ *     the last (the last feeds WTA), on e = (C(d_arb) - C(d)) / A_hat with A_hat the same
+ *     pass pairs applied to an all-ones plane (|C| <= A_hat, so e lies in [-2, 2]), scaled
+ *     by T = 16383 (the largest T with 2T inside int16; the paper's T = 21 belongs to its
+ *     unnormalised costs), rounded to nearest (ties to even) and clamped to int16; the
+ *     decoded value -E/T * A_hat replaces C (the offset C(d_arb) is not added back: a
+ *     per-pixel offset changes no argmax, and the paper's Eq. (DT_new) drops it too).
  *
  * Layouts: images uint8 [H][W] (row pitch = W); cost volumes double [H][W][nd], the
  * disparity axis fastest.
