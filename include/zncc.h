@@ -91,6 +91,16 @@ zncc_status zncc_window_stats(zncc_ctx* ctx, const uint8_t* img, int pitch, int3
 zncc_status zncc_cost_volume(zncc_ctx* ctx, const uint8_t* left, const uint8_t* right,
                              int pitch, void* cost, zncc_dtype dtype);
 
+/* The same cost volume by the paper's "original" progressive scan (the comparison method of
+ * Sec. V-B, Fig. ZNCC_compare): per (row, disparity) the window sum of products slides along
+ * the row, one column of 2r+1 products in and one out, every column recomputed from the
+ * pixels (no reuse across rows). An ablation baseline for zncc_cost_volume: identical
+ * values (the integer numerator is exact, the normalization the same expression), slower.
+ * Allocates 8 * (2W + D - 1) * H bytes of context scratch for window statistics on first use.
+ * cost: device [H][W][D] of `dtype` (ZNCC_F32 or ZNCC_F16). */
+zncc_status zncc_cost_volume_scan(zncc_ctx* ctx, const uint8_t* left, const uint8_t* right,
+                                  int pitch, void* cost, zncc_dtype dtype);
+
 /* DT cost aggregation in place (Sec. III-B, Eqs. (3)-(6) with the weights of Eq. (11)),
  * `iters` times the pass chain left-to-right, right-to-left, up-to-down, down-to-up.
  * Weights: W = K * exp(-|G(p) - G(q)| / sigma_r), K = exp(-1/sigma_s), G = guide / 255

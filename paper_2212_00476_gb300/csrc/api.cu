@@ -52,11 +52,11 @@ namespace {
 // Kernel kinds for per-kernel timing (zncc_profile_*).
 enum Kind {
     K_STATS = 0, K_COEF, K_ZNCC_RAW, K_ZNCC_HPAIR, K_ZNCC_WTA, K_DT_HPAIR, K_DT_VPAIR,
-    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_AHAT, K_WTA_FINISH, K_NKINDS
+    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_AHAT, K_WTA_FINISH, K_ZNCC_SCAN, K_NKINDS
 };
 const char* const kKindNames[K_NKINDS] = {
     "window_stats", "dt_coef", "zncc_cost", "zncc_cost_hpair", "zncc_cost_wta",
-    "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume", "ahat_pair", "wta_finish"};
+    "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume", "ahat_pair", "wta_finish", "zncc_cost_scan"};
 
 struct ProfRecord {
     int kind, ev0, ev1;
@@ -91,6 +91,7 @@ struct zncc_ctx {
     int h_tq = 0, v_tq = 0;       // DT pairs: forced lanes per chunk (0 = automatic)
     int num_sms = 0;
     std::vector<LinePlan> plans;  // line-pass launch shapes, by pass signature
+    int2* scan_stats = nullptr;   // (progressive scan) packed statistics: left [H][W], right [H][W+D-1]
     uint8_t* img = nullptr;       // device copies for zncc_run_host: 2 x [H][W]
     uint16_t* disp = nullptr;     // [H][W]
     bool profiling = false;
@@ -174,6 +175,7 @@ void release(zncc_ctx* c) {
     c->nahat = c->nmul = 0;
     free_dev(c->img);
     free_dev(c->disp);
+    free_dev(c->scan_stats);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     c->records.clear();
@@ -820,6 +822,35 @@ zncc_status zncc_cost_volume(zncc_ctx* c, const uint8_t* left, const uint8_t* ri
     if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
     PairIO io{c, left, right, pitch, nullptr, cost, c->D};
     return run_rows(c, &io, 1, kModeRaw, dtype, 0.0f, 0.0f, 0.0f, K_ZNCC_RAW, "ZNCC cost");
+}
+
+zncc_status zncc_cost_volume_scan(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch,
+                                  void* cost, zncc_dtype dtype) {
+    if (!c) return ZNCC_EINVAL;
+    c->err.clear();
+    ZNCC_TRY(check_images(c, left, right, pitch));
+    if (!cost) return fail(c, ZNCC_EINVAL, "cost pointer is NULL");
+    if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
+    const size_t nl = (size_t)c->W * c->H, nr = (size_t)(c->W + c->D - 1) * c->H;
+    if (!c->scan_stats) ZNCC_TRY(alloc_dev(c, (void**)&c->scan_stats, (nl + nr) * sizeof(int2), "scan statistics"));
+    int2* pl = c->scan_stats;
+    int2* pr = c->scan_stats + nl;
+    ZNCC_LAUNCH(c, K_STATS, launch_window_stats(left, pitch, c->W, c->H, c->r, 0, c->W, nullptr, nullptr, nullptr,
+                                                pl, c->cur), "window statistics (left)");
+    ZNCC_LAUNCH(c, K_STATS, launch_window_stats(right, pitch, c->W, c->H, c->r, -(c->D - 1), c->W + c->D - 1,
+                                                nullptr, nullptr, nullptr, pr, c->cur), "window statistics (right)");
+    ScanArgs a;
+    a.left = left;
+    a.right = right;
+    a.pitch = pitch;
+    a.W = c->W;
+    a.H = c->H;
+    a.D = c->D;
+    a.packL = pl;
+    a.packR = pr;
+    a.vol = cost;
+    ZNCC_LAUNCH(c, K_ZNCC_SCAN, launch_zncc_scan(c->r, a, dtype, c->cur), "progressive-scan ZNCC");
+    return ZNCC_OK;
 }
 
 zncc_status dt_aggregate(zncc_ctx* c, const uint8_t* guide, int pitch, void* cost, zncc_dtype dtype,

@@ -165,6 +165,19 @@ struct WtaFinishBatch {
 cudaError_t launch_wta_finish(const WtaFinishBatch& b, cudaStream_t st);
 // The multiplier map of a pass along rows (horiz) or columns of a W x H image: for each
 // (line, position), (ain ? ain[pix] : 1, aout ? s2 / aout[pix] : s2), ain/aout [H][W].
+// The progressive-scan ZNCC (ablation baseline): packL [H][W] and packR [H][W + D - 1]
+// hold (S, inv_sigma bits) of the window centred at x (left) and at x - d (right, centre c
+// at index c + D - 1), from k_window_stats.
+struct ScanArgs {
+    const uint8_t* left;
+    const uint8_t* right;
+    int pitch, W, H, D;
+    const int2* packL;
+    const int2* packR;
+    void* vol;                // [H][W][D] float or half
+};
+cudaError_t launch_zncc_scan(int R, const ScanArgs& a, int dtype, cudaStream_t st);
+
 cudaError_t launch_mulmap(const float* ain, float xscale, float s2, int W, int H, bool horiz, float2* out,
                           cudaStream_t st);
 cudaError_t launch_fastdt_codec(const int16_t* values, int n, uint8_t* codes, int16_t* decoded, cudaStream_t st);
@@ -184,7 +197,8 @@ cudaError_t noalloc_scratch_address(void** p);
     cudaError_t launch_zncc_row_r##R(const RowBatch& b, int threads, size_t smem, int mode, int dtype, \
                                      cudaStream_t st);                                             \
     cudaError_t zncc_row_occupancy_r##R(int mode, int dtype, int threads, size_t smem, bool minb2, bool single, \
-                                        int* bps);
+                                        int* bps);                                                    \
+    cudaError_t launch_zncc_scan_r##R(const ScanArgs& a, int dtype, cudaStream_t st);
 ZNCC_DECLARE_ROW(1)
 ZNCC_DECLARE_ROW(2)
 ZNCC_DECLARE_ROW(3)

@@ -113,6 +113,24 @@ def test_cost_volume_matches_oracle(h, w, d, win):
     ctx.close()
 
 
+@pytest.mark.parametrize("h,w,d,win", COST_CASES)
+def test_progressive_scan_cost_equals_packed_cost(h, w, d, win):
+    """The progressive-scan ablation kernel gives the packed-column kernel's values bit for bit
+    (exact integer numerator, same normalization), hence the oracle's within ZNCC_TOL."""
+    p = rand_pair(h, w, max(d, 1), seed=h * 7 + w + d + win)
+    ctx = Z.ZnccContext(w, h, d, win)
+    c = gpu_cost(ctx, p.left, p.right)
+    s = torch.empty_like(c)
+    ctx.zncc_cost_volume_scan(dev(p.left), dev(p.right), s)
+    torch.cuda.synchronize()
+    assert torch.equal(c, s)
+    s16 = torch.empty((h, w, d), dtype=torch.float16, device="cuda")
+    ctx.zncc_cost_volume_scan(dev(p.left), dev(p.right), s16, Z.ZNCC_F16)
+    torch.cuda.synchronize()
+    assert torch.equal(c.half(), s16)
+    ctx.close()
+
+
 def test_cost_volume_fp16_storage_is_rounded_fp32():
     p = rand_pair(30, 90, 24, seed=9)
     ctx = Z.ZnccContext(90, 30, 24, 9)
