@@ -236,7 +236,7 @@ struct PairIO {
 };
 
 // DT coefficients of every pair (guide = left image), one launch.
-zncc_status run_coef(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, float sigma_r) {
+zncc_status run_coef(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, float sigma_r, bool rows = true) {
     CoefBatch b;
     memset(&b, 0, sizeof(b));
     b.npairs = n;
@@ -253,11 +253,13 @@ zncc_status run_coef(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, float
         a.inv_sr255 = inv;
         a.coefH = io[i].c->coefH;
         a.coefV = io[i].c->coefV;
+        a.rows = rows ? 1 : 0;
         a.thread0 = t;
-        t += dt_coef_threads(a.W, a.H);
+        t += rows ? dt_coef_threads(a.W, a.H, true) : dt_coef_col_blocks(a.W, a.H);
     }
     b.total_threads = t;
-    ZNCC_LAUNCH(lc, K_COEF, launch_dt_coef(b, lc->cur), "DT coefficients");
+    if (rows) ZNCC_LAUNCH(lc, K_COEF, launch_dt_coef(b, lc->cur), "DT coefficients");
+    else ZNCC_LAUNCH(lc, K_COEF, launch_dt_coef_cols(b, lc->cur), "DT column coefficients");
     return ZNCC_OK;
 }
 
@@ -308,6 +310,7 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
             a.mulmap = io[i].mulmap1;
             a.K = K;
             a.inv_sr255 = inv_sr255;
+            a.coefH_out = mode == kModeHPair ? c->coefH : nullptr;
             a.s2 = s2;
             a.minb2 = c->row_minb2;
             a.wta.disp = io[i].disp;
@@ -612,8 +615,9 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
     const int npairs = 2 * iters;
     // The DT weights of the line pairs (and the A_hat maps) depend only on the guide; they are
     // computed first, on the same stream: the persistent cost kernel fills every SM, so work
-    // on a second stream would only run after it anyway (the cost kernel computes the weights
-    // of its own rows).
+    // on a second stream would only run after it anyway. The cost kernel computes the
+    // coefficients of its own rows and stores them for the later horizontal pairs, so the
+    // coefficient kernel computes the columns' only.
     // Half storage keeps each stored pair p >= 2 divided by A_hat_p (the per-pixel bound of
     // |cost|), so that it stays inside the half range wherever the guide isolates a pixel;
     // the next pair multiplies it back. The factor is the same for every d of a pixel.
@@ -624,7 +628,7 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
         for (int i = 0; i < n; ++i)
             if (ensure_ahat(io[i].c, npairs - 1, npairs - pfirst + 1) != ZNCC_OK)
                 return fail(lc, ZNCC_ENOMEM, io[i].c->err);
-    ZNCC_TRY(run_coef(lc, io, n, sigma_s, sigma_r));
+    ZNCC_TRY(run_coef(lc, io, n, sigma_s, sigma_r, false));     // the cost kernel writes the rows'
     for (int p = 1; norm && p <= npairs - 1; ++p)
         ZNCC_TRY(run_ahat(lc, io, n, p, pfirst, npairs, K, inv_sr255, s2, dt == 2));
     // the last pair's multipliers (A_hat_{npairs-1}, s2): its result is not stored
@@ -939,7 +943,8 @@ zncc_status dt_aggregate_noalloc(const uint8_t* guide, int pitch, int width, int
     ca.inv_sr255 = (float)(1.0 / (255.0 * (double)sigma_r));
     ca.coefH = coefH;
     ca.coefV = coefV;
-    cb.total_threads = dt_coef_threads(width, height);
+    ca.rows = 1;
+    cb.total_threads = dt_coef_threads(width, height, true);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     e = launch_dt_coef(cb, st);
     if (e != cudaSuccess) return noalloc_cuda_fail(e, "DT coefficients");

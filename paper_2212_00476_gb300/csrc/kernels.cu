@@ -98,8 +98,9 @@ __global__ void k_dt_coef(const __grid_constant__ CoefBatch b) {
     const long long local = gid - a.thread0;
     int chunk = (int)(local / kL);
     const int i = (int)(local & (kL - 1));
-    const bool horiz = chunk < H * nchH;
-    if (!horiz) chunk -= H * nchH;
+    const int nH = a.rows ? H * nchH : 0;
+    const bool horiz = chunk < nH;
+    if (!horiz) chunk -= nH;
     const bool live = gid < b.total_threads && (horiz || chunk < W * nchV);
     const int n = horiz ? W : H;
     const int nchl = horiz ? nchH : nchV;
@@ -250,8 +251,70 @@ cudaError_t launch_ahat_pair(const AhatBatch& b, cudaStream_t st) {
     return cudaLaunchKernelEx(&cfg, k_ahat_pair, b);
 }
 
-long long dt_coef_threads(int W, int H) {
-    return (long long)kL * ((long long)H * ((W + kL - 1) / kL) + (long long)W * ((H + kL - 1) / kL));
+// The column coefficients alone (coefV), coalesced: thread (column x, chunk c) computes the
+// chunk's 16 positions in order (guide reads of one row are consecutive across the warp's
+// columns), and the warp writes its 32 columns x 16 positions through shared memory so that
+// each column's 256 contiguous bytes go out together. Values as in k_dt_coef.
+constexpr int kColWarps = 4;
+
+__global__ void __launch_bounds__(32 * kColWarps) k_dt_coef_cols(const __grid_constant__ CoefBatch b) {
+    __shared__ float4 tile[kColWarps][32][kL + 1];
+    griddep_wait();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int pi = 0;
+    while (pi + 1 < b.npairs && (long long)blockIdx.x >= b.p[pi + 1].thread0) ++pi;
+    const CoefArgs& a = b.p[pi];
+    const int W = a.W, H = a.H;
+    const int nchV = (H + kL - 1) / kL, ncg = (nchV + kColWarps - 1) / kColWarps;
+    const int local = (int)(blockIdx.x - a.thread0);
+    const int x0 = (local / ncg) * 32, c = (local % ncg) * kColWarps + wib;
+    if (c >= nchV) return;                  // whole warps
+    const int x = x0 + lane, p0 = c * kL;
+    const bool live = x < W;
+    const uint8_t* g = a.guide + (live ? x : 0);
+    int gv[kL + 2];                         // guide at p0 - 1 .. p0 + 16
+#pragma unroll
+    for (int i = 0; i < kL + 2; ++i) {
+        const int p = p0 - 1 + i;
+        gv[i] = live && p >= 0 && p < H ? g[(size_t)p * a.pitch] : 0;
+    }
+    float w[kL + 1];                        // w(p0 + i): the step p0 + i - 1 -> p0 + i
+#pragma unroll
+    for (int i = 0; i <= kL; ++i) {
+        const int q = p0 + i;
+        w[i] = (q >= 1 && q < H) ? a.K * expf(-fabsf((float)(gv[i + 1] - gv[i])) * a.inv_sr255) : 0.0f;
+    }
+    float A = 1.0f, B[kL];
+    B[kL - 1] = w[kL];
+#pragma unroll
+    for (int i = kL - 2; i >= 0; --i) B[i] = B[i + 1] * w[i + 1];
+#pragma unroll
+    for (int i = 0; i < kL; ++i) {
+        A = i == 0 ? w[0] : A * w[i];
+        tile[wib][lane][i] = make_float4(w[i], A, w[i + 1], B[i]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {          // columns 2k, 2k+1: 16 lanes each
+        const int col = 2 * k + (lane >> 4), i = lane & (kL - 1);
+        if (x0 + col < W && p0 + i < H) a.coefV[(size_t)(x0 + col) * H + p0 + i] = tile[wib][col][i];
+    }
+}
+
+long long dt_coef_col_blocks(int W, int H) {
+    const int nchV = (H + kL - 1) / kL;
+    return (long long)((W + 31) / 32) * ((nchV + kColWarps - 1) / kColWarps);
+}
+
+cudaError_t launch_dt_coef_cols(const CoefBatch& b, cudaStream_t st) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    launch_config(cfg, attr, dim3((unsigned)b.total_threads), dim3(32 * kColWarps), 0, st, 1);
+    return cudaLaunchKernelEx(&cfg, k_dt_coef_cols, b);
+}
+
+long long dt_coef_threads(int W, int H, bool rows) {
+    return (long long)kL * ((rows ? (long long)H * ((W + kL - 1) / kL) : 0ll) + (long long)W * ((H + kL - 1) / kL));
 }
 
 cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st) {

@@ -31,6 +31,7 @@ struct RowArgs {
     int d_out0;               // disparity stored at entry 0 of a pixel
     int vec;                  // 16-byte (float) / 8-byte (half) accesses allowed
     float K, inv_sr255;       // DT weights (HPair): exp(-1/sigma_s), 1/(255 sigma_r); guide = left
+    float4* coefH_out;        // (HPair) if set, the row coefficients go here too ([H][W], as k_dt_coef)
     const float2* mulmap;     // (HPair, FastDT codes) [H][W]: (unused, output scale (1-K)^2/A_hat_1)
     float s2;                 // (1 - K)^2
     WtaOut wta;               // (Wta)
@@ -119,6 +120,7 @@ struct CoefArgs {
     float K, inv_sr255;       // exp(-1/sigma_s), 1/(255 sigma_r)
     float4* coefH;            // [H][W]
     float4* coefV;            // [W][H]
+    int rows;                 // 0: columns only (the cost kernel writes the rows' coefficients)
     long long thread0;        // first thread of this pair in the launch
 };
 struct CoefBatch {
@@ -147,7 +149,11 @@ struct AhatBatch {
     AhatArgs p[kMaxBatch];
 };
 cudaError_t launch_ahat_pair(const AhatBatch& b, cudaStream_t st);
-long long dt_coef_threads(int W, int H);
+long long dt_coef_threads(int W, int H, bool rows);
+// The column coefficients only, coalesced: one block per 32 columns x 4 chunks; thread0 and
+// total_threads of the batch count blocks.
+cudaError_t launch_dt_coef_cols(const CoefBatch& b, cudaStream_t st);
+long long dt_coef_col_blocks(int W, int H);
 cudaError_t launch_wta_volume(const void* cost, int dtype, int W, int H, int D, uint16_t* disp,
                               cudaStream_t st);
 

@@ -107,6 +107,7 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
                 if (i + off < kL) B *= b2;
             }
             co[cpos(t)] = t < W ? make_float4(w, A, wn, B) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a.coefH_out && s_begin == 0 && t < W) a.coefH_out[(size_t)y * W + t] = make_float4(w, A, wn, B);
             if constexpr (kFast)
                 mrow[cpos(t)] = t < W ? __ldg(a.mulmap + (size_t)y * W + t) : make_float2(0.f, 0.f);
         }
