@@ -147,9 +147,9 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # the CPU oracle (the cpu_baseline leg and the reference arm)
 
-def time_oracle(pair, wl, iters, max_seconds=12.0, min_runs=1, max_runs=5):
+def time_oracle(pair, wl, iters, max_seconds=12.0, min_runs=1, max_runs=5, cores=None):
     import oracle
-    cores = host_cores()
+    cores = cores or host_cores()
     oracle.load()
     times = []
     t_start = time.perf_counter()
@@ -216,6 +216,32 @@ def algorithmic_bytes(kind, wl, elt_bytes):
         # no volume (iters = 0): the two images in, the disparity map out
         "zncc_cost_wta": 4 * wl["w"] * wl["h"],
     }.get(kind)
+
+
+# Lane operations per volume element in the path's model (window sums and Eq. (2) ~10, two
+# per DT pass over 4 * iters passes, WTA ~2): the ALU side of the whole step's roofline.
+ALU_OPS_ZNCC, ALU_OPS_PER_PASS, ALU_OPS_WTA = 10, 2, 2
+ALU_LANES_PER_SM = 128
+
+
+def step_roofline(n, iters, elt_bytes, ms, peak_gbs, peak_src, clocks):
+    """Both bounds of a whole fused step: HBM (the volume written once by the cost kernel, read
+    and written by every middle pass pair, read by the last: (4 * iters - 2) transfers) and
+    ALU (the lane-operation model above against SMs x 128 lanes x the SM clock under load)."""
+    import torch
+    hbm_bytes = elt_bytes * n * max(0, 4 * iters - 2)
+    hbm_us = hbm_bytes / (peak_gbs * 1e9) * 1e6
+    ops = n * (ALU_OPS_ZNCC + ALU_OPS_PER_PASS * 4 * iters + (ALU_OPS_WTA if iters else 0))
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak_ops = sms * ALU_LANES_PER_SM * mhz * 1e6
+    step_us = ms * 1e3
+    return {"step_us": round(step_us, 2),
+            "hbm": {"bytes": hbm_bytes, "min_us": round(hbm_us, 2), "peak_gbs": peak_gbs,
+                    "peak_source": peak_src, "frac": round(hbm_us / step_us, 4) if hbm_bytes else None},
+            "alu": {"lane_ops_per_elt": ops / n, "lane_ops": ops, "min_us": round(ops / peak_ops * 1e6, 2),
+                    "peak_tops": round(peak_ops / 1e12, 2), "sms": sms, "sm_mhz": mhz,
+                    "frac": round(ops / peak_ops * 1e6 / step_us, 4)}}
 
 
 def load_traffic(kind, digest):
@@ -362,6 +388,7 @@ def run_gb300(args):
                      "traffic": load_traffic(dom, zbuild._sources_digest()),
                      "algorithmic_bytes_per_launch": dom_bytes,
                      "launch_ms": round(dom_ms, 5)},
+        "roofline_step": step_roofline(W * H * D, iters, elt_bytes, ms, peak, peak_src, clocks),
         "kernels_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in prof.items()},
         "e2e": {"value": round(replica_throughput(units, world, e2e_s), 3), "unit": "Gdisp/s",
                 "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 2 * W * H,
@@ -377,6 +404,11 @@ def run_gb300(args):
                                 "cores": cores, "kind": "oracle",
                                 "sample": f"{len(times)} full {W}x{H} D={D} pair(s), "
                                           f"{tb:.2f} s each"}
+        if iters == 0:              # the small plain workload: one host core as well
+            t1, _ = time_oracle(pair, wl, iters, max_seconds=5.0, max_runs=20, cores=1)
+            line["cpu_baseline"]["single_core"] = {"value": round(units / (sum(t1) / len(t1)) / 1e9, 6),
+                                                   "unit": "Gdisp/s", "cores": 1,
+                                                   "sample": f"{len(t1)} full pair(s)"}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -399,9 +431,10 @@ def run_batch(args):
     dev = torch.device("cuda", 0)
     specs = batch_specs(16, 300)
     stream = torch.cuda.Stream(device=dev)
-    ctxs, L, R, D, units = [], [], [], [], 0
+    ctxs, L, R, D, units, pairs = [], [], [], [], 0, []
     for sp in specs:
         p = make_pair(sp["h"], sp["w"], sp["max_disp"], sp["seed"], disp="planes", occlusion_frac=0.05)
+        pairs.append(p)
         ctxs.append(Z.ZnccContext(sp["w"], sp["h"], sp["max_disp"], sp["win"], stream=stream))
         L.append(torch.from_numpy(p.left).to(dev))
         R.append(torch.from_numpy(p.right).to(dev))
@@ -470,6 +503,23 @@ def run_batch(args):
         "launches_per_batched_step": int(launches),
         "launch_shapes": tuned or "defaults",
     }
+    if not args.no_cpu_baseline:               # the oracle pair by pair, about 12 s of it
+        import oracle
+        oracle.load()
+        cores = host_cores()
+        done, t_all, per_pair = 0, 0.0, []
+        for sp, p in zip(specs, pairs):
+            t0 = time.perf_counter()
+            oracle.run(p.left, p.right, sp["max_disp"], sp["win"] // 2, SIG_S, SIG_R, ITERS, nthreads=cores)
+            dt = time.perf_counter() - t0
+            t_all += dt
+            done += sp["w"] * sp["h"] * sp["max_disp"]
+            per_pair.append(f"{sp['w']}x{sp['h']}/D{sp['max_disp']}/w{sp['win']}: {dt:.2f} s")
+            if t_all > 12.0:
+                break
+        line["cpu_baseline"] = {"value": round(done / t_all / 1e9, 6), "unit": "Gdisp/s", "cores": cores,
+                                "kind": "oracle", "sample": f"the first {len(per_pair)} of the 16 pairs, "
+                                                            "one after another: " + "; ".join(per_pair)}
     print(json.dumps(line))
     for c in ctxs:
         c.close()

@@ -68,9 +68,10 @@ def test_codec_empty_and_null_outputs():
 
 
 # (h, w, D, window, iterations): one stored pair (the cost kernel's), a stored pair of each
-# direction, ragged sizes, several tiles along a line, a single row
+# direction, ragged sizes, several tiles along a line, a single row, D not a multiple of 4 (a
+# partly valid last word of codes) and D below 4
 I8_CASES = [(60, 200, 32, 9, 1), (60, 200, 32, 9, 2), (47, 133, 20, 5, 3), (96, 320, 48, 9, 3),
-            (1, 150, 16, 3, 2), (130, 37, 24, 7, 2)]
+            (1, 150, 16, 3, 2), (130, 37, 24, 7, 2), (40, 90, 13, 5, 2), (20, 33, 3, 3, 2)]
 
 
 @pytest.mark.parametrize("h,w,d,win,iters", I8_CASES)
@@ -83,6 +84,24 @@ def test_fastdt_run_matches_oracle(h, w, d, win, iters):
     bad = diff & ~(gap < GAP_TOL_I8 * A)
     assert not bad.any(), f"{int(bad.sum())} disparities differ away from near-ties " \
                           f"(first at {np.argwhere(bad)[:5].tolist()})"
+    assert diff.mean() <= RATE_I8, diff.mean()
+
+
+def test_fastdt_lines_spanning_clusters_match_oracle():
+    """Eight lanes per chunk on 1100-pixel rows: a row spans the two CTAs of a cluster in the
+    horizontal pairs (the reference of d = 0 and the codes are per CTA)."""
+    h, w, d, win, iters = 24, 1100, 16, 5, 2
+    p = make_pair(h, w, d, seed=77)
+    ctx = Z.ZnccContext(w, h, d, win)
+    ctx.set_tuning(Z.ZNCC_TUNE_H_TQ, 8)
+    ctx.set_tuning(Z.ZNCC_TUNE_V_TQ, 8)
+    disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, iters, Z.ZNCC_I8)
+    got = host_u16(disp)
+    ref, gap = oracle.run_fastdt(p.left, p.right, d, win // 2, SIG_S, SIG_R, iters)
+    A = oracle.ones_response(p.left, SIG_S, SIG_R, iters)
+    diff = got != ref
+    assert not (diff & ~(gap < GAP_TOL_I8 * A)).any()
     assert diff.mean() <= RATE_I8, diff.mean()
 
 
