@@ -332,7 +332,8 @@ cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st) {
 // (Sec. V-C fuses WTA with D2U in the same way).
 //
 // Work: lines in groups of lpc, each group with nslices disparity slices of 4*tq
-// disparities; an item is (group, slice), numbered group-major. The grid is sized to the
+// disparities; an item is (group, slice), numbered group-major (FastDT stores: a whole group,
+// whose slices are coded against d = 0 of the first). The grid is sized to the
 // resident blocks (persistent); block b processes the items [b*per_block, (b+1)*per_block)
 // in order, restaging the coefficients when the group changes. A line longer than one block
 // can hold at the chosen lanes per chunk spans the CTAs of a thread-block cluster (one line

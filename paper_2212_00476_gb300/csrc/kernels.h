@@ -78,7 +78,8 @@ struct LineArgs {
 
 // One line-pair launch over up to kMaxBatch pairs, passed by value. Of G blocks (or clusters),
 // block b takes the items [b * total / G, (b+1) * total / G) of all pairs, in order; an item is
-// one step (line group, disparity slice) in both modes.
+// one step (line group, disparity slice) in both modes, or a whole line group for FastDT
+// stores.
 struct LineBatch {
     int npairs, total_items, total_steps, grid;
     int co_async;             // coefficients streamed by cp.async (two buffers; line_coef_async)

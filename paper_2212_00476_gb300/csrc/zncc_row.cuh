@@ -279,7 +279,8 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
 // SINGLE: the launch holds one pair, whose arguments are then read at constant offsets of
 // the parameter block instead of through a dynamic index.
 // Work units: (row, disparity slice) in row-major order, pair by pair (Wta: whole rows, since
-// a row's running best stays in registers). Block b takes the units [b*total/G, (b+1)*total/G)
+// a row's running best stays in registers; FastDT codes: whole rows, since every slice is
+// coded against d = 0 of the first). Block b takes the units [b*total/G, (b+1)*total/G)
 // and visits them row by row, at most spb slices per visit, so that the band of a row is
 // staged once per visit and every block gets the same work within one unit.
 template <int R, typename T, int MODE, int MINB, bool SINGLE>
