@@ -123,13 +123,14 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
         const uint4* col = is_left ? LP : RP;
         const int pc = is_left ? pLP : pRP;
         const int ib = is_left ? cs : cs - R - xr0;                 // column index of cs - R
+        // (ib = 16 t, or 16 (t - nch) on the right: both multiples of 4)
         int Sx[kL], Qx[kL];
 #pragma unroll
         for (int i = 0; i < kL; ++i) Sx[i] = Qx[i] = 0;
         unsigned ps = 0u, pq = 0u;
 #pragma unroll
         for (int u = 0; u < kL + 2 * R; ++u) {
-            const uint4 w = col[p4(ib + u, pc)];
+            const uint4 w = at4(col, ib, u, pc);            // ib is a multiple of 4 (see below)
             ps = __dp4a(w.x, 0x01010101u, ps);
             pq = __dp4a(w.x, w.x, pq);
             if (NW > 1) { ps = __dp4a(w.y, 0x01010101u, ps); pq = __dp4a(w.y, w.y, pq); }
@@ -143,8 +144,8 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
             const int var = (int)(n * (unsigned)Qx[i] - (unsigned)Sx[i] * (unsigned)Sx[i]);
             const float is = var > 0 ? 1.0f / sqrtf((float)var) : 0.0f;
             const int2 st = make_int2(Sx[i], __float_as_int(is));
-            if (is_left) SL[p4(cs + i, pX)] = st;
-            else if (cs + i - c0 < NSR) SR[p4(cs + i - c0, pSR)] = st;
+            if (is_left) at4(SL, cs, i, pX) = st;
+            else if (cs + i - c0 < NSR) at4(SR, cs - c0, i, pSR) = st;
         }
     }
     __syncthreads();
@@ -166,17 +167,20 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
             for (int i = 0; i < kL; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) P[i][j] = 0;
-            // RP index of column x' - d_first - j at step t (x' = x0 - R + t) is rbase + t - j
+            // RP index of column x' - d_first - j at step t (x' = x0 - R + t) is rbase + t - j;
+            // rbase + 1 = x0 - d_first + blk_hi is a multiple of 4 (as are x0, d_first and
+            // blk_hi, d_lo being one), so every index below has a constant plane
             const int rbase = x0 - R - d_first - xr0;      // >= 3: d_first + 3 < blk_hi
+            const int rb4 = rbase + 1;
             uint4 rp[4];
-            rp[1] = RP[p4(rbase - 1, pRP)];
-            rp[2] = RP[p4(rbase - 2, pRP)];
-            rp[3] = RP[p4(rbase - 3, pRP)];
+            rp[1] = at4(RP, rb4, -2, pRP);
+            rp[2] = at4(RP, rb4, -3, pRP);
+            rp[3] = at4(RP, rb4, -4, pRP);
             unsigned pre[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int t = 0; t < kL + 2 * R; ++t) {
-                const uint4 lp = LP[p4(x0 + t, pLP)];
-                rp[0] = RP[p4(rbase + t, pRP)];
+                const uint4 lp = at4(LP, x0, t, pLP);
+                rp[0] = at4(RP, rb4, t - 1, pRP);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     pre[j] = __dp4a(lp.x, rp[j].x, pre[j]);
@@ -193,15 +197,16 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
 
             // ---- normalization, Eq. (2); the target statistics slide like the columns ----
             const int cb = x0 - d_first - c0;               // SR index of (i, j) is cb + i - j >= 3
+            const int cb4 = cb + 1;                         // a multiple of 4, like rb4
             int2 sr[4];
-            sr[1] = SR[p4(cb - 1, pSR)];
-            sr[2] = SR[p4(cb - 2, pSR)];
-            sr[3] = SR[p4(cb - 3, pSR)];
+            sr[1] = at4(SR, cb4, -2, pSR);
+            sr[2] = at4(SR, cb4, -3, pSR);
+            sr[3] = at4(SR, cb4, -4, pSR);
 #pragma unroll
             for (int i = 0; i < kL; ++i) {
                 const int x = x0 + i;
                 const int2 st = at4(SL, x0, i, pX);
-                sr[0] = SR[p4(cb + i, pSR)];
+                sr[0] = at4(SR, cb4, i - 1, pSR);
                 const float isl = __int_as_float(st.y);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
