@@ -268,13 +268,16 @@ const char* zncc_status_string(zncc_status status);
  *   ZNCC_TUNE_ROW_SPB    cost kernel: disparity slices per block
  *   ZNCC_TUNE_H_TQ       horizontal DT pairs: lanes per 16-pixel chunk (2, 4 or 8)
  *   ZNCC_TUNE_V_TQ       vertical DT pairs: lanes per 16-pixel chunk (2, 4 or 8)
+ *   ZNCC_TUNE_AHAT_SMS   (F16, I8 storage) SMs the cost kernel leaves free for the A_hat chain,
+ *                        which runs beside it on a second stream (default 8)
  * A value a launch cannot use (too many threads or too much shared memory) makes the next
  * call fail with ZNCC_EUNSUPPORTED. Unknown keys give ZNCC_EINVAL. */
 typedef enum {
     ZNCC_TUNE_ROW_MINB2 = 1,
     ZNCC_TUNE_ROW_SPB = 2,
     ZNCC_TUNE_H_TQ = 3,
-    ZNCC_TUNE_V_TQ = 4
+    ZNCC_TUNE_V_TQ = 4,
+    ZNCC_TUNE_AHAT_SMS = 5
 } zncc_tune_key;
 zncc_status zncc_set_tuning(zncc_ctx* ctx, int key, int value);
 

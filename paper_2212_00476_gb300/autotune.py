@@ -28,7 +28,7 @@ CANDIDATES = {
     Z.ZNCC_TUNE_V_TQ: [0, 2, 4, 8],
 }
 NAMES = {Z.ZNCC_TUNE_ROW_MINB2: "row_minb2", Z.ZNCC_TUNE_ROW_SPB: "row_spb",
-         Z.ZNCC_TUNE_H_TQ: "h_tq", Z.ZNCC_TUNE_V_TQ: "v_tq"}
+         Z.ZNCC_TUNE_H_TQ: "h_tq", Z.ZNCC_TUNE_V_TQ: "v_tq", Z.ZNCC_TUNE_AHAT_SMS: "ahat_sms"}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 _lock = threading.Lock()
 

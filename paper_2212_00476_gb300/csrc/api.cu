@@ -76,6 +76,8 @@ struct zncc_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cur = nullptr;       // the stream launches go to
+    cudaStream_t side = nullptr;      // (F16, I8) the A_hat chain beside the cost kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     float4* coefH = nullptr;      // [H][W]       horizontal DT coefficients
     float4* coefV = nullptr;      // [W][H]       vertical DT coefficients
@@ -88,6 +90,7 @@ struct zncc_ctx {
     int smem_max = 0;             // opt-in shared memory per block of the device
     int row_minb2 = 1;            // cost kernel: two-blocks-per-SM variant where it applies
     int row_spb = 0;              // cost kernel: slices per block (0 = automatic)
+    int ahat_sms = 0;             // SMs the cost kernel leaves to the A_hat chain (0 = automatic)
     int h_tq = 0, v_tq = 0;       // DT pairs: forced lanes per chunk (0 = automatic)
     int num_sms = 0;
     std::vector<LinePlan> plans;  // line-pass launch shapes, by pass signature
@@ -176,6 +179,11 @@ void release(zncc_ctx* c) {
     free_dev(c->img);
     free_dev(c->disp);
     free_dev(c->scan_stats);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    c->side = nullptr;
+    c->ev_fork = c->ev_join = nullptr;
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     c->records.clear();
@@ -268,7 +276,7 @@ zncc_status run_coef(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, float
 // shrinks until the block fits in shared memory); in Wta mode a block covers every
 // disparity of its row.
 zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype, float s2, float K,
-                     float inv_sr255, int kind,
+                     float inv_sr255, int kind, int reserve_sms,
                      const char* what) {
     // pairs share a launch when they share the window radius and the block shape; a pair large
     // enough to fill the device by itself takes a launch of its own
@@ -338,7 +346,7 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
         int bps = 0;
         ZNCC_CUDA(lc, zncc_row_occupancy(r, mode, dtype, threads, smem, minb2, b.npairs == 1, &bps),
                   "occupancy query");
-        b.grid = std::max(1, std::min(b.total_items, lc->num_sms * std::max(1, bps)));
+        b.grid = std::max(1, std::min(b.total_items, std::max(1, lc->num_sms - reserve_sms) * std::max(1, bps)));
         ZNCC_LAUNCH(lc, kind, launch_zncc_row(r, b, threads, smem, mode, dtype, lc->cur), what);
     }
     return ZNCC_OK;
@@ -361,10 +369,12 @@ struct LinePass {
 };
 
 // The block shape of a pair's pass: among lane counts per chunk (8, 4, 2, or the forced
-// one) and lines per block that fit in shared memory, prefer whole 64-byte segments per
-// chunk, then streaming through shared memory (async), then at least two resident blocks
-// per SM, then the most resident warps. `found` is false when no shape fits; on success
-// the shape is also left in a.
+// one) and lines per block that fit in shared memory, prefer a line inside one block (a
+// cluster's barriers cost more than shorter segments: half-precision rows of 1280 pixels ran
+// 30% faster with 32-byte segments in one block than with 64-byte segments over two CTAs),
+// then whole 64-byte, then whole 32-byte segments per chunk position, then streaming through
+// shared memory (async), then at least two resident blocks per SM, then the most resident
+// warps. `found` is false when no shape fits; on success the shape is also left in a.
 cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePass& p, LinePlan& best,
                              bool& found) {
     found = false;
@@ -400,8 +410,9 @@ cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePa
                     if (ncl < 1) continue;
                 }
                 const long long warps = (long long)bps * lpc * per_line / 32;
-                const long long score = (whole_bursts ? 10000000LL : 0) + async * 1000000LL +
-                                        (bps >= 2 ? 100000LL : 0) + warps * 100 + (cs == 1 ? 50 : 0) + tq;
+                const long long score = (cs == 1 ? 1000000000LL : 0) +
+                                        (whole_bursts ? 10000000LL : (seg >= 32 ? 5000000LL : 0)) +
+                                        async * 1000000LL + (bps >= 2 ? 100000LL : 0) + warps * 100 + tq;
                 if (score > best_score) {
                     best_score = score;
                     best.tq = tq; best.lpc = lpc; best.nch = nch; best.async = async; best.blocks = bps;
@@ -560,6 +571,10 @@ zncc_status ensure_ahat(zncc_ctx* c, int nahat, int nmul) {
     return ZNCC_OK;
 }
 
+// SMs the cost kernel leaves to the A_hat chain by default (F16 step 0.662 -> 0.629 ms at
+// 1280x384x128 with 8; 16 to 32 gave the same).
+constexpr int kAhatSideSms = 8;
+
 // Pass pair p of the A_hat chain (A_hat_p from A_hat_{p-1}, or from ones for p = 1) for every
 // pair of the batch, one launch, with the multipliers of pair p when it has a map (p >= pfirst).
 zncc_status run_ahat(zncc_ctx* lc, const PairIO* io, int n, int p, int pfirst, int npairs, float K,
@@ -600,7 +615,7 @@ zncc_status run_ahat(zncc_ctx* lc, const PairIO* io, int n, int p, int pfirst, i
 // radius for the cost kernel).
 zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigma_r, int iters,
                       int storage) {
-    if (iters == 0) return run_rows(lc, io, n, kModeWta, 0, 0.0f, 0.0f, 0.0f, K_ZNCC_WTA, "ZNCC + WTA");
+    if (iters == 0) return run_rows(lc, io, n, kModeWta, 0, 0.0f, 0.0f, 0.0f, K_ZNCC_WTA, 0, "ZNCC + WTA");
     const int dt = storage;                         // 0 float, 1 half, 2 FastDT codes
     zncc_ctx* ctxs[kMaxBatch];
     for (int i = 0; i < n; ++i) {
@@ -629,21 +644,47 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
             if (ensure_ahat(io[i].c, npairs - 1, npairs - pfirst + 1) != ZNCC_OK)
                 return fail(lc, ZNCC_ENOMEM, io[i].c->err);
     ZNCC_TRY(run_coef(lc, io, n, sigma_s, sigma_r, false));     // the cost kernel writes the rows'
-    for (int p = 1; norm && p <= npairs - 1; ++p)
-        ZNCC_TRY(run_ahat(lc, io, n, p, pfirst, npairs, K, inv_sr255, s2, dt == 2));
+    // The A_hat chain is small and latency-bound (one warp per line): it runs on a second
+    // stream on the SMs the cost kernel leaves free. FastDT needs A_hat_1 in the cost kernel
+    // itself, so that pass comes first.
+    const int side = norm ? (lc->ahat_sms > 0 ? lc->ahat_sms : kAhatSideSms) : 0;
+    int p_first_side = 1;
+    if (dt == 2) {
+        ZNCC_TRY(run_ahat(lc, io, n, 1, pfirst, npairs, K, inv_sr255, s2, true));
+        p_first_side = 2;
+    }
+    if (side > 0) {
+        if (!lc->side) {
+            ZNCC_CUDA(lc, cudaStreamCreateWithFlags(&lc->side, cudaStreamNonBlocking), "side stream");
+            ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_fork, cudaEventDisableTiming), "fork event");
+            ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_join, cudaEventDisableTiming), "join event");
+        }
+        ZNCC_CUDA(lc, cudaEventRecord(lc->ev_fork, lc->stream), "fork");
+        ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->side, lc->ev_fork, 0), "fork");
+        lc->cur = lc->side;
+    }
+    zncc_status st = ZNCC_OK;
+    for (int p = p_first_side; norm && p <= npairs - 1 && st == ZNCC_OK; ++p)
+        st = run_ahat(lc, io, n, p, pfirst, npairs, K, inv_sr255, s2, dt == 2);
     // the last pair's multipliers (A_hat_{npairs-1}, s2): its result is not stored
-    for (int i = 0; norm && i < n; ++i) {
+    for (int i = 0; norm && i < n && st == ZNCC_OK; ++i) {
         const int W = io[i].c->W, H = io[i].c->H;
         const size_t npix = (size_t)W * H;
         const float* ain = npairs - 1 >= pfirst ? io[i].c->ahat + (size_t)(npairs - 2) * npix : nullptr;
-        ZNCC_LAUNCH(lc, K_AHAT,
-                    launch_mulmap(ain, dt == 2 ? 1.0f / kFastT : 1.0f, s2, W, H, (npairs % 2) == 1,
-                                  io[i].c->mulmap + (size_t)(npairs - pfirst) * npix, lc->cur),
-                    "A_hat multipliers");
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        const cudaError_t e = launch_mulmap(ain, dt == 2 ? 1.0f / kFastT : 1.0f, s2, W, H, (npairs % 2) == 1,
+                                            io[i].c->mulmap + (size_t)(npairs - pfirst) * npix, lc->cur);
+        if (e != cudaSuccess) st = cuda_fail(lc, e, "A_hat multipliers");
     }
+    lc->cur = lc->stream;
+    ZNCC_TRY(st);
+    if (side > 0) ZNCC_CUDA(lc, cudaEventRecord(lc->ev_join, lc->side), "join");
     if (dt == 2)
         for (int i = 0; i < n; ++i) io[i].mulmap1 = io[i].c->mulmap;
-    ZNCC_TRY(run_rows(lc, io, n, kModeHPair, dt, s2, K, inv_sr255, K_ZNCC_HPAIR, "ZNCC + horizontal DT pair"));
+    ZNCC_TRY(run_rows(lc, io, n, kModeHPair, dt, s2, K, inv_sr255, K_ZNCC_HPAIR, side,
+                      "ZNCC + horizontal DT pair"));
+    if (side > 0) ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_join, 0), "join of the A_hat stream");
+
     for (int pair = 2; pair <= npairs; ++pair) {    // pair 1 is the cost kernel's
         LinePass lp[kMaxBatch];
         for (int i = 0; i < n; ++i) {
@@ -825,7 +866,7 @@ zncc_status zncc_cost_volume(zncc_ctx* c, const uint8_t* left, const uint8_t* ri
     if (!cost) return fail(c, ZNCC_EINVAL, "cost pointer is NULL");
     if (dtype != ZNCC_F32 && dtype != ZNCC_F16) return fail(c, ZNCC_EINVAL, "unknown dtype");
     PairIO io{c, left, right, pitch, nullptr, cost, c->D};
-    return run_rows(c, &io, 1, kModeRaw, dtype, 0.0f, 0.0f, 0.0f, K_ZNCC_RAW, "ZNCC cost");
+    return run_rows(c, &io, 1, kModeRaw, dtype, 0.0f, 0.0f, 0.0f, K_ZNCC_RAW, 0, "ZNCC cost");
 }
 
 zncc_status zncc_cost_volume_scan(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch,
@@ -1098,6 +1139,7 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
     switch (key) {
         case ZNCC_TUNE_ROW_MINB2: c->row_minb2 = value ? 1 : 0; break;
         case ZNCC_TUNE_ROW_SPB: c->row_spb = value; break;
+        case ZNCC_TUNE_AHAT_SMS: c->ahat_sms = value; break;
         case ZNCC_TUNE_H_TQ:
         case ZNCC_TUNE_V_TQ:
             if (value != 0 && value != 2 && value != 4 && value != 8)

@@ -29,7 +29,7 @@ LIB_PATH = os.path.join(_PKG, "libzncc.so")
 ZNCC_OK, ZNCC_EINVAL, ZNCC_ENOMEM, ZNCC_ECUDA, ZNCC_EBUSY, ZNCC_ENOTREADY, ZNCC_ETIMEOUT, \
     ZNCC_EUNSUPPORTED = range(8)
 ZNCC_F32, ZNCC_F16, ZNCC_I8 = 0, 1, 2
-ZNCC_TUNE_ROW_MINB2, ZNCC_TUNE_ROW_SPB, ZNCC_TUNE_H_TQ, ZNCC_TUNE_V_TQ = 1, 2, 3, 4
+ZNCC_TUNE_ROW_MINB2, ZNCC_TUNE_ROW_SPB, ZNCC_TUNE_H_TQ, ZNCC_TUNE_V_TQ, ZNCC_TUNE_AHAT_SMS = 1, 2, 3, 4, 5
 STATUS_NAMES = ["ZNCC_OK", "ZNCC_EINVAL", "ZNCC_ENOMEM", "ZNCC_ECUDA", "ZNCC_EBUSY",
                 "ZNCC_ENOTREADY", "ZNCC_ETIMEOUT", "ZNCC_EUNSUPPORTED"]
 

@@ -31,9 +31,10 @@ def _dt_case(h, w, d, iters, seed):
     return guide, C, ref, A
 
 
-# (h, w, d, iters, tuning): rows of 3000 and 3072 pixels (two CTAs at 4 lanes per chunk),
-# columns of 3000, and 1280-pixel rows at 8 lanes per chunk (forced)
-F32_CASES = [(6, 3000, 8, 1, {}), (3000, 6, 8, 1, {}), (5, 3072, 12, 2, {}),
+# (h, w, d, iters, tuning): rows of 3000 and 3072 pixels and columns of 3000 (two CTAs at 4
+# lanes per chunk, forced), and 1280-pixel rows at 8 lanes per chunk (forced)
+F32_CASES = [(6, 3000, 8, 1, {Z.ZNCC_TUNE_H_TQ: 4}), (3000, 6, 8, 1, {Z.ZNCC_TUNE_V_TQ: 4}),
+             (5, 3072, 12, 2, {Z.ZNCC_TUNE_H_TQ: 4, Z.ZNCC_TUNE_V_TQ: 4}),
              (24, 1280, 40, 2, {Z.ZNCC_TUNE_H_TQ: 8}), (1280, 20, 24, 1, {Z.ZNCC_TUNE_V_TQ: 8})]
 
 
@@ -50,14 +51,16 @@ def test_clustered_dt_matches_oracle(h, w, d, iters, tuning):
     assert rel <= AGG_TOL, f"max |dC|/A_hat = {rel}"
 
 
-# half storage: 8 lanes per chunk (64-byte segments) need two CTAs beyond 1024 pixels and
-# four at 3072
+# half storage: 8 lanes per chunk (64-byte segments, forced) need two CTAs beyond 1024 pixels
+# and four at 3072
 @pytest.mark.parametrize("h,w,d,iters", [(6, 1100, 16, 1), (4, 3072, 8, 1), (1100, 5, 16, 2)])
 def test_clustered_dt_fp16_within_rounding_bound(h, w, d, iters):
     guide, C, ref, A = _dt_case(h, w, d, iters, seed=h + 3 * w)
     C16 = C.astype(np.float16)
     ref = oracle.dt_aggregate(C16.astype(np.float64), oracle.dt_weights(guide, SIG_S, SIG_R), SIG_S, iters)
     ctx = Z.ZnccContext(w, h, d, 3)
+    ctx.set_tuning(Z.ZNCC_TUNE_H_TQ, 8)
+    ctx.set_tuning(Z.ZNCC_TUNE_V_TQ, 8)
     t = dev(C16)
     ctx.dt_aggregate(dev(guide), t, SIG_S, SIG_R, iters, Z.ZNCC_F16)
     torch.cuda.synchronize()
@@ -69,7 +72,7 @@ def test_clustered_dt_fp16_within_rounding_bound(h, w, d, iters):
 @pytest.mark.parametrize("h,w,d,win,storage,tuning", [
     (1100, 64, 24, 9, Z.ZNCC_F32, {Z.ZNCC_TUNE_V_TQ: 8}),     # clustered V pairs, WTA in one
     (48, 1280, 32, 9, Z.ZNCC_F32, {Z.ZNCC_TUNE_H_TQ: 8}),     # clustered H pairs
-    (1100, 80, 16, 7, Z.ZNCC_F16, {}),                         # half: clustered V pairs + WTA
+    (1100, 80, 16, 7, Z.ZNCC_F16, {Z.ZNCC_TUNE_V_TQ: 8}),      # half: clustered V pairs + WTA
 ])
 def test_clustered_fused_run_matches_oracle(h, w, d, win, storage, tuning):
     p = make_pair(h, w, d, seed=h + w + d)
