@@ -70,20 +70,18 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
     float* ref = reinterpret_cast<float*>(mrow + nch * kCS);
 
     // ---- stage the packed bands (and the DT coefficients) ----
-    for (int t = tid; t < NLP + NRP; t += blockDim.x) {
-        const bool is_left = t < NLP;
-        const int ix = is_left ? t : t - NLP;
-        const int xc = min(max(is_left ? ix - R : xr0 + ix, 0), W - 1);
-        const uint8_t* img = is_left ? a.left : a.right;
-        unsigned w[4] = {0u, 0u, 0u, 0u};
+    {
+        size_t roff[l];                                 // the band's clamped rows
 #pragma unroll
-        for (int j = 0; j < l; ++j) {
-            const int yc = min(max(y - R + j, 0), H - 1);
-            w[j >> 2] |= (unsigned)img[(size_t)yc * a.pitch + xc] << (8 * (j & 3));
-        }
-        const uint4 pk = make_uint4(w[0], w[1], w[2], w[3]);
-        if (is_left) LP[p4(ix, pLP)] = pk;
-        else RP[p4(ix, pRP)] = pk;
+        for (int j = 0; j < l; ++j) roff[j] = (size_t)min(max(y - R + j, 0), H - 1) * a.pitch;
+        auto pack = [&](const uint8_t* img, int xc) {
+            unsigned w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int j = 0; j < l; ++j) w[j >> 2] |= (unsigned)img[roff[j] + xc] << (8 * (j & 3));
+            return make_uint4(w[0], w[1], w[2], w[3]);
+        };
+        for (int t = tid; t < NLP; t += blockDim.x) LP[p4(t, pLP)] = pack(a.left, min(max(t - R, 0), W - 1));
+        for (int t = tid; t < NRP; t += blockDim.x) RP[p4(t, pRP)] = pack(a.right, min(max(xr0 + t, 0), W - 1));
     }
     if constexpr (MODE == kModeHPair) {
         // the row's DT coefficients (w, chunk prefix product, next w, chunk suffix product),

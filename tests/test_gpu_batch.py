@@ -71,3 +71,31 @@ def test_batch_rejects_bad_arguments():
     with pytest.raises(Z.ZnccError) as e:
         Z.zncc_run_batch(many, [img] * 33, [img] * 33, out, SIG_S, SIG_R, 1)
     assert e.value.status == Z.ZNCC_EINVAL
+
+
+@pytest.mark.parametrize("storage", [Z.ZNCC_F32, Z.ZNCC_F16, Z.ZNCC_I8])
+def test_batch_replayed_from_a_cuda_graph_equals_separate_runs(storage):
+    """The batched run captured in a CUDA graph (with F16 and I8 storage the A_hat chain forks
+    to a second stream and joins back inside the capture) and replayed gives the maps of
+    separate runs."""
+    specs = SPECS[:4]
+    stream = torch.cuda.Stream()
+    pairs, _, L, R, D = _setup(specs, seed0=950)
+    ctxs = [Z.ZnccContext(w, h, d, win, stream=stream) for (h, w, d, win) in specs]
+    single = []
+    with torch.cuda.stream(stream):
+        for c, l, r, d in zip(ctxs, L, R, D):
+            c.zncc_run(l, r, d, SIG_S, SIG_R, 3, storage)
+            single.append(d.clone())
+        Z.zncc_run_batch(ctxs, L, R, D, SIG_S, SIG_R, 3, storage)     # buffers and plans first
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        Z.zncc_run_batch(ctxs, L, R, D, SIG_S, SIG_R, 3, storage)
+    for d in D:
+        d.fill_(-1)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    for i, (a, b) in enumerate(zip(single, D)):
+        assert torch.equal(a, b), f"pair {i} {specs[i]} differs between the graph and single runs"
