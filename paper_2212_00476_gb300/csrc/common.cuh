@@ -261,10 +261,14 @@ struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
-template <bool SCALE = true, typename Hook = NoHook>
+// The output scale of a position: the y of a multiplier pair, or the value itself.
+__device__ __forceinline__ float out_scale(const float2& m) { return m.y; }
+__device__ __forceinline__ float out_scale(float m) { return m; }
+
+template <bool SCALE = true, typename Hook = NoHook, typename MulT = float2>
 __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restrict__ co, int tq, int dq,
                                         int lane, int wl, int nwl, float* sa, float4* sb, float s2,
-                                        const float2* __restrict__ mul = nullptr,
+                                        const MulT* __restrict__ mul = nullptr,
                                         Hook after_forward = Hook(), bool active = true, int cs = 1) {
     float A = 0.f, Ae = 1.f;
     float B[4], Be[4], F[4], G[4];
@@ -396,7 +400,7 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
 #pragma unroll
         for (int i = 0; i < kL; ++i) {
             const float b = co[i].w;
-            const float m = SCALE ? (mul ? mul[i].y : s2) : 1.0f;
+            const float m = SCALE ? (mul ? out_scale(mul[i]) : s2) : 1.0f;
 #pragma unroll
             for (int j = 0; j < 4; ++j) v[i][j] = SCALE ? m * fmaf(b, G[j], v[i][j]) : fmaf(b, G[j], v[i][j]);
         }

@@ -66,8 +66,8 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
     float* sa = reinterpret_cast<float*>(sb + 2 * nwl * tq);
     // FastDT codes (HPair): the row's output scales and the reference values v(d_arb = 0)
     constexpr bool kFast = std::is_same<T, uint8_t>::value;
-    float2* mrow = reinterpret_cast<float2*>(sa + 2 * nwl * tq);     // chunk-major (kCS)
-    float* ref = reinterpret_cast<float*>(mrow + nch * kCS);
+    float* mrow = sa + 2 * nwl * tq;                                 // chunk-major (kCS)
+    float* ref = mrow + nch * kCS;
 
     // ---- stage the packed bands (and the DT coefficients) ----
     {
@@ -107,7 +107,7 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
             co[cpos(t)] = t < W ? make_float4(w, A, wn, B) : make_float4(0.f, 0.f, 0.f, 0.f);
             if (a.coefH_out && s_begin == 0 && t < W) a.coefH_out[(size_t)y * W + t] = make_float4(w, A, wn, B);
             if constexpr (kFast)
-                mrow[cpos(t)] = t < W ? __ldg(a.mulmap + (size_t)y * W + t) : make_float2(0.f, 0.f);
+                mrow[cpos(t)] = t < W ? __ldg(a.mulmap + (size_t)y * W + t).y : 0.0f;
         }
     }
     __syncthreads();
@@ -328,7 +328,7 @@ inline size_t zncc_row_smem(int R, int mode, int dtype, const RowArgs& a, int nt
     const int pX = plane_of(span);
     b += 8ull * 4 * (pX + plane_of(span + drange - 1));
     if (mode == kModeHPair) b += 16ull * a.nch * kCS + dt_scan_bytes(nthreads / 32, a.tq);
-    if (mode == kModeHPair && dtype == 2) b += 12ull * a.nch * kCS;      // FastDT: scales, references
+    if (mode == kModeHPair && dtype == 2) b += 8ull * a.nch * kCS;       // FastDT: scales, references
     return b;
 }
 
