@@ -261,9 +261,8 @@ zncc_status run_coef(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, float
         a.inv_sr255 = inv;
         a.coefH = io[i].c->coefH;
         a.coefV = io[i].c->coefV;
-        a.rows = rows ? 1 : 0;
         a.thread0 = t;
-        t += rows ? dt_coef_threads(a.W, a.H, true) : dt_coef_col_blocks(a.W, a.H);
+        t += rows ? dt_coef_threads(a.W, a.H) : dt_coef_col_blocks(a.W, a.H);
     }
     b.total_threads = t;
     if (rows) ZNCC_LAUNCH(lc, K_COEF, launch_dt_coef(b, lc->cur), "DT coefficients");
@@ -984,8 +983,7 @@ zncc_status dt_aggregate_noalloc(const uint8_t* guide, int pitch, int width, int
     ca.inv_sr255 = (float)(1.0 / (255.0 * (double)sigma_r));
     ca.coefH = coefH;
     ca.coefV = coefV;
-    ca.rows = 1;
-    cb.total_threads = dt_coef_threads(width, height, true);
+    cb.total_threads = dt_coef_threads(width, height);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     e = launch_dt_coef(cb, st);
     if (e != cudaSuccess) return noalloc_cuda_fail(e, "DT coefficients");

@@ -98,9 +98,8 @@ __global__ void k_dt_coef(const __grid_constant__ CoefBatch b) {
     const long long local = gid - a.thread0;
     int chunk = (int)(local / kL);
     const int i = (int)(local & (kL - 1));
-    const int nH = a.rows ? H * nchH : 0;
-    const bool horiz = chunk < nH;
-    if (!horiz) chunk -= nH;
+    const bool horiz = chunk < H * nchH;
+    if (!horiz) chunk -= H * nchH;
     const bool live = gid < b.total_threads && (horiz || chunk < W * nchV);
     const int n = horiz ? W : H;
     const int nchl = horiz ? nchH : nchV;
@@ -313,8 +312,8 @@ cudaError_t launch_dt_coef_cols(const CoefBatch& b, cudaStream_t st) {
     return cudaLaunchKernelEx(&cfg, k_dt_coef_cols, b);
 }
 
-long long dt_coef_threads(int W, int H, bool rows) {
-    return (long long)kL * ((rows ? (long long)H * ((W + kL - 1) / kL) : 0ll) + (long long)W * ((H + kL - 1) / kL));
+long long dt_coef_threads(int W, int H) {
+    return (long long)kL * ((long long)H * ((W + kL - 1) / kL) + (long long)W * ((H + kL - 1) / kL));
 }
 
 cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st) {

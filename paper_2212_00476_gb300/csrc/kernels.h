@@ -121,8 +121,7 @@ struct CoefArgs {
     float K, inv_sr255;       // exp(-1/sigma_s), 1/(255 sigma_r)
     float4* coefH;            // [H][W]
     float4* coefV;            // [W][H]
-    int rows;                 // 0: columns only (the cost kernel writes the rows' coefficients)
-    long long thread0;        // first thread of this pair in the launch
+    long long thread0;        // first thread (k_dt_coef_cols: block) of this pair in the launch
 };
 struct CoefBatch {
     int npairs;
@@ -150,7 +149,7 @@ struct AhatBatch {
     AhatArgs p[kMaxBatch];
 };
 cudaError_t launch_ahat_pair(const AhatBatch& b, cudaStream_t st);
-long long dt_coef_threads(int W, int H, bool rows);
+long long dt_coef_threads(int W, int H);
 // The column coefficients only, coalesced: one block per 32 columns x 4 chunks; thread0 and
 // total_threads of the batch count blocks.
 cudaError_t launch_dt_coef_cols(const CoefBatch& b, cudaStream_t st);
