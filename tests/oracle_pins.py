@@ -12,6 +12,8 @@ from __future__ import annotations
 import math
 from fractions import Fraction
 
+import os
+
 import numpy as np
 
 import oracle
@@ -412,6 +414,28 @@ def pin_fastdt_codec_examples(lib):
         assert dec(code) == back, (hex(code), dec(code), back)
 
 
+def golden_fastdt_codes():
+    """(value, code, decoded) rows of tests/golden/fastdt_codes.txt (worked by hand from the
+    rules of Sec. IV-C)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fastdt_codes.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                v, c, d = line.split()
+                rows.append((int(v), int(c, 16), int(d)))
+    return rows
+
+
+def pin_fastdt_codec_golden(lib):
+    """The code table of tests/golden/fastdt_codes.txt (Sec. IV-C's rules by hand)."""
+    rows = golden_fastdt_codes()
+    assert len(rows) >= 20
+    for v, code, back in rows:
+        assert oracle.fastdt_encode(v, lib=lib) == code, (v, code)
+        assert oracle.fastdt_decode(code, lib=lib) == back, (code, back)
+
+
 def pin_fastdt_codec_properties(lib):
     """Over every 16-bit value: the decoded value never exceeds the original (the dropped low
     bits are zeroed, the kept bits and the leading ones are exact), its error is below the
@@ -473,5 +497,6 @@ ALL_PINS = [
     pin_dt_edge_stop,
     pin_wta_bruteforce_and_ties,
     pin_end_to_end_recovery,
-    pin_fastdt_codec_examples, pin_fastdt_codec_properties, pin_fastdt_store, pin_fastdt_chain_accuracy,
+    pin_fastdt_codec_examples, pin_fastdt_codec_golden, pin_fastdt_codec_properties, pin_fastdt_store,
+    pin_fastdt_chain_accuracy,
 ]

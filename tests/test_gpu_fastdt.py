@@ -55,6 +55,18 @@ def test_codec_bit_exact_over_every_16bit_value():
     assert np.array_equal(decoded.cpu().numpy(), ref_dec)
 
 
+def test_codec_matches_the_golden_table():
+    from oracle_pins import golden_fastdt_codes
+    rows = golden_fastdt_codes()
+    values = np.array([v for v, _, _ in rows], np.int16)
+    codes = torch.empty(len(rows), dtype=torch.uint8, device="cuda")
+    decoded = torch.empty(len(rows), dtype=torch.int16, device="cuda")
+    Z.fastdt_codec(dev(values), codes, decoded)
+    torch.cuda.synchronize()
+    assert codes.cpu().numpy().tolist() == [c for _, c, _ in rows]
+    assert decoded.cpu().numpy().tolist() == [d for _, _, d in rows]
+
+
 def test_codec_empty_and_null_outputs():
     v = dev(np.array([-5, 7, -30000], np.int16))
     Z.fastdt_codec(v[:0])
