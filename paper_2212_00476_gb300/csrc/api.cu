@@ -368,12 +368,13 @@ struct LinePass {
 };
 
 // The block shape of a pair's pass: among lane counts per chunk (8, 4, 2, or the forced
-// one) and lines per block that fit in shared memory, prefer a line inside one block (a
-// cluster's barriers cost more than shorter segments: half-precision rows of 1280 pixels ran
-// 30% faster with 32-byte segments in one block than with 64-byte segments over two CTAs),
-// then whole 64-byte, then whole 32-byte segments per chunk position, then streaming through
-// shared memory (async), then at least two resident blocks per SM, then the most resident
-// warps. `found` is false when no shape fits; on success the shape is also left in a.
+// one) and lines per block that fit in shared memory, prefer whole 64-byte segments per
+// chunk, then streaming through shared memory (async), then at least two resident blocks
+// per SM, then the most resident warps, then a line inside one block. Which of a cluster with
+// 64-byte segments and one block with 32-byte segments is faster depends on the shape
+// (half-precision rows of 1280 pixels: one block, 181 against 235 us per pair; of 1920
+// pixels: the cluster, 839 against 954 us), so the autotuner settles it per shape.
+// `found` is false when no shape fits; on success the shape is also left in a.
 cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePass& p, LinePlan& best,
                              bool& found) {
     found = false;
@@ -409,9 +410,8 @@ cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePa
                     if (ncl < 1) continue;
                 }
                 const long long warps = (long long)bps * lpc * per_line / 32;
-                const long long score = (cs == 1 ? 1000000000LL : 0) +
-                                        (whole_bursts ? 10000000LL : (seg >= 32 ? 5000000LL : 0)) +
-                                        async * 1000000LL + (bps >= 2 ? 100000LL : 0) + warps * 100 + tq;
+                const long long score = (whole_bursts ? 10000000LL : 0) + async * 1000000LL +
+                                        (bps >= 2 ? 100000LL : 0) + warps * 100 + (cs == 1 ? 50 : 0) + tq;
                 if (score > best_score) {
                     best_score = score;
                     best.tq = tq; best.lpc = lpc; best.nch = nch; best.async = async; best.blocks = bps;
