@@ -244,7 +244,9 @@ def step_roofline(n, iters, elt_bytes, ms, peak_gbs, peak_src, clocks):
                     "frac": round(ops / peak_ops * 1e6 / step_us, 4)}}
 
 
-def load_traffic(kind, digest):
+def load_traffic(kind, digest, workload, storage):
+    """DRAM bytes per launch of a kernel kind from the committed ncu capture, if it was taken
+    on this workload and storage type with the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -252,7 +254,8 @@ def load_traffic(kind, digest):
     except (OSError, ValueError):
         return None
     ent = t.get("kernels", {}).get(kind)
-    if not ent or t.get("source_digest") != digest:
+    if (not ent or t.get("source_digest") != digest or t.get("workload_key") != workload
+            or t.get("storage") != storage):
         return None
     return ent.get("bytes_per_launch")
 
@@ -385,7 +388,7 @@ def run_gb300(args):
                      "kernel": dom, "achieved": round(achieved, 1),
                      "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
-                     "traffic": load_traffic(dom, zbuild._sources_digest()),
+                     "traffic": load_traffic(dom, zbuild._sources_digest(), args.workload, args.storage),
                      "algorithmic_bytes_per_launch": dom_bytes,
                      "launch_ms": round(dom_ms, 5)},
         "roofline_step": step_roofline(W * H * D, iters, elt_bytes, ms, peak, peak_src, clocks),
