@@ -769,6 +769,65 @@ def run_ablation(args):
     return 0
 
 
+def run_plane_ablation(args):
+    """The plane-resident fused path (each disparity plane kept in shared memory through the
+    cost, every DT pass pair and the WTA; ZNCC_TUNE_PLANE = 1) against the streaming path (the
+    cost volume in device memory) on the pair shapes it applies to: 320x96 and 640x192 pairs of
+    the configuration generator (seed 3), 9x9 window, 3 DT iterations, F32; CUDA events around
+    each fused run, L2 flushed before each. The two give the same disparity maps (tested; the
+    mismatch share is reported)."""
+    import numpy as np
+    import torch
+
+    from paper_2212_00476_gb300 import zncc as Z
+    from synth import make_pair
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    rows = []
+    for (H, W, D) in ((96, 320, 32), (96, 320, 128), (192, 640, 64), (192, 640, 128), (192, 640, 256)):
+        p = make_pair(H, W, min(D, 128), seed=3)
+        left = torch.from_numpy(p.left).to(dev)
+        right = torch.from_numpy(p.right).to(dev)
+        row = {"W": W, "H": H, "D": D}
+        maps = {}
+        for plane in (1, 0):
+            ctx = Z.ZnccContext(W, H, D, 9)
+            ctx.set_tuning(Z.ZNCC_TUNE_PLANE, plane)
+            disp = torch.empty((H, W), dtype=torch.int16, device=dev)
+            ms = []
+            for i in range(args.warmup + args.steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                ctx.zncc_run(left, right, disp, 20.0, 0.1, 3, Z.ZNCC_F32)
+                b.record()
+                b.synchronize()
+                if i >= args.warmup:
+                    ms.append(a.elapsed_time(b))
+            t = sorted(ms)[len(ms) // 2]
+            row["plane_ms" if plane else "streaming_ms"] = round(t, 4)
+            row["plane_gdisp_s" if plane else "streaming_gdisp_s"] = round(W * H * D / t / 1e6, 2)
+            maps[plane] = disp.cpu().numpy()
+            ctx.close()
+        row["map_mismatch"] = float(np.mean(maps[0] != maps[1]))
+        rows.append(row)
+    at = next(r for r in rows if r["W"] == 640 and r["D"] == 128)
+    line = {
+        "metric": "fused ZNCC+DT+WTA time, plane-resident path vs streaming path (ratio at 640x192, D=128)",
+        "value": round(at["streaming_ms"] / at["plane_ms"], 3), "unit": "x (streaming time / plane time)",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "plane_ablation: 320x96 and 640x192 pairs (seed 3), 9x9, 3 iterations, F32",
+                   "l2": "flushed before every timed call (256 MB write outside the events)"},
+        "rows": rows,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -777,7 +836,7 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--storage", choices=["f32", "f16", "i8"], default="f32")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch_uneven16", "serving", "precision_sweep",
-                                                           "zncc_ablation"],
+                                                           "zncc_ablation", "plane_ablation"],
                     default="paper_1280x384")
     ap.add_argument("--rates", default="200,500,1000,2000", help="serving: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests per rate")
@@ -800,6 +859,8 @@ def main():
         return run_precision(args)
     if args.workload == "zncc_ablation":
         return run_ablation(args)
+    if args.workload == "plane_ablation":
+        return run_plane_ablation(args)
     if args.workload == "batch_uneven16":
         return run_batch(args)
     return run_gb300(args)

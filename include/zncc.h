@@ -270,6 +270,15 @@ const char* zncc_status_string(zncc_status status);
  *   ZNCC_TUNE_V_TQ       vertical DT pairs: lanes per 16-pixel chunk (2, 4 or 8)
  *   ZNCC_TUNE_AHAT_SMS   (F16, I8 storage) SMs the cost kernel leaves free for the A_hat chain,
  *                        which runs beside it on a second stream (default 8)
+ *   ZNCC_TUNE_PLANE      (F32 storage, iters >= 1) 1 = the plane-resident path for pairs with
+ *                        W <= 1024 whose rows split into bands of at most 32 rows over a
+ *                        cluster of 1, 2, 4 or 8 CTAs that fit in shared memory (H <= 256):
+ *                        each disparity plane stays in shared memory for the cost, every DT
+ *                        pass pair and the WTA, and the cost volume is never stored; 0 = the
+ *                        streaming path (cost volume in device memory; the default, faster on
+ *                        GB300 at every measured shape)
+ *   ZNCC_TUNE_PLANE_CS   the plane-resident path's cluster size (1, 2, 4 or 8; 0 = automatic);
+ *                        a size whose band does not fit sends the pair to the streaming path
  * A value a launch cannot use (too many threads or too much shared memory) makes the next
  * call fail with ZNCC_EUNSUPPORTED. Unknown keys give ZNCC_EINVAL. */
 typedef enum {
@@ -277,7 +286,9 @@ typedef enum {
     ZNCC_TUNE_ROW_SPB = 2,
     ZNCC_TUNE_H_TQ = 3,
     ZNCC_TUNE_V_TQ = 4,
-    ZNCC_TUNE_AHAT_SMS = 5
+    ZNCC_TUNE_AHAT_SMS = 5,
+    ZNCC_TUNE_PLANE = 6,
+    ZNCC_TUNE_PLANE_CS = 7
 } zncc_tune_key;
 zncc_status zncc_set_tuning(zncc_ctx* ctx, int key, int value);
 

@@ -39,6 +39,7 @@ def _units():
     units = [(os.path.join(CSRC, "api.cu"), "api.o", []),
              (os.path.join(CSRC, "kernels.cu"), "kernels.o", []),
              (os.path.join(CSRC, "static_scratch.cu"), "static_scratch.o", []),
+             (os.path.join(CSRC, "plane.cu"), "plane.o", []),
              (os.path.join(CSRC, "serve.cpp"), "serve.o", [])]
     for r in RADII:
         units.append((os.path.join(CSRC, "zncc_row.cu"), f"zncc_row_r{r}.o", [f"-DZNCC_R={r}"]))

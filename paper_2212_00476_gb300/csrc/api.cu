@@ -52,11 +52,12 @@ namespace {
 // Kernel kinds for per-kernel timing (zncc_profile_*).
 enum Kind {
     K_STATS = 0, K_COEF, K_ZNCC_RAW, K_ZNCC_HPAIR, K_ZNCC_WTA, K_DT_HPAIR, K_DT_VPAIR,
-    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_AHAT, K_WTA_FINISH, K_ZNCC_SCAN, K_NKINDS
+    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_AHAT, K_WTA_FINISH, K_ZNCC_SCAN, K_PLANE, K_NKINDS
 };
 const char* const kKindNames[K_NKINDS] = {
     "window_stats", "dt_coef", "zncc_cost", "zncc_cost_hpair", "zncc_cost_wta",
-    "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume", "ahat_pair", "wta_finish", "zncc_cost_scan"};
+    "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume", "ahat_pair", "wta_finish", "zncc_cost_scan",
+    "zncc_plane"};
 
 struct ProfRecord {
     int kind, ev0, ev1;
@@ -92,6 +93,10 @@ struct zncc_ctx {
     int row_spb = 0;              // cost kernel: slices per block (0 = automatic)
     int ahat_sms = 0;             // SMs the cost kernel leaves to the A_hat chain (0 = automatic)
     int h_tq = 0, v_tq = 0;       // DT pairs: forced lanes per chunk (0 = automatic)
+    int plane_mode = 0;           // F32 fused runs: the plane-resident path where it applies
+    int plane_force_cs = 0;       // its cluster size (0 = automatic)
+    int plane_cs = -1;            // chosen cluster size (0: streaming path; -1: not chosen yet)
+    int plane_smem = 0, plane_clusters = 0;
     int num_sms = 0;
     std::vector<LinePlan> plans;  // line-pass launch shapes, by pass signature
     int2* scan_stats = nullptr;   // (progressive scan) packed statistics: left [H][W], right [H][W+D-1]
@@ -612,9 +617,114 @@ zncc_status run_ahat(zncc_ctx* lc, const PairIO* io, int n, int p, int pfirst, i
 // coefficients, the cost kernel with the first horizontal pair, the remaining pairs, and
 // WTA in the last vertical pair; every step is one launch for all pairs (one per window
 // radius for the cost kernel).
+// The cluster size of the plane-resident path for a context's shape, or 0 where the pair
+// takes the streaming path: the row length fits the lanes of a warp (W <= 1024) and a band of
+// at most kPlaneBandMax rows per CTA with its image rows fits in shared memory. Among the
+// sizes that fit, the one with the least modelled time: waves of planes (D over the resident
+// clusters) times the rows per CTA plus a fixed cost per plane (barriers, the cost rows' start).
+int plane_choice(zncc_ctx* c) {
+    if (c->plane_cs >= 0) return c->plane_cs;
+    c->plane_cs = 0;
+    if (!c->plane_mode || c->W > kPlaneMaxW || c->W + 2 * c->r > kPlaneThreads * kPlaneColsPerThread) return 0;
+    double best = 0.0;
+    for (int cs = 1; cs <= 8; cs *= 2) {
+        if (c->plane_force_cs && cs != c->plane_force_cs) continue;
+        const PlaneLayout L = plane_layout(c->W, c->H, c->r, cs);
+        if (L.hb > kPlaneBandMax || (long long)L.total > (long long)c->smem_max) continue;
+        int clusters = 0;
+        if (plane_max_clusters(cs, L.total, &clusters) != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const double t = (double)((c->D + clusters - 1) / clusters) * (L.hb + 8);
+        if (c->plane_cs == 0 || t < best) {
+            best = t;
+            c->plane_cs = cs;
+            c->plane_smem = (int)L.total;
+            c->plane_clusters = clusters;
+        }
+    }
+    return c->plane_cs;
+}
+
+// The plane-resident path for F32 runs of the pairs whose shape allows it: the window
+// statistics of both images, one launch per cluster size among the pairs, the WTA finish.
+zncc_status run_plane(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, float sigma_r, int iters) {
+    for (int i = 0; i < n; ++i) {
+        zncc_ctx* c = io[i].c;
+        const size_t nl = (size_t)c->W * c->H, nr = (size_t)(c->W + c->D - 1) * c->H;
+        if (!c->scan_stats && alloc_dev(c, (void**)&c->scan_stats, (nl + nr) * sizeof(int2), "window statistics") != ZNCC_OK)
+            return fail(lc, ZNCC_ENOMEM, c->err);
+        ZNCC_LAUNCH(lc, K_STATS, launch_window_stats(io[i].left, io[i].pitch, c->W, c->H, c->r, 0, c->W, nullptr,
+                                                     nullptr, nullptr, c->scan_stats, lc->cur),
+                    "window statistics (left)");
+        ZNCC_LAUNCH(lc, K_STATS, launch_window_stats(io[i].right, io[i].pitch, c->W, c->H, c->r, -(c->D - 1),
+                                                     c->W + c->D - 1, nullptr, nullptr, nullptr,
+                                                     c->scan_stats + nl, lc->cur),
+                    "window statistics (right)");
+    }
+    for (int cs = 1; cs <= 8; cs *= 2) {
+        PlaneBatch b;
+        memset(&b, 0, sizeof(b));
+        size_t smem = 0;
+        for (int i = 0; i < n; ++i) {
+            zncc_ctx* c = io[i].c;
+            if (c->plane_cs != cs) continue;
+            PlaneArgs& a = b.p[b.npairs++];
+            a.left = io[i].left;
+            a.right = io[i].right;
+            a.pitch = io[i].pitch;
+            a.W = c->W;
+            a.H = c->H;
+            a.D = c->D;
+            a.r = c->r;
+            a.statsL = c->scan_stats;
+            a.statsR = c->scan_stats + (size_t)c->W * c->H;
+            a.keys = c->keys;
+            a.item0 = b.total_items;
+            b.total_items += c->D;
+            smem = std::max(smem, (size_t)c->plane_smem);
+        }
+        if (b.npairs == 0) continue;
+        int clusters = 0;
+        ZNCC_CUDA(lc, plane_max_clusters(cs, smem, &clusters), "plane-resident path occupancy");
+        if (clusters < 1) return fail(lc, ZNCC_EUNSUPPORTED, "plane-resident path: no cluster fits on the device");
+        b.nclusters = std::min(clusters, b.total_items);
+        b.cs = cs;
+        b.iters = iters;
+        b.K = (float)exp(-1.0 / (double)sigma_s);
+        b.inv_sr255 = (float)(1.0 / (255.0 * (double)sigma_r));
+        b.s2 = scale_s2(sigma_s);
+        ZNCC_LAUNCH(lc, K_PLANE, launch_plane(b, smem, lc->cur), "plane-resident ZNCC + DT + WTA");
+    }
+    WtaFinishBatch fb;
+    memset(&fb, 0, sizeof(fb));
+    fb.npairs = n;
+    for (int i = 0; i < n; ++i) {
+        fb.p[i].keys = io[i].c->keys;
+        fb.p[i].disp = io[i].disp;
+        fb.p[i].npix = (long long)io[i].c->W * io[i].c->H;
+        fb.p[i].thread0 = fb.total_threads;
+        fb.total_threads += fb.p[i].npix;
+    }
+    ZNCC_LAUNCH(lc, K_WTA_FINISH, launch_wta_finish(fb, lc->cur), "WTA finish");
+    return ZNCC_OK;
+}
+
 zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigma_r, int iters,
                       int storage) {
     if (iters == 0) return run_rows(lc, io, n, kModeWta, 0, 0.0f, 0.0f, 0.0f, K_ZNCC_WTA, 0, "ZNCC + WTA");
+    if (storage == ZNCC_F32) {      // pairs whose planes fit on chip take the plane-resident path
+        PairIO plane[kMaxBatch];
+        int np = 0, ns = 0;
+        for (int i = 0; i < n; ++i) {
+            if (plane_choice(io[i].c) > 0) plane[np++] = io[i];
+            else io[ns++] = io[i];
+        }
+        if (np) ZNCC_TRY(run_plane(lc, plane, np, sigma_s, sigma_r, iters));
+        if (ns == 0) return ZNCC_OK;
+        n = ns;
+    }
     const int dt = storage;                         // 0 float, 1 half, 2 FastDT codes
     zncc_ctx* ctxs[kMaxBatch];
     for (int i = 0; i < n; ++i) {
@@ -1138,6 +1248,12 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
         case ZNCC_TUNE_ROW_MINB2: c->row_minb2 = value ? 1 : 0; break;
         case ZNCC_TUNE_ROW_SPB: c->row_spb = value; break;
         case ZNCC_TUNE_AHAT_SMS: c->ahat_sms = value; break;
+        case ZNCC_TUNE_PLANE: c->plane_mode = value ? 1 : 0; break;
+        case ZNCC_TUNE_PLANE_CS:
+            if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+                return fail(c, ZNCC_EINVAL, "plane cluster size must be 0, 1, 2, 4 or 8");
+            c->plane_force_cs = value;
+            break;
         case ZNCC_TUNE_H_TQ:
         case ZNCC_TUNE_V_TQ:
             if (value != 0 && value != 2 && value != 4 && value != 8)
@@ -1147,6 +1263,7 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
         default: return fail(c, ZNCC_EINVAL, "unknown tuning key");
     }
     c->plans.clear();
+    c->plane_cs = -1;
     return ZNCC_OK;
 }
 

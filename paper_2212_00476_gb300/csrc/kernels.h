@@ -186,6 +186,67 @@ cudaError_t launch_zncc_scan(int R, const ScanArgs& a, int dtype, cudaStream_t s
 
 cudaError_t launch_mulmap(const float* ain, float xscale, float s2, int W, int H, bool horiz, float2* out,
                           cudaStream_t st);
+
+// The plane-resident fused path (plane.cu): a cluster of cs CTAs holds one disparity plane,
+// CTA q the rows [q hb, (q+1) hb), for the cost, every DT pass pair and the WTA.
+constexpr int kPlaneThreads = 384;
+constexpr int kPlaneWarps = kPlaneThreads / 32;
+constexpr int kPlaneSegMax = 33;          // positions of a row per lane: W <= 1024
+constexpr int kPlaneBandMax = 32;         // rows per CTA (a column's run stays in registers)
+constexpr int kPlaneTileRows = 4;         // rows of window column sums per cost step
+constexpr int kPlaneColsPerThread = 4;    // window-sum columns per thread: W + 2r <= 1536
+constexpr int kPlaneMaxW = 1024;
+
+// Byte offsets of a CTA's shared memory for a W x H pair of window radius r in clusters of cs.
+struct PlaneLayout {
+    int hb;                   // rows per CTA
+    int wb;                   // row pitch of the image rows (bytes)
+    int vw;                   // window-sum columns: W + 2r
+    unsigned lut, plane, vt, st, cf, cb, lb, rb, total;
+};
+__host__ __device__ inline PlaneLayout plane_layout(int W, int H, int r, int cs) {
+    PlaneLayout L;
+    L.hb = (H + cs - 1) / cs;
+    L.wb = (W + 15) & ~15;
+    L.vw = W + 2 * r;
+    auto up = [](unsigned o) { return (o + 15u) & ~15u; };
+    unsigned o = 0;
+    L.lut = o;
+    o = up(o + 256u * 4u);
+    L.plane = o;                                        // float [hb][W]
+    o = up(o + (unsigned)L.hb * W * 4u);
+    L.vt = o;                                           // int [kPlaneTileRows][vw]
+    o = up(o + (unsigned)kPlaneTileRows * L.vw * 4u);
+    L.st = o;                                           // int2 [2][kPlaneTileRows][W]: statistics
+    o = up(o + 2u * kPlaneTileRows * W * 8u);
+    L.cf = o;                                           // float2 [W]: forward maps (cs > 1)
+    o = up(o + (cs > 1 ? (unsigned)W * 8u : 0u));
+    L.cb = o;                                           // float2 [W]: backward maps (cs > 1)
+    o = up(o + (cs > 1 ? (unsigned)W * 8u : 0u));
+    L.lb = o;                                           // uint8 [hb + 2r][wb]: left rows
+    o = up(o + (unsigned)(L.hb + 2 * r) * L.wb);
+    L.rb = o;                                           // uint8 [hb + 2r][wb]: right rows
+    o = up(o + (unsigned)(L.hb + 2 * r) * L.wb);
+    L.total = o;
+    return L;
+}
+
+struct PlaneArgs {
+    const uint8_t* left;
+    const uint8_t* right;
+    int pitch, W, H, D, r;
+    const int2* statsL;       // [H][W] (S, inv_sigma bits) of the left windows
+    const int2* statsR;       // [H][W + D - 1]: right windows centred at c, at index c + D - 1
+    unsigned long long* keys; // [H][W] WTA keys, zero before the launch
+    int item0;                // items item0 + d, d in [0, D), are this pair's planes
+};
+struct PlaneBatch {
+    int npairs, total_items, nclusters, cs, iters;
+    float K, inv_sr255, s2;   // exp(-1/sigma_s), 1/(255 sigma_r), (1 - K)^2
+    PlaneArgs p[kMaxBatch];
+};
+cudaError_t plane_max_clusters(int cs, size_t smem, int* clusters);
+cudaError_t launch_plane(const PlaneBatch& b, size_t smem, cudaStream_t st);
 cudaError_t launch_fastdt_codec(const int16_t* values, int n, uint8_t* codes, int16_t* decoded, cudaStream_t st);
 
 // Device allocation of the library (cudaMalloc, or an injected out-of-memory failure when the
