@@ -712,10 +712,10 @@ def run_serving(args):
 def run_ablation(args):
     """The paper's Z²-ZNCC vs "original" progressive-scan comparison (Sec. V-B, Fig.
     ZNCC_compare) as an ablation of this repository's kernels: the cost volume of the
-    1280x384 pair (seed 2) by the packed-column cost kernel (zncc_cost_volume) and by the
-    progressive-scan kernel (zncc_cost_volume_scan), F32 volume, window sides 3..15, D = 96 and
-    128; CUDA events around each call, L2 flushed before each. The two give identical values
-    (tested)."""
+    1280x384 pair (seed 2) by the packed-column cost kernel (zncc_cost_volume), by the
+    progressive-scan kernel (zncc_cost_volume_scan) and by the tensor-core banded product
+    (zncc_cost_volume_mma), F32 volume, window sides 3..15, D = 96 and 128; CUDA events around
+    each call, L2 flushed before each. The three give identical values (tested)."""
     import torch
 
     from paper_2212_00476_gb300 import zncc as Z
@@ -750,8 +750,10 @@ def run_ablation(args):
             ctx = Z.ZnccContext(W, H, D, win)
             t_packed = timed(lambda: ctx.zncc_cost_volume(left, right, vol))
             t_scan = timed(lambda: ctx.zncc_cost_volume_scan(left, right, vol))
+            t_mma = timed(lambda: ctx.zncc_cost_volume_mma(left, right, vol))
             rows.append({"win": win, "D": D, "packed_ms": round(t_packed, 4), "scan_ms": round(t_scan, 4),
-                         "speedup": round(t_scan / t_packed, 3)})
+                         "mma_ms": round(t_mma, 4), "speedup": round(t_scan / t_packed, 3),
+                         "mma_vs_packed": round(t_packed / t_mma, 3)})
             ctx.close()
         del vol
     at9 = next(r for r in rows if r["win"] == 9 and r["D"] == 128)

@@ -101,6 +101,16 @@ zncc_status zncc_cost_volume(zncc_ctx* ctx, const uint8_t* left, const uint8_t* 
 zncc_status zncc_cost_volume_scan(zncc_ctx* ctx, const uint8_t* left, const uint8_t* right,
                                   int pitch, void* cost, zncc_dtype dtype);
 
+/* The same cost volume with the window cross sums P on the tensor cores (the banded
+ * correlation as a matrix product): per image row, A[x][(j,i)] = I_R(x+i, y+j) and
+ * B[c][(j,i)] = I_T(c+i, y+j) in BF16 (pixels are exact), P(x, d) = (A B^T)[x][x-d] accumulated
+ * in FP32, exact because every partial sum of a window stays below 2^24; then Eq. (2) as in
+ * zncc_cost_volume. An ablation of the packed-column kernel: identical values. Allocates the
+ * same statistics scratch as zncc_cost_volume_scan on first use.
+ * cost: device [H][W][D] of `dtype` (ZNCC_F32 or ZNCC_F16). */
+zncc_status zncc_cost_volume_mma(zncc_ctx* ctx, const uint8_t* left, const uint8_t* right,
+                                 int pitch, void* cost, zncc_dtype dtype);
+
 /* DT cost aggregation in place (Sec. III-B, Eqs. (3)-(6) with the weights of Eq. (11)),
  * `iters` times the pass chain left-to-right, right-to-left, up-to-down, down-to-up.
  * Weights: W = K * exp(-|G(p) - G(q)| / sigma_r), K = exp(-1/sigma_s), G = guide / 255

@@ -52,12 +52,12 @@ namespace {
 // Kernel kinds for per-kernel timing (zncc_profile_*).
 enum Kind {
     K_STATS = 0, K_COEF, K_ZNCC_RAW, K_ZNCC_HPAIR, K_ZNCC_WTA, K_DT_HPAIR, K_DT_VPAIR,
-    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_AHAT, K_WTA_FINISH, K_ZNCC_SCAN, K_PLANE, K_NKINDS
+    K_DT_VPAIR_WTA, K_WTA_VOLUME, K_AHAT, K_WTA_FINISH, K_ZNCC_SCAN, K_PLANE, K_ZNCC_MMA, K_NKINDS
 };
 const char* const kKindNames[K_NKINDS] = {
     "window_stats", "dt_coef", "zncc_cost", "zncc_cost_hpair", "zncc_cost_wta",
     "dt_hpair", "dt_vpair", "dt_vpair_wta", "wta_volume", "ahat_pair", "wta_finish", "zncc_cost_scan",
-    "zncc_plane"};
+    "zncc_plane", "zncc_cost_mma"};
 
 struct ProfRecord {
     int kind, ev0, ev1;
@@ -978,8 +978,13 @@ zncc_status zncc_cost_volume(zncc_ctx* c, const uint8_t* left, const uint8_t* ri
     return run_rows(c, &io, 1, kModeRaw, dtype, 0.0f, 0.0f, 0.0f, K_ZNCC_RAW, 0, "ZNCC cost");
 }
 
-zncc_status zncc_cost_volume_scan(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch,
-                                  void* cost, zncc_dtype dtype) {
+}  // extern "C"
+
+namespace {
+// The cost-volume ablations (progressive scan, tensor-core banded product): the window
+// statistics of both images (left centres x, right centres x - d for d < D), then the kernel.
+zncc_status cost_volume_variant(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch, void* cost,
+                                zncc_dtype dtype, bool mma) {
     if (!c) return ZNCC_EINVAL;
     c->err.clear();
     ZNCC_TRY(check_images(c, left, right, pitch));
@@ -1003,8 +1008,22 @@ zncc_status zncc_cost_volume_scan(zncc_ctx* c, const uint8_t* left, const uint8_
     a.packL = pl;
     a.packR = pr;
     a.vol = cost;
-    ZNCC_LAUNCH(c, K_ZNCC_SCAN, launch_zncc_scan(c->r, a, dtype, c->cur), "progressive-scan ZNCC");
+    if (mma) ZNCC_LAUNCH(c, K_ZNCC_MMA, launch_zncc_mma(c->r, a, dtype, c->cur), "tensor-core ZNCC");
+    else ZNCC_LAUNCH(c, K_ZNCC_SCAN, launch_zncc_scan(c->r, a, dtype, c->cur), "progressive-scan ZNCC");
     return ZNCC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+zncc_status zncc_cost_volume_scan(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch,
+                                  void* cost, zncc_dtype dtype) {
+    return cost_volume_variant(c, left, right, pitch, cost, dtype, false);
+}
+
+zncc_status zncc_cost_volume_mma(zncc_ctx* c, const uint8_t* left, const uint8_t* right, int pitch,
+                                 void* cost, zncc_dtype dtype) {
+    return cost_volume_variant(c, left, right, pitch, cost, dtype, true);
 }
 
 zncc_status dt_aggregate(zncc_ctx* c, const uint8_t* guide, int pitch, void* cost, zncc_dtype dtype,

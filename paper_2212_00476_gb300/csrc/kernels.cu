@@ -839,6 +839,19 @@ cudaError_t launch_zncc_scan(int R, const ScanArgs& a, int dtype, cudaStream_t s
     }
 }
 
+cudaError_t launch_zncc_mma(int R, const ScanArgs& a, int dtype, cudaStream_t st) {
+    switch (R) {
+        case 1: return launch_zncc_mma_r1(a, dtype, st);
+        case 2: return launch_zncc_mma_r2(a, dtype, st);
+        case 3: return launch_zncc_mma_r3(a, dtype, st);
+        case 4: return launch_zncc_mma_r4(a, dtype, st);
+        case 5: return launch_zncc_mma_r5(a, dtype, st);
+        case 6: return launch_zncc_mma_r6(a, dtype, st);
+        case 7: return launch_zncc_mma_r7(a, dtype, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t zncc_row_occupancy(int R, int mode, int dtype, int threads, size_t smem, bool minb2,
                                bool single, int* blocks_per_sm) {
     switch (R) {

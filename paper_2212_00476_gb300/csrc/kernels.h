@@ -183,6 +183,9 @@ struct ScanArgs {
     void* vol;                // [H][W][D] float or half
 };
 cudaError_t launch_zncc_scan(int R, const ScanArgs& a, int dtype, cudaStream_t st);
+// The same cost volume with the window cross sums as a banded BF16 matrix product on the
+// tensor cores (mma.sync, exact FP32 accumulation): identical values (zncc_mma.cuh).
+cudaError_t launch_zncc_mma(int R, const ScanArgs& a, int dtype, cudaStream_t st);
 
 cudaError_t launch_mulmap(const float* ain, float xscale, float s2, int W, int H, bool horiz, float2* out,
                           cudaStream_t st);
@@ -265,7 +268,8 @@ cudaError_t noalloc_scratch_address(void** p);
                                      cudaStream_t st);                                             \
     cudaError_t zncc_row_occupancy_r##R(int mode, int dtype, int threads, size_t smem, bool minb2, bool single, \
                                         int* bps);                                                    \
-    cudaError_t launch_zncc_scan_r##R(const ScanArgs& a, int dtype, cudaStream_t st);
+    cudaError_t launch_zncc_scan_r##R(const ScanArgs& a, int dtype, cudaStream_t st);                \
+    cudaError_t launch_zncc_mma_r##R(const ScanArgs& a, int dtype, cudaStream_t st);
 ZNCC_DECLARE_ROW(1)
 ZNCC_DECLARE_ROW(2)
 ZNCC_DECLARE_ROW(3)

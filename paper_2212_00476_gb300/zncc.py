@@ -6,8 +6,8 @@ loaded, every call raises.
 
 The methods of ZnccContext carry the names of the C calls they wrap:
 
-    zncc_window_stats, zncc_cost_volume, zncc_cost_volume_scan, dt_aggregate, wta_disparity,
-    zncc_run, zncc_run_host
+    zncc_window_stats, zncc_cost_volume, zncc_cost_volume_scan, zncc_cost_volume_mma,
+    dt_aggregate, wta_disparity, zncc_run, zncc_run_host
 
 and the module-level zncc_run_batch, dt_aggregate_noalloc and fastdt_codec wrap the batched
 call, the context-free aggregation that allocates nothing and the FastDT code on the device. serve_create, serve_submit, serve_poll and
@@ -44,6 +44,7 @@ SIGNATURES = [
     ("zncc_window_stats", _i, [_vp, _vp, _i, _vp, _vp, _vp]),
     ("zncc_cost_volume", _i, [_vp, _vp, _vp, _i, _vp, _i]),
     ("zncc_cost_volume_scan", _i, [_vp, _vp, _vp, _i, _vp, _i]),
+    ("zncc_cost_volume_mma", _i, [_vp, _vp, _vp, _i, _vp, _i]),
     ("dt_aggregate", _i, [_vp, _vp, _i, _vp, _i, _f, _f, _i]),
     ("dt_aggregate_noalloc", _i, [_vp, _i, _i, _i, _i, _vp, _i, _f, _f, _i, _vp]),
     ("wta_disparity", _i, [_vp, _vp, _i, _vp]),
@@ -285,6 +286,10 @@ class ZnccContext:
     def zncc_cost_volume_scan(self, left, right, cost, dtype: int = ZNCC_F32):
         self._check(lib().zncc_cost_volume_scan(self._h, _ptr(left), _ptr(right), left.stride(0),
                                                 _ptr(cost), dtype))
+
+    def zncc_cost_volume_mma(self, left, right, cost, dtype: int = ZNCC_F32):
+        self._check(lib().zncc_cost_volume_mma(self._h, _ptr(left), _ptr(right), left.stride(0),
+                                               _ptr(cost), dtype))
 
     def dt_aggregate(self, guide, cost, sigma_s: float, sigma_r: float, iters: int,
                      dtype: int = ZNCC_F32):

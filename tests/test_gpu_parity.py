@@ -131,6 +131,50 @@ def test_progressive_scan_cost_equals_packed_cost(h, w, d, win):
     ctx.close()
 
 
+# (h, w, D, window): several 64-pixel tiles with a ragged last one, strips of 8 rows with a
+# ragged last one, two and three 128-disparity chunks, D = 1 and 3, every window side
+MMA_CASES = COST_CASES + [(19, 200, 300, 9), (9, 130, 129, 15), (12, 64, 3, 3), (17, 70, 1, 5),
+                          (21, 150, 96, 11), (8, 65, 40, 13), (10, 100, 60, 7)]
+
+
+@pytest.mark.parametrize("h,w,d,win", MMA_CASES)
+def test_tensor_core_cost_equals_packed_cost(h, w, d, win):
+    """The tensor-core ablation (window cross sums as a banded BF16 product, FP32 accumulation)
+    gives the packed-column kernel's values bit for bit: the products are exact integers."""
+    p = rand_pair(h, w, max(d, 1), seed=h * 11 + w + d + win)
+    ctx = Z.ZnccContext(w, h, d, win)
+    c = gpu_cost(ctx, p.left, p.right)
+    s = torch.empty_like(c)
+    ctx.zncc_cost_volume_mma(dev(p.left), dev(p.right), s)
+    torch.cuda.synchronize()
+    assert torch.equal(c, s), f"{int((c != s).sum())} of {c.numel()} values differ"
+    s16 = torch.empty((h, w, d), dtype=torch.float16, device="cuda")
+    ctx.zncc_cost_volume_mma(dev(p.left), dev(p.right), s16, Z.ZNCC_F16)
+    torch.cuda.synchronize()
+    assert torch.equal(c.half(), s16)
+    ctx.close()
+
+
+def test_tensor_core_cost_at_full_size_on_sampled_pixels():
+    """1280x384, D = 128, 9x9 (the bench pair's shape, random texture): identical to the packed
+    kernel everywhere and to the FP64 oracle on sampled pixels within ZNCC_TOL."""
+    h, w, d, win = 384, 1280, 128, 9
+    p = rand_pair(h, w, d, seed=5)
+    ctx = Z.ZnccContext(w, h, d, win)
+    c = gpu_cost(ctx, p.left, p.right)
+    s = torch.empty_like(c)
+    ctx.zncc_cost_volume_mma(dev(p.left), dev(p.right), s)
+    torch.cuda.synchronize()
+    assert torch.equal(c, s)
+    rng = np.random.default_rng(0)
+    sc = s.cpu().numpy()
+    lib = oracle.load()
+    for y, x, dd in zip(rng.integers(0, h, 512), rng.integers(0, w, 512), rng.integers(0, d, 512)):
+        ref = oracle.zncc_at(p.left, p.right, win // 2, int(x), int(y), int(dd), lib=lib)
+        assert abs(float(sc[y, x, dd]) - ref) <= ZNCC_TOL
+    ctx.close()
+
+
 def test_cost_volume_fp16_storage_is_rounded_fp32():
     p = rand_pair(30, 90, 24, seed=9)
     ctx = Z.ZnccContext(90, 30, 24, 9)
