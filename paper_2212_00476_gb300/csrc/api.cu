@@ -96,7 +96,7 @@ struct zncc_ctx {
     int plane_mode = 0;           // F32 fused runs: the plane-resident path where it applies
     int plane_force_cs = 0;       // its cluster size (0 = automatic)
     int plane_cs = -1;            // chosen cluster size (0: streaming path; -1: not chosen yet)
-    int plane_smem = 0, plane_clusters = 0;
+    int plane_cls = 0, plane_smem = 0, plane_clusters = 0;   // its size class, shared memory, clusters
     int num_sms = 0;
     std::vector<LinePlan> plans;  // line-pass launch shapes, by pass signature
     int2* scan_stats = nullptr;   // (progressive scan) packed statistics: left [H][W], right [H][W+D-1]
@@ -619,9 +619,10 @@ zncc_status run_ahat(zncc_ctx* lc, const PairIO* io, int n, int p, int pfirst, i
 // radius for the cost kernel).
 // The cluster size of the plane-resident path for a context's shape, or 0 where the pair
 // takes the streaming path: the row length fits the lanes of a warp (W <= 1024) and a band of
-// at most kPlaneBandMax rows per CTA with its image rows fits in shared memory. Among the
-// sizes that fit, the one with the least modelled time: waves of planes (D over the resident
-// clusters) times the rows per CTA plus a fixed cost per plane (barriers, the cost rows' start).
+// at most kPlaneBandMax rows per CTA with its image rows fits in shared memory; with it the
+// kernel's size class (plane_class). Among the sizes that fit, the one with the least modelled
+// time: waves of planes (D over the resident clusters) times the rows per CTA plus a fixed cost
+// per plane (barriers, the cost rows' start).
 int plane_choice(zncc_ctx* c) {
     if (c->plane_cs >= 0) return c->plane_cs;
     c->plane_cs = 0;
@@ -630,9 +631,10 @@ int plane_choice(zncc_ctx* c) {
     for (int cs = 1; cs <= 8; cs *= 2) {
         if (c->plane_force_cs && cs != c->plane_force_cs) continue;
         const PlaneLayout L = plane_layout(c->W, c->H, c->r, cs);
-        if (L.hb > kPlaneBandMax || (long long)L.total > (long long)c->smem_max) continue;
+        const int cls = plane_class(c->W, L.hb);
+        if (cls < 0 || (long long)L.total > (long long)c->smem_max) continue;
         int clusters = 0;
-        if (plane_max_clusters(cs, L.total, &clusters) != cudaSuccess || clusters < 1) {
+        if (plane_max_clusters(cls, cs, L.total, &clusters) != cudaSuccess || clusters < 1) {
             cudaGetLastError();
             continue;
         }
@@ -640,6 +642,7 @@ int plane_choice(zncc_ctx* c) {
         if (c->plane_cs == 0 || t < best) {
             best = t;
             c->plane_cs = cs;
+            c->plane_cls = cls;
             c->plane_smem = (int)L.total;
             c->plane_clusters = clusters;
         }
@@ -663,13 +666,14 @@ zncc_status run_plane(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, floa
                                                      c->scan_stats + nl, lc->cur),
                     "window statistics (right)");
     }
-    for (int cs = 1; cs <= 8; cs *= 2) {
+    for (int group = 0; group < 4 * kPlaneClasses; ++group) {      // one launch per (cluster size, class)
+        const int cs = 1 << (group / kPlaneClasses), cls = group % kPlaneClasses;
         PlaneBatch b;
         memset(&b, 0, sizeof(b));
         size_t smem = 0;
         for (int i = 0; i < n; ++i) {
             zncc_ctx* c = io[i].c;
-            if (c->plane_cs != cs) continue;
+            if (c->plane_cs != cs || c->plane_cls != cls) continue;
             PlaneArgs& a = b.p[b.npairs++];
             a.left = io[i].left;
             a.right = io[i].right;
@@ -687,7 +691,7 @@ zncc_status run_plane(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, floa
         }
         if (b.npairs == 0) continue;
         int clusters = 0;
-        ZNCC_CUDA(lc, plane_max_clusters(cs, smem, &clusters), "plane-resident path occupancy");
+        ZNCC_CUDA(lc, plane_max_clusters(cls, cs, smem, &clusters), "plane-resident path occupancy");
         if (clusters < 1) return fail(lc, ZNCC_EUNSUPPORTED, "plane-resident path: no cluster fits on the device");
         b.nclusters = std::min(clusters, b.total_items);
         b.cs = cs;
@@ -695,7 +699,7 @@ zncc_status run_plane(zncc_ctx* lc, const PairIO* io, int n, float sigma_s, floa
         b.K = (float)exp(-1.0 / (double)sigma_s);
         b.inv_sr255 = (float)(1.0 / (255.0 * (double)sigma_r));
         b.s2 = scale_s2(sigma_s);
-        ZNCC_LAUNCH(lc, K_PLANE, launch_plane(b, smem, lc->cur), "plane-resident ZNCC + DT + WTA");
+        ZNCC_LAUNCH(lc, K_PLANE, launch_plane(b, cls, smem, lc->cur), "plane-resident ZNCC + DT + WTA");
     }
     WtaFinishBatch fb;
     memset(&fb, 0, sizeof(fb));

@@ -194,8 +194,15 @@ cudaError_t launch_mulmap(const float* ain, float xscale, float s2, int W, int H
 // CTA q the rows [q hb, (q+1) hb), for the cost, every DT pass pair and the WTA.
 constexpr int kPlaneThreads = 384;
 constexpr int kPlaneWarps = kPlaneThreads / 32;
-constexpr int kPlaneSegMax = 33;          // positions of a row per lane: W <= 1024
-constexpr int kPlaneBandMax = 32;         // rows per CTA (a column's run stays in registers)
+// Size classes of the kernel (template instances): the longest row segment per lane and the
+// most rows per CTA its registers hold, and the CTAs per SM it is compiled for. The host picks
+// the smallest class that fits a pair: shorter unrolled loops and, for the first, twice the
+// warps per SM.
+constexpr int kPlaneClasses = 3;
+constexpr int kPlaneSegMaxOf[kPlaneClasses] = {11, 21, 33};      // W <= 352, 672, 1024
+constexpr int kPlaneBandMaxOf[kPlaneClasses] = {16, 24, 32};
+constexpr int kPlaneMinBlocksOf[kPlaneClasses] = {2, 1, 1};
+constexpr int kPlaneBandMax = 32;         // rows per CTA in the largest class
 constexpr int kPlaneTileRows = 4;         // rows of window column sums per cost step
 constexpr int kPlaneColsPerThread = 4;    // window-sum columns per thread: W + 2r <= 1536
 constexpr int kPlaneMaxW = 1024;
@@ -248,8 +255,15 @@ struct PlaneBatch {
     float K, inv_sr255, s2;   // exp(-1/sigma_s), 1/(255 sigma_r), (1 - K)^2
     PlaneArgs p[kMaxBatch];
 };
-cudaError_t plane_max_clusters(int cs, size_t smem, int* clusters);
-cudaError_t launch_plane(const PlaneBatch& b, size_t smem, cudaStream_t st);
+// The smallest size class holding rows of W pixels and bands of hb rows, or -1.
+inline int plane_class(int W, int hb) {
+    const int seg = ((W + 31) / 32) | 1;
+    for (int k = 0; k < kPlaneClasses; ++k)
+        if (seg <= kPlaneSegMaxOf[k] && hb <= kPlaneBandMaxOf[k]) return k;
+    return -1;
+}
+cudaError_t plane_max_clusters(int cls, int cs, size_t smem, int* clusters);
+cudaError_t launch_plane(const PlaneBatch& b, int cls, size_t smem, cudaStream_t st);
 cudaError_t launch_fastdt_codec(const int16_t* values, int n, uint8_t* codes, int16_t* decoded, cudaStream_t st);
 
 // Device allocation of the library (cudaMalloc, or an injected out-of-memory failure when the

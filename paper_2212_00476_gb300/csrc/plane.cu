@@ -3,9 +3,9 @@
 // cost volume ever leaving shared memory.
 //
 // A thread-block cluster of cs CTAs owns one plane C(., ., d) at a time: CTA q holds the rows
-// [q hb, (q+1) hb) of it (hb = ceil(H / cs) <= kPlaneBandMax) as FP32 in shared memory, with
-// the left and right image rows of its band and r halo rows above and below (clamped to the
-// image, as every window access is). Per disparity d:
+// [q hb, (q+1) hb) of it (hb = ceil(H / cs) <= BANDMAX, the size class's) as FP32 in shared
+// memory, with the left and right image rows of its band and r halo rows above and below
+// (clamped to the image, as every window access is). Per disparity d:
 //   cost      column sums of L(x', .) R(x' - d, .) over the 2r+1 rows of each window, slid
 //             down the band four rows at a time, then the row sum of 2r+1 of them and Eq. (2)
 //             with the window statistics of k_window_stats, which stream into shared memory
@@ -45,7 +45,8 @@ __device__ __forceinline__ float weight(const float* lut, int a, int b) { return
 
 }  // namespace
 
-__global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constant__ PlaneBatch b) {
+template <int SEGMAX, int BANDMAX, int MINB>
+__global__ void __launch_bounds__(kPlaneThreads, MINB) k_plane(const __grid_constant__ PlaneBatch b) {
     extern __shared__ __align__(16) unsigned char psm[];
     griddep_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -167,10 +168,10 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constan
                 for (int t = warp; t < hq; t += kPlaneWarps) {
                     float* row = plane + t * W;
                     const uint8_t* g = G + t * wb;
-                    float xv[kPlaneSegMax], w[kPlaneSegMax + 1];     // w[k]: the step p0+k-1 -> p0+k
+                    float xv[SEGMAX], w[SEGMAX + 1];     // w[k]: the step p0+k-1 -> p0+k
                     int gp = g[max(p0 - 1, 0)];
 #pragma unroll
-                    for (int k = 0; k <= kPlaneSegMax; ++k) {
+                    for (int k = 0; k <= SEGMAX; ++k) {
                         if (k <= len) {
                             const int pos = p0 + k;
                             const int gc = pos < W ? g[pos] : gp;
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constan
                     // forward: f(x) = c(x) + w(x) f(x-1)
                     float u = 0.0f, P = 1.0f;
 #pragma unroll
-                    for (int k = 0; k < kPlaneSegMax; ++k)
+                    for (int k = 0; k < SEGMAX; ++k)
                         if (k < len) {
                             u = fmaf(w[k], u, xv[k]);
                             P *= w[k];
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constan
                     float c = __shfl_up_sync(kFull, u, 1);
                     if (lane == 0) c = 0.0f;
 #pragma unroll
-                    for (int k = 0; k < kPlaneSegMax; ++k)
+                    for (int k = 0; k < SEGMAX; ++k)
                         if (k < len) {
                             c = fmaf(w[k], c, xv[k]);
                             xv[k] = c;
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constan
                     u = 0.0f;
                     P = 1.0f;
 #pragma unroll
-                    for (int k = kPlaneSegMax - 1; k >= 0; --k)
+                    for (int k = SEGMAX - 1; k >= 0; --k)
                         if (k < len) {
                             u = fmaf(w[k + 1], u, xv[k]);
                             P *= w[k + 1];
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constan
                     c = __shfl_down_sync(kFull, u, 1);
                     if (lane == 31) c = 0.0f;
 #pragma unroll
-                    for (int k = kPlaneSegMax - 1; k >= 0; --k)
+                    for (int k = SEGMAX - 1; k >= 0; --k)
                         if (k < len) {
                             c = fmaf(w[k + 1], c, xv[k]);
                             row[p0 + k] = s2 * c;
@@ -232,11 +233,11 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constan
                 for (int x0 = 0; x0 < W; x0 += kPlaneThreads) {    // the same count in every CTA
                     const int x = x0 + tid;
                     const bool col = x < W, live = col && hq > 0;
-                    float xv[kPlaneBandMax], w[kPlaneBandMax + 1];   // w[k]: the step y0+k-1 -> y0+k
+                    float xv[BANDMAX], w[BANDMAX + 1];   // w[k]: the step y0+k-1 -> y0+k
                     if (live) {
                         int gp = G[-wb + x];
 #pragma unroll
-                        for (int k = 0; k <= kPlaneBandMax; ++k) {
+                        for (int k = 0; k <= BANDMAX; ++k) {
                             if (k <= hq) {
                                 const int y = y0 + k;
                                 const int gc = y < H ? G[k * wb + x] : gp;
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constan
                     float u = 0.0f, P = 1.0f;
                     if (live) {
 #pragma unroll
-                        for (int k = 0; k < kPlaneBandMax; ++k)
+                        for (int k = 0; k < BANDMAX; ++k)
                             if (k < hq) {
                                 u = fmaf(w[k], u, xv[k]);
                                 P *= w[k];
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constan
                     }
                     if (live) {
 #pragma unroll
-                        for (int k = 0; k < kPlaneBandMax; ++k)
+                        for (int k = 0; k < BANDMAX; ++k)
                             if (k < hq) {
                                 c = fmaf(w[k], c, xv[k]);
                                 xv[k] = c;
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constan
                     P = 1.0f;
                     if (live) {
 #pragma unroll
-                        for (int k = kPlaneBandMax - 1; k >= 0; --k)
+                        for (int k = BANDMAX - 1; k >= 0; --k)
                             if (k < hq) {
                                 u = fmaf(w[k + 1], u, xv[k]);
                                 P *= w[k + 1];
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constan
                     }
                     if (live) {
 #pragma unroll
-                        for (int k = kPlaneBandMax - 1; k >= 0; --k)
+                        for (int k = BANDMAX - 1; k >= 0; --k)
                             if (k < hq) {
                                 c = fmaf(w[k + 1], c, xv[k]);
                                 const float v = s2 * c;
@@ -311,12 +312,25 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(const __grid_constan
     if (cs > 1) cluster_sync_all();           // no CTA leaves while another may read its carries
 }
 
-cudaError_t plane_max_clusters(int cs, size_t smem, int* clusters) {
-    cudaError_t e = cudaFuncSetAttribute(k_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+namespace {
+using PlaneKernel = void (*)(PlaneBatch);
+PlaneKernel plane_kernel(int cls) {
+    switch (cls) {
+        case 0: return k_plane<kPlaneSegMaxOf[0], kPlaneBandMaxOf[0], kPlaneMinBlocksOf[0]>;
+        case 1: return k_plane<kPlaneSegMaxOf[1], kPlaneBandMaxOf[1], kPlaneMinBlocksOf[1]>;
+        default: return k_plane<kPlaneSegMaxOf[2], kPlaneBandMaxOf[2], kPlaneMinBlocksOf[2]>;
+    }
+}
+}  // namespace
+
+cudaError_t plane_max_clusters(int cls, int cs, size_t smem, int* clusters) {
+    if (cls < 0 || cls >= kPlaneClasses) return cudaErrorInvalidValue;
+    PlaneKernel fn = plane_kernel(cls);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (cs == 1) {
         int bps = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_plane, kPlaneThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kPlaneThreads, smem);
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         *clusters = bps * sms;
@@ -333,16 +347,18 @@ cudaError_t plane_max_clusters(int cs, size_t smem, int* clusters) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(clusters, k_plane, &cfg);
+    return cudaOccupancyMaxActiveClusters(clusters, fn, &cfg);
 }
 
-cudaError_t launch_plane(const PlaneBatch& b, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_plane(const PlaneBatch& b, int cls, size_t smem, cudaStream_t st) {
+    if (cls < 0 || cls >= kPlaneClasses) return cudaErrorInvalidValue;
+    PlaneKernel fn = plane_kernel(cls);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[2];
     launch_config(cfg, attr, dim3((unsigned)(b.nclusters * b.cs)), dim3(kPlaneThreads), smem, st, b.cs);
-    return cudaLaunchKernelEx(&cfg, k_plane, b);
+    return cudaLaunchKernelEx(&cfg, fn, b);
 }
 
 }  // namespace zncc
