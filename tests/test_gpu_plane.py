@@ -8,9 +8,10 @@ thread-block cluster by rows.
                     input: identical except at such near-ties
   batch             a batch mixing plane-resident and streaming pairs equals the single runs
 
-Cases span every cluster size (1, 2, 4, 8), bands whose last one is partial or empty, rows of
-more than one column group (W > 384 threads), the widest rows (W = 1024) with the largest
-window, a single row, D = 1 and D not a multiple of 4.
+Cases span every cluster size (1, 2, 4, 8) and all three size classes of the kernel (row
+segments per lane up to 11, 21 and 33 positions, bands up to 16, 24 and 32 rows), bands whose
+last one is partial or empty, rows of more than one column group (W > 384 threads), the widest
+rows (W = 1024) with the largest window, a single row, D = 1 and D not a multiple of 4.
 """
 
 import numpy as np
