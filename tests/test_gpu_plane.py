@@ -32,7 +32,7 @@ GAP_TOL = 1e-5
 CASES = [(20, 64, 16, 5, 1, 1), (30, 100, 24, 7, 2, 1), (60, 133, 20, 9, 3, 2),
          (96, 320, 32, 9, 3, 4), (130, 200, 13, 3, 2, 8), (9, 50, 8, 3, 2, 8),
          (1, 150, 16, 3, 2, 1), (100, 1024, 16, 15, 1, 8), (64, 700, 40, 11, 2, 4),
-         (5, 40, 1, 3, 1, 2)]
+         (5, 40, 1, 3, 1, 2), (96, 320, 48, 9, 3, 8)]
 
 
 def dev(a):
