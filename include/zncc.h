@@ -285,8 +285,8 @@ const char* zncc_status_string(zncc_status status);
  *                        cluster of 1, 2, 4 or 8 CTAs that fit in shared memory (H <= 256):
  *                        each disparity plane stays in shared memory for the cost, every DT
  *                        pass pair and the WTA, and the cost volume is never stored; 0 = the
- *                        streaming path (cost volume in device memory; the default, faster on
- *                        GB300 at every measured shape)
+ *                        streaming path (cost volume in device memory; the default: on GB300
+ *                        as fast at 320x96, D = 32 and faster at every larger measured shape)
  *   ZNCC_TUNE_PLANE_CS   the plane-resident path's cluster size (1, 2, 4 or 8; 0 = automatic);
  *                        a size whose band does not fit sends the pair to the streaming path
  * A value a launch cannot use (too many threads or too much shared memory) makes the next
