@@ -130,20 +130,26 @@ zncc_status dt_aggregate(zncc_ctx* ctx, const uint8_t* guide_left, int pitch, vo
  *    waits for every stream of the device), nor a host heap allocation,
  *  - code that runs where the allocator must not be entered (inside a custom allocator's
  *    own callbacks, or while another thread holds the allocator's lock).
- * It computes what dt_aggregate computes (Sec. III-B, Eqs. (3)-(6), weights of Eq. (11)) on
- * a width x height x max_disp volume, without a context: the DT coefficients go to a scratch
- * array compiled into the library's device code (a static __device__ array of 64 MiB), which
- * the CUDA driver reserves on a device when that code is loaded there, once per process. The
- * call makes no cudaMalloc, cudaFree or host heap allocation, and keeps no pointer.
+ * It computes what dt_aggregate computes, on a width x height x max_disp volume, without a
+ * context: the DT coefficients go to a scratch array compiled into the library's device code
+ * (a static __device__ array of 64 MiB). The CUDA driver reserves it on a device when that
+ * code is loaded into the device's context: under lazy module loading (CUDA_MODULE_LOADING=
+ * LAZY, the default) at the first call of this entry point on the device; under eager loading
+ * (CUDA_MODULE_LOADING=EAGER) when the context is created, in every process that loads the
+ * library, whether it calls this entry point or not. It stays reserved until the context is
+ * destroyed. The call makes no cudaMalloc, cudaFree or host heap allocation, and keeps no
+ * device pointer between calls: it looks up the scratch's address (cudaGetSymbolAddress, a
+ * host-side lookup) on every call, so a context that is destroyed and created again (after
+ * cudaDeviceReset) gets the new address.
  *
  * Limit: width * height <= 2,097,152 pixels (32 bytes of scratch per pixel; 1920 x 1080
  * fits), with width <= 3072, height <= 4096, max_disp <= 1024. A larger image returns
  * ZNCC_EUNSUPPORTED before anything is queued, with the limit in zncc_last_error(NULL).
  *
- * Set-up: the first call on each device obtains the scratch's address (cudaGetSymbolAddress,
- * which may load the library's device code) and the device's limits; the first call for each
- * new line length, disparity count and storage type chooses its launch shapes (occupancy
- * queries). Make these first calls once, at set-up, before any stream capture begins.
+ * Set-up: the first call on each device reads the device's limits, and its lookup of the
+ * scratch's address may load the library's device code; the first call for each new line
+ * length, disparity count and storage type chooses its launch shapes (occupancy queries).
+ * Make these first calls once, at set-up, before any stream capture begins.
  *
  * Zero state: nothing in the scratch needs to start at zero. Each call writes every
  * coefficient of its image before it reads any, so leftovers of an earlier call are never

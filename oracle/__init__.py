@@ -244,6 +244,21 @@ def fastdt_store(C, ahat, d_arb=FASTDT_D_ARB, T=FASTDT_T, lib=None):
     return C
 
 
+def dt_aggregate_fastdt(C, guide, sigma_s, sigma_r, iters, d_arb=FASTDT_D_ARB, T=FASTDT_T, nthreads=None,
+                        lib=None):
+    """The DT chain with FastDT storage between pass pairs on a float64 [H][W][nd] volume
+    (returns a new array): the aggregated volume that WTA reads."""
+    lib = lib or load()
+    C = np.array(C, dtype=np.float64, copy=True, order="C")
+    H, W, nd = C.shape
+    g = _img(guide)
+    assert g.shape == (H, W)
+    _check(lib.oracle_dt_aggregate_fastdt(_p(C, ctypes.c_double), _p(g, ctypes.c_uint8), W, H, nd,
+                                          float(sigma_s), float(sigma_r), int(iters), int(d_arb), float(T),
+                                          nthreads or default_threads()), "dt_aggregate_fastdt")
+    return C
+
+
 def run_fastdt(left, right, max_disp, r, sigma_s=20.0, sigma_r=0.1, iters=3, d_arb=FASTDT_D_ARB,
                T=FASTDT_T, nthreads=None, lib=None):
     """The whole path with FastDT storage between pass pairs: (disparity, gap)."""

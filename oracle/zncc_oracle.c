@@ -14,7 +14,7 @@
  *   - disparity (WTA):  Sec. III-C, Eq. (WTA1)
  *   - FastDT storage:   Sec. IV-C (near-zero-mean normalization, 16-bit values, 8-bit code)
  *
- * Readings of passages the paper leaves open (each listed in the design doc):
+ * Readings of passages the paper leaves open or garbles:
  *   - reference image I_R = left, target I_T = right; I_R(x,y) is matched to I_T(x-d,y);
  *   - every pixel read is clamped to the image (clamp-to-edge), also for centres x-d < 0;
  *   - a window with zero variance gives cost 0;

@@ -830,8 +830,11 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
 }
 
 // ---- dt_aggregate_noalloc: per-device state of the static scratch --------------------
-// Everything here has static storage: the scratch address and device limits, resolved once
-// per device, and a fixed-capacity cache of line-pass shapes. A mutex guards both.
+// Everything here has static storage: the device limits, read once per device, and a
+// fixed-capacity cache of line-pass shapes. A mutex guards both. The scratch's address is
+// not kept: it is looked up on every call, because it belongs to the device context that
+// loaded the module and changes when that context is torn down and created again (after a
+// cudaDeviceReset, say), where a kept address would point at memory that no longer exists.
 constexpr int kNoallocDevices = 64;
 constexpr int kNoallocPlans = 16;
 
@@ -843,7 +846,6 @@ struct NoallocPlan {
 
 struct NoallocDevice {
     bool ready;
-    unsigned char* scratch;
     int smem_max, num_sms;
     NoallocPlan plans[kNoallocPlans];
     int next;                       // the cache slot replaced next when it is full
@@ -857,19 +859,21 @@ zncc_status noalloc_cuda_fail(cudaError_t e, const char* what) {
     return ZNCC_ECUDA;
 }
 
-// The device's state, set up on its first use (the caller holds g_noalloc_mu).
-zncc_status noalloc_device(int dev, NoallocDevice** out) {
+// The device's state, set up on its first use, and the scratch's address in the current
+// context of the current device (the caller holds g_noalloc_mu). cudaGetSymbolAddress is a
+// host-side lookup; it allocates nothing once the module is loaded in the context.
+zncc_status noalloc_device(int dev, NoallocDevice** out, unsigned char** scratch) {
     NoallocDevice& d = g_noalloc[dev];
     if (!d.ready) {
-        void* p = nullptr;
-        cudaError_t e = noalloc_scratch_address(&p);
-        if (e != cudaSuccess) return noalloc_cuda_fail(e, "scratch address (cudaGetSymbolAddress)");
-        e = cudaDeviceGetAttribute(&d.smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaError_t e = cudaDeviceGetAttribute(&d.smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return noalloc_cuda_fail(e, "device attributes");
-        d.scratch = static_cast<unsigned char*>(p);
         d.ready = true;
     }
+    void* p = nullptr;
+    const cudaError_t e = noalloc_scratch_address(&p);
+    if (e != cudaSuccess) return noalloc_cuda_fail(e, "scratch address (cudaGetSymbolAddress)");
+    *scratch = static_cast<unsigned char*>(p);
     *out = &d;
     return ZNCC_OK;
 }
@@ -1100,8 +1104,9 @@ zncc_status dt_aggregate_noalloc(const uint8_t* guide, int pitch, int width, int
     const cudaStream_t st = (cudaStream_t)cuda_stream;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     NoallocDevice* d = nullptr;
-    ZNCC_TRY(noalloc_device(dev, &d));
-    float4* coefH = reinterpret_cast<float4*>(d->scratch);
+    unsigned char* scratch = nullptr;
+    ZNCC_TRY(noalloc_device(dev, &d, &scratch));
+    float4* coefH = reinterpret_cast<float4*>(scratch);
     float4* coefV = coefH + npix;
 
     CoefBatch cb;

@@ -1,8 +1,10 @@
 // static_scratch.cu -- the device scratch of dt_aggregate_noalloc: a file-scope array that is
 // part of the library's device code, so that the call itself never allocates. The CUDA
-// driver reserves it on a device when this module's code is loaded there (at the first
-// cudaGetSymbolAddress of it, under lazy module loading). It has its own translation unit so
-// that the other calls never load it.
+// driver reserves it on a device when this module's code is loaded into the device's
+// context: under lazy module loading (the default) at the first cudaGetSymbolAddress of it;
+// under eager loading (CUDA_MODULE_LOADING=EAGER) when the context is created, whether the
+// entry point is ever called or not. It has its own translation unit so that, under lazy
+// loading, the other calls never load it.
 #include "kernels.h"
 
 namespace zncc {

@@ -126,6 +126,16 @@ def dt_aggregate_noalloc(guide, cost, sigma_s, sigma_r, iters, dtype=ZNCC_F32, s
     uint8), without a context and without any allocation: the coefficients go to the
     library's static device scratch (W * H <= 2,097,152). stream: a torch.cuda.Stream or
     None (legacy default stream). Calls whose GPU work overlaps race on the scratch."""
+    import torch
+    if guide.dim() != 2 or guide.dtype != torch.uint8:
+        raise ValueError("guide must be a 2-D uint8 tensor [H][W]")
+    if cost.dim() != 3 or tuple(cost.shape[:2]) != tuple(guide.shape):
+        raise ValueError(f"cost must be [H][W][D] with [H][W] = {tuple(guide.shape)}, got {tuple(cost.shape)}")
+    want = {ZNCC_F32: torch.float32, ZNCC_F16: torch.float16}.get(int(dtype))
+    if want is None or cost.dtype != want:
+        raise ValueError(f"cost dtype {cost.dtype} does not match the storage flag {dtype}")
+    if guide.device != cost.device or guide.device.type != "cuda":
+        raise ValueError("guide and cost must be tensors on the same CUDA device")
     H, W = int(guide.shape[0]), int(guide.shape[1])
     D = int(cost.shape[-1])
     s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)

@@ -474,6 +474,41 @@ def pin_fastdt_store(lib):
                     assert got >= exact - 0.5 - 1e-9 and got - exact < 512 + 0.5, (got, exact)
 
 
+def pin_fastdt_chain_composition(lib):
+    """The FastDT chain on a textured 5x4 guide equals its definition composed from pinned
+    parts: each pass pair applied with the dense pass matrices (built from the closed form of
+    the recurrences), the all-ones response A_hat_p after the same p pairs (the same matrices
+    on a plane of ones), and the FastDT store (pinned by the codec and store pins) after every
+    pair but the last, dividing by A_hat_p. One and two iterations; d_arb = 0."""
+    rng = _rng(23)
+    H, W, nd = 4, 5, 6
+    g = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    sig_s, sig_r = 3.0, 0.3
+    WL, WR, WU, WD = oracle.dt_weights(g, sig_s, sig_r, lib=lib)
+    s = 1 - _K(sig_s)
+
+    def pass_pair(X, horiz):
+        X = X.copy()
+        if horiz:
+            for y in range(H):
+                X[y] = _pass_matrix(WR[y], s, False) @ (_pass_matrix(WL[y], s, True) @ X[y])
+        else:
+            for x in range(W):
+                X[:, x] = _pass_matrix(WD[:, x], s, False) @ (_pass_matrix(WU[:, x], s, True) @ X[:, x])
+        return X
+
+    for iters in (1, 2):
+        C = rng.uniform(-1, 1, (H, W, nd))
+        ref, ones = C.copy(), np.ones((H, W, 1))
+        for pair in range(1, 2 * iters + 1):
+            horiz = pair % 2 == 1
+            ref, ones = pass_pair(ref, horiz), pass_pair(ones, horiz)
+            if pair < 2 * iters:
+                ref = oracle.fastdt_store(ref, ones[:, :, 0], d_arb=0, lib=lib)
+        out = oracle.dt_aggregate_fastdt(C, g, sig_s, sig_r, iters, d_arb=0, lib=lib)
+        assert np.allclose(out, ref, rtol=1e-12, atol=1e-15), (iters, np.abs(out - ref).max())
+
+
 def pin_fastdt_chain_accuracy(lib):
     """The chain with FastDT storage still recovers a constant disparity on textured noise
     (>= 99% of interior pixels) and agrees with the exact chain on most pixels of a
@@ -498,5 +533,5 @@ ALL_PINS = [
     pin_wta_bruteforce_and_ties,
     pin_end_to_end_recovery,
     pin_fastdt_codec_examples, pin_fastdt_codec_golden, pin_fastdt_codec_properties, pin_fastdt_store,
-    pin_fastdt_chain_accuracy,
+    pin_fastdt_chain_composition, pin_fastdt_chain_accuracy,
 ]

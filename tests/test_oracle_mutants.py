@@ -45,6 +45,16 @@ MUTANTS = [
      "if (mid4 != 0xF) return (uint8_t)((((v >> 5) & 0x3F) << 2) | 1u);"),
     ("fastdt_fill_short", "for (int b = low + 6; b < 16; ++b) v |= 1u << b;",
      "for (int b = low + 7; b < 16; ++b) v |= 1u << b;"),
+    ("fastdt_store_after_last_pair", "if (pair < 2 * iters) rc = oracle_fastdt_store(C, ones, W, H, nd, d_arb, T);",
+     "if (pair <= 2 * iters) rc = oracle_fastdt_store(C, ones, W, H, nd, d_arb, T);"),
+    # the store divides by A_hat of the previous pair (all ones before the first)
+    ("fastdt_ahat_one_pair_behind",
+     "if (pair < 2 * iters) rc = oracle_fastdt_store(C, ones, W, H, nd, d_arb, T);",
+     "{ static double lag[1 << 16]; if (pair == 1) for (size_t i = 0; i < n; ++i) lag[i] = 1.0;\n"
+     "          if (pair < 2 * iters) rc = oracle_fastdt_store(C, lag, W, H, nd, d_arb, T);\n"
+     "          for (size_t i = 0; i < n; ++i) lag[i] = ones[i]; }"),
+    ("fastdt_d_arb_one", "const double ref = c[d_arb], a = ahat[p];",
+     "const double ref = c[d_arb + (nd > 1)], a = ahat[p];"),
     ("fastdt_reference_sign", "double e = rint(T * (ref - c[d]) / a);", "double e = rint(T * (c[d] - ref) / a);"),
 ]
 

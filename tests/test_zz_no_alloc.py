@@ -1,6 +1,8 @@
 """dt_aggregate_noalloc: the context-free DT aggregation whose scratch is a static device
-array. On the GPU it gives what dt_aggregate gives, call after call, without changing the
-device's free memory; sizes beyond the static scratch are rejected before any CUDA call.
+array, for callers that cannot allocate while they run. On the GPU it matches the FP64 oracle
+within the DT tolerance and gives what dt_aggregate gives, call after call, without changing
+the device's free memory; sizes beyond the static scratch and mismatched tensors are rejected
+before any CUDA call.
 
 This file is collected last on purpose: its GPU test must pass both alone and after every
 other test of the suite has run in the same process."""
@@ -10,6 +12,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2212_00476_gb300 import build as zbuild
 from paper_2212_00476_gb300 import zncc as Z
 from synth import make_pair
@@ -20,6 +23,7 @@ MAX_PIXELS = 2_097_152            # 64 MiB of scratch at 32 bytes per pixel
 # bit; the bound leaves room only for a different shape choice (a different association
 # of the chunk carries), far below the 1e-4 * A_hat the DT kernels meet against the oracle.
 TOL = 1e-6
+AGG_TOL = 1e-4                    # against the FP64 oracle: |gpu - oracle| <= 1e-4 * A_hat(x, y)
 
 
 @pytest.fixture(scope="module")
@@ -48,12 +52,35 @@ def test_noalloc_rejects_sizes_beyond_the_static_scratch(lib):
         assert lib.dt_aggregate_noalloc(*args) == want, args
 
 
-def _volume(torch, ctx, p):
+def test_noalloc_wrapper_rejects_mismatched_tensors(lib):
+    """The binding checks shapes, dtypes and devices before it passes pointers to the library
+    (the call itself has no context that would catch a volume of the wrong size or type)."""
+    torch = pytest.importorskip("torch")
+    g = torch.zeros((6, 10), dtype=torch.uint8)
+    bad = [(g, torch.zeros((6, 10, 4), dtype=torch.float16), Z.ZNCC_F32),    # half volume, F32 flag
+           (g, torch.zeros((6, 10, 4), dtype=torch.float32), Z.ZNCC_F16),    # float volume, F16 flag
+           (g, torch.zeros((5, 10, 4), dtype=torch.float32), Z.ZNCC_F32),    # fewer rows than the guide
+           (g, torch.zeros((6, 10), dtype=torch.float32), Z.ZNCC_F32),       # not [H][W][D]
+           (g.float(), torch.zeros((6, 10, 4), dtype=torch.float32), Z.ZNCC_F32),  # guide not uint8
+           (g, torch.zeros((6, 10, 4), dtype=torch.float32), Z.ZNCC_F32)]    # host tensors
+    for guide, cost, flag in bad:
+        with pytest.raises(ValueError):
+            Z.dt_aggregate_noalloc(guide, cost, SIG_S, SIG_R, ITERS, flag)
+
+
+def _volume(torch, ctx, p, seed):
+    """The guide on the device and a seeded synthetic cost volume in [-1, 1] (FP32), the same
+    input for the oracle and both device paths."""
     left = torch.from_numpy(p.left).cuda()
-    right = torch.from_numpy(p.right).cuda()
-    cost = torch.empty((ctx.H, ctx.W, ctx.D), dtype=torch.float32, device="cuda")
-    ctx.zncc_cost_volume(left, right, cost)
-    return left, cost
+    C = np.random.default_rng(seed).uniform(-1, 1, (ctx.H, ctx.W, ctx.D)).astype(np.float32)
+    return left, torch.from_numpy(C).cuda(), C
+
+
+def _oracle_error(p, C, out, iters):
+    """max |out - oracle| / A_hat over the volume."""
+    ref = oracle.dt_aggregate(C.astype(np.float64), oracle.dt_weights(p.left, SIG_S, SIG_R), SIG_S, iters)
+    A = oracle.ones_response(p.left, SIG_S, SIG_R, iters)[:, :, None]
+    return float((np.abs(out.float().cpu().numpy().astype(np.float64) - ref) / A).max())
 
 
 @pytest.mark.gpu
@@ -62,7 +89,7 @@ def test_noalloc_matches_dt_aggregate_on_two_calls_in_a_row(lib):
     H, W, D = 75, 203, 37                      # several chunks and slices, ragged tails
     p = make_pair(H, W, D, seed=4242)
     ctx = Z.ZnccContext(W, H, D, 9)
-    left, cost = _volume(torch, ctx, p)
+    left, cost, C = _volume(torch, ctx, p, 4243)
     ref = cost.clone()
     ctx.dt_aggregate(left, ref, SIG_S, SIG_R, ITERS)
     torch.cuda.synchronize()
@@ -78,6 +105,8 @@ def test_noalloc_matches_dt_aggregate_on_two_calls_in_a_row(lib):
     for i, out in enumerate(outs):
         err = (out - ref).abs().max().item()
         assert err <= TOL, (i, err)
+        rel = _oracle_error(p, C, out, ITERS)
+        assert rel <= AGG_TOL, (i, rel)
     assert free_after == free_before, (free_before, free_after)
 
     # half storage, on a stream of its own
@@ -101,7 +130,7 @@ def test_noalloc_at_the_size_limit_then_a_smaller_image(lib):
         assert W * H <= MAX_PIXELS
         p = make_pair(H, W, D, seed=seed)
         ctx = Z.ZnccContext(W, H, D, 5)
-        left, cost = _volume(torch, ctx, p)
+        left, cost, C = _volume(torch, ctx, p, seed + 1)
         ref = cost.clone()
         ctx.dt_aggregate(left, ref, SIG_S, SIG_R, 1)
         out = cost.clone()
@@ -110,3 +139,5 @@ def test_noalloc_at_the_size_limit_then_a_smaller_image(lib):
         err = (out - ref).abs().max().item()
         assert err <= TOL, ((H, W, D), err)
         assert np.isfinite(out.cpu().numpy()).all()
+        rel = _oracle_error(p, C, out, 1)
+        assert rel <= AGG_TOL, ((H, W, D), rel)
