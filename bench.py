@@ -7,7 +7,12 @@ One step = one pass of the whole path (window statistics, ZNCC fused with the fi
 horizontal DT pair, the remaining DT passes, WTA fused into the last vertical pair) over one
 synthetic 1280x384 pair, D = 128, 9x9 window, sigma_s = 20, sigma_r = 0.1, 3 iterations.
 Inputs are resident in HBM; L2 is flushed (a 256 MB write) before every timed step and the
-flush is outside the step's CUDA events. Rank 0 prints one JSON line.
+flush is outside the step's CUDA events. Rank 0 prints one JSON line. With the default
+workload on one GPU the line also carries "precision" (the same pair with F32, F16 and FastDT
+I8 storage: step time and disparity mismatch against the FP64 oracle) and "serving" (Poisson
+requests of mixed size and disparity range through the serving calls, continuous batching
+against one pair per launch: p50/p99, throughput, the p99 latency breakdown and a saturation
+leg); --no-extras leaves them out.
 
 --impl reference times the FP64 CPU oracle (the only reference this method has) on the host
 cores, one full pair per step.
@@ -412,12 +417,77 @@ def run_gb300(args):
             line["cpu_baseline"]["single_core"] = {"value": round(units / (sum(t1) / len(t1)) / 1e9, 6),
                                                    "unit": "Gdisp/s", "cores": 1,
                                                    "sample": f"{len(t1)} full pair(s)"}
+    if rank == 0 and world == 1 and args.workload == "paper_1280x384" and not args.no_extras:
+        line["precision"] = precision_leg(Z, ctx, pair, wl, iters, left, right, disp, flush, stream, args)
+        sweep, sat = serving_legs(Z, Z.ZNCC_F32, [SERVE_RATE], SERVE_REQUESTS, sat_n=SERVE_SAT_REQUESTS)
+        head = sweep[0]
+        line["serving"] = {
+            "config": SERVE_CONFIG + f"; {SERVE_REQUESTS} requests at {SERVE_RATE:g} req/s; saturation: "
+                                     f"{SERVE_SAT_REQUESTS} requests queued at once",
+            "rate_req_per_s": SERVE_RATE,
+            "p50_ms": head["batched"]["p50_ms"], "p99_ms": head["batched"]["p99_ms"],
+            "throughput_req_per_s": head["batched"]["served_req_per_s"],
+            "throughput_gdisp_s": head["batched"]["served_gdisp_s"],
+            "p99_breakdown": head["batched"]["p99_breakdown"],
+            "plain": {"p50_ms": head["one_pair_per_launch"]["p50_ms"],
+                      "p99_ms": head["one_pair_per_launch"]["p99_ms"],
+                      "throughput_req_per_s": head["one_pair_per_launch"]["served_req_per_s"],
+                      "throughput_gdisp_s": head["one_pair_per_launch"]["served_gdisp_s"],
+                      "p99_breakdown": head["one_pair_per_launch"]["p99_breakdown"]},
+            "saturation": sat,
+        }
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def precision_leg(Z, ctx, pair, wl, iters, left, right, disp, flush, stream, args, steps=10):
+    """The same pair with F32, F16 and FastDT I8 volume storage: step time (CUDA events, L2
+    flushed, each storage autotuned) and the disparity map against the FP64 oracle's: the share
+    of pixels that differ, and of those whose oracle best-vs-second gap is at least 1e-5 A_hat
+    (away from near-ties)."""
+    import torch
+
+    import oracle
+    ref, gap = oracle.run(pair.left, pair.right, wl["d"], wl["win"] // 2, SIG_S, SIG_R, iters)
+    A = oracle.ones_response(pair.left, SIG_S, SIG_R, iters)
+    clear = gap >= 1e-5 * A
+    out = {"reference": "FP64 oracle map of the same pair",
+           "pixels": int(ref.size), "pixels_away_from_ties": int(clear.sum())}
+    for name in ("f32", "f16", "i8"):
+        st = storage_code(Z, name)
+        tuned = None
+        if not args.no_autotune:
+            from paper_2212_00476_gb300 import autotune
+            with torch.cuda.stream(stream):
+                tuned = autotune.tune(ctx, left, right, disp, SIG_S, SIG_R, iters, st)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                ctx.zncc_run(left, right, disp, SIG_S, SIG_R, iters, st)
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                ctx.zncc_run(left, right, disp, SIG_S, SIG_R, iters, st)
+                b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        got = disp.cpu().numpy().view(np.uint16)
+        diff = got != ref
+        out[name] = {"ms_per_step": round(ms, 4),
+                     "gdisp_s": round(wl["w"] * wl["h"] * wl["d"] / (ms * 1e-3) / 1e9, 3),
+                     "mismatch_rate": round(float(diff.mean()), 7),
+                     "mismatch_rate_away_from_ties": round(float((diff & clear).sum() / max(1, clear.sum())), 7),
+                     "launch_shapes": tuned["settings"] if tuned else "defaults"}
+    # leave the context with the F32 shapes the timed region used
+    if not args.no_autotune:
+        from paper_2212_00476_gb300 import autotune
+        with torch.cuda.stream(stream):
+            autotune.tune(ctx, left, right, disp, SIG_S, SIG_R, iters, Z.ZNCC_F32)
+    return out
 
 
 def run_batch(args):
@@ -629,29 +699,31 @@ def run_precision(args):
     return 0
 
 
-def run_serving(args):
+SERVE_RATE, SERVE_REQUESTS, SERVE_SAT_REQUESTS = 200.0, 400, 300
+
+
+def serving_legs(Z, storage, rates, n, sat_n=0, seed=5):
     """Poisson arrivals (seed 5) of requests of size {640x192, 1280x384, 1920x1080} and D
     {64, 128, 256}, 9x9, 3 DT iterations, through the serving calls with continuous batching
-    (max_slots 32) and one pair per launch (max_slots 1), under a 40 GB budget. Latency =
-    time from a request's scheduled arrival until serve_poll returns its map; one loop submits
-    on schedule and polls every outstanding ticket. The images of a (size, D) shape come from
-    one seeded pair (seed 500000 + shape index), reused by every request of that shape."""
-    import torch
-
-    from paper_2212_00476_gb300 import zncc as Z
+    (max_slots 32) and one pair per launch (max_slots 1), under a 40 GB budget. Latency = time
+    from a request's scheduled arrival until serve_poll returns its map; one loop submits on
+    schedule and polls every outstanding ticket. The images of a (size, D) shape come from one
+    seeded pair (seed 500000 + shape index), reused by every request of that shape. Per rate:
+    p50/p99/max latency, served throughput, and the server's breakdown of the requests at or
+    above p99 (host queue, wait on the stream, uploads, fused run, result copies). sat_n > 0
+    adds a saturation leg: sat_n requests offered at 20000 req/s (all queued at once), whose
+    served rate is each server's capacity on this mix."""
     from synth.stereo import SERVE_DISPS, SERVE_SIZES, make_pair, serving_requests
 
-    torch.cuda.set_device(0)
-    storage = storage_code(Z, args.storage)
     shapes = [(h, w, d) for (h, w) in SERVE_SIZES for d in SERVE_DISPS]
     pool = {sh: make_pair(sh[0], sh[1], sh[2], 500000 + i, disp="planes", occlusion_frac=0.05)
             for i, sh in enumerate(shapes)}
     outs = {sh: np.zeros(sh[:2], np.uint16) for sh in shapes}
-    rates = [float(r) for r in args.rates.split(",")]
     budget = 40 * 10**9
+    parts = ("queue_ms", "device_wait_ms", "h2d_ms", "run_ms", "d2h_ms")
 
     def serve(rate, max_slots, n):
-        reqs = serving_requests(n, rate, seed=5)
+        reqs = serving_requests(n, rate, seed=seed)
         with Z.ZnccServer(budget, max_slots) as srv:
             for sh in shapes:                                   # contexts exist before timing
                 p = pool[sh]
@@ -670,9 +742,9 @@ def run_serving(args):
                     i += 1
                 done = []
                 for tk, (sh, ta) in pending.items():
-                    st = srv.poll(tk, outs[sh], 0)
+                    st, tm = srv.poll_timed(tk, outs[sh], 0)
                     if st == Z.ZNCC_OK:
-                        lat.append(time.perf_counter() - t0 - ta)
+                        lat.append((time.perf_counter() - t0 - ta, sh, tm))
                         done.append(tk)
                     elif st != Z.ZNCC_ENOTREADY:
                         raise RuntimeError(f"request failed: {Z.STATUS_NAMES[st]} {srv.last_error()}")
@@ -681,29 +753,62 @@ def run_serving(args):
                 if not done:
                     time.sleep(2e-5)
             span = time.perf_counter() - t0
-        lat.sort()
-        q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] * 1e3
-        return {"p50_ms": round(q(0.50), 3), "p99_ms": round(q(0.99), 3), "max_ms": round(lat[-1] * 1e3, 3),
+        lat.sort(key=lambda e: e[0])
+        q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))][0] * 1e3
+        tail = [e for e in lat[min(len(lat) - 1, int(0.99 * len(lat))):] if e[2]]
+        mix = {}
+        for e in tail:
+            k = f"{e[1][1]}x{e[1][0]}_D{e[1][2]}"
+            mix[k] = mix.get(k, 0) + 1
+        brk = {k: round(sum(e[2][k] for e in tail) / len(tail), 3) for k in parts} if tail else None
+        if brk:
+            brk["client_ms"] = round(sum(e[0] * 1e3 - e[2]["total_ms"] for e in tail) / len(tail), 3)
+            brk["batch_pairs"] = round(sum(e[2]["batch_pairs"] for e in tail) / len(tail), 2)
+            brk["shapes"] = mix
+            brk["requests"] = len(tail)
+        return {"p50_ms": round(q(0.50), 3), "p99_ms": round(q(0.99), 3), "max_ms": round(lat[-1][0] * 1e3, 3),
                 "requests": n, "span_s": round(span, 3), "served_req_per_s": round(n / span, 1),
-                "served_gdisp_s": round(units / span / 1e9, 3)}
+                "served_gdisp_s": round(units / span / 1e9, 3), "p99_breakdown": brk}
 
-    sweep = []
+    out = []
     for rate in rates:
-        n = args.requests
-        sweep.append({"rate_req_per_s": rate, "batched": serve(rate, 32, n), "one_pair_per_launch": serve(rate, 1, n)})
+        out.append({"rate_req_per_s": rate, "batched": serve(rate, 32, n),
+                    "one_pair_per_launch": serve(rate, 1, n)})
+    sat = None
+    if sat_n:
+        sat = {"offered_req_per_s": 20000.0, "requests": sat_n,
+               "batched": serve(20000.0, 32, sat_n), "one_pair_per_launch": serve(20000.0, 1, sat_n)}
+        for k in ("batched", "one_pair_per_launch"):
+            sat[k] = {m: sat[k][m] for m in ("served_req_per_s", "served_gdisp_s", "p50_ms", "p99_ms")}
+    return out, sat
+
+
+SERVE_CONFIG = ("serving: Poisson arrivals seed 5; sizes 640x192/1280x384/1920x1080, D 64/128/256, "
+                "9x9, sigma_s 20, sigma_r 0.1, 3 iterations; 40 GB budget; continuous batching "
+                "(max_slots 32) vs one pair per launch (max_slots 1)")
+
+
+def run_serving(args):
+    """C5 on its own: the serving legs at every rate of --rates (--requests each) and a
+    saturation leg."""
+    from paper_2212_00476_gb300 import zncc as Z
+
+    import torch
+    torch.cuda.set_device(0)
+    storage = storage_code(Z, args.storage)
+    rates = [float(r) for r in args.rates.split(",")]
+    sweep, sat = serving_legs(Z, storage, rates, args.requests, sat_n=max(SERVE_SAT_REQUESTS, args.requests // 4))
     head = sweep[0]
     line = {
         "metric": f"served p50/p99 latency at {rates[0]:g} req/s (continuous batching vs one pair per launch)",
         "value": head["batched"]["p99_ms"], "unit": "ms (p99)", "n_gpus": 1, "steps": args.requests,
-        "warmup": len(shapes), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "warmup": 9, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "storage": args.storage, "data": "synthetic",
-        "config": {"workload": "serving: Poisson arrivals seed 5; sizes 640x192/1280x384/1920x1080, "
-                               "D 64/128/256, 9x9, sigma_s 20, sigma_r 0.1, 3 iterations; 40 GB budget",
-                   "l2": "not flushed (a live request stream)"},
+        "config": {"workload": SERVE_CONFIG, "l2": "not flushed (a live request stream)"},
         "p50_ms": head["batched"]["p50_ms"], "p99_ms": head["batched"]["p99_ms"],
         "plain_p50_ms": head["one_pair_per_launch"]["p50_ms"],
         "plain_p99_ms": head["one_pair_per_launch"]["p99_ms"],
-        "sweep": sweep,
+        "sweep": sweep, "saturation": sat,
     }
     print(json.dumps(line))
     return 0
@@ -843,6 +948,8 @@ def main():
     ap.add_argument("--rates", default="200,500,1000,2000", help="serving: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests per rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the precision and serving legs of the JSON line")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default="", help="fixed launch shapes instead of autotuning, "
                     "e.g. row_minb2=0,row_spb=8")

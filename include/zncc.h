@@ -260,6 +260,27 @@ zncc_status serve_submit(zncc_server* server, const uint8_t* left_host, const ui
  * ZNCC_ETIMEOUT otherwise (the ticket stays valid). Unknown ticket: ZNCC_EINVAL. */
 zncc_status serve_poll(zncc_server* server, uint64_t ticket, uint16_t* disp_host, int timeout_us);
 
+/* Where a served request's latency went, measured by the server (milliseconds). Host
+ * timestamps: submit (serve_submit), issue (the scheduler starts queuing the request's batch
+ * on a stream) and completion (the host function behind the batch's result copies runs);
+ * CUDA events around the batch's image uploads, its fused run and its result copies.
+ *   queue_ms        submit -> issue: waiting for a slot, budget room or the scheduler
+ *   device_wait_ms  issue -> completion, less the batch's event-timed work: waiting on the
+ *                   stream behind earlier batches, plus the completion callback's delay
+ *   h2d_ms, run_ms, d2h_ms  the batch's uploads, fused run (every pair of the batch) and
+ *                   result copies
+ *   total_ms        submit -> completion = the sum of the five above
+ *   batch_pairs     pairs in the request's batch
+ * valid is 0 when the request failed before its batch ran (the times are then 0). */
+typedef struct {
+    double queue_ms, device_wait_ms, h2d_ms, run_ms, d2h_ms, total_ms;
+    int batch_pairs, valid;
+} zncc_serve_timing;
+
+/* serve_poll, and on completion the request's latency breakdown in *timing (may be NULL). */
+zncc_status serve_poll_timed(zncc_server* server, uint64_t ticket, uint16_t* disp_host, int timeout_us,
+                             zncc_serve_timing* timing);
+
 /* Stop the server: requests not yet started end with ZNCC_EBUSY, running batches are waited
  * for (at most 30 s), then every context, buffer and stream is freed. If the running work
  * does not finish in time, returns ZNCC_ETIMEOUT and leaves the server's memory allocated

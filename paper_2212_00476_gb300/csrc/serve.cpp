@@ -76,6 +76,14 @@ struct HostBuf {
     bool pinned = false;
 };
 
+// The CUDA events of one batch (uploads start, uploads done, run done, copies done), shared
+// by its requests; the last request polled returns them to the server's pool.
+struct BatchTiming {
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool recorded = false;
+    int refs = 0, pairs = 0;
+};
+
 struct Request {
     uint64_t ticket = 0;
     ShapeKey key{};
@@ -84,6 +92,8 @@ struct Request {
     enum State { QUEUED, RUNNING, DONE } state = QUEUED;
     zncc_status status = ZNCC_OK;
     Slot* slot = nullptr;
+    Clock::time_point t_submit, t_issue, t_done;
+    BatchTiming* timing = nullptr;
 };
 
 }  // namespace
@@ -98,6 +108,7 @@ struct zncc_server {
     std::unordered_map<uint64_t, Request*> tickets;
     std::vector<Slot*> slots;
     std::multimap<size_t, HostBuf> free_bufs;   // host buffers for reuse, by size
+    std::vector<cudaEvent_t> free_events;         // timing events for reuse
     size_t charged = 0;
     int inflight = 0;                      // requests on the GPU
     uint64_t next_ticket = 1, use_clock = 0, completions = 0;
@@ -221,6 +232,7 @@ Slot* create_slot(const ShapeKey& key, size_t charge, zncc_status* st, char* err
 void finish(zncc_server* s, Request* r, zncc_status st) {
     r->status = st;
     r->state = Request::DONE;
+    r->t_done = Clock::now();
     if (r->slot) {
         r->slot->busy = false;
         r->slot->last_use = ++s->use_clock;
@@ -255,6 +267,30 @@ void launch(zncc_server* s, Batch* b) {
     uint16_t* disps[zncc::kMaxBatch];
     zncc_status status = ZNCC_OK;
     cudaError_t e = cudaSuccess;
+    // the batch's timing events, from the pool or created (outside the lock)
+    BatchTiming* bt = new BatchTiming();
+    bt->refs = n;
+    bt->pairs = n;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (int k = 0; k < 4 && !s->free_events.empty(); ++k) {
+            bt->ev[k] = s->free_events.back();
+            s->free_events.pop_back();
+        }
+    }
+    bool timed = true;
+    for (int k = 0; k < 4; ++k)
+        if (!bt->ev[k] && cudaEventCreate(&bt->ev[k]) != cudaSuccess) {
+            cudaGetLastError();
+            bt->ev[k] = nullptr;
+            timed = false;
+        }
+    const Clock::time_point t_issue = Clock::now();
+    for (Request* r : b->reqs) {
+        r->t_issue = t_issue;
+        r->timing = bt;
+    }
+    if (timed) timed = cudaEventRecord(bt->ev[0], st) == cudaSuccess;
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         Request* r = b->reqs[i];
         Slot* sl = r->slot;
@@ -267,6 +303,7 @@ void launch(zncc_server* s, Batch* b) {
         pitches[i] = r->key.W;
         disps[i] = sl->d_disp;
     }
+    if (timed && e == cudaSuccess) timed = cudaEventRecord(bt->ev[1], st) == cudaSuccess;
     if (e == cudaSuccess) {
         const Request* r0 = b->reqs[0];
         status = zncc_run_batch(ctxs, lefts, rights, pitches, disps, n, r0->sigma_s, r0->sigma_r,
@@ -276,11 +313,15 @@ void launch(zncc_server* s, Batch* b) {
             set_err(s, "batched run: %s", zncc_last_error(ctxs[0]));
         }
     }
+    if (timed && e == cudaSuccess && status == ZNCC_OK) timed = cudaEventRecord(bt->ev[2], st) == cudaSuccess;
     for (int i = 0; i < n && e == cudaSuccess && status == ZNCC_OK; ++i) {
         Request* r = b->reqs[i];
         e = cudaMemcpyAsync(r->disp.p, r->slot->d_disp, (size_t)r->key.W * r->key.H * sizeof(uint16_t),
                             cudaMemcpyDeviceToHost, st);
     }
+    if (timed && e == cudaSuccess && status == ZNCC_OK) timed = cudaEventRecord(bt->ev[3], st) == cudaSuccess;
+    if (!timed) cudaGetLastError();
+    bt->recorded = timed;
     if (e == cudaSuccess && status == ZNCC_OK) e = cudaLaunchHostFunc(st, on_batch_done, b);
     if (e == cudaSuccess && status == ZNCC_OK) return;
     if (e != cudaSuccess) {
@@ -392,6 +433,21 @@ zncc_status check_request(int W, int H, int D, int win, float ss, float sr, int 
     return ZNCC_OK;
 }
 
+// Drops a request's share of its batch's timing; the last one returns the events to the pool.
+// Under the lock.
+void release_timing(zncc_server* s, Request* r) {
+    BatchTiming* bt = r->timing;
+    r->timing = nullptr;
+    if (!bt || --bt->refs > 0) return;
+    for (cudaEvent_t e : bt->ev)
+        if (e) s->free_events.push_back(e);
+    delete bt;
+}
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
 }  // namespace
 
 extern "C" {
@@ -443,6 +499,7 @@ zncc_status serve_submit(zncc_server* s, const uint8_t* left_host, const uint8_t
     r->key = key;
     r->sigma_s = sigma_s;
     r->sigma_r = sigma_r;
+    r->t_submit = Clock::now();
     std::unique_lock<std::mutex> lk(s->mu);
     if (s->stopping || s->tickets.size() >= kMaxQueued) {
         delete r;
@@ -478,6 +535,11 @@ zncc_status serve_submit(zncc_server* s, const uint8_t* left_host, const uint8_t
 }
 
 zncc_status serve_poll(zncc_server* s, uint64_t ticket, uint16_t* disp_host, int timeout_us) {
+    return serve_poll_timed(s, ticket, disp_host, timeout_us, nullptr);
+}
+
+zncc_status serve_poll_timed(zncc_server* s, uint64_t ticket, uint16_t* disp_host, int timeout_us,
+                             zncc_serve_timing* timing) {
     if (!s || !disp_host || timeout_us < 0) return ZNCC_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->tickets.find(ticket);
@@ -488,6 +550,26 @@ zncc_status serve_poll(zncc_server* s, uint64_t ticket, uint16_t* disp_host, int
     if (r->state != Request::DONE) return timeout_us == 0 ? ZNCC_ENOTREADY : ZNCC_ETIMEOUT;
     const zncc_status st = r->status;
     if (st == ZNCC_OK) memcpy(disp_host, r->disp.p, (size_t)r->key.W * r->key.H * sizeof(uint16_t));
+    if (timing) {
+        *timing = zncc_serve_timing{};
+        const BatchTiming* bt = r->timing;
+        float e[3] = {0.f, 0.f, 0.f};
+        // the events completed before the completion function ran, so these do not wait
+        bool ok = st == ZNCC_OK && bt && bt->recorded;
+        for (int k = 0; ok && k < 3; ++k) ok = cudaEventElapsedTime(&e[k], bt->ev[k], bt->ev[k + 1]) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+        if (ok) {
+            timing->queue_ms = ms_between(r->t_submit, r->t_issue);
+            timing->h2d_ms = e[0];
+            timing->run_ms = e[1];
+            timing->d2h_ms = e[2];
+            timing->total_ms = ms_between(r->t_submit, r->t_done);
+            timing->device_wait_ms = timing->total_ms - timing->queue_ms - (e[0] + e[1] + e[2]);
+            timing->batch_pairs = bt->pairs;
+            timing->valid = 1;
+        }
+    }
+    release_timing(s, r);
     s->tickets.erase(it);
     give_buf(s, r->img);
     give_buf(s, r->disp);
@@ -516,11 +598,13 @@ zncc_status serve_destroy(zncc_server* s) {
     s->worker.join();
     for (Slot* sl : s->slots) destroy_slot(sl);
     for (auto& kv : s->tickets) {
+        release_timing(s, kv.second);
         drop_buf(kv.second->img);
         drop_buf(kv.second->disp);
         delete kv.second;
     }
     for (auto& kv : s->free_bufs) drop_buf(kv.second);
+    for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
     for (cudaStream_t st : s->streams)
         if (st) cudaStreamDestroy(st);
     delete s;

@@ -10,8 +10,9 @@ The methods of ZnccContext carry the names of the C calls they wrap:
     dt_aggregate, wta_disparity, zncc_run, zncc_run_host
 
 and the module-level zncc_run_batch, dt_aggregate_noalloc and fastdt_codec wrap the batched
-call, the context-free aggregation that allocates nothing and the FastDT code on the device. serve_create, serve_submit, serve_poll and
-serve_destroy wrap the serving calls (a handle in, numpy arrays for the host images), and
+call, the context-free aggregation that allocates nothing and the FastDT code on the device.
+serve_create, serve_submit, serve_poll, serve_poll_timed and serve_destroy wrap the serving
+calls (a handle in, numpy arrays for the host images), and
 ZnccServer bundles them.
 """
 
@@ -56,6 +57,7 @@ SIGNATURES = [
     ("serve_submit", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _f, _f, _i, _i,
                           ctypes.POINTER(ctypes.c_uint64)]),
     ("serve_poll", _i, [_vp, ctypes.c_uint64, _vp, _i]),
+    ("serve_poll_timed", _i, [_vp, ctypes.c_uint64, _vp, _i, _vp]),
     ("serve_destroy", _i, [_vp]),
     ("serve_last_error", ctypes.c_char_p, [_vp]),
     ("zncc_last_error", ctypes.c_char_p, [_vp]),
@@ -187,6 +189,26 @@ def serve_poll(server, ticket: int, disp: np.ndarray, timeout_us: int = 0) -> in
     return int(lib().serve_poll(server, ctypes.c_uint64(ticket), disp.ctypes.data, int(timeout_us)))
 
 
+class ServeTiming(ctypes.Structure):
+    """zncc_serve_timing: where a served request's latency went (milliseconds)."""
+    _fields_ = [("queue_ms", ctypes.c_double), ("device_wait_ms", ctypes.c_double),
+                ("h2d_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("d2h_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("batch_pairs", ctypes.c_int), ("valid", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def serve_poll_timed(server, ticket: int, disp: np.ndarray, timeout_us: int = 0):
+    """serve_poll, plus the request's latency breakdown once it has finished: (status, dict or
+    None)."""
+    assert disp.dtype == np.uint16 and disp.flags.c_contiguous
+    t = ServeTiming()
+    st = int(lib().serve_poll_timed(server, ctypes.c_uint64(ticket), disp.ctypes.data, int(timeout_us),
+                                    ctypes.byref(t)))
+    return st, (t.as_dict() if st == ZNCC_OK and t.valid else None)
+
+
 def serve_destroy(server) -> int:
     return int(lib().serve_destroy(server))
 
@@ -202,6 +224,9 @@ class ZnccServer:
 
     def poll(self, ticket, disp, timeout_us=0):
         return serve_poll(self._h, ticket, disp, timeout_us)
+
+    def poll_timed(self, ticket, disp, timeout_us=0):
+        return serve_poll_timed(self._h, ticket, disp, timeout_us)
 
     def last_error(self) -> str:
         return lib().serve_last_error(self._h).decode()

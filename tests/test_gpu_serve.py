@@ -1,14 +1,17 @@
 """Serving on the GPU: a mix of requests of uneven size, disparity range, window, DT
 parameters and storage, submitted together, gives for every request exactly the map of a
-single zncc_run on its own context; so does a one-pair-per-launch server and a server whose
-budget forces contexts to be evicted and re-created. An injected device-allocation failure
-comes back through serve_poll as ZNCC_ENOMEM and the server keeps serving."""
+single zncc_run on its own context, and the FP64 oracle's map within the disparity
+tolerance; so does a one-pair-per-launch server and a server whose budget forces contexts to
+be evicted and re-created. An injected device-allocation failure comes back through
+serve_poll as ZNCC_ENOMEM and the server keeps serving. serve_poll_timed's latency breakdown
+adds up to the request's total."""
 
 import os
 
 import numpy as np
 import pytest
 
+import oracle
 from synth import make_pair
 
 torch = pytest.importorskip("torch")
@@ -62,6 +65,41 @@ def test_served_maps_equal_maps_computed_alone(budget, max_slots):
     served = _served(pairs, budget, max_slots)
     for i, (a, b) in enumerate(zip(alone, served)):
         assert np.array_equal(a, b), f"request {i} {MIX[i]} differs in the mix"
+
+
+def test_served_maps_match_the_oracle():
+    """Served maps against the FP64 oracle: F32 requests exact away from near-ties (best -
+    second gap below 1e-5, times A_hat after aggregation); the half-storage request differs on
+    fewer than 1% of its pixels."""
+    pairs = _pairs()
+    served = _served(pairs, 4 << 30, 32)
+    for (h, w, d, win, ss, sr, it, st, seed), p, got in zip(MIX, pairs, served):
+        ref, gap = oracle.run(p.left, p.right, d, win // 2, ss, sr, it)
+        scale = oracle.ones_response(p.left, ss, sr, it) if it else 1.0
+        bad = (got != ref) & (gap >= 1e-5 * scale)
+        if st == Z.ZNCC_F32:
+            assert not bad.any(), (h, w, d, win, it, int(bad.sum()))
+        else:
+            assert (got != ref).mean() < 0.01, (h, w, d, win, it, float((got != ref).mean()))
+
+
+def test_poll_timed_breakdown_adds_up():
+    """The server's latency breakdown of each request: every part is measured, the device work
+    is positive, and the parts add up to the total (the stream wait is the remainder, so it may
+    read a few microseconds below zero where host and device clocks differ)."""
+    pairs = _pairs()
+    with Z.ZnccServer(4 << 30, 32) as srv:
+        tickets = [srv.submit(p.left, p.right, d, win, ss, sr, it, st)
+                   for (h, w, d, win, ss, sr, it, st, seed), p in zip(MIX, pairs)]
+        for (h, w, *_), t in zip(MIX, tickets):
+            disp = np.zeros((h, w), np.uint16)
+            st, tm = srv.poll_timed(t, disp, 20_000_000)
+            assert st == Z.ZNCC_OK and tm is not None and tm["valid"] == 1, (st, tm)
+            assert tm["h2d_ms"] > 0 and tm["run_ms"] > 0 and tm["d2h_ms"] > 0, tm
+            assert tm["queue_ms"] >= 0 and tm["device_wait_ms"] > -0.05, tm
+            parts = tm["queue_ms"] + tm["device_wait_ms"] + tm["h2d_ms"] + tm["run_ms"] + tm["d2h_ms"]
+            assert abs(parts - tm["total_ms"]) < 1e-6, tm
+            assert 1 <= tm["batch_pairs"] <= len(MIX), tm
 
 
 def test_injected_allocation_failure_is_reported_and_recovered():
