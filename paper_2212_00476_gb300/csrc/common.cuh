@@ -421,6 +421,10 @@ struct WtaRegs {
         for (int i = 0; i < kL / 2; ++i) rd[i] = 0xFFFFFFFFu;
     }
     __device__ __forceinline__ void fold(const float (&v)[kL][4], int nvalid, int d_first) {
+        if (nvalid == 4) {
+            fold4(v, d_first);
+            return;
+        }
 #pragma unroll
         for (int i = 0; i < kL; ++i) {
             float m = -INFINITY;
@@ -433,6 +437,23 @@ struct WtaRegs {
                 const unsigned d = (unsigned)(d_first + jj) & 0xFFFFu;
                 rd[i >> 1] = (i & 1) ? ((rd[i >> 1] & 0x0000FFFFu) | (d << 16)) : ((rd[i >> 1] & 0xFFFF0000u) | d);
             }
+        }
+    }
+    // A whole group of four disparities: the group's maximum by three fmaxf, its index from
+    // the pair compares (the first pair wins a tie between the pairs, the first element a tie
+    // within a pair: the smallest d), and the 16-bit disparity inserted by a byte permute.
+    __device__ __forceinline__ void fold4(const float (&v)[kL][4], int d_first) {
+#pragma unroll
+        for (int i = 0; i < kL; ++i) {
+            const float m01 = fmaxf(v[i][0], v[i][1]), m23 = fmaxf(v[i][2], v[i][3]);
+            const bool lo = m01 >= m23;
+            const float m = lo ? m01 : m23;
+            const int jj = lo ? (v[i][0] >= v[i][1] ? 0 : 1) : (v[i][2] >= v[i][3] ? 2 : 3);
+            const bool better = m > rv[i];
+            rv[i] = better ? m : rv[i];
+            const unsigned d = (unsigned)(d_first + jj);
+            const unsigned ins = (i & 1) ? __byte_perm(rd[i >> 1], d, 0x5410) : __byte_perm(rd[i >> 1], d, 0x3254);
+            rd[i >> 1] = better ? ins : rd[i >> 1];
         }
     }
     __device__ __forceinline__ float2 entry(int i) const {

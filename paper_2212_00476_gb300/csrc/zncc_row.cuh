@@ -160,11 +160,9 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
         float v[kL][4];
         if (active) {
             // ---- window sums of products P for 16 pixels x 4 disparities ----
+            // P[i] = prefix(i + 2R) - prefix(i - 1): each entry is set at its first touch
+            // (-prefix(i - 1) at step i - 1; P[0] at step 2R) and completed at step i + 2R
             int P[kL][4];
-#pragma unroll
-            for (int i = 0; i < kL; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) P[i][j] = 0;
             // RP index of column x' - d_first - j at step t (x' = x0 - R + t) is rbase + t - j;
             // rbase + 1 = x0 - d_first + blk_hi is a multiple of 4 (as are x0, d_first and
             // blk_hi, d_lo being one), so every index below has a constant plane
@@ -185,8 +183,9 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
                     if (NW > 1) pre[j] = __dp4a(lp.y, rp[j].y, pre[j]);
                     if (NW > 2) pre[j] = __dp4a(lp.z, rp[j].z, pre[j]);
                     if (NW > 3) pre[j] = __dp4a(lp.w, rp[j].w, pre[j]);
-                    if (t - 2 * R >= 0 && t - 2 * R < kL) P[t - 2 * R][j] += (int)pre[j];
-                    if (t + 1 < kL) P[t + 1][j] -= (int)pre[j];
+                    if (t == 2 * R) P[0][j] = (int)pre[j];
+                    else if (t - 2 * R > 0 && t - 2 * R < kL) P[t - 2 * R][j] += (int)pre[j];
+                    if (t + 1 < kL) P[t + 1][j] = -(int)pre[j];
                 }
                 rp[3] = rp[2];
                 rp[2] = rp[1];
@@ -196,35 +195,47 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
             // ---- normalization, Eq. (2); the target statistics slide like the columns ----
             const int cb = x0 - d_first - c0;               // SR index of (i, j) is cb + i - j >= 3
             const int cb4 = cb + 1;                         // a multiple of 4, like rb4
+            // A fused horizontal pair (F32, F16) in the scaled form multiplies its result by
+            // s2 = (1-K)^2; the pair is linear, so the factor is folded into the left
+            // statistic here instead (FastDT codes take per-position scales in the pair).
+            const float lscale = (MODE == kModeHPair && !kFast) ? a.s2 : 1.0f;
             int2 sr[4];
             sr[1] = at4(SR, cb4, -2, pSR);
             sr[2] = at4(SR, cb4, -3, pSR);
             sr[3] = at4(SR, cb4, -4, pSR);
+            auto normalize = [&](auto full) {
 #pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                const int x = x0 + i;
-                const int2 st = at4(SL, x0, i, pX);
-                sr[0] = at4(SR, cb4, i - 1, pSR);
-                const float isl = __int_as_float(st.y);
+                for (int i = 0; i < kL; ++i) {
+                    const int x = x0 + i;
+                    const int2 st = at4(SL, x0, i, pX);
+                    sr[0] = at4(SR, cb4, i - 1, pSR);
+                    const float isl = __int_as_float(st.y) * lscale;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const unsigned num = n * (unsigned)P[i][j] - (unsigned)st.x * (unsigned)sr[j].x;
-                    const bool ok = x < W && j < nvalid;
-                    v[i][j] = ok ? (float)(int)num * isl * __int_as_float(sr[j].y) : 0.0f;
+                    for (int j = 0; j < 4; ++j) {
+                        const unsigned num = n * (unsigned)P[i][j] - (unsigned)st.x * (unsigned)sr[j].x;
+                        const float c = (float)(int)num * isl * __int_as_float(sr[j].y);
+                        if constexpr (decltype(full)::value) v[i][j] = c;
+                        else v[i][j] = (x < W && j < nvalid) ? c : 0.0f;
+                    }
+                    sr[3] = sr[2];
+                    sr[2] = sr[1];
+                    sr[1] = sr[0];
                 }
-                sr[3] = sr[2];
-                sr[2] = sr[1];
-                sr[1] = sr[0];
-            }
+            };
+            // whole chunks of whole 4-disparity groups take the path without predicates
+            if (x0 + kL <= W && nvalid == 4) normalize(std::true_type());
+            else normalize(std::false_type());
         }
 
         if constexpr (MODE == kModeWta) {
             if (active) wr.fold(v, nvalid, d_first);
             continue;
         }
-        if constexpr (MODE == kModeHPair)
-            dt_pair(v, co + k * kCS, tq, dq, lane, wl, nwl, sa, sb, a.s2, kFast ? mrow + k * kCS : nullptr,
-                    NoHook(), active);
+        if constexpr (MODE == kModeHPair && kFast)
+            dt_pair(v, co + k * kCS, tq, dq, lane, wl, nwl, sa, sb, a.s2, mrow + k * kCS, NoHook(), active);
+        else if constexpr (MODE == kModeHPair)       // s2 already folded into the costs
+            dt_pair<false>(v, co + k * kCS, tq, dq, lane, wl, nwl, sa, sb, 1.0f, (const float2*)nullptr,
+                           NoHook(), active);
 
         if constexpr (kFast) {
             // near-zero-mean codes against d_arb = 0, held by lane dq 0 in slice 0 (a visit covers
@@ -246,10 +257,15 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
         } else if (active && nvalid > 0) {
             // ---- store [H][W][dstride] ----
             T* q = out + ((size_t)y * W + x0) * a.dstride + (d_first - a.d_out0);
+            if (vec && nvalid == 4 && x0 + kL <= W) {        // a whole chunk of whole groups
 #pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                if (x0 + i < W) st4(q, nvalid, vec, v[i]);
-                q += a.dstride;
+                for (int i = 0; i < kL; ++i) st4(q + (size_t)i * a.dstride, 4, true, v[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < kL; ++i) {
+                    if (x0 + i < W) st4(q, nvalid, vec, v[i]);
+                    q += a.dstride;
+                }
             }
         }
     }
