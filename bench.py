@@ -8,11 +8,12 @@ horizontal DT pair, the remaining DT passes, WTA fused into the last vertical pa
 synthetic 1280x384 pair, D = 128, 9x9 window, sigma_s = 20, sigma_r = 0.1, 3 iterations.
 Inputs are resident in HBM; L2 is flushed (a 256 MB write) before every timed step and the
 flush is outside the step's CUDA events. Rank 0 prints one JSON line. With the default
-workload on one GPU the line also carries "precision" (the same pair with F32, F16 and FastDT
-I8 storage: step time and disparity mismatch against the FP64 oracle) and "serving" (Poisson
-requests of mixed size and disparity range through the serving calls, continuous batching
-against one pair per launch: p50/p99, throughput, the p99 latency breakdown and a saturation
-leg); --no-extras leaves them out.
+workload on one GPU the line also carries, measured after the timed region: "precision" (the
+same pair with F32, F16 and FastDT I8 storage: step time and disparity mismatch against the
+FP64 oracle), "serving" (Poisson requests of mixed size and disparity range through the
+serving calls, continuous batching against one pair per launch: p50/p99, throughput, the p99
+latency breakdown and a saturation leg) and "configs" (the lines of --workload plain_320x96,
+batch_uneven16 and precision_sweep, run as child processes); --no-extras leaves them out.
 
 --impl reference times the FP64 CPU oracle (the only reference this method has) on the host
 cores, one full pair per step.
@@ -419,11 +420,13 @@ def run_gb300(args):
                                                    "sample": f"{len(t1)} full pair(s)"}
     if rank == 0 and world == 1 and args.workload == "paper_1280x384" and not args.no_extras:
         line["precision"] = precision_leg(Z, ctx, pair, wl, iters, left, right, disp, flush, stream, args)
-        sweep, sat = serving_legs(Z, Z.ZNCC_F32, [SERVE_RATE], SERVE_REQUESTS, sat_n=SERVE_SAT_REQUESTS)
-        head = sweep[0]
+        sweep, sat = serving_legs(Z, Z.ZNCC_F32, [SERVE_RATE, SERVE_RATE_BUSY], SERVE_REQUESTS,
+                                  sat_n=SERVE_SAT_REQUESTS)
+        head, busy = sweep
         line["serving"] = {
-            "config": SERVE_CONFIG + f"; {SERVE_REQUESTS} requests at {SERVE_RATE:g} req/s; saturation: "
-                                     f"{SERVE_SAT_REQUESTS} requests queued at once",
+            "config": SERVE_CONFIG + f"; {SERVE_REQUESTS} requests at {SERVE_RATE:g} and at "
+                                     f"{SERVE_RATE_BUSY:g} req/s; saturation: {SERVE_SAT_REQUESTS} "
+                                     "requests queued at once",
             "rate_req_per_s": SERVE_RATE,
             "p50_ms": head["batched"]["p50_ms"], "p99_ms": head["batched"]["p99_ms"],
             "throughput_req_per_s": head["batched"]["served_req_per_s"],
@@ -434,14 +437,52 @@ def run_gb300(args):
                       "throughput_req_per_s": head["one_pair_per_launch"]["served_req_per_s"],
                       "throughput_gdisp_s": head["one_pair_per_launch"]["served_gdisp_s"],
                       "p99_breakdown": head["one_pair_per_launch"]["p99_breakdown"]},
+            "busy": {"rate_req_per_s": SERVE_RATE_BUSY,
+                     "batched": {k: busy["batched"][k] for k in ("p50_ms", "p99_ms", "served_req_per_s")},
+                     "plain": {k: busy["one_pair_per_launch"][k] for k in ("p50_ms", "p99_ms", "served_req_per_s")}},
             "saturation": sat,
         }
+    if rank == 0 and world == 1 and args.workload == "paper_1280x384" and not args.no_extras:
+        ctx.close()
+        torch.cuda.synchronize()
+        line["configs"] = other_configs(args)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+OTHER_CONFIGS = [("plain_320x96", ["--workload", "plain_320x96"]),
+                 ("batch_uneven16", ["--workload", "batch_uneven16"]),
+                 ("precision_1920x1080", ["--workload", "precision_sweep"])]
+
+
+def other_configs(args):
+    """The other configurations of the paper-shaped workload family, each in a child process
+    after the timed region (so that their lines reach the record of a default run): the plain
+    320x96 pair (ZNCC + WTA, latency), 16 uneven pairs batched under a CUDA graph against one
+    pair per launch, and the 1920x1080 precision sweep (F32 / F16 / FastDT I8 against the FP64
+    oracle). A child that fails is recorded with its error instead."""
+    out = {}
+    for name, extra in OTHER_CONFIGS:
+        cmd = [sys.executable, os.path.abspath(__file__), *extra, "--steps", "10", "--warmup", "3",
+               "--no-cpu-baseline"]
+        if args.no_autotune:
+            cmd.append("--no-autotune")
+        t0 = time.perf_counter()
+        try:
+            p = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            lines = [x for x in p.stdout.splitlines() if x.startswith("{")]
+            if p.returncode != 0 or not lines:
+                out[name] = {"error": f"exit {p.returncode}: {(p.stderr or p.stdout)[-400:]}"}
+            else:
+                out[name] = json.loads(lines[-1])
+        except (subprocess.TimeoutExpired, OSError, ValueError) as e:
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 def precision_leg(Z, ctx, pair, wl, iters, left, right, disp, flush, stream, args, steps=10):
@@ -699,7 +740,7 @@ def run_precision(args):
     return 0
 
 
-SERVE_RATE, SERVE_REQUESTS, SERVE_SAT_REQUESTS = 200.0, 400, 300
+SERVE_RATE, SERVE_RATE_BUSY, SERVE_REQUESTS, SERVE_SAT_REQUESTS = 200.0, 500.0, 1000, 300
 
 
 def serving_legs(Z, storage, rates, n, sat_n=0, seed=5):

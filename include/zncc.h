@@ -225,8 +225,10 @@ zncc_status zncc_run_host(zncc_ctx* ctx, const uint8_t* left_host, const uint8_t
  * DT parameters and storage type. Whenever requests wait and slots are free, the scheduler
  * admits them in submission order and launches the small ones (W*H*D < 2^25) that share the
  * DT parameters, the iteration count and the storage type as one batched fused run
- * (zncc_run_batch, up to 32 pairs) and a larger one, which fills the GPU by itself, alone; on
- * one of two streams, so that a new launch starts while earlier ones still run.
+ * (zncc_run_batch, up to 32 pairs) and a larger one, which fills the GPU by itself, alone, so
+ * that a new launch starts while earlier ones still run: larger pairs in arrival order on a
+ * high-priority stream, the batches on a low-priority one, which fill the SMs the larger pairs
+ * leave free.
  * Results are identical to running each pair alone: the batched kernels compute every pair
  * exactly as a single zncc_run does. Contexts are reused per request shape; the device memory
  * they hold (cost volume, DT coefficients, A_hat maps, images and disparity map) is charged
@@ -296,6 +298,14 @@ const char* serve_last_error(const zncc_server* server);
  * (zncc_create, dt_aggregate_noalloc) on the calling host thread. */
 const char* zncc_last_error(const zncc_ctx* ctx);
 
+/* Faults the context's kernels recorded on the device since the last call (0: none), then
+ * cleared. A kernel that waits for asynchronous copies gives up after a bounded number of polls
+ * instead of waiting without end, records the fault here and stops: bit 0 = a bulk copy of the
+ * cost kernel's image rows did not complete in time (the results of that launch are not
+ * valid), bit 1 = the copies had still not landed after a second bounded wait. Synchronizes
+ * the context's stream. ZNCC_EINVAL for a NULL argument; ZNCC_ECUDA if the read fails. */
+zncc_status zncc_device_faults(zncc_ctx* ctx, uint32_t* faults);
+
 /* Static text for a status code. */
 const char* zncc_status_string(zncc_status status);
 
@@ -316,6 +326,10 @@ const char* zncc_status_string(zncc_status status);
  *                        as fast at 320x96, D = 32 and faster at every larger measured shape)
  *   ZNCC_TUNE_PLANE_CS   the plane-resident path's cluster size (1, 2, 4 or 8; 0 = automatic);
  *                        a size whose band does not fit sends the pair to the streaming path
+ *   ZNCC_TUNE_ROW_LOADS  cost kernel fused with the first horizontal pair: 1 = stage the image
+ *                        rows with plain loads; 0 (automatic) = bulk asynchronous copies (the
+ *                        TMA unit) where both images and the pitch are 16-byte aligned and W is
+ *                        a multiple of 16, plain loads elsewhere
  * A value a launch cannot use (too many threads or too much shared memory) makes the next
  * call fail with ZNCC_EUNSUPPORTED. Unknown keys give ZNCC_EINVAL. */
 typedef enum {
@@ -325,7 +339,8 @@ typedef enum {
     ZNCC_TUNE_V_TQ = 4,
     ZNCC_TUNE_AHAT_SMS = 5,
     ZNCC_TUNE_PLANE = 6,
-    ZNCC_TUNE_PLANE_CS = 7
+    ZNCC_TUNE_PLANE_CS = 7,
+    ZNCC_TUNE_ROW_LOADS = 8
 } zncc_tune_key;
 zncc_status zncc_set_tuning(zncc_ctx* ctx, int key, int value);
 

@@ -91,6 +91,7 @@ struct zncc_ctx {
     int smem_max = 0;             // opt-in shared memory per block of the device
     int row_minb2 = 1;            // cost kernel: two-blocks-per-SM variant where it applies
     int row_spb = 0;              // cost kernel: slices per block (0 = automatic)
+    int row_nobulk = 0;           // cost kernel: stage the image rows with plain loads
     int ahat_sms = 0;             // SMs the cost kernel leaves to the A_hat chain (0 = automatic)
     int h_tq = 0, v_tq = 0;       // DT pairs: forced lanes per chunk (0 = automatic)
     int plane_mode = 0;           // F32 fused runs: the plane-resident path where it applies
@@ -102,6 +103,7 @@ struct zncc_ctx {
     int2* scan_stats = nullptr;   // (progressive scan) packed statistics: left [H][W], right [H][W+D-1]
     uint8_t* img = nullptr;       // device copies for zncc_run_host: 2 x [H][W]
     uint16_t* disp = nullptr;     // [H][W]
+    unsigned* fault = nullptr;    // device word: faults the kernels recorded (kFault*), zero initially
     bool profiling = false;
     std::vector<cudaEvent_t> events;
     int events_used = 0;
@@ -184,6 +186,7 @@ void release(zncc_ctx* c) {
     free_dev(c->img);
     free_dev(c->disp);
     free_dev(c->scan_stats);
+    free_dev(c->fault);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -294,6 +297,7 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
         RowBatch b;
         memset(&b, 0, sizeof(b));
         b.mode = mode;
+        b.fault = lc->fault;
         int threads = 0;
         size_t smem = 0;
         bool minb2 = true;
@@ -335,8 +339,16 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
             const bool whole_rows = mode == kModeWta || dtype == 2;
             if (whole_rows) a.spb = nslices;
             else a.spb = c->row_spb > 0 ? std::min(c->row_spb, nslices) : nslices;
+            // the image rows by bulk copies where both images and the pitch are 16-byte aligned
+            // and W is a multiple of 16, while the rows fit in the region they share and the
+            // guide row's buffer fits in shared memory; else plain loads
+            a.bulk = mode == kModeHPair && a.W % 16 == 0 && a.pitch % 16 == 0 &&
+                     (uintptr_t)a.left % 16 == 0 && (uintptr_t)a.right % 16 == 0 && !c->row_nobulk ? 1 : 0;
             while (!whole_rows && a.spb > 1 && zncc_row_smem_bytes(r, mode, dtype, a, nthr) > (size_t)lc->smem_max)
                 --a.spb;
+            if (a.bulk && (zncc_row_smem_bytes(r, mode, dtype, a, nthr) > (size_t)lc->smem_max ||
+                           !zncc_row_bulk_fits_host(r, dtype, a, nthr)))
+                a.bulk = 0;
             const size_t sm = zncc_row_smem_bytes(r, mode, dtype, a, nthr);
             if (sm > (size_t)lc->smem_max)
                 return fail(lc, ZNCC_EUNSUPPORTED, "the cost kernel's row band does not fit in shared memory");
@@ -931,6 +943,8 @@ zncc_status zncc_create(int width, int height, int max_disp, int win, zncc_ctx**
     if (e == cudaSuccess) e = device_alloc((void**)&c->coefV, npix * sizeof(float4));
     if (e == cudaSuccess) e = device_alloc((void**)&c->keys, npix * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->keys, 0, npix * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = device_alloc((void**)&c->fault, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->fault, 0, sizeof(unsigned));
     if (e != cudaSuccess) {
         zncc_status s = e == cudaErrorMemoryAllocation ? ZNCC_ENOMEM : ZNCC_ECUDA;
         std::string m = std::string("zncc_create: ") + cudaGetErrorString(e);
@@ -1277,6 +1291,7 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
         case ZNCC_TUNE_ROW_SPB: c->row_spb = value; break;
         case ZNCC_TUNE_AHAT_SMS: c->ahat_sms = value; break;
         case ZNCC_TUNE_PLANE: c->plane_mode = value ? 1 : 0; break;
+        case ZNCC_TUNE_ROW_LOADS: c->row_nobulk = value ? 1 : 0; break;
         case ZNCC_TUNE_PLANE_CS:
             if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
                 return fail(c, ZNCC_EINVAL, "plane cluster size must be 0, 1, 2, 4 or 8");
@@ -1292,6 +1307,18 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
     }
     c->plans.clear();
     c->plane_cs = -1;
+    return ZNCC_OK;
+}
+
+zncc_status zncc_device_faults(zncc_ctx* c, uint32_t* faults) {
+    if (!c || !faults) return ZNCC_EINVAL;
+    c->err.clear();
+    *faults = 0;
+    unsigned v = 0;
+    ZNCC_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    ZNCC_CUDA(c, cudaMemcpy(&v, c->fault, sizeof(v), cudaMemcpyDeviceToHost), "fault word read");
+    if (v) ZNCC_CUDA(c, cudaMemset(c->fault, 0, sizeof(unsigned)), "fault word clear");
+    *faults = v;
     return ZNCC_OK;
 }
 

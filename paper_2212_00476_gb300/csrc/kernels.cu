@@ -808,6 +808,10 @@ cudaError_t launch_wta_volume(const void* cost, int dtype, int W, int H, int D, 
     return cudaGetLastError();
 }
 
+bool zncc_row_bulk_fits_host(int R, int dtype, const RowArgs& a, int nthreads) {
+    return zncc_row_bulk_fits(R, dtype, a, nthreads);
+}
+
 size_t zncc_row_smem_bytes(int R, int mode, int dtype, const RowArgs& a, int nthreads) {
     return zncc_row_smem(R, mode, dtype, a, nthreads);
 }

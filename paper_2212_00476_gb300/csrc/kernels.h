@@ -36,6 +36,8 @@ struct RowArgs {
     float s2;                 // (1 - K)^2
     WtaOut wta;               // (Wta)
     int minb2;                // use the two-blocks-per-SM variant where the block allows
+    int bulk;                 // (HPair) stage the image rows by bulk asynchronous copies: both
+                              // images and the pitch 16-byte aligned, W a multiple of 16
     int item0, nitems;        // this pair's units (row, slice), or rows (Wta), in a batched launch
 };
 
@@ -43,8 +45,16 @@ struct RowArgs {
 // value. Of G blocks, block b takes the units [b * total / G, (b+1) * total / G), in order.
 struct RowBatch {
     int npairs, total_items, grid, mode;
+    unsigned* fault;          // device word of the launching context: bits of kFault* set by the kernel
     RowArgs p[kMaxBatch];
 };
+
+// Device-side faults a kernel records instead of waiting without end (ZNCC_FAULT_* of zncc.h).
+constexpr unsigned kFaultBulkWait = 1u;      // a bulk copy of image rows did not complete in time
+constexpr unsigned kFaultBulkDrain = 2u;     // ... nor after the second wait (the block then stopped)
+// Polls of an mbarrier before a wait counts as timed out (each poll may suspend the thread for a
+// while; a copy from L2 or HBM completes within a few thousand).
+constexpr unsigned kBulkWaitPolls = 1u << 24;
 
 struct LineArgs {
     void* vol;                // float or half cost volume (output, and input unless src is set)
@@ -94,6 +104,7 @@ void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, dim3 grid
                    cudaStream_t st, int cluster);
 
 size_t zncc_row_smem_bytes(int R, int mode, int dtype, const RowArgs& a, int nthreads);
+bool zncc_row_bulk_fits_host(int R, int dtype, const RowArgs& a, int nthreads);
 // A pass whose coefficients (and multipliers) can be streamed (at least two slices per line
 // group); the shared memory of a block with one or two buffers of them.
 bool line_coef_async(const LineArgs& a);

@@ -2,8 +2,12 @@
 // requests from host memory, admitted under a device-memory budget onto a pool of contexts
 // and run by continuous batching: whenever requests wait and slots are free, the scheduler
 // thread launches the waiting small ones that share DT parameters as one zncc_run_batch (up
-// to 32 pairs of uneven sizes), and a pair large enough to fill the GPU by itself alone, on
-// one of two streams, so that a new launch starts while earlier ones are still on the GPU.
+// to 32 pairs of uneven sizes), and a pair large enough to fill the GPU by itself alone, so
+// that a new launch starts while earlier ones are still on the GPU. Large pairs go to a
+// high-priority stream, in arrival order, batches of small pairs to a low-priority one: the
+// block scheduler then gives a large pair the SMs as they free up and the small batches fill
+// the gaps, so that two large pairs never share the GPU (each would finish as late as the
+// pair of them in sequence) and a large pair never waits behind small ones.
 // Completion is signalled by a host function queued behind each batch's result copies.
 //
 // Contexts (and their image, disparity and volume buffers) are kept per request shape and
@@ -113,8 +117,7 @@ struct zncc_server {
     int inflight = 0;                      // requests on the GPU
     uint64_t next_ticket = 1, use_clock = 0, completions = 0;
     bool stopping = false, thread_done = false;
-    cudaStream_t streams[2] = {nullptr, nullptr};
-    int next_stream = 0;
+    cudaStream_t streams[2] = {nullptr, nullptr};   // large pairs (high priority), batches (low)
     char err[512] = {0};
     std::thread worker;
 };
@@ -258,8 +261,8 @@ void CUDART_CB on_batch_done(void* p) {
 // Called without the lock; on failure the batch's requests end with the error.
 void launch(zncc_server* s, Batch* b) {
     const int n = (int)b->reqs.size();
-    cudaStream_t st = s->streams[s->next_stream];
-    s->next_stream ^= 1;
+    const Request* head = b->reqs[0];
+    cudaStream_t st = s->streams[runs_alone(head->key.W, head->key.H, head->key.D) ? 0 : 1];
     zncc_ctx* ctxs[zncc::kMaxBatch];
     const uint8_t* lefts[zncc::kMaxBatch];
     const uint8_t* rights[zncc::kMaxBatch];
@@ -345,8 +348,11 @@ void launch(zncc_server* s, Batch* b) {
 // allow, batch those that share the DT parameters and storage, launch, repeat.
 void worker_main(zncc_server* s) {
     bool ok = cudaSetDevice(s->device) == cudaSuccess;
+    int least = 0, greatest = 0;                  // numerically: greatest priority <= least
+    if (ok) ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess;
     for (int i = 0; ok && i < 2; ++i)
-        ok = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) == cudaSuccess;
+        ok = cudaStreamCreateWithPriority(&s->streams[i], cudaStreamNonBlocking, i == 0 ? greatest : least) ==
+             cudaSuccess;
     std::unique_lock<std::mutex> lk(s->mu);
     if (!ok) {
         cudaGetLastError();

@@ -35,9 +35,48 @@ namespace zncc {
 // __dp4a(word, 0x01010101) and its sum of squares __dp4a(word, word), slid like P.
 // One visit of the cost kernel: row y of one pair, disparity slices [s_begin, s_end).
 // Threads beyond the pair's nch * tq (whole warps) only take part in the barriers.
+// Four packed columns xs .. xs+3 (all inside the row) of a band of l raw rows in shared memory
+// (row j at raw + j * Wr, Wr a multiple of 16), xs = S (mod 4): per row one 32-bit word of the
+// four pixels (two aligned words funnel-shifted when S > 0), then a 4 x 4 byte transpose per
+// packed word.
+template <int l, int S>
+__device__ __forceinline__ void pack4_raw(const uint8_t* raw, int Wr, int xs, uint4 (&col)[4]) {
+    constexpr int NW = (l + 3) / 4;
+    const unsigned* r32 = reinterpret_cast<const unsigned*>(raw);
+    const int a4 = (xs - S) >> 2, wr4 = Wr >> 2;
+    unsigned w[4 * NW];
+#pragma unroll
+    for (int j = 0; j < 4 * NW; ++j) {
+        if (j < l) {
+            const unsigned lo = r32[j * wr4 + a4];
+            w[j] = S ? __funnelshift_r(lo, r32[j * wr4 + a4 + 1], 8 * S) : lo;
+        } else {
+            w[j] = 0u;
+        }
+    }
+    unsigned o[4][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        const unsigned t0 = __byte_perm(w[4 * k], w[4 * k + 1], 0x5140), t1 = __byte_perm(w[4 * k + 2], w[4 * k + 3], 0x5140);
+        const unsigned t2 = __byte_perm(w[4 * k], w[4 * k + 1], 0x7362), t3 = __byte_perm(w[4 * k + 2], w[4 * k + 3], 0x7362);
+        o[0][k] = __byte_perm(t0, t1, 0x5410);
+        o[1][k] = __byte_perm(t0, t1, 0x7632);
+        o[2][k] = __byte_perm(t2, t3, 0x5410);
+        o[3][k] = __byte_perm(t2, t3, 0x7632);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) col[c] = make_uint4(o[c][0], o[c][1], o[c][2], o[c][3]);
+}
+
+// Bytes of the rows a visit stages by bulk copies: l rows of each image, Wr = W + 16 apart.
+__host__ __device__ inline int bulk_row_stride(int W) { return W + 16; }
+
+// Returns false when a bulk copy of the image rows timed out (the fault is recorded; the
+// block stops).
 template <int R, typename T, int MODE>
-__device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_begin, int s_end,
-                                              uint4* smem_u4) {
+__device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_begin, int s_end,
+                                              uint4* smem_u4, unsigned long long* bar, unsigned& phase,
+                                              unsigned* fault) {
     constexpr int l = 2 * R + 1;
     constexpr int NW = (l + 3) / 4;     // packed words per column
     const int tq = a.tq, ds = kG * tq, nch = a.nch, span = nch * kL;
@@ -68,9 +107,70 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
     constexpr bool kFast = std::is_same<T, uint8_t>::value;
     float* mrow = sa + 2 * nwl * tq;                                 // chunk-major (kCS)
     float* ref = mrow + nch * kCS;
+    // (bulk) the guide row y for the coefficients, after everything else
+    uint8_t* grow = reinterpret_cast<uint8_t*>(kFast ? ref + nch * kCS : mrow);
 
     // ---- stage the packed bands (and the DT coefficients) ----
-    {
+    const bool bulk = MODE == kModeHPair && a.bulk;
+    if (bulk) {
+        // Bulk copies (the TMA unit) of the clamped rows y-R .. y+R of both images into the
+        // region that the statistics and coefficients take once the bands are packed, and of
+        // the guide row y; one thread issues them, every thread waits on the mbarrier.
+        const int Wr = bulk_row_stride(W);
+        uint8_t* rawL = reinterpret_cast<uint8_t*>(SL);
+        uint8_t* rawR = rawL + l * Wr;
+        fence_proxy_async_smem();                       // earlier accesses of the region, then the copies
+        __syncthreads();
+        if (tid == 0) {
+            mbar_expect_tx(bar, (unsigned)((2 * l + 1) * W));
+#pragma unroll
+            for (int j = 0; j < l; ++j) {
+                const size_t ro = (size_t)min(max(y - R + j, 0), H - 1) * a.pitch;
+                bulk_copy_g2s(rawL + j * Wr, a.left + ro, (unsigned)W, bar);
+                bulk_copy_g2s(rawR + j * Wr, a.right + ro, (unsigned)W, bar);
+            }
+            bulk_copy_g2s(grow, a.left + (size_t)y * a.pitch, (unsigned)W, bar);
+        }
+        bool ok = mbar_wait(bar, phase, kBulkWaitPolls);
+        if (__syncthreads_or(!ok)) {                     // a copy did not land in time: record it,
+            if (tid == 0) atomicOr(fault, kFaultBulkWait);
+            ok = mbar_wait(bar, phase, kBulkWaitPolls);  // wait for the copies still in flight
+            if (__syncthreads_or(!ok) && tid == 0) atomicOr(fault, kFaultBulkDrain);
+            return false;
+        }
+        phase ^= 1u;
+        // pack four columns per thread where they lie inside the row, single columns (clamped)
+        // at the ends
+        auto pack1 = [&](const uint8_t* raw, int xc) {
+            unsigned w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int j = 0; j < l; ++j) w[j >> 2] |= (unsigned)raw[j * Wr + xc] << (8 * (j & 3));
+            return make_uint4(w[0], w[1], w[2], w[3]);
+        };
+        constexpr int SLS = ((-R) % 4 + 4) % 4, SRS = ((1 - R) % 4 + 4) % 4;   // (-R) & 3, xr0 & 3
+        const int ngl = (NLP + 3) >> 2, ngr = (NRP + 3) >> 2;
+        for (int g = tid; g < ngl + ngr; g += blockDim.x) {
+            const bool left = g < ngl;
+            const int g4 = left ? g : g - ngl;
+            const int xs = left ? 4 * g4 - R : xr0 + 4 * g4;   // image column of entry 4 g4
+            const int nent = left ? NLP : NRP;
+            uint4* dst = left ? LP : RP;
+            const int pl = left ? pLP : pRP;
+            const uint8_t* raw = left ? rawL : rawR;
+            if (xs >= 0 && xs + 3 < W && 4 * g4 + 3 < nent) {
+                uint4 col[4];
+                if (left) pack4_raw<l, SLS>(raw, Wr, xs, col);
+                else pack4_raw<l, SRS>(raw, Wr, xs, col);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dst[c * pl + g4] = col[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (4 * g4 + c < nent) dst[c * pl + g4] = pack1(raw, min(max(xs + c, 0), W - 1));
+            }
+        }
+        __syncthreads();                                 // the raw rows are consumed
+    } else {
         size_t roff[l];                                 // the band's clamped rows
 #pragma unroll
         for (int j = 0; j < l; ++j) roff[j] = (size_t)min(max(y - R + j, 0), H - 1) * a.pitch;
@@ -87,7 +187,7 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
         // the row's DT coefficients (w, chunk prefix product, next w, chunk suffix product),
         // computed here from the guide (the left image) as k_dt_coef computes them: 16
         // consecutive lanes hold one chunk (span and the block are whole warps)
-        const uint8_t* g = a.left + (size_t)y * a.pitch;
+        const uint8_t* g = bulk ? grow : a.left + (size_t)y * a.pitch;
         auto weight = [&](int q) -> float {      // the step q-1 -> q
             return (q >= 1 && q < W) ? a.K * expf(-fabsf((float)(g[q] - g[q - 1])) * a.inv_sr255) : 0.0f;
         };
@@ -293,6 +393,7 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
             }
         }
     }
+    return true;
 }
 
 // SINGLE: the launch holds one pair, whose arguments are then read at constant offsets of
@@ -305,6 +406,10 @@ __device__ __forceinline__ void zncc_row_item(const RowArgs& a, int y, int s_beg
 template <int R, typename T, int MODE, int MINB, bool SINGLE>
 __global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(const __grid_constant__ RowBatch b) {
     extern __shared__ uint4 smem_u4[];
+    __shared__ unsigned long long bar;                  // bulk copies of the image rows (HPair)
+    unsigned phase = 0;
+    if (MODE == kModeHPair && threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
     griddep_wait();
     const int i0 = (int)((long long)blockIdx.x * b.total_items / b.grid);
     const int i1 = (int)((long long)(blockIdx.x + 1) * b.total_items / b.grid);
@@ -330,7 +435,7 @@ __global__ void __launch_bounds__(MINB == 2 ? 320 : 512, MINB) k_zncc_row(const 
             u += s_end - s_begin;
         }
         if (u >= i1) griddep_launch_dependents();       // this block's last visit
-        zncc_row_item<R, T, MODE>(a, y, s_begin, s_end, smem_u4);
+        if (!zncc_row_item<R, T, MODE>(a, y, s_begin, s_end, smem_u4, &bar, phase, b.fault)) return;
         __syncthreads();                                 // the next visit restages shared memory
     }
 }
@@ -345,7 +450,20 @@ inline size_t zncc_row_smem(int R, int mode, int dtype, const RowArgs& a, int nt
     b += 8ull * 4 * (pX + plane_of(span + drange - 1));
     if (mode == kModeHPair) b += 16ull * a.nch * kCS + dt_scan_bytes(nthreads / 32, a.tq);
     if (mode == kModeHPair && dtype == 2) b += 8ull * a.nch * kCS;       // FastDT: scales, references
+    if (mode == kModeHPair && a.bulk) b += (size_t)(a.W + 15) / 16 * 16; // the guide row
     return b;
+}
+
+// Whether a visit's raw rows (both images, bulk_row_stride apart) fit in the shared memory that
+// the statistics and the later per-visit arrays take (HPair): the region after the packed bands.
+inline bool zncc_row_bulk_fits(int R, int dtype, const RowArgs& a, int nthreads) {
+    const int ds = kG * a.tq, span = a.nch * kL;
+    const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
+    const int drange = std::min(a.spb, nslices) * ds;
+    size_t after = 8ull * 4 * (plane_of(span) + plane_of(span + drange - 1)) + 16ull * a.nch * kCS +
+                   dt_scan_bytes(nthreads / 32, a.tq);
+    if (dtype == 2) after += 8ull * a.nch * kCS;
+    return 2ull * (2 * R + 1) * bulk_row_stride(a.W) <= after;
 }
 
 template <int R, int MINB, bool SINGLE>

@@ -31,7 +31,7 @@ ZNCC_OK, ZNCC_EINVAL, ZNCC_ENOMEM, ZNCC_ECUDA, ZNCC_EBUSY, ZNCC_ENOTREADY, ZNCC_
     ZNCC_EUNSUPPORTED = range(8)
 ZNCC_F32, ZNCC_F16, ZNCC_I8 = 0, 1, 2
 ZNCC_TUNE_ROW_MINB2, ZNCC_TUNE_ROW_SPB, ZNCC_TUNE_H_TQ, ZNCC_TUNE_V_TQ, ZNCC_TUNE_AHAT_SMS = 1, 2, 3, 4, 5
-ZNCC_TUNE_PLANE, ZNCC_TUNE_PLANE_CS = 6, 7
+ZNCC_TUNE_PLANE, ZNCC_TUNE_PLANE_CS, ZNCC_TUNE_ROW_LOADS = 6, 7, 8
 STATUS_NAMES = ["ZNCC_OK", "ZNCC_EINVAL", "ZNCC_ENOMEM", "ZNCC_ECUDA", "ZNCC_EBUSY",
                 "ZNCC_ENOTREADY", "ZNCC_ETIMEOUT", "ZNCC_EUNSUPPORTED"]
 
@@ -64,6 +64,7 @@ SIGNATURES = [
     ("zncc_status_string", ctypes.c_char_p, [_i]),
     ("zncc_kernel_launch_count", ctypes.c_uint64, []),
     ("zncc_set_tuning", _i, [_vp, _i, _i]),
+    ("zncc_device_faults", _i, [_vp, ctypes.POINTER(ctypes.c_uint32)]),
     ("zncc_profile_enable", _i, [_vp, _i]),
     ("zncc_profile_read", _i, [_vp, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_uint64), _i]),
@@ -293,6 +294,12 @@ class ZnccContext:
 
     def set_tuning(self, key: int, value: int):
         self._check(lib().zncc_set_tuning(self._h, int(key), int(value)))
+
+    def device_faults(self) -> int:
+        """Faults the context's kernels recorded on the device since the last call (0: none)."""
+        v = ctypes.c_uint32(0)
+        self._check(lib().zncc_device_faults(self._h, ctypes.byref(v)))
+        return int(v.value)
 
     def profile_enable(self, on: bool = True):
         self._check(lib().zncc_profile_enable(self._h, 1 if on else 0))

@@ -386,3 +386,34 @@ def test_full_size_paper_workload_matches_oracle():
     # and accuracy against the synthetic ground truth (context for the method, not parity)
     v = p.valid
     assert (host_u16(disp)[v] == p.gt[v]).mean() > 0.5
+
+
+# (h, w, D, window): widths that are multiples of 16 take the bulk-copy staging of the image rows
+# (both S offsets of the 4-column groups occur across the windows); 3072-pixel rows; a width
+# that is not a multiple of 16 takes the plain loads either way
+BULK_CASES = [(96, 320, 32, 9), (40, 1280, 128, 9), (33, 208, 40, 15), (21, 48, 16, 3),
+              (17, 2048, 24, 13), (9, 3072, 8, 11), (12, 64, 13, 5), (10, 100, 20, 7)]
+
+
+@pytest.mark.parametrize("h,w,d,win", BULK_CASES)
+@pytest.mark.parametrize("storage", [Z.ZNCC_F32, Z.ZNCC_F16, Z.ZNCC_I8])
+def test_bulk_row_staging_equals_plain_loads(h, w, d, win, storage):
+    """The cost kernel stages the image rows by bulk asynchronous copies (TMA unit) where the
+    rows are 16-byte aligned, else with plain loads; both give the same maps bit for bit, the
+    F32 map matches the oracle away from near-ties, and no kernel records a fault."""
+    p = rand_pair(h, w, d, seed=h + 3 * w + d + win, disp="planes")
+    maps = []
+    for loads in (0, 1):
+        ctx = Z.ZnccContext(w, h, d, win)
+        ctx.set_tuning(Z.ZNCC_TUNE_ROW_LOADS, loads)
+        disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, 3, storage)
+        torch.cuda.synchronize()
+        assert ctx.device_faults() == 0
+        maps.append(host_u16(disp).copy())
+        ctx.close()
+    assert np.array_equal(maps[0], maps[1]), int((maps[0] != maps[1]).sum())
+    if storage == Z.ZNCC_F32:
+        ref, gap = oracle.run(p.left, p.right, d, win // 2, SIG_S, SIG_R, 3)
+        A = oracle.ones_response(p.left, SIG_S, SIG_R, 3)
+        check_disp(maps[0], ref, gap, A, "bulk staging")
