@@ -445,6 +445,26 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
     }
 }
 
+// One round of the transposed lane reduction of WtaRegs::merge: of the P (value, d) entries a
+// lane holds, it keeps the lower half (upper == false) or the upper half and sends the other
+// half to its partner lane (lane ^ off), merging what it receives: larger value, then smaller d.
+template <int P>
+__device__ __forceinline__ void wta_halve(float (&bv)[kL], int (&bd)[kL], bool upper, int off) {
+#pragma unroll
+    for (int k = 0; k < P / 2; ++k) {
+        const float ov = __shfl_xor_sync(kFull, upper ? bv[k] : bv[k + P / 2], off);
+        const int od = __shfl_xor_sync(kFull, upper ? bd[k] : bd[k + P / 2], off);
+        float mv = upper ? bv[k + P / 2] : bv[k];
+        int md = upper ? bd[k + P / 2] : bd[k];
+        if (ov > mv || (ov == mv && od < md)) {
+            mv = ov;
+            md = od;
+        }
+        bv[k] = mv;
+        bd[k] = md;
+    }
+}
+
 // ---- per-thread WTA running best over the slices a block visits, in registers -----------
 // rv[i]: best value of position i over this thread's disparities so far; rd: the matching
 // disparities as 16-bit fields, two per word. Ties keep the smaller d (slices arrive in
@@ -493,6 +513,28 @@ struct WtaRegs {
             const unsigned ins = (i & 1) ? __byte_perm(rd[i >> 1], d, 0x5410) : __byte_perm(rd[i >> 1], d, 0x3254);
             rd[i >> 1] = better ? ins : rd[i >> 1];
         }
+    }
+    // Reduces the running bests of the tq lanes of a chunk (consecutive lanes, tq a power of two
+    // up to 16) by halving rounds: after them lane dq holds the bests of kL / tq positions of the
+    // chunk, which it passes to emit(position in the chunk, value, d); every lane emits a share.
+    template <typename Emit>
+    __device__ __forceinline__ void merge(int tq, int lane, Emit emit) const {
+        float bv[kL];
+        int bd[kL];
+#pragma unroll
+        for (int i = 0; i < kL; ++i) {
+            const float2 e = entry(i);
+            bv[i] = e.x;
+            bd[i] = __float_as_int(e.y);
+        }
+        int base = 0, held = kL;
+        if (tq > 1) { const bool u = (lane & 1) != 0; wta_halve<16>(bv, bd, u, 1); base += u ? 8 : 0; held = 8; }
+        if (tq > 2) { const bool u = (lane & 2) != 0; wta_halve<8>(bv, bd, u, 2); base += u ? 4 : 0; held = 4; }
+        if (tq > 4) { const bool u = (lane & 4) != 0; wta_halve<4>(bv, bd, u, 4); base += u ? 2 : 0; held = 2; }
+        if (tq > 8) { const bool u = (lane & 8) != 0; wta_halve<2>(bv, bd, u, 8); base += u ? 1 : 0; held = 1; }
+#pragma unroll
+        for (int k = 0; k < kL; ++k)
+            if (k < held) emit(base + k, bv[k], bd[k]);
     }
     __device__ __forceinline__ float2 entry(int i) const {
         const unsigned d = (i & 1) ? (rd[i >> 1] >> 16) : (rd[i >> 1] & 0xFFFFu);

@@ -596,17 +596,13 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
             if (active) wr.fold(v, nvalid, a.d_base + dl);
             // at the group's last slice, or the block's last step, merge this block's best
             if ((o.sl == o.nslices - 1 || o.s + 1 == s1) && active) {
-#pragma unroll
-                for (int i = 0; i < kL; ++i) {
-                    float best;
-                    int bd;
-                    wta_reduce_lanes(wr.entry(i), tq, best, bd);
+                wr.merge(tq, lane, [&](int i, float best, int bd) {
                     const int pos = kg * kL + i;
-                    if (dq == 0 && line_ok && pos < a.n) {
+                    if (line_ok && pos < a.n) {
                         const size_t pix = (size_t)line * a.pix_line + (size_t)pos * a.pix_pos;
                         atomicMax(a.keys + pix, wta_key(best, bd));
                     }
-                }
+                });
             }
         } else if constexpr (kFast) {
             // near-zero-mean codes against d_arb = 0, held by lane dq 0 in the group's first
