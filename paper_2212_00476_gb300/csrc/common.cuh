@@ -553,18 +553,6 @@ __device__ __forceinline__ uint16_t wta_key_disparity(unsigned long long key) {
     return (uint16_t)(~(unsigned)key);
 }
 
-// Reduces the tq lanes of a pixel (consecutive lanes of a warp); all lanes get the result:
-// the largest value, and the smallest d among equal values.
-__device__ __forceinline__ void wta_reduce_lanes(float2 e, int tq, float& best, int& bd) {
-    best = e.x;
-    bd = __float_as_int(e.y);
-    for (int off = 1; off < tq; off <<= 1) {
-        const float ob = __shfl_xor_sync(kFull, best, off);
-        const int od = __shfl_xor_sync(kFull, bd, off);
-        if (ob > best || (ob == best && od < bd)) { best = ob; bd = od; }
-    }
-}
-
 // Shared-memory bytes of one line's scan buffers.
 __host__ __device__ inline size_t dt_scan_bytes(int nwl, int tq) {
     return (size_t)2 * nwl * tq * (sizeof(float4) + sizeof(float));

@@ -372,13 +372,10 @@ __device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_beg
 
     if constexpr (MODE == kModeWta) {
         if (active) {
-#pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                float best;
-                int bd;
-                wta_reduce_lanes(wr.entry(i), tq, best, bd);
+            // the chunk's lanes merge their running bests; each lane writes its share of positions
+            wr.merge(tq, lane, [&](int i, float best, int bd) {
                 const int x = x0 + i;
-                if (dq == 0 && x < W) {
+                if (x < W) {
                     const size_t o = (size_t)y * W + x;
                     if (!a.wta.first) {                                // earlier launches: smaller d
                         const float pb = a.wta.bestv[o];
@@ -390,7 +387,7 @@ __device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_beg
                         a.wta.bestd[o] = bd;
                     }
                 }
-            }
+            });
         }
     }
     return true;
