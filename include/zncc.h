@@ -311,7 +311,9 @@ const char* zncc_status_string(zncc_status status);
 
 /* Launch-shape knobs of a context (0 = automatic for every key), for autotuning:
  *   ZNCC_TUNE_ROW_MINB2  cost kernel: 1 = register-limited variant with two blocks per SM
- *                        where the block has at most 320 threads (default), 0 = one block
+ *                        where the block has at most 320 threads, 0 = one block per SM
+ *                        without spills, beside which the column coefficients and the A_hat
+ *                        chain run on a second stream (default)
  *   ZNCC_TUNE_ROW_SPB    cost kernel: disparity slices per block
  *   ZNCC_TUNE_H_TQ       horizontal DT pairs: lanes per 16-pixel chunk (2, 4 or 8)
  *   ZNCC_TUNE_V_TQ       vertical DT pairs: lanes per 16-pixel chunk (2, 4 or 8)

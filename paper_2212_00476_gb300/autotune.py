@@ -22,7 +22,7 @@ import threading
 from . import zncc as Z
 
 CANDIDATES = {
-    Z.ZNCC_TUNE_ROW_MINB2: [1, 0],
+    Z.ZNCC_TUNE_ROW_MINB2: [0, 1],
     Z.ZNCC_TUNE_ROW_SPB: [0, 1, 2, 4, 8],
     Z.ZNCC_TUNE_H_TQ: [0, 2, 4, 8],
     Z.ZNCC_TUNE_V_TQ: [0, 2, 4, 8],
@@ -97,7 +97,6 @@ def tune(ctx, left, right, disp, sigma_s, sigma_r, iters, storage=Z.ZNCC_F32, re
         ctx.zncc_run(left, right, disp, sigma_s, sigma_r, iters, storage)
 
     settings = {NAMES[k]: 0 for k in CANDIDATES}
-    settings["row_minb2"] = 1
     apply(ctx, settings)
     best_ms = _time(ctx, run, reps)
     for _ in range(rounds):

@@ -89,7 +89,7 @@ struct zncc_ctx {
     float2* mulmap = nullptr;     // [nmul] maps of the pairs from 2 (F16) or 1 (I8) on:
     int nahat = 0, nmul = 0;      //        (A_hat_{p-1}, s2 / A_hat_p), line-major
     int smem_max = 0;             // opt-in shared memory per block of the device
-    int row_minb2 = 1;            // cost kernel: two-blocks-per-SM variant where it applies
+    int row_minb2 = 0;            // cost kernel: two-blocks-per-SM variant where it applies
     int row_spb = 0;              // cost kernel: slices per block (0 = automatic)
     int row_nobulk = 0;           // cost kernel: stage the image rows with plain loads
     int ahat_sms = 0;             // SMs the cost kernel leaves to the A_hat chain (0 = automatic)
@@ -768,17 +768,20 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
         for (int i = 0; i < n; ++i)
             if (ensure_ahat(io[i].c, npairs - 1, npairs - pfirst + 1) != ZNCC_OK)
                 return fail(lc, ZNCC_ENOMEM, io[i].c->err);
-    ZNCC_TRY(run_coef(lc, io, n, sigma_s, sigma_r, false));     // the cost kernel writes the rows'
-    // The A_hat chain is small and latency-bound (one warp per line): it runs on a second
-    // stream on the SMs the cost kernel leaves free. FastDT needs A_hat_1 in the cost kernel
-    // itself, so that pass comes first.
-    const int side = norm ? (lc->ahat_sms > 0 ? lc->ahat_sms : kAhatSideSms) : 0;
+    // Side work beside the cost kernel, on a second stream joined before the first line pair:
+    // the column DT coefficients (the cost kernel writes the rows') and, with F16 or I8
+    // storage, the A_hat chain (small and latency-bound, one warp per line). The cost kernel's
+    // 128-register variant holds one block per SM and leaves registers and shared memory for
+    // the side kernels' blocks on every SM; its two-blocks-per-SM variant fills the registers,
+    // so with the A_hat chain `reserve` SMs are left to it. FastDT needs A_hat_1 in the cost
+    // kernel itself, so that pass comes first, on the main stream.
+    const int reserve = norm && lc->row_minb2 ? (lc->ahat_sms > 0 ? lc->ahat_sms : kAhatSideSms) : 0;
     int p_first_side = 1;
     if (dt == 2) {
         ZNCC_TRY(run_ahat(lc, io, n, 1, pfirst, npairs, K, inv_sr255, s2, true));
         p_first_side = 2;
     }
-    if (side > 0) {
+    {
         if (!lc->side) {
             ZNCC_CUDA(lc, cudaStreamCreateWithFlags(&lc->side, cudaStreamNonBlocking), "side stream");
             ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_fork, cudaEventDisableTiming), "fork event");
@@ -788,7 +791,7 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
         ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->side, lc->ev_fork, 0), "fork");
         lc->cur = lc->side;
     }
-    zncc_status st = ZNCC_OK;
+    zncc_status st = run_coef(lc, io, n, sigma_s, sigma_r, false);
     for (int p = p_first_side; norm && p <= npairs - 1 && st == ZNCC_OK; ++p)
         st = run_ahat(lc, io, n, p, pfirst, npairs, K, inv_sr255, s2, dt == 2);
     // the last pair's multipliers (A_hat_{npairs-1}, s2): its result is not stored
@@ -803,12 +806,12 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
     }
     lc->cur = lc->stream;
     ZNCC_TRY(st);
-    if (side > 0) ZNCC_CUDA(lc, cudaEventRecord(lc->ev_join, lc->side), "join");
+    ZNCC_CUDA(lc, cudaEventRecord(lc->ev_join, lc->side), "join");
     if (dt == 2)
         for (int i = 0; i < n; ++i) io[i].mulmap1 = io[i].c->mulmap;
-    ZNCC_TRY(run_rows(lc, io, n, kModeHPair, dt, s2, K, inv_sr255, K_ZNCC_HPAIR, side,
+    ZNCC_TRY(run_rows(lc, io, n, kModeHPair, dt, s2, K, inv_sr255, K_ZNCC_HPAIR, reserve,
                       "ZNCC + horizontal DT pair"));
-    if (side > 0) ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_join, 0), "join of the A_hat stream");
+    ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_join, 0), "join of the side stream");
 
     for (int pair = 2; pair <= npairs; ++pair) {    // pair 1 is the cost kernel's
         LinePass lp[kMaxBatch];
