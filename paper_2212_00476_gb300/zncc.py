@@ -106,6 +106,21 @@ def _ptr(t) -> int:
     return t.data_ptr()
 
 
+def _img(t) -> int:
+    """Device pointer of an image: a 2-D uint8 tensor whose rows are contiguous; its row stride
+    (stride(0), at least the width) is passed as the pitch."""
+    assert t.dim() == 2 and t.stride(1) == 1 and t.stride(0) >= t.shape[1], \
+        "images passed to libzncc must be 2-D with contiguous rows"
+    return t.data_ptr()
+
+
+def _pitch(*imgs) -> int:
+    """The common row pitch of images passed together."""
+    p = imgs[0].stride(0)
+    assert all(t.stride(0) == p for t in imgs), "images passed together must share their row pitch"
+    return p
+
+
 def launch_count() -> int:
     return int(lib().zncc_kernel_launch_count())
 
@@ -115,9 +130,9 @@ def zncc_run_batch(ctxs, lefts, rights, disps, sigma_s, sigma_r, iters, storage=
     context's stream carries the launches)."""
     n = len(ctxs)
     VP = ctypes.c_void_p * n
-    st = lib().zncc_run_batch(VP(*[c._h.value for c in ctxs]), VP(*[_ptr(t) for t in lefts]),
-                              VP(*[_ptr(t) for t in rights]),
-                              (ctypes.c_int * n)(*[t.stride(0) for t in lefts]),
+    st = lib().zncc_run_batch(VP(*[c._h.value for c in ctxs]), VP(*[_img(t) for t in lefts]),
+                              VP(*[_img(t) for t in rights]),
+                              (ctypes.c_int * n)(*[_pitch(l, r) for l, r in zip(lefts, rights)]),
                               VP(*[_ptr(t) for t in disps]), n, float(sigma_s), float(sigma_r),
                               int(iters), int(storage))
     if st != ZNCC_OK:
@@ -142,7 +157,7 @@ def dt_aggregate_noalloc(guide, cost, sigma_s, sigma_r, iters, dtype=ZNCC_F32, s
     H, W = int(guide.shape[0]), int(guide.shape[1])
     D = int(cost.shape[-1])
     s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
-    st = lib().dt_aggregate_noalloc(_ptr(guide), guide.stride(0), W, H, D, _ptr(cost), int(dtype),
+    st = lib().dt_aggregate_noalloc(_img(guide), guide.stride(0), W, H, D, _ptr(cost), int(dtype),
                                     float(sigma_s), float(sigma_r), int(iters), s)
     if st != ZNCC_OK:
         raise ZnccError(st, lib().zncc_last_error(None).decode())
@@ -316,26 +331,26 @@ class ZnccContext:
 
     # -- the C calls --------------------------------------------------------------------
     def zncc_window_stats(self, img, S=None, Q=None, inv_sigma=None):
-        self._check(lib().zncc_window_stats(self._h, _ptr(img), img.stride(0),
+        self._check(lib().zncc_window_stats(self._h, _img(img), img.stride(0),
                                             _ptr(S) if S is not None else None,
                                             _ptr(Q) if Q is not None else None,
                                             _ptr(inv_sigma) if inv_sigma is not None else None))
 
     def zncc_cost_volume(self, left, right, cost, dtype: int = ZNCC_F32):
-        self._check(lib().zncc_cost_volume(self._h, _ptr(left), _ptr(right), left.stride(0),
+        self._check(lib().zncc_cost_volume(self._h, _img(left), _img(right), _pitch(left, right),
                                            _ptr(cost), dtype))
 
     def zncc_cost_volume_scan(self, left, right, cost, dtype: int = ZNCC_F32):
-        self._check(lib().zncc_cost_volume_scan(self._h, _ptr(left), _ptr(right), left.stride(0),
+        self._check(lib().zncc_cost_volume_scan(self._h, _img(left), _img(right), _pitch(left, right),
                                                 _ptr(cost), dtype))
 
     def zncc_cost_volume_mma(self, left, right, cost, dtype: int = ZNCC_F32):
-        self._check(lib().zncc_cost_volume_mma(self._h, _ptr(left), _ptr(right), left.stride(0),
+        self._check(lib().zncc_cost_volume_mma(self._h, _img(left), _img(right), _pitch(left, right),
                                                _ptr(cost), dtype))
 
     def dt_aggregate(self, guide, cost, sigma_s: float, sigma_r: float, iters: int,
                      dtype: int = ZNCC_F32):
-        self._check(lib().dt_aggregate(self._h, _ptr(guide), guide.stride(0), _ptr(cost), dtype,
+        self._check(lib().dt_aggregate(self._h, _img(guide), guide.stride(0), _ptr(cost), dtype,
                                        float(sigma_s), float(sigma_r), int(iters)))
 
     def wta_disparity(self, cost, disp, dtype: int = ZNCC_F32):
@@ -343,7 +358,7 @@ class ZnccContext:
 
     def zncc_run(self, left, right, disp, sigma_s: float, sigma_r: float, iters: int,
                  storage: int = ZNCC_F32):
-        self._check(lib().zncc_run(self._h, _ptr(left), _ptr(right), left.stride(0),
+        self._check(lib().zncc_run(self._h, _img(left), _img(right), _pitch(left, right),
                                    float(sigma_s), float(sigma_r), int(iters), int(storage),
                                    _ptr(disp)))
 

@@ -99,3 +99,31 @@ def test_batch_replayed_from_a_cuda_graph_equals_separate_runs(storage):
     torch.cuda.synchronize()
     for i, (a, b) in enumerate(zip(single, D)):
         assert torch.equal(a, b), f"pair {i} {specs[i]} differs between the graph and single runs"
+
+
+def test_batch_mixing_bulk_and_plain_staging_equals_separate_runs():
+    """Two pairs of one shape share the cost kernel's launch; the first one's images are 16-byte
+    aligned (bulk-copy staging of its rows), the second's start one byte past alignment (plain
+    loads): each gives the map of its own zncc_run, and no fault is recorded."""
+    h, w, d, win = 48, 256, 40, 9
+    ctxs, L, R, D, single = [], [], [], [], []
+    for i, offset in enumerate((0, 1)):
+        p = make_pair(h, w, d, seed=970 + i, disp="planes")
+        ctxs.append(Z.ZnccContext(w, h, d, win))
+        imgs = []
+        for img in (p.left, p.right):
+            buf = torch.zeros(h * w + 64, dtype=torch.uint8, device="cuda")
+            v = buf[offset:offset + h * w].view(h, w)
+            v.copy_(dev(img))
+            imgs.append(v)
+        L.append(imgs[0])
+        R.append(imgs[1])
+        D.append(torch.empty((h, w), dtype=torch.int16, device="cuda"))
+        s = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        ctxs[-1].zncc_run(dev(p.left), dev(p.right), s, SIG_S, SIG_R, 3)
+        single.append(s)
+    Z.zncc_run_batch(ctxs, L, R, D, SIG_S, SIG_R, 3)
+    torch.cuda.synchronize()
+    assert ctxs[0].device_faults() == 0
+    for a, b in zip(single, D):
+        assert torch.equal(a, b)

@@ -417,3 +417,33 @@ def test_bulk_row_staging_equals_plain_loads(h, w, d, win, storage):
         ref, gap = oracle.run(p.left, p.right, d, win // 2, SIG_S, SIG_R, 3)
         A = oracle.ones_response(p.left, SIG_S, SIG_R, 3)
         check_disp(maps[0], ref, gap, A, "bulk staging")
+
+
+def _embedded(img, pad, offset):
+    """The image as a row-strided view into a larger device buffer: rows `pad` bytes wider than
+    the image, starting `offset` bytes past a 256-byte aligned base."""
+    h, w = img.shape
+    buf = torch.zeros(h * (w + pad) + offset + 64, dtype=torch.uint8, device="cuda")
+    view = buf[offset:offset + h * (w + pad)].view(h, w + pad)[:, :w]
+    view.copy_(torch.from_numpy(img).cuda())
+    return view
+
+
+@pytest.mark.parametrize("pad,offset", [(48, 0), (16, 32), (0, 1), (5, 0)])
+def test_pitched_and_unaligned_images(pad, offset):
+    """Images given as row-strided views: a pitch wider than the row that keeps 16-byte alignment
+    takes the bulk-copy staging, an odd offset or pitch the plain loads; the maps equal those of
+    contiguous images (and the oracle's away from near-ties), with no fault recorded."""
+    h, w, d, win = 40, 320, 48, 9
+    p = rand_pair(h, w, d, seed=900 + pad + offset, disp="planes")
+    ctx = Z.ZnccContext(w, h, d, win)
+    ref_map = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.zncc_run(dev(p.left), dev(p.right), ref_map, SIG_S, SIG_R, 3)
+    got = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.zncc_run(_embedded(p.left, pad, offset), _embedded(p.right, pad, offset), got, SIG_S, SIG_R, 3)
+    torch.cuda.synchronize()
+    assert ctx.device_faults() == 0
+    assert torch.equal(ref_map, got)
+    ref, gap = oracle.run(p.left, p.right, d, win // 2, SIG_S, SIG_R, 3)
+    check_disp(host_u16(got), ref, gap, oracle.ones_response(p.left, SIG_S, SIG_R, 3), "pitched")
+    ctx.close()
