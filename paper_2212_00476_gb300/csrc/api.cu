@@ -1256,10 +1256,17 @@ zncc_status zncc_run_host(zncc_ctx* c, const uint8_t* left_host, const uint8_t* 
             return fail(c, ZNCC_ENOMEM, std::string("image buffers: ") + cudaGetErrorString(e));
         }
     }
-    ZNCC_CUDA(c, cudaMemcpy2DAsync(c->img, c->W, left_host, pitch, c->W, c->H, cudaMemcpyHostToDevice, c->stream),
-              "left image upload");
-    ZNCC_CUDA(c, cudaMemcpy2DAsync(c->img + npix, c->W, right_host, pitch, c->W, c->H, cudaMemcpyHostToDevice,
-                                   c->stream), "right image upload");
+    // contiguous rows go up as one linear copy each, pitched ones row by row
+    if (pitch == c->W) {
+        ZNCC_CUDA(c, cudaMemcpyAsync(c->img, left_host, npix, cudaMemcpyHostToDevice, c->stream), "left image upload");
+        ZNCC_CUDA(c, cudaMemcpyAsync(c->img + npix, right_host, npix, cudaMemcpyHostToDevice, c->stream),
+                  "right image upload");
+    } else {
+        ZNCC_CUDA(c, cudaMemcpy2DAsync(c->img, c->W, left_host, pitch, c->W, c->H, cudaMemcpyHostToDevice,
+                                       c->stream), "left image upload");
+        ZNCC_CUDA(c, cudaMemcpy2DAsync(c->img + npix, c->W, right_host, pitch, c->W, c->H, cudaMemcpyHostToDevice,
+                                       c->stream), "right image upload");
+    }
     ZNCC_TRY(zncc_run(c, c->img, c->img + npix, c->W, sigma_s, sigma_r, iters, storage, c->disp));
     ZNCC_CUDA(c, cudaMemcpyAsync(disp_host, c->disp, npix * sizeof(uint16_t), cudaMemcpyDeviceToHost, c->stream),
               "disparity download");
