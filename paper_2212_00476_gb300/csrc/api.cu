@@ -749,10 +749,15 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
         if (ensure_volume(io[i].c, dt, io[i].dstride) != ZNCC_OK) return fail(lc, ZNCC_ENOMEM, io[i].c->err);
         io[i].vol = io[i].c->vol;
     }
-    const float s2 = scale_s2(sigma_s);
     const float K = (float)exp(-1.0 / (double)sigma_s);
     const float inv_sr255 = (float)(1.0 / (255.0 * (double)sigma_r));
     const int npairs = 2 * iters;
+    // The scaled form multiplies every pass pair's output by s2 = (1-K)^2 so that |cost| <= 1.
+    // With F32 storage only the disparity map leaves the fused path, and a positive constant
+    // factor changes no argmax, so the passes run the literal chain (s2 = 1, no multiply) while
+    // its values stay far inside the float range: |value| <= (1/(1-K))^(4 iters) <= 1e30.
+    const bool literal = dt == 0 && 4.0 * iters * -log(1.0 - (double)K) <= log(1e30);
+    const float s2 = literal ? 1.0f : scale_s2(sigma_s);
     // The DT weights of the line pairs (and the A_hat maps) depend only on the guide; they are
     // computed first, on the same stream: the persistent cost kernel fills every SM, so work
     // on a second stream would only run after it anyway. The cost kernel computes the

@@ -435,12 +435,21 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) G[j] = fmaf(Ae, G[j], Be[j]);
+        if (SCALE && (mul || s2 != 1.0f)) {
 #pragma unroll
-        for (int i = 0; i < kL; ++i) {
-            const float b = co[i].w;
-            const float m = SCALE ? (mul ? out_scale(mul[i]) : s2) : 1.0f;
+            for (int i = 0; i < kL; ++i) {
+                const float b = co[i].w;
+                const float m = mul ? out_scale(mul[i]) : s2;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[i][j] = SCALE ? m * fmaf(b, G[j], v[i][j]) : fmaf(b, G[j], v[i][j]);
+                for (int j = 0; j < 4; ++j) v[i][j] = m * fmaf(b, G[j], v[i][j]);
+            }
+        } else {                            // unscaled (s2 == 1: the caller runs the literal chain)
+#pragma unroll
+            for (int i = 0; i < kL; ++i) {
+                const float b = co[i].w;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[i][j] = fmaf(b, G[j], v[i][j]);
+            }
         }
     }
 }
