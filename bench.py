@@ -399,6 +399,9 @@ def run_gb300(args):
                      "launch_ms": round(dom_ms, 5)},
         "roofline_step": step_roofline(W * H * D, iters, elt_bytes, ms, peak, peak_src, clocks),
         "kernels_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in prof.items()},
+        "kernels_on_second_stream": {"kinds": [k for k in ("dt_coef", "ahat_pair") if k in prof],
+                                     "note": "timed on the second stream beside the cost kernel, "
+                                             "so their spans overlap it and are not additive"},
         "e2e": {"value": round(replica_throughput(units, world, e2e_s), 3), "unit": "Gdisp/s",
                 "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 2 * W * H,
                 "ms_per_step": round(e2e_s * 1e3, 4)},
