@@ -33,8 +33,6 @@ namespace zncc {
 // block and serve all of its disparity slices; the window statistics of both images
 // (Sec. IV-B-1, Eq. (sum1)) come from the same packed columns: a column's pixel sum is
 // __dp4a(word, 0x01010101) and its sum of squares __dp4a(word, word), slid like P.
-// One visit of the cost kernel: row y of one pair, disparity slices [s_begin, s_end).
-// Threads beyond the pair's nch * tq (whole warps) only take part in the barriers.
 // Four packed columns xs .. xs+3 (all inside the row) of a band of l raw rows in shared memory
 // (row j at raw + j * Wr, Wr a multiple of 16), xs = S (mod 4): per row one 32-bit word of the
 // four pixels (two aligned words funnel-shifted when S > 0), then a 4 x 4 byte transpose per
@@ -71,8 +69,9 @@ __device__ __forceinline__ void pack4_raw(const uint8_t* raw, int Wr, int xs, ui
 // Bytes of the rows a visit stages by bulk copies: l rows of each image, Wr = W + 16 apart.
 __host__ __device__ inline int bulk_row_stride(int W) { return W + 16; }
 
-// Returns false when a bulk copy of the image rows timed out (the fault is recorded; the
-// block stops).
+// One visit of the cost kernel: row y of one pair, disparity slices [s_begin, s_end).
+// Threads beyond the pair's nch * tq (whole warps) only take part in the barriers. Returns
+// false when a bulk copy of the image rows timed out (the fault is recorded; the block stops).
 template <int R, typename T, int MODE>
 __device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_begin, int s_end,
                                               uint4* smem_u4, unsigned long long* bar, unsigned& phase,
