@@ -72,6 +72,13 @@ struct LinePlan {
 
 }  // namespace
 
+// An occupancy answer (blocks or clusters per SM) for a kernel variant, block size and shared
+// memory, kept by the context so that repeated runs make no occupancy query.
+struct OccEntry {
+    long long key[3];
+    int value;
+};
+
 struct zncc_ctx {
     int W = 0, H = 0, D = 0, win = 0, r = 0;
     int device = 0;
@@ -100,6 +107,7 @@ struct zncc_ctx {
     int plane_cls = 0, plane_smem = 0, plane_clusters = 0;   // its size class, shared memory, clusters
     int num_sms = 0;
     std::vector<LinePlan> plans;  // line-pass launch shapes, by pass signature
+    std::vector<OccEntry> occ;    // occupancy answers
     int2* scan_stats = nullptr;   // (progressive scan) packed statistics: left [H][W], right [H][W+D-1]
     uint8_t* img = nullptr;       // device copies for zncc_run_host: 2 x [H][W]
     uint16_t* disp = nullptr;     // [H][W]
@@ -166,6 +174,19 @@ int padded_chunks(int n, int tq) {
     const int per_warp = 32 / tq;
     const int nch = (n + kL - 1) / kL;
     return (nch + per_warp - 1) / per_warp * per_warp;
+}
+
+// The context's cached occupancy answer for key, or query() (which fills *value) on a miss.
+template <typename Query>
+cudaError_t cached_occupancy(zncc_ctx* c, long long k0, long long k1, long long k2, Query query, int* value) {
+    for (const OccEntry& o : c->occ)
+        if (o.key[0] == k0 && o.key[1] == k1 && o.key[2] == k2) {
+            *value = o.value;
+            return cudaSuccess;
+        }
+    const cudaError_t e = query(value);
+    if (e == cudaSuccess) c->occ.push_back(OccEntry{{k0, k1, k2}, *value});
+    return e;
 }
 
 template <typename T>
@@ -360,8 +381,10 @@ zncc_status run_rows(zncc_ctx* lc, const PairIO* io, int n, int mode, int dtype,
             minb2 = minb2 && a.minb2;
         }
         int bps = 0;
-        ZNCC_CUDA(lc, zncc_row_occupancy(r, mode, dtype, threads, smem, minb2, b.npairs == 1, &bps),
-                  "occupancy query");
+        const long long k0 = ((((long long)r * 4 + mode) * 4 + dtype) * 2 + (minb2 ? 1 : 0)) * 2 + (b.npairs == 1);
+        ZNCC_CUDA(lc, cached_occupancy(lc, 1, k0 * 4096 + threads, (long long)smem, [&](int* v) {
+                      return zncc_row_occupancy(r, mode, dtype, threads, smem, minb2, b.npairs == 1, v);
+                  }, &bps), "occupancy query");
         b.grid = std::max(1, std::min(b.total_items, std::max(1, lc->num_sms - reserve_sms) * std::max(1, bps)));
         ZNCC_LAUNCH(lc, kind, launch_zncc_row(r, b, threads, smem, mode, dtype, lc->cur), what);
     }
@@ -445,18 +468,20 @@ cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePa
 }
 
 // Grid of a line-pair launch: the resident blocks (or clusters of cs CTAs), at most one per item.
-cudaError_t size_line_grid(LineBatch& b, int threads, size_t smem, int mode, int dtype, int num_sms) {
+// With a context the occupancy answer comes from its cache.
+cudaError_t size_line_grid(LineBatch& b, int threads, size_t smem, int mode, int dtype, int num_sms,
+                           zncc_ctx* c = nullptr) {
     const int cs = b.p[0].cs;
-    cudaError_t e;
-    if (cs > 1) {
-        int ncl = 0;
-        e = line_pair_max_clusters(mode, dtype, threads, smem, b.npairs == 1, cs, &ncl);
-        b.grid = cs * std::max(1, std::min(b.total_items, ncl));
-    } else {
-        int bps = 0;
-        e = line_pair_occupancy(mode, dtype, threads, smem, b.npairs == 1, false, &bps);
-        b.grid = std::max(1, std::min(b.total_items, num_sms * std::max(1, bps)));
-    }
+    const bool single = b.npairs == 1;
+    auto query = [&](int* v) {
+        return cs > 1 ? line_pair_max_clusters(mode, dtype, threads, smem, single, cs, v)
+                      : line_pair_occupancy(mode, dtype, threads, smem, single, false, v);
+    };
+    int n = 0;
+    const long long k0 = (((long long)mode * 4 + dtype) * 2 + (single ? 1 : 0)) * 8 + cs;
+    const cudaError_t e = c ? cached_occupancy(c, 2, k0 * 4096 + threads, (long long)smem, query, &n) : query(&n);
+    if (cs > 1) b.grid = cs * std::max(1, std::min(b.total_items, n));
+    else b.grid = std::max(1, std::min(b.total_items, num_sms * std::max(1, n)));
     return e;
 }
 
@@ -559,7 +584,7 @@ zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passe
         b.stage_bytes = (long long)stage;
         const size_t smem = stage + rest;
         if (smem > (size_t)lc->smem_max) return fail(lc, ZNCC_EUNSUPPORTED, "DT pass exceeds shared memory");
-        ZNCC_CUDA(lc, size_line_grid(b, threads, smem, mode, dtype, lc->num_sms), "occupancy query");
+        ZNCC_CUDA(lc, size_line_grid(b, threads, smem, mode, dtype, lc->num_sms, lc), "occupancy query");
         ZNCC_LAUNCH(lc, kind, launch_line_batch(b, threads, smem, mode, dtype, lc->cur), "DT pass pair");
     }
     return ZNCC_OK;
@@ -938,6 +963,7 @@ zncc_status zncc_create(int width, int height, int max_disp, int win, zncc_ctx**
         return fail(nullptr, ZNCC_EINVAL, "win must be odd and in [3, 15]");
     zncc_ctx* c = new (std::nothrow) zncc_ctx();
     if (!c) return fail(nullptr, ZNCC_ENOMEM, "host allocation failed");
+    forget_smem_attributes();
     c->W = width;
     c->H = height;
     c->D = max_disp;
@@ -1321,6 +1347,7 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
         default: return fail(c, ZNCC_EINVAL, "unknown tuning key");
     }
     c->plans.clear();
+    c->occ.clear();
     c->plane_cs = -1;
     return ZNCC_OK;
 }

@@ -1,12 +1,45 @@
 // kernels.cu -- window statistics, DT coefficients, DT line pairs and WTA kernels.
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
 #include "zncc_row.cuh"
 
 namespace zncc {
+
+namespace {
+struct SmemAttr {
+    int dev;
+    const void* fn;
+    size_t smem;
+};
+std::mutex g_smem_attr_mu;
+std::vector<SmemAttr> g_smem_attr;
+}  // namespace
+
+cudaError_t set_max_smem(const void* fn, size_t smem) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_smem_attr_mu);
+    SmemAttr* rec = nullptr;
+    for (SmemAttr& a : g_smem_attr)
+        if (a.dev == dev && a.fn == fn) rec = &a;
+    if (rec && rec->smem >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (rec) rec->smem = smem;
+    else g_smem_attr.push_back(SmemAttr{dev, fn, smem});
+    return cudaSuccess;
+}
+
+void forget_smem_attributes() {
+    std::lock_guard<std::mutex> lk(g_smem_attr_mu);
+    g_smem_attr.clear();
+}
 
 void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, dim3 grid, dim3 block, size_t smem,
                    cudaStream_t st, int cluster) {
@@ -242,7 +275,7 @@ __global__ void __launch_bounds__(32 * kAhatWarps) k_ahat_pair(const __grid_cons
 
 cudaError_t launch_ahat_pair(const AhatBatch& b, cudaStream_t st) {
     const size_t smem = (size_t)kAhatWarps * kAhatArrays * b.nmax * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_ahat_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_smem((const void*)k_ahat_pair, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[2];
@@ -713,7 +746,7 @@ static void (*line_pair_fn(int mode, int dtype, bool single, bool cluster))(Line
 cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, bool single, bool cluster,
                                 int* blocks_per_sm) {
     void (*fn)(LineBatch) = line_pair_fn(mode, dtype, single, cluster);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_smem((const void*)fn, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
 }
@@ -721,7 +754,7 @@ cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, b
 cudaError_t line_pair_max_clusters(int mode, int dtype, int threads, size_t smem, bool single, int cs,
                                    int* clusters) {
     void (*fn)(LineBatch) = line_pair_fn(mode, dtype, single, true);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_smem((const void*)fn, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);
@@ -741,7 +774,7 @@ cudaError_t launch_line_batch(const LineBatch& b, int threads, size_t smem, int 
                               cudaStream_t st) {
     const int cs = b.p[0].cs;
     void (*fn)(LineBatch) = line_pair_fn(mode, dtype, b.npairs == 1, cs > 1);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_smem((const void*)fn, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[2];

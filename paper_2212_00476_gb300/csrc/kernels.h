@@ -104,6 +104,12 @@ void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, dim3 grid
                    cudaStream_t st, int cluster);
 
 size_t zncc_row_smem_bytes(int R, int mode, int dtype, const RowArgs& a, int nthreads);
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for a kernel on the current device, made only
+// when the size exceeds what an earlier call set (a launch pays for it once, not every time);
+// forget_smem_attributes() drops the record (zncc_create calls it, so that contexts created
+// after a device reset set the attributes again).
+cudaError_t set_max_smem(const void* fn, size_t smem);
+void forget_smem_attributes();
 bool zncc_row_bulk_fits_host(int R, int dtype, const RowArgs& a, int nthreads);
 // A pass whose coefficients (and multipliers) can be streamed (at least two slices per line
 // group); the shared memory of a block with one or two buffers of them.

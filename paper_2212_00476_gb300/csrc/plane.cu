@@ -326,7 +326,7 @@ PlaneKernel plane_kernel(int cls) {
 cudaError_t plane_max_clusters(int cls, int cs, size_t smem, int* clusters) {
     if (cls < 0 || cls >= kPlaneClasses) return cudaErrorInvalidValue;
     PlaneKernel fn = plane_kernel(cls);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_smem((const void*)fn, smem);
     if (e != cudaSuccess) return e;
     if (cs == 1) {
         int bps = 0, dev = 0, sms = 0;
@@ -353,7 +353,7 @@ cudaError_t plane_max_clusters(int cls, int cs, size_t smem, int* clusters) {
 cudaError_t launch_plane(const PlaneBatch& b, int cls, size_t smem, cudaStream_t st) {
     if (cls < 0 || cls >= kPlaneClasses) return cudaErrorInvalidValue;
     PlaneKernel fn = plane_kernel(cls);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_smem((const void*)fn, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[2];

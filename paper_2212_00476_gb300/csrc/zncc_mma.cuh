@@ -179,11 +179,11 @@ cudaError_t launch_zncc_mma_impl(const ScanArgs& a, int dtype, cudaStream_t st) 
     const size_t smem = MmaShape<R>::smem;
     const dim3 grid((a.W + kMmaTM - 1) / kMmaTM, (a.D + kMmaTD - 1) / kMmaTD, (a.H + kMmaRows - 1) / kMmaRows);
     if (dtype == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_zncc_mma<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = set_max_smem((const void*)k_zncc_mma<R, float>, smem);
         if (e != cudaSuccess) return e;
         k_zncc_mma<R, float><<<grid, kMmaThreads, smem, st>>>(a);
     } else {
-        cudaError_t e = cudaFuncSetAttribute(k_zncc_mma<R, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = set_max_smem((const void*)k_zncc_mma<R, __half>, smem);
         if (e != cudaSuccess) return e;
         k_zncc_mma<R, __half><<<grid, kMmaThreads, smem, st>>>(a);
     }

@@ -489,7 +489,7 @@ cudaError_t zncc_row_occupancy_impl(int mode, int dtype, int threads, size_t sme
                                     int* bps) {
     void (*fn)(RowBatch) = row_fn<R>(mode, dtype, minb2 && threads <= 320, single);
     if (!fn) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_smem((const void*)fn, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, threads, smem);
 }
@@ -501,7 +501,7 @@ cudaError_t launch_zncc_row_impl(const RowBatch& b, int threads, size_t smem, in
     for (int i = 0; i < b.npairs; ++i) minb2 = minb2 && b.p[i].minb2;
     void (*fn)(RowBatch) = row_fn<R>(mode, dtype, minb2 && threads <= 320, b.npairs == 1);
     if (!fn) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_smem((const void*)fn, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[2];
