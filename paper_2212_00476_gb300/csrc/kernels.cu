@@ -64,7 +64,8 @@ void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, dim3 grid
 // ---------------------------------------------------------------------------------------
 // Window statistics (Sec. IV-B-1, Eq. (sum1), Method 1 made separable): block per row y;
 // column sums of the 2r+1 clamped rows for every column the row's windows touch, then the
-// horizontal window sum of those. S, Q exact int32; inv_sigma = 1/sqrt(n Q - S^2) or 0.
+// horizontal window sum of those. S, Q exact int32; inv_sigma = rsqrtf(n Q - S^2) (within 2
+// ulp of 1/sqrt) or 0; the cost kernel computes its statistics the same way, bit for bit.
 // n Q - S^2 < 2^31 for every window side <= 15 (its maximum is n^2 * 127.5^2), so it is
 // computed modulo 2^32 in unsigned arithmetic even where n Q alone would not fit.
 // `packed` receives (S, inv_sigma bits) per centre for the cost kernel.
@@ -97,7 +98,7 @@ __global__ void k_window_stats(const uint8_t* __restrict__ img, int pitch, int W
         }
         const size_t o = (size_t)y * nx + t;
         const int var = (int)(n * (unsigned)q - (unsigned)s * (unsigned)s);
-        const float is = var > 0 ? 1.0f / sqrtf((float)var) : 0.0f;
+        const float is = var > 0 ? rsqrtf((float)var) : 0.0f;
         if (S) S[o] = s;
         if (Q) Q[o] = q;
         if (isig) isig[o] = is;

@@ -66,6 +66,11 @@ __device__ __forceinline__ void pack4_raw(const uint8_t* raw, int Wr, int xs, ui
     for (int c = 0; c < 4; ++c) col[c] = make_uint4(o[c][0], o[c][1], o[c][2], o[c][3]);
 }
 
+// Centres per item of the window statistics. An item's column walk reads up to kStatsItem - 1
+// columns past the last centre of the band, so the packed band planes hold kStatsItem spare
+// entries.
+constexpr int kStatsItem = 12;
+
 // Bytes of the rows a visit stages by bulk copies: l rows of each image, Wr = W + 16 apart.
 __host__ __device__ inline int bulk_row_stride(int W) { return W + 16; }
 
@@ -94,7 +99,7 @@ __device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_beg
     const int xr0 = -R - (blk_hi - 1);                 // right columns x'' in [xr0, xr0+NRP)
     const int NSR = span + (blk_hi - blk_lo) - 1;      // right centres c in [c0, c0+NSR)
     const int c0 = -(blk_hi - 1);
-    const int pLP = plane_of(NLP), pRP = plane_of(NRP), pX = plane_of(span), pSR = plane_of(NSR);
+    const int pLP = plane_of(NLP + kStatsItem), pRP = plane_of(NRP + kStatsItem), pX = plane_of(span), pSR = plane_of(NSR);
     uint4* LP = smem_u4;
     uint4* RP = LP + 4 * pLP;
     int2* SL = reinterpret_cast<int2*>(RP + 4 * pRP);               // (S, 1/sigma bits) per x
@@ -211,38 +216,44 @@ __device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_beg
     }
     __syncthreads();
 
-    // ---- window statistics: 16 consecutive centres per thread, left then right ----
+    // ---- window statistics: kSC consecutive centres per thread, left then right ----
+    // Items of 12 centres start 12 columns apart, so the 16-byte column loads of the eight
+    // lanes of a quarter warp fall in distinct bank groups (16 apart, they would share two).
+    constexpr int kSC = kStatsItem;
     const unsigned n = (unsigned)(l * l);
-    const int nrc = (NSR + kL - 1) / kL;
-    for (int t = tid; t < nch + nrc; t += blockDim.x) {
-        const bool is_left = t < nch;
-        const int cs = is_left ? t * kL : c0 + (t - nch) * kL;     // first centre
+    const int nlc = (span + kSC - 1) / kSC, nrc = (NSR + kSC - 1) / kSC;
+    for (int t = tid; t < nlc + nrc; t += blockDim.x) {
+        const bool is_left = t < nlc;
+        const int cs = is_left ? t * kSC : c0 + (t - nlc) * kSC;   // first centre
         const uint4* col = is_left ? LP : RP;
         const int pc = is_left ? pLP : pRP;
         const int ib = is_left ? cs : cs - R - xr0;                 // column index of cs - R
-        // (ib = 16 t, or 16 (t - nch) on the right: both multiples of 4)
-        int Sx[kL], Qx[kL];
+        // (ib = 12 t, or 12 (t - nlc) on the right: both multiples of 4)
+        int Sx[kSC], Qx[kSC];
 #pragma unroll
-        for (int i = 0; i < kL; ++i) Sx[i] = Qx[i] = 0;
+        for (int i = 0; i < kSC; ++i) Sx[i] = Qx[i] = 0;
         unsigned ps = 0u, pq = 0u;
 #pragma unroll
-        for (int u = 0; u < kL + 2 * R; ++u) {
-            const uint4 w = at4(col, ib, u, pc);            // ib is a multiple of 4 (see below)
+        for (int u = 0; u < kSC + 2 * R; ++u) {
+            const uint4 w = at4(col, ib, u, pc);
             ps = __dp4a(w.x, 0x01010101u, ps);
             pq = __dp4a(w.x, w.x, pq);
             if (NW > 1) { ps = __dp4a(w.y, 0x01010101u, ps); pq = __dp4a(w.y, w.y, pq); }
             if (NW > 2) { ps = __dp4a(w.z, 0x01010101u, ps); pq = __dp4a(w.z, w.z, pq); }
             if (NW > 3) { ps = __dp4a(w.w, 0x01010101u, ps); pq = __dp4a(w.w, w.w, pq); }
-            if (u - 2 * R >= 0 && u - 2 * R < kL) { Sx[u - 2 * R] += (int)ps; Qx[u - 2 * R] += (int)pq; }
-            if (u + 1 < kL) { Sx[u + 1] -= (int)ps; Qx[u + 1] -= (int)pq; }
+            if (u - 2 * R >= 0 && u - 2 * R < kSC) { Sx[u - 2 * R] += (int)ps; Qx[u - 2 * R] += (int)pq; }
+            if (u + 1 < kSC) { Sx[u + 1] -= (int)ps; Qx[u + 1] -= (int)pq; }
         }
 #pragma unroll
-        for (int i = 0; i < kL; ++i) {
+        for (int i = 0; i < kSC; ++i) {
             const int var = (int)(n * (unsigned)Qx[i] - (unsigned)Sx[i] * (unsigned)Sx[i]);
-            const float is = var > 0 ? 1.0f / sqrtf((float)var) : 0.0f;
+            const float is = var > 0 ? rsqrtf((float)var) : 0.0f;      // as k_window_stats
             const int2 st = make_int2(Sx[i], __float_as_int(is));
-            if (is_left) at4(SL, cs, i, pX) = st;
-            else if (cs + i - c0 < NSR) at4(SR, cs - c0, i, pSR) = st;
+            if (is_left) {
+                if (cs + i < span) at4(SL, cs, i, pX) = st;
+            } else if (cs + i - c0 < NSR) {
+                at4(SR, cs - c0, i, pSR) = st;
+            }
         }
     }
     __syncthreads();
@@ -441,7 +452,7 @@ inline size_t zncc_row_smem(int R, int mode, int dtype, const RowArgs& a, int nt
     const int ds = kG * a.tq, span = a.nch * kL;
     const int nslices = (a.d_hi - a.d_lo + ds - 1) / ds;
     const int drange = std::min(a.spb, nslices) * ds;
-    size_t b = 16ull * 4 * (plane_of(span + 2 * R) + plane_of(span + 2 * R + drange - 1));
+    size_t b = 16ull * 4 * (plane_of(span + 2 * R + kStatsItem) + plane_of(span + 2 * R + drange - 1 + kStatsItem));
     const int pX = plane_of(span);
     b += 8ull * 4 * (pX + plane_of(span + drange - 1));
     if (mode == kModeHPair) b += 16ull * a.nch * kCS + dt_scan_bytes(nthreads / 32, a.tq);
