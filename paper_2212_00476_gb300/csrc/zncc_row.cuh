@@ -221,6 +221,10 @@ __device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_beg
     // lanes of a quarter warp fall in distinct bank groups (16 apart, they would share two).
     constexpr int kSC = kStatsItem;
     const unsigned n = (unsigned)(l * l);
+    // A fused horizontal pair (F32, F16) in the scaled form multiplies its result by
+    // s2 = (1-K)^2; the pair is linear, so the factor rides on the left 1/sigma instead
+    // (FastDT codes take per-position scales in the pair).
+    const float lscale = (MODE == kModeHPair && !kFast) ? a.s2 : 1.0f;
     const int nlc = (span + kSC - 1) / kSC, nrc = (NSR + kSC - 1) / kSC;
     for (int t = tid; t < nlc + nrc; t += blockDim.x) {
         const bool is_left = t < nlc;
@@ -248,7 +252,7 @@ __device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_beg
         for (int i = 0; i < kSC; ++i) {
             const int var = (int)(n * (unsigned)Qx[i] - (unsigned)Sx[i] * (unsigned)Sx[i]);
             const float is = var > 0 ? rsqrtf((float)var) : 0.0f;      // as k_window_stats
-            const int2 st = make_int2(Sx[i], __float_as_int(is));
+            const int2 st = make_int2(Sx[i], __float_as_int(is_left ? is * lscale : is));
             if (is_left) {
                 if (cs + i < span) at4(SL, cs, i, pX) = st;
             } else if (cs + i - c0 < NSR) {
@@ -269,10 +273,11 @@ __device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_beg
         const int nvalid = max(0, min(4, a.d_hi - d_first));
         float v[kL][4];
         if (active) {
-            // ---- window sums of products P for 16 pixels x 4 disparities ----
-            // P[i] = prefix(i + 2R) - prefix(i - 1): each entry is set at its first touch
-            // (-prefix(i - 1) at step i - 1; P[0] at step 2R) and completed at step i + 2R
-            int P[kL][4];
+            // ---- window sums of products, times n, for 16 pixels x 4 disparities ----
+            // n P[i] = n prefix(i + 2R) - n prefix(i - 1): each entry is set at its first touch
+            // (-n prefix(i - 1) at step i - 1; n P[0] at step 2R) and completed at step i + 2R;
+            // the factor n of Eq. (2)'s numerator rides on those multiply-adds (mod 2^32)
+            unsigned P[kL][4];
             // RP index of column x' - d_first - j at step t (x' = x0 - R + t) is rbase + t - j;
             // rbase + 1 = x0 - d_first + blk_hi is a multiple of 4 (as are x0, d_first and
             // blk_hi, d_lo being one), so every index below has a constant plane
@@ -293,9 +298,9 @@ __device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_beg
                     if (NW > 1) pre[j] = __dp4a(lp.y, rp[j].y, pre[j]);
                     if (NW > 2) pre[j] = __dp4a(lp.z, rp[j].z, pre[j]);
                     if (NW > 3) pre[j] = __dp4a(lp.w, rp[j].w, pre[j]);
-                    if (t == 2 * R) P[0][j] = (int)pre[j];
-                    else if (t - 2 * R > 0 && t - 2 * R < kL) P[t - 2 * R][j] += (int)pre[j];
-                    if (t + 1 < kL) P[t + 1][j] = -(int)pre[j];
+                    if (t == 2 * R) P[0][j] = n * pre[j];
+                    else if (t - 2 * R > 0 && t - 2 * R < kL) P[t - 2 * R][j] += n * pre[j];
+                    if (t + 1 < kL) P[t + 1][j] = (0u - n) * pre[j];
                 }
                 rp[3] = rp[2];
                 rp[2] = rp[1];
@@ -305,10 +310,6 @@ __device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_beg
             // ---- normalization, Eq. (2); the target statistics slide like the columns ----
             const int cb = x0 - d_first - c0;               // SR index of (i, j) is cb + i - j >= 3
             const int cb4 = cb + 1;                         // a multiple of 4, like rb4
-            // A fused horizontal pair (F32, F16) in the scaled form multiplies its result by
-            // s2 = (1-K)^2; the pair is linear, so the factor is folded into the left
-            // statistic here instead (FastDT codes take per-position scales in the pair).
-            const float lscale = (MODE == kModeHPair && !kFast) ? a.s2 : 1.0f;
             int2 sr[4];
             sr[1] = at4(SR, cb4, -2, pSR);
             sr[2] = at4(SR, cb4, -3, pSR);
@@ -319,10 +320,11 @@ __device__ __forceinline__ bool zncc_row_item(const RowArgs& a, int y, int s_beg
                     const int x = x0 + i;
                     const int2 st = at4(SL, x0, i, pX);
                     sr[0] = at4(SR, cb4, i - 1, pSR);
-                    const float isl = __int_as_float(st.y) * lscale;
+                    const float isl = __int_as_float(st.y);      // (times the pair's scale)
+                    const unsigned nsl = 0u - (unsigned)st.x;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const unsigned num = n * (unsigned)P[i][j] - (unsigned)st.x * (unsigned)sr[j].x;
+                        const unsigned num = nsl * (unsigned)sr[j].x + P[i][j];       // n P - S_R S_T
                         const float c = (float)(int)num * isl * __int_as_float(sr[j].y);
                         if constexpr (decltype(full)::value) v[i][j] = c;
                         else v[i][j] = (x < W && j < nvalid) ? c : 0.0f;
