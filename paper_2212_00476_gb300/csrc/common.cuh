@@ -331,7 +331,11 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
         A = co[kL - 1].y;
 #pragma unroll
         for (int j = 0; j < 4; ++j) B[j] = v[kL - 1][j];
-        for (int off = tq; off < 32; off <<= 1) {
+        // rounds at lane offsets tq, 2 tq, .. 16, unrolled with constant offsets
+#pragma unroll
+        for (int r5 = 0; r5 < 5; ++r5) {
+            const int off = 1 << r5;
+            if (off < tq) continue;
             const float A2 = __shfl_up_sync(kFull, A, off);
             float B2[4];
 #pragma unroll
@@ -366,6 +370,9 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
 
     // ---- phase 2: carry from the warps before, corrected forward values, backward sweep ----
     if (active) {
+        // the warps before: a short loop, not unrolled (a few iterations; unrolling it cost
+        // issue slots and registers)
+#pragma unroll 1
         for (int w2 = 0; w2 < wl; ++w2) {
             const float a2 = sa[w2 * tq + dq];
             const float4 b2 = sb[w2 * tq + dq];
@@ -390,7 +397,10 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
         A = co[0].w;
 #pragma unroll
         for (int j = 0; j < 4; ++j) B[j] = h[j];
-        for (int off = tq; off < 32; off <<= 1) {
+#pragma unroll
+        for (int r5 = 0; r5 < 5; ++r5) {
+            const int off = 1 << r5;
+            if (off < tq) continue;
             const float A2 = __shfl_down_sync(kFull, A, off);
             float B2[4];
 #pragma unroll
@@ -425,6 +435,7 @@ __device__ __forceinline__ void dt_pair(float (&v)[kL][4], const float4* __restr
 
     // ---- phase 3: carry from the warps after, backward correction, scale ----
     if (active) {
+#pragma unroll 1
         for (int w2 = nwl - 1; w2 > wl; --w2) {
             const float a2 = sa[(nwl + w2) * tq + dq];
             const float4 b2 = sb[(nwl + w2) * tq + dq];
