@@ -332,6 +332,11 @@ const char* zncc_status_string(zncc_status status);
  *                        rows with plain loads; 0 (automatic) = bulk asynchronous copies (the
  *                        TMA unit) where both images and the pitch are 16-byte aligned and W is
  *                        a multiple of 16, plain loads elsewhere
+ *   ZNCC_TUNE_V_LPC      vertical DT pairs that store the volume: at most this many adjacent
+ *                        columns per block (1, 2 or 4; 0 = automatic, which prefers two
+ *                        resident blocks per SM). Adjacent columns of a row share DRAM pages,
+ *                        so wider groups make longer runs per page at the cost of residency;
+ *                        the last vertical pair with WTA keeps the automatic shape
  * A value a launch cannot use (too many threads or too much shared memory) makes the next
  * call fail with ZNCC_EUNSUPPORTED. Unknown keys give ZNCC_EINVAL. */
 typedef enum {
@@ -342,7 +347,8 @@ typedef enum {
     ZNCC_TUNE_AHAT_SMS = 5,
     ZNCC_TUNE_PLANE = 6,
     ZNCC_TUNE_PLANE_CS = 7,
-    ZNCC_TUNE_ROW_LOADS = 8
+    ZNCC_TUNE_ROW_LOADS = 8,
+    ZNCC_TUNE_V_LPC = 9
 } zncc_tune_key;
 zncc_status zncc_set_tuning(zncc_ctx* ctx, int key, int value);
 

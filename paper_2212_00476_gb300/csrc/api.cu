@@ -101,6 +101,7 @@ struct zncc_ctx {
     int row_nobulk = 0;           // cost kernel: stage the image rows with plain loads
     int ahat_sms = 0;             // SMs the cost kernel leaves to the A_hat chain (0 = automatic)
     int h_tq = 0, v_tq = 0;       // DT pairs: forced lanes per chunk (0 = automatic)
+    int v_lpc = 0;                // vertical store pairs: most columns per block (0 = automatic)
     int plane_mode = 0;           // F32 fused runs: the plane-resident path where it applies
     int plane_force_cs = 0;       // its cluster size (0 = automatic)
     int plane_cs = -1;            // chosen cluster size (0: streaming path; -1: not chosen yet)
@@ -408,15 +409,16 @@ struct LinePass {
 };
 
 // The block shape of a pair's pass: among lane counts per chunk (8, 4, 2, or the forced
-// one) and lines per block that fit in shared memory, prefer whole 64-byte segments per
-// chunk, then streaming through shared memory (async), then at least two resident blocks
-// per SM, then the most resident warps, then a line inside one block. Which of a cluster with
+// one) and lines per block that fit in shared memory (at most 256 threads of lines, or
+// max_lpc lines when that is set), prefer whole 64-byte segments per chunk, then streaming
+// through shared memory (async), then at least two resident blocks per SM (unless max_lpc
+// is set), then the most resident warps, then a line inside one block. Which of a cluster with
 // 64-byte segments and one block with 32-byte segments is faster depends on the shape
 // (half-precision rows of 1280 pixels: one block, 181 against 235 us per pair; of 1920
 // pixels: the cluster, 839 against 954 us), so the autotuner settles it per shape.
 // `found` is false when no shape fits; on success the shape is also left in a.
-cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePass& p, LinePlan& best,
-                             bool& found) {
+cudaError_t choose_line_plan(int smem_max, int forced, int max_lpc, LineArgs& a, const LinePass& p,
+                             LinePlan& best, bool& found) {
     found = false;
     long long best_score = -1;
     const int tqs[4] = {8, 4, 2, 1};
@@ -435,7 +437,9 @@ cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePa
         const int seg = tq * 4 * (p.dtype == 0 ? 4 : (p.dtype == 1 ? 2 : 1));   // bytes per chunk position
         const bool whole_bursts = seg >= 64;
         for (int async = a.vec ? 1 : 0; async >= 0; --async) {
-            for (int lpc = cs > 1 ? 1 : std::max(1, std::min(8, 256 / per_line)); lpc >= 1; --lpc) {
+            const int lpc0 = cs > 1 ? 1 : max_lpc > 0 ? std::max(1, std::min(max_lpc, 512 / per_line))
+                                                      : std::max(1, std::min(8, 256 / per_line));
+            for (int lpc = lpc0; lpc >= 1; --lpc) {
                 a.tq = tq; a.nch = nch; a.lpc = lpc; a.async = async; a.cs = cs;
                 const size_t smem = line_pair_smem_bytes(p.mode, p.dtype, a, line_coef_async(a));
                 if (smem > (size_t)smem_max) continue;
@@ -451,7 +455,8 @@ cudaError_t choose_line_plan(int smem_max, int forced, LineArgs& a, const LinePa
                 }
                 const long long warps = (long long)bps * lpc * per_line / 32;
                 const long long score = (whole_bursts ? 10000000LL : 0) + async * 1000000LL +
-                                        (bps >= 2 ? 100000LL : 0) + warps * 100 + (cs == 1 ? 50 : 0) + tq;
+                                        (bps >= 2 && max_lpc == 0 ? 100000LL : 0) + warps * 100 +
+                                        (cs == 1 ? 50 : 0) + tq;
                 if (score > best_score) {
                     best_score = score;
                     best.tq = tq; best.lpc = lpc; best.nch = nch; best.async = async; best.blocks = bps;
@@ -489,8 +494,10 @@ cudaError_t size_line_grid(LineBatch& b, int threads, size_t smem, int mode, int
 // signature.
 zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
     const int forced = p.force_tq ? p.force_tq : (p.horiz ? c->h_tq : c->v_tq);
+    const int max_lpc = (!p.horiz && p.mode == kLineStore) ? c->v_lpc : 0;
     const long long key = ((((long long)p.horiz * 2 + p.mode) * 2 + p.dtype) * 2 + (a.vec ? 1 : 0)) * 16 +
-                          forced + ((long long)p.dcount << 20) + ((long long)(p.mulmap ? 1 : 0) << 40);
+                          forced + ((long long)p.dcount << 20) + ((long long)(p.mulmap ? 1 : 0) << 40) +
+                          ((long long)max_lpc << 44);
     for (const LinePlan& pl : c->plans)
         if (pl.key == key) {
             a.tq = pl.tq; a.lpc = pl.lpc; a.nch = pl.nch; a.async = pl.async; a.cs = pl.cs;
@@ -498,7 +505,7 @@ zncc_status plan_line_pass(zncc_ctx* c, LineArgs& a, const LinePass& p) {
         }
     LinePlan best{key, 0, 0, 0, 0, 0, 0, 1};
     bool found = false;
-    ZNCC_CUDA(c, choose_line_plan(c->smem_max, forced, a, p, best, found), "occupancy query");
+    ZNCC_CUDA(c, choose_line_plan(c->smem_max, forced, max_lpc, a, p, best, found), "occupancy query");
     if (!found) return fail(c, ZNCC_EUNSUPPORTED, "line too long for the DT kernel's shared memory");
     c->plans.push_back(best);
     return ZNCC_OK;
@@ -934,7 +941,7 @@ zncc_status noalloc_plan(NoallocDevice& d, LineArgs& a, const LinePass& p) {
         }
     LinePlan best{0, 0, 0, 0, 0, 0, 0, 1};
     bool found = false;
-    cudaError_t e = choose_line_plan(d.smem_max, 0, a, p, best, found);
+    cudaError_t e = choose_line_plan(d.smem_max, 0, 0, a, p, best, found);
     if (e != cudaSuccess) return noalloc_cuda_fail(e, "occupancy query");
     if (!found) {
         set_free_error("dt_aggregate_noalloc: a line of %d pixels does not fit the DT kernel's shared memory", a.n);
@@ -1333,6 +1340,11 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
         case ZNCC_TUNE_AHAT_SMS: c->ahat_sms = value; break;
         case ZNCC_TUNE_PLANE: c->plane_mode = value ? 1 : 0; break;
         case ZNCC_TUNE_ROW_LOADS: c->row_nobulk = value ? 1 : 0; break;
+        case ZNCC_TUNE_V_LPC:
+            if (value != 0 && value != 1 && value != 2 && value != 4)
+                return fail(c, ZNCC_EINVAL, "columns per block must be 0, 1, 2 or 4");
+            c->v_lpc = value;
+            break;
         case ZNCC_TUNE_PLANE_CS:
             if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
                 return fail(c, ZNCC_EINVAL, "plane cluster size must be 0, 1, 2, 4 or 8");

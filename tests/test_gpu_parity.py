@@ -419,6 +419,47 @@ def test_bulk_row_staging_equals_plain_loads(h, w, d, win, storage):
         check_disp(maps[0], ref, gap, A, "bulk staging")
 
 
+# (h, w, D): column groups of 1, 2 and 4 in the vertical store pairs, widths that are not a
+# multiple of the group, and the paper's column height
+V_LPC_CASES = [(384, 64, 128), (40, 37, 24), (130, 9, 40)]
+
+
+@pytest.mark.parametrize("h,w,d", V_LPC_CASES)
+@pytest.mark.parametrize("lpc", [1, 2, 4])
+def test_vertical_column_groups_match_oracle(h, w, d, lpc):
+    """ZNCC_TUNE_V_LPC puts up to 1, 2 or 4 adjacent columns in one block of the vertical pairs
+    that store the volume: dt_aggregate stays within the aggregation tolerance of the oracle,
+    and the fused map matches the oracle's away from near-ties."""
+    rng = np.random.default_rng(7 * h + w + d + lpc)
+    guide = make_pair(h, w, 4, seed=h + 2 * w).left
+    C = rng.uniform(-1, 1, (h, w, d)).astype(np.float32)
+    ctx = Z.ZnccContext(w, h, d, 9)
+    ctx.set_tuning(Z.ZNCC_TUNE_V_LPC, lpc)
+    t = dev(C)
+    ctx.dt_aggregate(dev(guide), t, SIG_S, SIG_R, 2)
+    torch.cuda.synchronize()
+    ref = oracle.dt_aggregate(C.astype(np.float64), oracle.dt_weights(guide, SIG_S, SIG_R), SIG_S, 2)
+    A = oracle.ones_response(guide, SIG_S, SIG_R, 2)
+    rel = (np.abs(t.cpu().numpy().astype(np.float64) - ref) / A[:, :, None]).max()
+    assert rel <= AGG_TOL, f"max |dC|/A_hat = {rel}"
+    p = rand_pair(h, w, d, seed=50 + h + w + lpc, disp="planes")
+    disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, 3, Z.ZNCC_F32)
+    torch.cuda.synchronize()
+    assert ctx.device_faults() == 0
+    mref, gap = oracle.run(p.left, p.right, d, 4, SIG_S, SIG_R, 3)
+    check_disp(host_u16(disp), mref, gap, oracle.ones_response(p.left, SIG_S, SIG_R, 3), "column groups")
+    ctx.close()
+
+
+def test_vertical_column_groups_reject_other_values():
+    ctx = Z.ZnccContext(32, 16, 8, 3)
+    for bad in (-1, 3, 5, 8):
+        with pytest.raises(Exception):
+            ctx.set_tuning(Z.ZNCC_TUNE_V_LPC, bad)
+    ctx.close()
+
+
 def _embedded(img, pad, offset):
     """The image as a row-strided view into a larger device buffer: rows `pad` bytes wider than
     the image, starting `offset` bytes past a 256-byte aligned base."""
