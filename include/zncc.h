@@ -214,7 +214,10 @@ zncc_status zncc_run_batch(zncc_ctx* const* ctxs, const uint8_t* const* lefts,
 /* zncc_run from host memory: copies the two images (row pitch `pitch`) to context-owned
  * device buffers, runs the fused path, copies the disparity map back to disp_host
  * (uint16 [H][W]) and synchronizes the stream before returning. Host buffers may be
- * pageable or pinned (pinned copies run asynchronously with respect to other streams). */
+ * pageable or pinned (pinned copies run asynchronously with respect to other streams). When
+ * disp_host is page-locked host memory that the device can address (cudaHostAlloc,
+ * cudaHostRegister, pinned torch tensors), the last kernel writes the map there directly
+ * and there is no download copy. */
 zncc_status zncc_run_host(zncc_ctx* ctx, const uint8_t* left_host, const uint8_t* right_host,
                           int pitch, float sigma_s, float sigma_r, int iters,
                           zncc_dtype storage, uint16_t* disp_host);

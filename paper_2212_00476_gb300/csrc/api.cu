@@ -1305,9 +1305,19 @@ zncc_status zncc_run_host(zncc_ctx* c, const uint8_t* left_host, const uint8_t* 
         ZNCC_CUDA(c, cudaMemcpy2DAsync(c->img + npix, c->W, right_host, pitch, c->W, c->H, cudaMemcpyHostToDevice,
                                        c->stream), "right image upload");
     }
-    ZNCC_TRY(zncc_run(c, c->img, c->img + npix, c->W, sigma_s, sigma_r, iters, storage, c->disp));
-    ZNCC_CUDA(c, cudaMemcpyAsync(disp_host, c->disp, npix * sizeof(uint16_t), cudaMemcpyDeviceToHost, c->stream),
-              "disparity download");
+    // a page-locked map the device can address takes the last kernel's stores directly
+    uint16_t* disp_dev = nullptr;
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, disp_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer && pa.device == c->device)
+        disp_dev = static_cast<uint16_t*>(pa.devicePointer);
+    else
+        cudaGetLastError();                         // (a pageable pointer is not an error)
+    ZNCC_TRY(zncc_run(c, c->img, c->img + npix, c->W, sigma_s, sigma_r, iters, storage,
+                      disp_dev ? disp_dev : c->disp));
+    if (!disp_dev)
+        ZNCC_CUDA(c, cudaMemcpyAsync(disp_host, c->disp, npix * sizeof(uint16_t), cudaMemcpyDeviceToHost,
+                                     c->stream), "disparity download");
     ZNCC_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
     return ZNCC_OK;
 }

@@ -331,6 +331,18 @@ def test_run_host_equals_device_run():
     host = np.zeros((h, w), np.uint16)
     ctx.zncc_run_host(p.left, p.right, host, SIG_S, SIG_R, 3)
     assert np.array_equal(host, host_u16(disp))
+    # a page-locked map buffer takes the last kernel's stores directly (no download copy);
+    # pinned image buffers still go up by copies
+    for storage in (Z.ZNCC_F32, Z.ZNCC_F16, Z.ZNCC_I8):
+        ref = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        ctx.zncc_run(dev(p.left), dev(p.right), ref, SIG_S, SIG_R, 3, storage)
+        pinned = torch.full((h, w), -1, dtype=torch.int16).pin_memory()
+        lp = torch.from_numpy(p.left).pin_memory().numpy()
+        rp = torch.from_numpy(p.right).pin_memory().numpy()
+        ctx.zncc_run_host(lp, rp, pinned.numpy().view(np.uint16), SIG_S, SIG_R, 3, storage)
+        assert torch.equal(pinned, ref.cpu()), storage
+    mref, gap = oracle.run(p.left, p.right, d, 4, SIG_S, SIG_R, 3)
+    check_disp(host, mref, gap, oracle.ones_response(p.left, SIG_S, SIG_R, 3), "host-buffer run")
 
 
 def test_fp16_storage_run_mismatch_rate_small():
