@@ -305,8 +305,11 @@ const char* zncc_last_error(const zncc_ctx* ctx);
  * cleared. A kernel that waits for asynchronous copies gives up after a bounded number of polls
  * instead of waiting without end, records the fault here and stops: bit 0 = a bulk copy of the
  * cost kernel's image rows did not complete in time (the results of that launch are not
- * valid), bit 1 = the copies had still not landed after a second bounded wait. Synchronizes
- * the context's stream. ZNCC_EINVAL for a NULL argument; ZNCC_ECUDA if the read fails. */
+ * valid), bit 1 = the copies had still not landed after a second bounded wait, bit 2 = a TMA
+ * copy of a DT pass's next slice did not complete in time (the pass then waits once more and
+ * goes on; the map of that run is not valid), bit 3 = a TMA destination in shared memory was
+ * not 128-byte aligned (the copy was skipped; the map is not valid). Synchronizes the
+ * context's stream. ZNCC_EINVAL for a NULL argument; ZNCC_ECUDA if the read fails. */
 zncc_status zncc_device_faults(zncc_ctx* ctx, uint32_t* faults);
 
 /* Static text for a status code. */
@@ -340,6 +343,12 @@ const char* zncc_status_string(zncc_status status);
  *                        resident blocks per SM). Adjacent columns of a row share DRAM pages,
  *                        so wider groups make longer runs per page at the cost of residency;
  *                        the last vertical pair with WTA keeps the automatic shape
+ *   ZNCC_TUNE_LINE_LOADS DT pairs: 1 = stream the next slices into shared memory with 16-byte
+ *                        cp.async per thread and position; 0 (automatic) = one TMA tensor copy
+ *                        per 16-position chunk and slice, completing on an mbarrier, where the
+ *                        staged reads stay within two chunks per shared-memory wavefront (F32
+ *                        with 4 or 8 lanes per chunk, F16 with 8), the volume and its pixel
+ *                        stride are 16-byte aligned and a line fits one CTA; cp.async elsewhere
  * A value a launch cannot use (too many threads or too much shared memory) makes the next
  * call fail with ZNCC_EUNSUPPORTED. Unknown keys give ZNCC_EINVAL. */
 typedef enum {
@@ -351,7 +360,8 @@ typedef enum {
     ZNCC_TUNE_PLANE = 6,
     ZNCC_TUNE_PLANE_CS = 7,
     ZNCC_TUNE_ROW_LOADS = 8,
-    ZNCC_TUNE_V_LPC = 9
+    ZNCC_TUNE_V_LPC = 9,
+    ZNCC_TUNE_LINE_LOADS = 10
 } zncc_tune_key;
 zncc_status zncc_set_tuning(zncc_ctx* ctx, int key, int value);
 

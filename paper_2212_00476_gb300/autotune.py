@@ -27,11 +27,12 @@ CANDIDATES = {
     Z.ZNCC_TUNE_H_TQ: [0, 2, 4, 8],
     Z.ZNCC_TUNE_V_TQ: [0, 2, 4, 8],
     Z.ZNCC_TUNE_V_LPC: [0, 2],
+    Z.ZNCC_TUNE_LINE_LOADS: [0, 1],
 }
 NAMES = {Z.ZNCC_TUNE_ROW_MINB2: "row_minb2", Z.ZNCC_TUNE_ROW_SPB: "row_spb",
          Z.ZNCC_TUNE_H_TQ: "h_tq", Z.ZNCC_TUNE_V_TQ: "v_tq", Z.ZNCC_TUNE_AHAT_SMS: "ahat_sms",
          Z.ZNCC_TUNE_PLANE: "plane", Z.ZNCC_TUNE_PLANE_CS: "plane_cs", Z.ZNCC_TUNE_ROW_LOADS: "row_loads",
-         Z.ZNCC_TUNE_V_LPC: "v_lpc"}
+         Z.ZNCC_TUNE_V_LPC: "v_lpc", Z.ZNCC_TUNE_LINE_LOADS: "line_loads"}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 _lock = threading.Lock()
 

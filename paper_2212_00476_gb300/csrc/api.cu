@@ -99,6 +99,7 @@ struct zncc_ctx {
     int row_minb2 = 0;            // cost kernel: two-blocks-per-SM variant where it applies
     int row_spb = 0;              // cost kernel: slices per block (0 = automatic)
     int row_nobulk = 0;           // cost kernel: stage the image rows with plain loads
+    int line_notma = 0;           // DT pairs: stream the slices with cp.async only
     int ahat_sms = 0;             // SMs the cost kernel leaves to the A_hat chain (0 = automatic)
     int h_tq = 0, v_tq = 0;       // DT pairs: forced lanes per chunk (0 = automatic)
     int v_lpc = 0;                // vertical store pairs: most columns per block (0 = automatic)
@@ -534,6 +535,72 @@ void fill_line_args(LineArgs& a, const LinePass& p, int W, int H, const float4* 
     a.pix_line = p.horiz ? W : 1;
     a.pix_pos = p.horiz ? 1 : W;
     a.cs = 1;
+    a.horiz = p.horiz ? 1 : 0;
+    a.tma = 0;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver
+// library), looked up once; NULL where the driver does not provide it.
+using TmapEncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+TmapEncodeFn tmap_encoder() {
+    static const TmapEncodeFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (TmapEncodeFn) nullptr;
+        }
+        return reinterpret_cast<TmapEncodeFn>(p);
+    }();
+    return fn;
+}
+
+// Whether a planned pass streams its slices by TMA, with its tensor map in m: the input volume
+// as {entries per pixel, W, H}, one box of kL + G - 1 positions per chunk and slice (G =
+// line_tma_chunks_per_wavefront). Taken for F32 and F16 where G <= 4, the volume and the pixel
+// stride are 16-byte aligned, a line stays in one CTA, and the larger slots keep the plan's
+// blocks per SM within shared memory.
+bool line_tma(zncc_ctx* c, const LineArgs& a, const LinePass& p, CUtensorMap& m) {
+    if (c->line_notma || !a.async || a.cs != 1 || p.ones || p.dtype == 2) return false;
+    const long long elem = p.dtype == 0 ? 4 : 2;
+    const int g = line_tma_chunks_per_wavefront(a.tq, (int)elem);
+    if (g > 4) return false;
+    LineArgs t = a;
+    t.tma = 1;
+    const size_t smem0 = line_pair_smem_bytes(p.mode, p.dtype, a, line_coef_async(a));
+    const size_t smem1 = line_pair_smem_bytes(p.mode, p.dtype, t, line_coef_async(t));
+    if (smem1 > (size_t)c->smem_max) return false;
+    if (smem1 > smem0) {
+        const int threads = a.lpc * a.nch * a.tq;
+        auto occ = [&](size_t smem, int* v) {
+            return cached_occupancy(c, 3, ((long long)p.mode * 4 + p.dtype) * 4096 + threads, (long long)smem,
+                                    [&](int* r) { return line_pair_occupancy(p.mode, p.dtype, threads, smem, true,
+                                                                             false, r); }, v);
+        };
+        int b0 = 0, b1 = 0;
+        if (occ(smem0, &b0) != cudaSuccess || occ(smem1, &b1) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (b1 < b0) return false;
+    }
+    const void* in = p.src ? p.src : p.vol;
+    if ((uintptr_t)in % 16 != 0 || (p.dstride * elem) % 16 != 0) return false;
+    const TmapEncodeFn enc = tmap_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)p.dstride, (cuuint64_t)c->W, (cuuint64_t)c->H};
+    const cuuint64_t strides[2] = {(cuuint64_t)(p.dstride * elem), (cuuint64_t)(p.dstride * elem * c->W)};
+    const cuuint32_t ds = (cuuint32_t)(kG * a.tq), np = (cuuint32_t)(kL + g - 1);
+    const cuuint32_t box[3] = {ds, p.horiz ? np : 1u, p.horiz ? 1u : np};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return enc(&m, p.dtype == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+               const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Appends a pair (its block shape chosen) to a launch: its items and steps, and the block's
@@ -564,12 +631,14 @@ void add_line_pair(LineBatch& b, const LineArgs& ai, int mode, int dtype, int& t
 zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passes, int n, int kind) {
     const int mode = passes[0].mode, dtype = passes[0].dtype;
     LineArgs args[kMaxBatch];
+    CUtensorMap tmaps[kMaxBatch];
     for (int i = 0; i < n; ++i) {
         zncc_ctx* c = ctxs[i];
         const LinePass& p = passes[i];
         LineArgs& a = args[i];
         fill_line_args(a, p, c->W, c->H, c->coefH, c->coefV);
         if (plan_line_pass(c, a, p) != ZNCC_OK) return fail(lc, ZNCC_EUNSUPPORTED, c->err);
+        a.tma = line_tma(c, a, p, tmaps[i]) ? 1 : 0;
     }
     bool done[kMaxBatch] = {false};
     for (int first = 0; first < n; ++first) {
@@ -583,12 +652,14 @@ zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passe
         for (int i = first; i < n; ++i) {
             const LineArgs& ai = args[i];
             if (done[i] || ai.tq != a0.tq || ai.nch != a0.nch || ai.lpc != a0.lpc || ai.async != a0.async ||
-                ai.cs != a0.cs || (i != first && (alone || fills_device(ctxs[i]))))
+                ai.cs != a0.cs || ai.tma != a0.tma || (i != first && (alone || fills_device(ctxs[i]))))
                 continue;
             done[i] = true;
             add_line_pair(b, ai, mode, dtype, threads, stage, rest);
+            if (ai.tma) b.tmap[b.npairs - 1] = tmaps[i];
         }
         b.stage_bytes = (long long)stage;
+        b.fault = lc->fault;
         const size_t smem = stage + rest;
         if (smem > (size_t)lc->smem_max) return fail(lc, ZNCC_EUNSUPPORTED, "DT pass exceeds shared memory");
         ZNCC_CUDA(lc, size_line_grid(b, threads, smem, mode, dtype, lc->num_sms, lc), "occupancy query");
@@ -1350,6 +1421,7 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
         case ZNCC_TUNE_AHAT_SMS: c->ahat_sms = value; break;
         case ZNCC_TUNE_PLANE: c->plane_mode = value ? 1 : 0; break;
         case ZNCC_TUNE_ROW_LOADS: c->row_nobulk = value ? 1 : 0; break;
+        case ZNCC_TUNE_LINE_LOADS: c->line_notma = value ? 1 : 0; break;
         case ZNCC_TUNE_V_LPC:
             if (value != 0 && value != 1 && value != 2 && value != 4)
                 return fail(c, ZNCC_EINVAL, "columns per block must be 0, 1, 2 or 4");

@@ -186,6 +186,19 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
                  "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar)) : "memory");
+}
+// A 3-D box of a tensor map (TMA) into shared memory (128-byte aligned), completing its bytes
+// on the mbarrier. Coordinates are element indices, innermost first; parts of the box outside
+// the tensor read as zero.
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
 // Orders this thread's earlier generic-proxy accesses of shared memory before later bulk copies
 // into it (the copies run in the async proxy).
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

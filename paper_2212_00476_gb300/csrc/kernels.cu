@@ -379,6 +379,7 @@ cudaError_t launch_dt_coef(const CoefBatch& b, cudaStream_t st) {
 static size_t elem_bytes(int dtype) { return dtype == 0 ? 4 : (dtype == 1 ? 2 : 1); }
 
 size_t line_stage_bytes(int dtype, const LineArgs& a) {
+    if (a.async && a.tma) return 2ull * a.lpc * a.nch * line_tma_slot_bytes(a.tq, (int)elem_bytes(dtype));
     return a.async ? 2ull * a.lpc * a.nch * a.tq * kL * (4 * elem_bytes(dtype)) : 0;
 }
 
@@ -390,7 +391,15 @@ size_t line_stage_bytes(int dtype, const LineArgs& a) {
 // offsets instead of through a dynamic index. CLUSTER: lines span the CTAs of a cluster.
 template <typename T, int MODE, bool SINGLE, bool CLUSTER>
 __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineBatch b) {
-    extern __shared__ float4 smem4[];
+    extern __shared__ __align__(128) float4 smem4[];
+    // (tma) per staging buffer and warp, an mbarrier that the first lanes of the warp's chunks
+    // arrive on once per fill (a line is whole warps, so a chunk never straddles two warps)
+    __shared__ unsigned long long tbar[2][16];
+    // TMA staging: the pairs' flag (the launcher groups pairs by it) and 128-byte aligned buffers
+    const bool tma = !CLUSTER && b.p[0].tma != 0 && b.p[0].async != 0 && (smem_addr(smem4) & 127u) == 0;
+    if (tma && threadIdx.x < 2 * (blockDim.x >> 5))
+        mbar_init(&tbar[threadIdx.x & 1][threadIdx.x >> 1], (unsigned)(32 / b.p[0].tq));
+    if (tma) __syncthreads();
     griddep_wait();
     auto P = [&](int pi) -> const LineArgs& { return b.p[SINGLE ? 0 : pi]; };
     const int lane = threadIdx.x & 31;
@@ -466,11 +475,20 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
         return (size_t)line_of(c) * a.line_stride + (size_t)(kg * kL) * a.elem_stride + c.sl * ds + dq * kG;
     };
     // staging buffers: [2][kL][threads] groups of 4 entries: position i of this thread's
-    // chunk at stage_at(buf) + i * sstride (consecutive threads, consecutive groups)
+    // chunk at stage_at(buf) + i * sstride (consecutive threads, consecutive groups). With TMA
+    // a buffer is [lines][chunks] slots of line_tma_slot_bytes, one box of kL + G - 1 positions
+    // x ds entries per (line, chunk), G = the chunks whose lanes share a shared-memory wavefront
+    // of the reads below: chunk k's box starts k mod G positions early, so that the G chunks
+    // read distinct banks; the thread's position i is at stage_at(buf) + (i + k mod G) * ds.
     const int nthr = lpc * per_line;
-    const int sstride = nthr * 4;
-    T* const stage0 = reinterpret_cast<T*>(smem4) + (size_t)threadIdx.x * 4;
-    auto stage_at = [&](int buf) -> T* { return stage0 + (size_t)buf * kL * sstride; };
+    const int sstride = tma ? ds : nthr * 4;
+    const int tma_g = line_tma_chunks_per_wavefront(tq, (int)sizeof(T));
+    const int tma_slot = line_tma_slot_bytes(tq, (int)sizeof(T)) / (int)sizeof(T);     // entries
+    T* const stage0 = reinterpret_cast<T*>(smem4) +
+                      (tma ? (size_t)(li * nch + k) * tma_slot + (k % tma_g) * ds + dq * kG
+                           : (size_t)threadIdx.x * 4);
+    const size_t buf_entries = tma ? (size_t)lpc * nch * tma_slot : (size_t)kL * nthr * 4;
+    auto stage_at = [&](int buf) -> T* { return stage0 + (size_t)buf * buf_entries; };
     // shared memory: [stage][coefficients: 1 or 2 buffers][multipliers: as many][scan
     // buffers], the per-position arrays [lpc][nch][kCS], chunk-major. Without A_hat scaling
     // (has_mul false) there are no multipliers; with co_async the arrays of a line group are
@@ -514,7 +532,7 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     // also brings the group's coefficients (co_async).
     auto prefetch = [&](const Cursor& pc, int buf) {
         if (co_async && pc.s < s1 && (pc.sl == 0 || pc.s == s0)) prefetch_coef(pc, pc.gseq & 1);
-        if (async && pc.s < s1 && active) {
+        if (!tma && async && pc.s < s1 && active) {
             const LineArgs& a = P(pc.pi);
             const T* src = a.src ? reinterpret_cast<const T*>(a.src) : reinterpret_cast<const T*>(a.vol);
             const bool ok = line_of(pc) < a.nlines && pc.sl * ds + dq * kG < a.dcount;
@@ -535,11 +553,34 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
         }
         cp_async_commit();
     };
+    // (tma) the step at cursor pc into buffer buf: the first lane of each chunk copies the
+    // chunk's box into the start of its slot (lines past the pass and positions or entries past
+    // the line read as zero). A slot start that is not 128-byte aligned (which the layout above
+    // rules out) is recorded as a fault and not copied to.
+    auto prefetch_tma = [&](const Cursor& pc, int buf) {
+        if (!tma || !active || dq != 0 || pc.s >= s1) return;
+        const LineArgs& a = P(pc.pi);
+        const CUtensorMap* m = &b.tmap[SINGLE ? 0 : pc.pi];
+        const int d0 = pc.sl * ds, p0 = kg * kL - k % tma_g, line = line_of(pc);
+        T* const slot = reinterpret_cast<T*>(smem4) + (size_t)buf * buf_entries + (size_t)(li * nch + k) * tma_slot;
+        unsigned long long* bar = &tbar[buf][threadIdx.x >> 5];
+        if (smem_addr(slot) & 127u) {
+            if (b.fault) atomicOr(b.fault, kFaultTmaAlign);
+            mbar_arrive(bar);
+            return;
+        }
+        fence_proxy_async_smem();                   // this warp's reads of the slot, then the copy
+        mbar_expect_tx(bar, (unsigned)((kL + tma_g - 1) * ds * sizeof(T)));
+        if (a.horiz) tma_load_3d(slot, m, d0, p0, line, bar);
+        else tma_load_3d(slot, m, d0, line, p0, bar);
+    };
     Cursor o = seek(s0);
     Cursor pf = o;                              // two steps ahead of o
     prefetch(pf, 0);
+    prefetch_tma(pf, 0);
     advance(pf);
     prefetch(pf, 1);
+    prefetch_tma(pf, 1);
     advance(pf);
 
     if (cs > 1) cluster_sync_all();                 // every CTA of the cluster has started
@@ -599,9 +640,23 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v[i][j] = (any && i < npos && j < nvalid) ? 1.0f : 0.0f;
         } else if (async) {
+            if (tma && active) {
+                // this warp's boxes of the step (bounded wait; a timeout is recorded, then waited
+                // for once more)
+                unsigned long long* bar = &tbar[n_s & 1][threadIdx.x >> 5];
+                const unsigned par = (unsigned)(n_s >> 1) & 1u;
+                if (!mbar_wait(bar, par, kBulkWaitPolls)) {
+                    if (b.fault) atomicOr(b.fault, kFaultTmaWait);
+                    mbar_wait(bar, par, kBulkWaitPolls);
+                }
+            }
             const T* st = stage_at(n_s & 1);
 #pragma unroll
             for (int i = 0; i < kL; ++i) lds4(st + i * sstride, v[i]);
+            if (tma) {
+                __syncwarp();                       // the chunk's lanes have read its slot
+                prefetch_tma(pf, n_s & 1);          // two steps ahead, into the same buffer
+            }
         } else {
             const T* src = a.src ? reinterpret_cast<const T*>(a.src) : vol;
             const T* q = src + (line_ok ? elem0(a, o) : 0);

@@ -1,6 +1,7 @@
 // kernels.h -- argument blocks and launchers of the device kernels (internal to libzncc).
 #pragma once
 
+#include <cuda.h>                 // CUtensorMap (the descriptor type only; no driver calls here)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,6 +53,8 @@ struct RowBatch {
 // Device-side faults a kernel records instead of waiting without end (ZNCC_FAULT_* of zncc.h).
 constexpr unsigned kFaultBulkWait = 1u;      // a bulk copy of image rows did not complete in time
 constexpr unsigned kFaultBulkDrain = 2u;     // ... nor after the second wait (the block then stopped)
+constexpr unsigned kFaultTmaWait = 4u;       // a TMA copy of a DT pass step did not complete in time
+constexpr unsigned kFaultTmaAlign = 8u;      // a TMA destination was not 128-byte aligned (not copied)
 // Polls of an mbarrier before a wait counts as timed out (each poll may suspend the thread for a
 // while; a copy from L2 or HBM completes within a few thousand).
 constexpr unsigned kBulkWaitPolls = 1u << 24;
@@ -76,6 +79,10 @@ struct LineArgs {
     float s2;
     int vec;                  // 16-byte (float) / 8-byte (half) accesses allowed
     int async;                // vec, and the next slices are streamed through shared memory
+    int horiz;                // lines are rows (positions x) rather than columns (positions y)
+    // the streamed slices arrive by TMA: one tensor copy per chunk and step from the pass's
+    // tensor map (LineBatch::tmap) instead of 16-byte cp.async per thread and position
+    int tma;
     // (Wta) per-pixel keys (ordered value << 32 | ~d), merged with atomicMax by every block that
     // saw part of a pixel's disparities; zero before the launch, turned into disparities (and
     // zeroed again) by k_wta_finish
@@ -94,7 +101,11 @@ struct LineBatch {
     int npairs, total_items, total_steps, grid;
     int co_async;             // coefficients streamed by cp.async (two buffers; line_coef_async)
     long long stage_bytes;    // staging region (the largest pair's), before the other arrays
+    unsigned* fault;          // device fault word (kFaultTmaWait), or NULL without TMA
     LineArgs p[kMaxBatch];
+    // (tma) per pair: the input volume as a 3-D tensor {entries per pixel, W, H}, box
+    // {4 tq, 16, 1} (rows) or {4 tq, 1, 16} (columns): one chunk's positions of one slice
+    CUtensorMap tmap[kMaxBatch];
 };
 
 // Launch configuration with programmatic stream serialization (the kernel may start while
@@ -123,6 +134,19 @@ cudaError_t launch_zncc_row(int R, const RowBatch& b, int threads, size_t smem, 
 cudaError_t zncc_row_occupancy(int R, int mode, int dtype, int threads, size_t smem, bool minb2,
                                bool single, int* blocks_per_sm);
 size_t line_stage_bytes(int dtype, const LineArgs& a);
+
+// TMA staging of the DT pairs: the chunks whose lanes share one shared-memory wavefront of
+// the staged reads (each lane reads 4 entries of elem bytes; a wavefront serves 128 bytes),
+// and the bytes of one chunk's slot: its box of kL + G - 1 positions x 4 tq entries, rounded up
+// to the 128-byte alignment of a tensor copy's destination.
+__host__ __device__ inline int line_tma_chunks_per_wavefront(int tq, int elem) {
+    const int g = 32 / (elem * tq);
+    return g > 1 ? g : 1;
+}
+__host__ __device__ inline int line_tma_slot_bytes(int tq, int elem) {
+    const int g = line_tma_chunks_per_wavefront(tq, elem);
+    return ((16 + g - 1) * 4 * tq * elem + 127) / 128 * 128;
+}
 // single: the variant for launches of one pair (npairs == 1), which the launchers pick
 cudaError_t line_pair_occupancy(int mode, int dtype, int threads, size_t smem, bool single, bool cluster,
                                 int* blocks_per_sm);

@@ -472,6 +472,42 @@ def test_vertical_column_groups_reject_other_values():
     ctx.close()
 
 
+# (h, w, D, storage): TMA staging of the DT pairs' slices where eligible (F32 rows and columns,
+# F16 columns), ragged lines and disparity counts, and a half-precision pixel stride of 20 entries
+# (40 bytes, not 16-byte aligned) that takes the cp.async path in both runs
+TMA_CASES = [(96, 320, 64, Z.ZNCC_F32), (40, 1280, 128, Z.ZNCC_F32), (33, 208, 40, Z.ZNCC_F32),
+             (1030, 24, 12, Z.ZNCC_F32), (50, 120, 24, Z.ZNCC_F16), (64, 96, 20, Z.ZNCC_F16)]
+
+
+@pytest.mark.parametrize("h,w,d,storage", TMA_CASES)
+def test_tma_staging_equals_cp_async(h, w, d, storage):
+    """ZNCC_TUNE_LINE_LOADS: the DT pairs stream their next slices by one TMA tensor copy per
+    chunk (0, automatic) or by cp.async per thread (1). The arithmetic is the same, so maps and
+    aggregated volumes agree bit for bit; the F32 map matches the oracle away from near-ties,
+    and no copy times out."""
+    p = rand_pair(h, w, d, seed=11 * h + w + d, disp="planes")
+    rng = np.random.default_rng(h + w + d)
+    C = rng.uniform(-1, 1, (h, w, d)).astype(np.float32)
+    maps, vols = [], []
+    for loads in (0, 1):
+        ctx = Z.ZnccContext(w, h, d, 9)
+        ctx.set_tuning(Z.ZNCC_TUNE_LINE_LOADS, loads)
+        disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, 3, storage)
+        t = dev(C)
+        ctx.dt_aggregate(dev(p.left), t, SIG_S, SIG_R, 2)
+        torch.cuda.synchronize()
+        assert ctx.device_faults() == 0
+        maps.append(host_u16(disp).copy())
+        vols.append(t.cpu().numpy())
+        ctx.close()
+    assert np.array_equal(maps[0], maps[1]), int((maps[0] != maps[1]).sum())
+    assert np.array_equal(vols[0], vols[1])
+    if storage == Z.ZNCC_F32:
+        ref, gap = oracle.run(p.left, p.right, d, 4, SIG_S, SIG_R, 3)
+        check_disp(maps[0], ref, gap, oracle.ones_response(p.left, SIG_S, SIG_R, 3), "TMA staging")
+
+
 def _embedded(img, pad, offset):
     """The image as a row-strided view into a larger device buffer: rows `pad` bytes wider than
     the image, starting `offset` bytes past a 256-byte aligned base."""
