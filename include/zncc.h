@@ -344,11 +344,14 @@ const char* zncc_status_string(zncc_status status);
  *                        so wider groups make longer runs per page at the cost of residency;
  *                        the last vertical pair with WTA keeps the automatic shape
  *   ZNCC_TUNE_LINE_LOADS DT pairs: 1 = stream the next slices into shared memory with 16-byte
- *                        cp.async per thread and position; 0 (automatic) = one TMA tensor copy
- *                        per 16-position chunk and slice, completing on an mbarrier, where the
- *                        staged reads stay within two chunks per shared-memory wavefront (F32
- *                        with 4 or 8 lanes per chunk, F16 with 8), the volume and its pixel
- *                        stride are 16-byte aligned and a line fits one CTA; cp.async elsewhere
+ *                        cp.async per thread and position; 0 (automatic) = in the horizontal
+ *                        pairs one TMA tensor copy per 16-position chunk and slice, completing
+ *                        on per-warp mbarriers, where the volume and its pixel stride are
+ *                        16-byte aligned, F32 or F16 reads span at most four chunks per
+ *                        shared-memory wavefront, a line fits one CTA and shared memory allows;
+ *                        cp.async elsewhere and in the vertical pairs; 2 = TMA in the vertical
+ *                        pairs too (a column box fetches one pixel row at a time: faster for
+ *                        some shapes, far slower for others)
  * A value a launch cannot use (too many threads or too much shared memory) makes the next
  * call fail with ZNCC_EUNSUPPORTED. Unknown keys give ZNCC_EINVAL. */
 typedef enum {

@@ -27,7 +27,7 @@ CANDIDATES = {
     Z.ZNCC_TUNE_H_TQ: [0, 2, 4, 8],
     Z.ZNCC_TUNE_V_TQ: [0, 2, 4, 8],
     Z.ZNCC_TUNE_V_LPC: [0, 2],
-    Z.ZNCC_TUNE_LINE_LOADS: [0, 1],
+    Z.ZNCC_TUNE_LINE_LOADS: [0, 1, 2],
 }
 NAMES = {Z.ZNCC_TUNE_ROW_MINB2: "row_minb2", Z.ZNCC_TUNE_ROW_SPB: "row_spb",
          Z.ZNCC_TUNE_H_TQ: "h_tq", Z.ZNCC_TUNE_V_TQ: "v_tq", Z.ZNCC_TUNE_AHAT_SMS: "ahat_sms",

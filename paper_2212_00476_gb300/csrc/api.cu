@@ -99,7 +99,7 @@ struct zncc_ctx {
     int row_minb2 = 0;            // cost kernel: two-blocks-per-SM variant where it applies
     int row_spb = 0;              // cost kernel: slices per block (0 = automatic)
     int row_nobulk = 0;           // cost kernel: stage the image rows with plain loads
-    int line_notma = 0;           // DT pairs: stream the slices with cp.async only
+    int line_loads = 0;           // DT pairs' staging: 0 TMA for rows, 1 cp.async only, 2 TMA for both
     int ahat_sms = 0;             // SMs the cost kernel leaves to the A_hat chain (0 = automatic)
     int h_tq = 0, v_tq = 0;       // DT pairs: forced lanes per chunk (0 = automatic)
     int v_lpc = 0;                // vertical store pairs: most columns per block (0 = automatic)
@@ -563,9 +563,14 @@ TmapEncodeFn tmap_encoder() {
 // as {entries per pixel, W, H}, one box of kL + G - 1 positions per chunk and slice (G =
 // line_tma_chunks_per_wavefront). Taken for F32 and F16 where G <= 4, the volume and the pixel
 // stride are 16-byte aligned, a line stays in one CTA, and the larger slots keep the plan's
-// blocks per SM within shared memory.
+// blocks per SM within shared memory; for columns only when asked (ZNCC_TUNE_LINE_LOADS = 2):
+// a column box is 16 + G - 1 rows of 64 or 128 bytes an image row of the volume apart, which
+// the tensor copy fetches row by row (at 1920x1080, D = 256 the F32 V pair took 1419 us so,
+// 1165 us with cp.async), while a row box reads consecutive pixels.
 bool line_tma(zncc_ctx* c, const LineArgs& a, const LinePass& p, CUtensorMap& m) {
-    if (c->line_notma || !a.async || a.cs != 1 || p.ones || p.dtype == 2) return false;
+    if (c->line_loads == 1 || (c->line_loads == 0 && !p.horiz) || !a.async || a.cs != 1 || p.ones ||
+        p.dtype == 2)
+        return false;
     const long long elem = p.dtype == 0 ? 4 : 2;
     const int g = line_tma_chunks_per_wavefront(a.tq, (int)elem);
     if (g > 4) return false;
@@ -1421,7 +1426,10 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
         case ZNCC_TUNE_AHAT_SMS: c->ahat_sms = value; break;
         case ZNCC_TUNE_PLANE: c->plane_mode = value ? 1 : 0; break;
         case ZNCC_TUNE_ROW_LOADS: c->row_nobulk = value ? 1 : 0; break;
-        case ZNCC_TUNE_LINE_LOADS: c->line_notma = value ? 1 : 0; break;
+        case ZNCC_TUNE_LINE_LOADS:
+            if (value > 2) return fail(c, ZNCC_EINVAL, "line staging must be 0, 1 or 2");
+            c->line_loads = value;
+            break;
         case ZNCC_TUNE_V_LPC:
             if (value != 0 && value != 1 && value != 2 && value != 4)
                 return fail(c, ZNCC_EINVAL, "columns per block must be 0, 1, 2 or 4");
