@@ -217,7 +217,12 @@ zncc_status zncc_run_batch(zncc_ctx* const* ctxs, const uint8_t* const* lefts,
  * pageable or pinned (pinned copies run asynchronously with respect to other streams). When
  * disp_host is page-locked host memory that the device can address (cudaHostAlloc,
  * cudaHostRegister, pinned torch tensors), the last kernel writes the map there directly
- * and there is no download copy. */
+ * and there is no download copy. A call that repeats the previous one with page-locked images
+ * and map (the same pointers, pitch, parameters and storage, no tuning or stream change in
+ * between) on a stream other than the legacy default stream is captured once as a CUDA graph
+ * and replayed from then on, so that the device runs the uploads, kernels and map stores without
+ * waiting for the host to issue them; the replay reads the buffers' contents at the time of the
+ * call. Where the capture fails the call is issued directly. */
 zncc_status zncc_run_host(zncc_ctx* ctx, const uint8_t* left_host, const uint8_t* right_host,
                           int pitch, float sigma_s, float sigma_r, int iters,
                           zncc_dtype storage, uint16_t* disp_host);

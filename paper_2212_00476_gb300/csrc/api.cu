@@ -118,6 +118,21 @@ struct zncc_ctx {
     std::vector<cudaEvent_t> events;
     int events_used = 0;
     std::vector<ProfRecord> records;
+    // zncc_run_host replayed as a CUDA graph: the arguments of the last call and of the captured
+    // one, and the instantiated graph; gen counts changes of tuning and stream
+    struct HostKey {
+        const void *left, *right, *disp;
+        int pitch, iters, storage;
+        float sigma_s, sigma_r;
+        unsigned gen;
+        bool operator==(const HostKey& o) const {
+            return left == o.left && right == o.right && disp == o.disp && pitch == o.pitch && iters == o.iters &&
+                   storage == o.storage && sigma_s == o.sigma_s && sigma_r == o.sigma_r && gen == o.gen;
+        }
+    };
+    HostKey host_last{}, host_key{}, host_nocapture{};
+    cudaGraphExec_t host_graph = nullptr;
+    unsigned gen = 1;
 };
 
 namespace {
@@ -220,6 +235,8 @@ void release(zncc_ctx* c) {
     c->records.clear();
     c->events_used = 0;
     c->plans.clear();
+    if (c->host_graph) cudaGraphExecDestroy(c->host_graph);
+    c->host_graph = nullptr;
 }
 
 zncc_status check_images(zncc_ctx* c, const void* a, const void* b, int pitch) {
@@ -250,6 +267,7 @@ void free_dev_f(float*& p) {
 }
 
 zncc_status alloc_dev(zncc_ctx* c, void** p, size_t bytes, const char* what) {
+    ++c->gen;                                       // a captured host-buffer run refers to the old buffers
     cudaError_t e = device_alloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1086,6 +1104,7 @@ zncc_status zncc_set_stream(zncc_ctx* c, void* stream) {
     if (!c) return ZNCC_EINVAL;
     c->stream = (cudaStream_t)stream;
     c->cur = c->stream;
+    ++c->gen;
     return ZNCC_OK;
 }
 
@@ -1352,6 +1371,46 @@ zncc_status zncc_run_batch(zncc_ctx* const* ctxs, const uint8_t* const* lefts, c
     return nsmall ? run_fused(lc, small, nsmall, sigma_s, sigma_r, iters, storage) : ZNCC_OK;
 }
 
+namespace {
+// The device work of zncc_run_host on the context's stream: the uploads, the fused run, and the
+// map's way back (disp_dev: the device address of a page-locked map, which the last kernel then
+// stores into; NULL: a copy from the context's map).
+zncc_status issue_host_run(zncc_ctx* c, const uint8_t* left_host, const uint8_t* right_host, int pitch,
+                           float sigma_s, float sigma_r, int iters, zncc_dtype storage, uint16_t* disp_host,
+                           uint16_t* disp_dev) {
+    const size_t npix = (size_t)c->W * c->H;
+    // contiguous rows go up as one linear copy each, pitched ones row by row
+    if (pitch == c->W) {
+        ZNCC_CUDA(c, cudaMemcpyAsync(c->img, left_host, npix, cudaMemcpyHostToDevice, c->stream), "left image upload");
+        ZNCC_CUDA(c, cudaMemcpyAsync(c->img + npix, right_host, npix, cudaMemcpyHostToDevice, c->stream),
+                  "right image upload");
+    } else {
+        ZNCC_CUDA(c, cudaMemcpy2DAsync(c->img, c->W, left_host, pitch, c->W, c->H, cudaMemcpyHostToDevice,
+                                       c->stream), "left image upload");
+        ZNCC_CUDA(c, cudaMemcpy2DAsync(c->img + npix, c->W, right_host, pitch, c->W, c->H, cudaMemcpyHostToDevice,
+                                       c->stream), "right image upload");
+    }
+    ZNCC_TRY(zncc_run(c, c->img, c->img + npix, c->W, sigma_s, sigma_r, iters, storage,
+                      disp_dev ? disp_dev : c->disp));
+    if (!disp_dev)
+        ZNCC_CUDA(c, cudaMemcpyAsync(disp_host, c->disp, npix * sizeof(uint16_t), cudaMemcpyDeviceToHost,
+                                     c->stream), "disparity download");
+    return ZNCC_OK;
+}
+
+// Whether p is page-locked host memory of the context's device; its device address in *dev.
+bool pinned_on(const zncc_ctx* c, const void* p, void** dev) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+        cudaGetLastError();                         // (a pageable pointer is not an error)
+        return false;
+    }
+    if (pa.type != cudaMemoryTypeHost || !pa.devicePointer || pa.device != c->device) return false;
+    if (dev) *dev = pa.devicePointer;
+    return true;
+}
+}  // namespace
+
 zncc_status zncc_run_host(zncc_ctx* c, const uint8_t* left_host, const uint8_t* right_host, int pitch,
                           float sigma_s, float sigma_r, int iters, zncc_dtype storage,
                           uint16_t* disp_host) {
@@ -1369,31 +1428,53 @@ zncc_status zncc_run_host(zncc_ctx* c, const uint8_t* left_host, const uint8_t* 
             free_dev(c->disp);
             return fail(c, ZNCC_ENOMEM, std::string("image buffers: ") + cudaGetErrorString(e));
         }
-    }
-    // contiguous rows go up as one linear copy each, pitched ones row by row
-    if (pitch == c->W) {
-        ZNCC_CUDA(c, cudaMemcpyAsync(c->img, left_host, npix, cudaMemcpyHostToDevice, c->stream), "left image upload");
-        ZNCC_CUDA(c, cudaMemcpyAsync(c->img + npix, right_host, npix, cudaMemcpyHostToDevice, c->stream),
-                  "right image upload");
-    } else {
-        ZNCC_CUDA(c, cudaMemcpy2DAsync(c->img, c->W, left_host, pitch, c->W, c->H, cudaMemcpyHostToDevice,
-                                       c->stream), "left image upload");
-        ZNCC_CUDA(c, cudaMemcpy2DAsync(c->img + npix, c->W, right_host, pitch, c->W, c->H, cudaMemcpyHostToDevice,
-                                       c->stream), "right image upload");
+        ++c->gen;
     }
     // a page-locked map the device can address takes the last kernel's stores directly
-    uint16_t* disp_dev = nullptr;
-    cudaPointerAttributes pa{};
-    if (cudaPointerGetAttributes(&pa, disp_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-        pa.devicePointer && pa.device == c->device)
-        disp_dev = static_cast<uint16_t*>(pa.devicePointer);
-    else
-        cudaGetLastError();                         // (a pageable pointer is not an error)
-    ZNCC_TRY(zncc_run(c, c->img, c->img + npix, c->W, sigma_s, sigma_r, iters, storage,
-                      disp_dev ? disp_dev : c->disp));
-    if (!disp_dev)
-        ZNCC_CUDA(c, cudaMemcpyAsync(disp_host, c->disp, npix * sizeof(uint16_t), cudaMemcpyDeviceToHost,
-                                     c->stream), "disparity download");
+    void* dmap = nullptr;
+    const bool map_pinned = pinned_on(c, disp_host, &dmap);
+    uint16_t* disp_dev = map_pinned ? static_cast<uint16_t*>(dmap) : nullptr;
+    // A call that repeats the previous one (the same host buffers, parameters, tuning, stream and
+    // context buffers) with page-locked host buffers, on a stream other than the legacy default
+    // one, is captured once as a CUDA graph and replayed from then on: the device runs the
+    // uploads, the kernels and the map's way back without waiting for the host to issue them.
+    // A capture that fails leaves the call to direct issue (and that argument set uncaptured).
+    const zncc_ctx::HostKey key{left_host, right_host, disp_host, pitch, iters, (int)storage, sigma_s, sigma_r, c->gen};
+    if (c->host_graph && key == c->host_key && !c->profiling) {
+        ZNCC_CUDA(c, cudaGraphLaunch(c->host_graph, c->stream), "graph launch");
+        ZNCC_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+        return ZNCC_OK;
+    }
+    const bool repeat = key == c->host_last && !(key == c->host_nocapture);
+    c->host_last = key;
+    if (repeat && !c->profiling && c->stream != nullptr && map_pinned && pinned_on(c, left_host, nullptr) &&
+        pinned_on(c, right_host, nullptr)) {
+        if (c->host_graph) cudaGraphExecDestroy(c->host_graph);
+        c->host_graph = nullptr;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const zncc_status s = issue_host_run(c, left_host, right_host, pitch, sigma_s, sigma_r, iters, storage,
+                                                 disp_host, disp_dev);
+            const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            ok = s == ZNCC_OK && e == cudaSuccess && g != nullptr && key.gen == c->gen;
+        }
+        if (ok) ok = cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        c->err.clear();
+        if (ok) {
+            c->host_graph = x;
+            c->host_key = key;
+            ZNCC_CUDA(c, cudaGraphLaunch(x, c->stream), "graph launch");
+            ZNCC_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+            return ZNCC_OK;
+        }
+        if (x) cudaGraphExecDestroy(x);
+        c->host_nocapture = key;
+    }
+    ZNCC_TRY(issue_host_run(c, left_host, right_host, pitch, sigma_s, sigma_r, iters, storage, disp_host, disp_dev));
     ZNCC_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
     return ZNCC_OK;
 }
@@ -1451,6 +1532,7 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
     c->plans.clear();
     c->occ.clear();
     c->plane_cs = -1;
+    ++c->gen;
     return ZNCC_OK;
 }
 

@@ -356,6 +356,41 @@ def test_fp16_storage_run_mismatch_rate_small():
     assert rate < 0.01, rate
 
 
+def test_run_host_repeated_calls_replay_the_same_work():
+    """Repeated zncc_run_host calls with the same page-locked buffers and arguments are captured
+    once as a CUDA graph and replayed; the replay reads the buffers' current contents, and a
+    change of arguments, tuning or storage (which reallocates the context's volume) issues the
+    call afresh. Every map equals a device-buffer run of the same inputs."""
+    h, w, d = 48, 160, 32
+    ctx = Z.ZnccContext(w, h, d, 9, stream=torch.cuda.Stream())
+    lp = torch.empty((h, w), dtype=torch.uint8).pin_memory()
+    rp = torch.empty_like(lp).pin_memory()
+    mp = torch.empty((h, w), dtype=torch.int16).pin_memory()
+    runs = [(1, 20.0, Z.ZNCC_F32, None), (2, 20.0, Z.ZNCC_F32, None), (3, 20.0, Z.ZNCC_F32, None),
+            (4, 20.0, Z.ZNCC_F32, None), (4, 12.0, Z.ZNCC_F32, None), (5, 12.0, Z.ZNCC_F32, None),
+            (5, 12.0, Z.ZNCC_F32, (Z.ZNCC_TUNE_LINE_LOADS, 1)), (6, 12.0, Z.ZNCC_F32, None),
+            (6, 12.0, Z.ZNCC_F16, None), (7, 12.0, Z.ZNCC_F16, None), (8, 12.0, Z.ZNCC_F16, None),
+            (9, 12.0, Z.ZNCC_F32, None), (10, 12.0, Z.ZNCC_F32, None)]
+    for seed, sig_s, storage, tune in runs:
+        if tune:
+            ctx.set_tuning(*tune)
+        p = rand_pair(h, w, d, seed=300 + seed, disp="planes")
+        lp.copy_(torch.from_numpy(p.left))
+        rp.copy_(torch.from_numpy(p.right))
+        mp.fill_(-1)
+        ctx.zncc_run_host(lp.numpy(), rp.numpy(), mp.numpy().view(np.uint16), sig_s, SIG_R, 3, storage)
+        ref = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        ld, rd = dev(p.left), dev(p.right)
+        torch.cuda.synchronize()                    # the inputs, then the context's stream
+        ctx.zncc_run(ld, rd, ref, sig_s, SIG_R, 3, storage)
+        torch.cuda.synchronize()
+        assert torch.equal(mp, ref.cpu()), (seed, storage)
+    assert ctx.device_faults() == 0
+    mref, gap = oracle.run(p.left, p.right, d, 4, 12.0, SIG_R, 3)
+    check_disp(host_u16(mp), mref, gap, oracle.ones_response(p.left, 12.0, SIG_R, 3), "replayed run")
+    ctx.close()
+
+
 def test_invalid_arguments_report_einval():
     ctx = Z.ZnccContext(16, 8, 4, 3)
     img = torch.zeros((8, 16), dtype=torch.uint8, device="cuda")
