@@ -510,12 +510,15 @@ def test_vertical_column_groups_reject_other_values():
 # (h, w, D, storage): TMA staging of the DT pairs' slices where eligible (F32 rows and columns,
 # F16 columns), ragged lines and disparity counts, and a half-precision pixel stride of 20 entries
 # (40 bytes, not 16-byte aligned) that takes the cp.async path in both runs
-TMA_CASES = [(96, 320, 64, Z.ZNCC_F32), (40, 1280, 128, Z.ZNCC_F32), (33, 208, 40, Z.ZNCC_F32),
-             (1030, 24, 12, Z.ZNCC_F32), (50, 120, 24, Z.ZNCC_F16), (64, 96, 20, Z.ZNCC_F16)]
+TMA_CASES = [(96, 320, 64, Z.ZNCC_F32, {}), (40, 1280, 128, Z.ZNCC_F32, {}), (33, 208, 40, Z.ZNCC_F32, {}),
+             (1030, 24, 12, Z.ZNCC_F32, {}), (50, 120, 24, Z.ZNCC_F16, {}), (64, 96, 20, Z.ZNCC_F16, {}),
+             # four chunks per shared-memory wavefront: boxes 19 positions tall, shifted 0-3
+             (40, 320, 64, Z.ZNCC_F16, {Z.ZNCC_TUNE_H_TQ: 4, Z.ZNCC_TUNE_V_TQ: 4}),
+             (37, 208, 24, Z.ZNCC_F32, {Z.ZNCC_TUNE_H_TQ: 2, Z.ZNCC_TUNE_V_TQ: 2})]
 
 
-@pytest.mark.parametrize("h,w,d,storage", TMA_CASES)
-def test_tma_staging_equals_cp_async(h, w, d, storage):
+@pytest.mark.parametrize("h,w,d,storage,tunings", TMA_CASES)
+def test_tma_staging_equals_cp_async(h, w, d, storage, tunings):
     """ZNCC_TUNE_LINE_LOADS: the DT pairs stream their next slices by one TMA tensor copy per
     chunk in the horizontal pairs (0, automatic), by cp.async per thread everywhere (1), or by
     TMA in both directions (2). The arithmetic is the same, so maps and aggregated volumes agree
@@ -526,6 +529,8 @@ def test_tma_staging_equals_cp_async(h, w, d, storage):
     maps, vols = [], []
     for loads in (0, 1, 2):
         ctx = Z.ZnccContext(w, h, d, 9)
+        for key, value in tunings.items():
+            ctx.set_tuning(key, value)
         ctx.set_tuning(Z.ZNCC_TUNE_LINE_LOADS, loads)
         disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
         ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, 3, storage)
