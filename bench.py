@@ -84,12 +84,15 @@ def storage_code(Z, name):
     return {"f32": Z.ZNCC_F32, "f16": Z.ZNCC_F16, "i8": Z.ZNCC_I8}[name]
 
 
-def workload_desc(name, storage):
+def workload_desc(name, storages=None):
+    """The workload: the pair, its sizes and the DT parameters. The volume's storage type is
+    the implementation's (the line's `dtype` / `storage` keys), so that both arms name the same
+    workload; a sweep over storage types names them."""
     wl = WORKLOADS[name]
     return (f"{name}: {wl['w']}x{wl['h']} D={wl['d']} win={wl['win']}x{wl['win']} DT "
-            f"sigma_s={SIG_S} sigma_r={SIG_R} iters={ITERS if name != 'plain_320x96' else 0} "
-            f"{storage.upper()} volume storage; seeded synthetic pair (blurred noise, slanted "
-            f"planes, 5% occlusion bands, gain/offset/noise)")
+            f"sigma_s={SIG_S} sigma_r={SIG_R} iters={ITERS if name != 'plain_320x96' else 0}"
+            + (f" {storages} volume storage" if storages else "") +
+            "; seeded synthetic pair (blurred noise, slanted planes, 5% occlusion bands, gain/offset/noise)")
 
 
 # ---------------------------------------------------------------------------------------
@@ -195,7 +198,7 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt * 1e3, 3), "fps": round(1.0 / dt, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(args.workload, "f64"),
+        "config": {"workload": workload_desc(args.workload),
                    "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": round(value, 6), "unit": "Gdisp/s", "cores": cores,
                          "kind": "oracle",
@@ -384,7 +387,7 @@ def run_gb300(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "fps": round(world * 1e3 / ms, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "storage": args.storage, "data": "synthetic",
-        "config": {"workload": workload_desc(args.workload, args.storage),
+        "config": {"workload": workload_desc(args.workload),
                    "l2": "flushed before every timed step (256 MB write outside the step events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "step_ms_min": round(min(step_ms), 4), "wall_ms_per_step_incl_flush":
@@ -729,7 +732,7 @@ def run_precision(args):
         "value": result["f16"]["map_mismatch_rate"], "unit": "share of pixels (F16 map vs oracle)",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_desc("precision_1920x1080", "f32/f16/i8"),
+        "config": {"workload": workload_desc("precision_1920x1080", "F32/F16/I8"),
                    "oracle_gt_within_1px": {"f64": gt_accuracy(ref), "fastdt": gt_accuracy(ref_fast)},
                    "near_tie_pixels": round(float(1 - clear.mean()), 6),
                    "pixels_with_ahat_below_2^-14": round(float((ahat < 2.0 ** -14).mean()), 6),
