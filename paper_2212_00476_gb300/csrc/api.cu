@@ -110,6 +110,15 @@ struct zncc_ctx {
     int num_sms = 0;
     std::vector<LinePlan> plans;  // line-pass launch shapes, by pass signature
     std::vector<OccEntry> occ;    // occupancy answers
+    // encoded tensor maps of the DT pairs' inputs, by (volume, pixel stride, element size,
+    // direction, box): a run then encodes none (the volume and strides repeat)
+    struct TmapEntry {
+        const void* base;
+        long long dstride;
+        int elem, horiz, ds, np;
+        CUtensorMap map;
+    };
+    std::vector<TmapEntry> tmaps;
     int2* scan_stats = nullptr;   // (progressive scan) packed statistics: left [H][W], right [H][W+D-1]
     uint8_t* img = nullptr;       // device copies for zncc_run_host: 2 x [H][W]
     uint16_t* disp = nullptr;     // [H][W]
@@ -268,6 +277,7 @@ void free_dev_f(float*& p) {
 
 zncc_status alloc_dev(zncc_ctx* c, void** p, size_t bytes, const char* what) {
     ++c->gen;                                       // a captured host-buffer run refers to the old buffers
+    c->tmaps.clear();                               // (a new buffer may reuse an old address)
     cudaError_t e = device_alloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -613,17 +623,26 @@ bool line_tma(zncc_ctx* c, const LineArgs& a, const LinePass& p, CUtensorMap& m)
     }
     const void* in = p.src ? p.src : p.vol;
     if ((uintptr_t)in % 16 != 0 || (p.dstride * elem) % 16 != 0) return false;
+    const cuuint32_t ds = (cuuint32_t)(kG * a.tq), np = (cuuint32_t)(kL + g - 1);
+    for (const zncc_ctx::TmapEntry& t : c->tmaps)
+        if (t.base == in && t.dstride == p.dstride && t.elem == (int)elem && t.horiz == (int)p.horiz &&
+            t.ds == (int)ds && t.np == (int)np) {
+            m = t.map;
+            return true;
+        }
     const TmapEncodeFn enc = tmap_encoder();
     if (!enc) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)p.dstride, (cuuint64_t)c->W, (cuuint64_t)c->H};
     const cuuint64_t strides[2] = {(cuuint64_t)(p.dstride * elem), (cuuint64_t)(p.dstride * elem * c->W)};
-    const cuuint32_t ds = (cuuint32_t)(kG * a.tq), np = (cuuint32_t)(kL + g - 1);
     const cuuint32_t box[3] = {ds, p.horiz ? np : 1u, p.horiz ? 1u : np};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
-    return enc(&m, p.dtype == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
-               const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (enc(&m, p.dtype == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+            const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (c->tmaps.size() >= 32) c->tmaps.clear();   // (callers' own volumes, e.g. dt_aggregate)
+    c->tmaps.push_back(zncc_ctx::TmapEntry{in, p.dstride, (int)elem, (int)p.horiz, (int)ds, (int)np, m});
+    return true;
 }
 
 // Appends a pair (its block shape chosen) to a launch: its items and steps, and the block's
