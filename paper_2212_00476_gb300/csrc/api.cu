@@ -130,12 +130,14 @@ struct zncc_ctx {
     // zncc_run_host replayed as a CUDA graph: the arguments of the last call and of the captured
     // one, and the instantiated graph; gen counts changes of tuning and stream
     struct HostKey {
-        const void *left, *right, *disp;
+        const void *left, *right, *disp;            // host addresses
+        const void *dleft, *dright, *ddisp;         // their device mappings (NULL: not page-locked)
         int pitch, iters, storage;
         float sigma_s, sigma_r;
         unsigned gen;
         bool operator==(const HostKey& o) const {
-            return left == o.left && right == o.right && disp == o.disp && pitch == o.pitch && iters == o.iters &&
+            return left == o.left && right == o.right && disp == o.disp && dleft == o.dleft &&
+                   dright == o.dright && ddisp == o.ddisp && pitch == o.pitch && iters == o.iters &&
                    storage == o.storage && sigma_s == o.sigma_s && sigma_r == o.sigma_r && gen == o.gen;
         }
     };
@@ -1450,24 +1452,27 @@ zncc_status zncc_run_host(zncc_ctx* c, const uint8_t* left_host, const uint8_t* 
         ++c->gen;
     }
     // a page-locked map the device can address takes the last kernel's stores directly
-    void* dmap = nullptr;
+    void *dmap = nullptr, *dleft = nullptr, *dright = nullptr;
     const bool map_pinned = pinned_on(c, disp_host, &dmap);
+    const bool imgs_pinned = pinned_on(c, left_host, &dleft) && pinned_on(c, right_host, &dright);
     uint16_t* disp_dev = map_pinned ? static_cast<uint16_t*>(dmap) : nullptr;
-    // A call that repeats the previous one (the same host buffers, parameters, tuning, stream and
-    // context buffers) with page-locked host buffers, on a stream other than the legacy default
-    // one, is captured once as a CUDA graph and replayed from then on: the device runs the
-    // uploads, the kernels and the map's way back without waiting for the host to issue them.
-    // A capture that fails leaves the call to direct issue (and that argument set uncaptured).
-    const zncc_ctx::HostKey key{left_host, right_host, disp_host, pitch, iters, (int)storage, sigma_s, sigma_r, c->gen};
-    if (c->host_graph && key == c->host_key && !c->profiling) {
+    // A call that repeats the previous one (the same host buffers, still page-locked at the same
+    // device mappings, parameters, tuning, stream and context buffers), on a stream other than
+    // the legacy default one, is captured once as a CUDA graph and replayed from then on: the
+    // device runs the uploads, the kernels and the map's way back without waiting for the host
+    // to issue them. The buffers are looked up on every call, so a buffer freed and allocated
+    // anew is never reached through an old mapping. A capture that fails leaves the call to
+    // direct issue (and that argument set uncaptured).
+    const zncc_ctx::HostKey key{left_host, right_host, disp_host, dleft,         dright,      dmap,
+                                pitch,     iters,      (int)storage, sigma_s, sigma_r, c->gen};
+    if (c->host_graph && map_pinned && imgs_pinned && key == c->host_key && !c->profiling) {
         ZNCC_CUDA(c, cudaGraphLaunch(c->host_graph, c->stream), "graph launch");
         ZNCC_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
         return ZNCC_OK;
     }
     const bool repeat = key == c->host_last && !(key == c->host_nocapture);
     c->host_last = key;
-    if (repeat && !c->profiling && c->stream != nullptr && map_pinned && pinned_on(c, left_host, nullptr) &&
-        pinned_on(c, right_host, nullptr)) {
+    if (repeat && !c->profiling && c->stream != nullptr && map_pinned && imgs_pinned) {
         if (c->host_graph) cudaGraphExecDestroy(c->host_graph);
         c->host_graph = nullptr;
         cudaGraph_t g = nullptr;

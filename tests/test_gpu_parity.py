@@ -385,6 +385,15 @@ def test_run_host_repeated_calls_replay_the_same_work():
         ctx.zncc_run(ld, rd, ref, sig_s, SIG_R, 3, storage)
         torch.cuda.synchronize()
         assert torch.equal(mp, ref.cpu()), (seed, storage)
+    # buffers replaced between calls (new page-locked tensors, then a pageable map): each call
+    # looks its buffers up afresh and never reaches an old one
+    for k in range(4):
+        lp, rp = torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory()
+        out = np.zeros((h, w), np.uint16) if k == 3 else torch.full((h, w), -1, dtype=torch.int16).pin_memory()
+        for _ in range(2):
+            host = out if k == 3 else out.numpy().view(np.uint16)
+            ctx.zncc_run_host(lp.numpy(), rp.numpy(), host, 12.0, SIG_R, 3, Z.ZNCC_F32)
+            assert np.array_equal(host, host_u16(ref)), k
     assert ctx.device_faults() == 0
     mref, gap = oracle.run(p.left, p.right, d, 4, 12.0, SIG_R, 3)
     check_disp(host_u16(mp), mref, gap, oracle.ones_response(p.left, 12.0, SIG_R, 3), "replayed run")
