@@ -9,8 +9,10 @@ runs apply it without searching:
     best = autotune.tune(ctx, left, right, disp, sigma_s, sigma_r, iters, storage)
 
 Knobs: the cost kernel's two-blocks-per-SM variant and disparity slices per block
-(band-tile depth), and the lanes per chunk of the horizontal and vertical DT pairs
-(disparities per block = 4 x lanes).
+(band-tile depth), the lanes per chunk of the horizontal and vertical DT pairs (disparities
+per block = 4 x lanes), the adjacent columns per block of the vertical pairs that store the
+volume, and how the DT pairs stage their next slices (TMA tensor copies in the horizontal
+pairs, cp.async only, or TMA in both directions).
 """
 
 from __future__ import annotations
