@@ -357,6 +357,11 @@ const char* zncc_status_string(zncc_status status);
  *                        cp.async elsewhere and in the vertical pairs; 2 = TMA in the vertical
  *                        pairs too (a column box fetches one pixel row at a time: faster for
  *                        some shapes, far slower for others)
+ *   ZNCC_TUNE_WAIT_DRILL (tests) 1 = every DT pair launch has one thread per block wait, with a
+ *                        64-poll limit, for an mbarrier phase that nothing completes; the wait
+ *                        runs out and records fault bit 2 (see zncc_device_faults) while the
+ *                        results stay those of a normal run. A check of the bounded-wait path
+ *                        that faults, traps and hangs nothing
  * A value a launch cannot use (too many threads or too much shared memory) makes the next
  * call fail with ZNCC_EUNSUPPORTED. Unknown keys give ZNCC_EINVAL. */
 typedef enum {
@@ -369,7 +374,8 @@ typedef enum {
     ZNCC_TUNE_PLANE_CS = 7,
     ZNCC_TUNE_ROW_LOADS = 8,
     ZNCC_TUNE_V_LPC = 9,
-    ZNCC_TUNE_LINE_LOADS = 10
+    ZNCC_TUNE_LINE_LOADS = 10,
+    ZNCC_TUNE_WAIT_DRILL = 11
 } zncc_tune_key;
 zncc_status zncc_set_tuning(zncc_ctx* ctx, int key, int value);
 

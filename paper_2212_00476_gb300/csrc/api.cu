@@ -100,6 +100,7 @@ struct zncc_ctx {
     int row_spb = 0;              // cost kernel: slices per block (0 = automatic)
     int row_nobulk = 0;           // cost kernel: stage the image rows with plain loads
     int line_loads = 0;           // DT pairs' staging: 0 TMA for rows, 1 cp.async only, 2 TMA for both
+    int wait_drill = 0;           // (tests) DT pairs wait out an mbarrier nobody arrives on
     int ahat_sms = 0;             // SMs the cost kernel leaves to the A_hat chain (0 = automatic)
     int h_tq = 0, v_tq = 0;       // DT pairs: forced lanes per chunk (0 = automatic)
     int v_lpc = 0;                // vertical store pairs: most columns per block (0 = automatic)
@@ -704,6 +705,7 @@ zncc_status run_lines(zncc_ctx* lc, zncc_ctx* const* ctxs, const LinePass* passe
         }
         b.stage_bytes = (long long)stage;
         b.fault = lc->fault;
+        b.drill = lc->wait_drill;
         const size_t smem = stage + rest;
         if (smem > (size_t)lc->smem_max) return fail(lc, ZNCC_EUNSUPPORTED, "DT pass exceeds shared memory");
         ZNCC_CUDA(lc, size_line_grid(b, threads, smem, mode, dtype, lc->num_sms, lc), "occupancy query");
@@ -1535,6 +1537,7 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
             if (value > 2) return fail(c, ZNCC_EINVAL, "line staging must be 0, 1 or 2");
             c->line_loads = value;
             break;
+        case ZNCC_TUNE_WAIT_DRILL: c->wait_drill = value ? 1 : 0; break;
         case ZNCC_TUNE_V_LPC:
             if (value != 0 && value != 1 && value != 2 && value != 4)
                 return fail(c, ZNCC_EINVAL, "columns per block must be 0, 1, 2 or 4");

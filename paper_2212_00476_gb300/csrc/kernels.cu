@@ -399,7 +399,14 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
     const bool tma = !CLUSTER && b.p[0].tma != 0 && b.p[0].async != 0 && (smem_addr(smem4) & 127u) == 0;
     if (tma && threadIdx.x < 2 * (blockDim.x >> 5))
         mbar_init(&tbar[threadIdx.x & 1][threadIdx.x >> 1], (unsigned)(32 / b.p[0].tq));
-    if (tma) __syncthreads();
+    // (tests) the wait drill: thread 0 waits, bounded, for a phase of an mbarrier that nothing
+    // arrives on, records the timeout like a copy that did not land, and goes on; no copy is in
+    // flight on that barrier, and the pass computes as without the drill
+    __shared__ unsigned long long drill_bar;
+    if (b.drill && threadIdx.x == 0) mbar_init(&drill_bar, 1);
+    if (tma || b.drill) __syncthreads();
+    if (b.drill && threadIdx.x == 0 && !mbar_wait(&drill_bar, 0, kDrillWaitPolls) && b.fault)
+        atomicOr(b.fault, kFaultTmaWait);
     griddep_wait();
     auto P = [&](int pi) -> const LineArgs& { return b.p[SINGLE ? 0 : pi]; };
     const int lane = threadIdx.x & 31;

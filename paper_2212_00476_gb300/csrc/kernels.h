@@ -58,6 +58,7 @@ constexpr unsigned kFaultTmaAlign = 8u;      // a TMA destination was not 128-by
 // Polls of an mbarrier before a wait counts as timed out (each poll may suspend the thread for a
 // while; a copy from L2 or HBM completes within a few thousand).
 constexpr unsigned kBulkWaitPolls = 1u << 24;
+constexpr unsigned kDrillWaitPolls = 64;     // the wait drill's limit (ZNCC_TUNE_WAIT_DRILL)
 
 struct LineArgs {
     void* vol;                // float or half cost volume (output, and input unless src is set)
@@ -102,6 +103,7 @@ struct LineBatch {
     int co_async;             // coefficients streamed by cp.async (two buffers; line_coef_async)
     long long stage_bytes;    // staging region (the largest pair's), before the other arrays
     unsigned* fault;          // device fault word (kFaultTmaWait), or NULL without TMA
+    int drill;                // (tests) one thread per block waits out an mbarrier nobody arrives on
     LineArgs p[kMaxBatch];
     // (tma) per pair: the input volume as a 3-D tensor {entries per pixel, W, H}, box
     // {4 tq, 16, 1} (rows) or {4 tq, 1, 16} (columns): one chunk's positions of one slice

@@ -400,6 +400,36 @@ def test_run_host_repeated_calls_replay_the_same_work():
     ctx.close()
 
 
+@pytest.mark.parametrize("storage,loads", [(Z.ZNCC_F32, 0), (Z.ZNCC_F32, 1), (Z.ZNCC_F16, 2)])
+def test_wait_drill_records_a_timeout_and_keeps_results(storage, loads):
+    """ZNCC_TUNE_WAIT_DRILL makes a bounded device wait run out (an mbarrier nothing completes):
+    the kernels record fault bit 2, which zncc_device_faults reports once and clears, the maps
+    stay those of a normal run, and without the drill no fault is recorded. Nothing faults,
+    traps or hangs."""
+    h, w, d = 40, 192, 48
+    p = rand_pair(h, w, d, seed=77, disp="planes")
+    ld, rd = dev(p.left), dev(p.right)
+    ctx = Z.ZnccContext(w, h, d, 9)
+    ctx.set_tuning(Z.ZNCC_TUNE_LINE_LOADS, loads)
+    ref = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.zncc_run(ld, rd, ref, SIG_S, SIG_R, 3, storage)
+    torch.cuda.synchronize()
+    assert ctx.device_faults() == 0
+    ctx.set_tuning(Z.ZNCC_TUNE_WAIT_DRILL, 1)
+    got = torch.empty_like(ref)
+    ctx.zncc_run(ld, rd, got, SIG_S, SIG_R, 3, storage)
+    torch.cuda.synchronize()
+    assert ctx.device_faults() == 4
+    assert ctx.device_faults() == 0                 # read and cleared
+    assert torch.equal(got, ref)
+    ctx.set_tuning(Z.ZNCC_TUNE_WAIT_DRILL, 0)
+    ctx.zncc_run(ld, rd, got, SIG_S, SIG_R, 3, storage)
+    torch.cuda.synchronize()
+    assert ctx.device_faults() == 0
+    assert torch.equal(got, ref)
+    ctx.close()
+
+
 def test_invalid_arguments_report_einval():
     ctx = Z.ZnccContext(16, 8, 4, 3)
     img = torch.zeros((8, 16), dtype=torch.uint8, device="cuda")
