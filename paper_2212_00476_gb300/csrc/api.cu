@@ -85,7 +85,8 @@ struct zncc_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t cur = nullptr;       // the stream launches go to
     cudaStream_t side = nullptr;      // (F16, I8) the A_hat chain beside the cost kernel
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_pair; // [p-2]: the side work line pair p needs is done
     std::string err;
     float4* coefH = nullptr;      // [H][W]       horizontal DT coefficients
     float4* coefV = nullptr;      // [W][H]       vertical DT coefficients
@@ -239,9 +240,10 @@ void release(zncc_ctx* c) {
     free_dev(c->fault);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (cudaEvent_t e : c->ev_pair) cudaEventDestroy(e);
+    c->ev_pair.clear();
     c->side = nullptr;
-    c->ev_fork = c->ev_join = nullptr;
+    c->ev_fork = nullptr;
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     c->records.clear();
@@ -922,9 +924,14 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
         for (int i = 0; i < n; ++i)
             if (ensure_ahat(io[i].c, npairs - 1, npairs - pfirst + 1) != ZNCC_OK)
                 return fail(lc, ZNCC_ENOMEM, io[i].c->err);
-    // Side work beside the cost kernel, on a second stream joined before the first line pair:
-    // the column DT coefficients (the cost kernel writes the rows') and, with F16 or I8
-    // storage, the A_hat chain (small and latency-bound, one warp per line). The cost kernel's
+    // Side work beside the cost kernel, on a second stream: the column DT coefficients (the
+    // cost kernel writes the rows') and, with F16 or I8 storage, the A_hat chain (small and
+    // latency-bound, one warp per line). With F16 storage line pair p waits for the side work
+    // it reads and no more: the coefficients and the A_hat passes up to p (pass p writes pair
+    // p's multipliers; the last pair's come from a separate kernel), so the later passes run
+    // beside the first line pairs instead of before them (1280x384x128, 3 iterations: step
+    // 0.549 -> 0.535 ms). FastDT's pairs measured slower that way (1.21 -> 1.23 ms), so there
+    // pair 2 waits for the whole side stream, as without multipliers. The cost kernel's
     // 128-register variant holds one block per SM and leaves registers and shared memory for
     // the side kernels' blocks on every SM; its two-blocks-per-SM variant fills the registers,
     // so with the A_hat chain `reserve` SMs are left to it. FastDT needs A_hat_1 in the cost
@@ -939,15 +946,33 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
         if (!lc->side) {
             ZNCC_CUDA(lc, cudaStreamCreateWithFlags(&lc->side, cudaStreamNonBlocking), "side stream");
             ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_fork, cudaEventDisableTiming), "fork event");
-            ZNCC_CUDA(lc, cudaEventCreateWithFlags(&lc->ev_join, cudaEventDisableTiming), "join event");
+        }
+        while ((int)lc->ev_pair.size() < npairs - 1) {
+            cudaEvent_t e = nullptr;
+            ZNCC_CUDA(lc, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "join event");
+            lc->ev_pair.push_back(e);
         }
         ZNCC_CUDA(lc, cudaEventRecord(lc->ev_fork, lc->stream), "fork");
         ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->side, lc->ev_fork, 0), "fork");
         lc->cur = lc->side;
     }
+    // mark(q) records, after the side stream's last launch, the events of pairs pj..q (the
+    // pairs that need nothing later); pj ends as the first pair with no event of its own
+    int pj = 2;
+    auto mark = [&](int upto) -> zncc_status {
+        for (; pj <= upto; ++pj) {
+            const cudaError_t e = cudaEventRecord(lc->ev_pair[pj - 2], lc->side);
+            if (e != cudaSuccess) return cuda_fail(lc, e, "join");
+        }
+        return ZNCC_OK;
+    };
+    const bool per_pair = norm && dt == 1;
     zncc_status st = run_coef(lc, io, n, sigma_s, sigma_r, false);
-    for (int p = p_first_side; norm && p <= npairs - 1 && st == ZNCC_OK; ++p)
+    if (st == ZNCC_OK && !norm) st = mark(2);       // later pairs follow pair 2 on the main stream
+    for (int p = p_first_side; norm && p <= npairs - 1 && st == ZNCC_OK; ++p) {
         st = run_ahat(lc, io, n, p, pfirst, npairs, K, inv_sr255, s2, dt == 2);
+        if (st == ZNCC_OK && per_pair) st = mark(p);
+    }
     // the last pair's multipliers (A_hat_{npairs-1}, s2): its result is not stored
     for (int i = 0; norm && i < n && st == ZNCC_OK; ++i) {
         const int W = io[i].c->W, H = io[i].c->H;
@@ -958,16 +983,17 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
                                             io[i].c->mulmap + (size_t)(npairs - pfirst) * npix, lc->cur);
         if (e != cudaSuccess) st = cuda_fail(lc, e, "A_hat multipliers");
     }
+    if (st == ZNCC_OK && norm) st = mark(per_pair ? npairs : 2);
     lc->cur = lc->stream;
     ZNCC_TRY(st);
-    ZNCC_CUDA(lc, cudaEventRecord(lc->ev_join, lc->side), "join");
     if (dt == 2)
         for (int i = 0; i < n; ++i) io[i].mulmap1 = io[i].c->mulmap;
     ZNCC_TRY(run_rows(lc, io, n, kModeHPair, dt, s2, K, inv_sr255, K_ZNCC_HPAIR, reserve,
                       "ZNCC + horizontal DT pair"));
-    ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_join, 0), "join of the side stream");
-
     for (int pair = 2; pair <= npairs; ++pair) {    // pair 1 is the cost kernel's
+        // every recorded event is waited on, so that a captured graph joins the side stream
+        if (pair < pj)
+            ZNCC_CUDA(lc, cudaStreamWaitEvent(lc->stream, lc->ev_pair[pair - 2], 0), "join of the side stream");
         LinePass lp[kMaxBatch];
         for (int i = 0; i < n; ++i) {
             const size_t npix = (size_t)io[i].c->W * io[i].c->H;
