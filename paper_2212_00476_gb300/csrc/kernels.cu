@@ -676,14 +676,10 @@ __global__ void __launch_bounds__(512) k_line_pair(const __grid_constant__ LineB
         }
         if (has_mul && active) {         // (FastDT codes always have multipliers)
 #pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                const float m = mul[i].x;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) v[i][j] *= m;
-            }
+            for (int i = 0; i < kL; ++i) mul4<true>(mul[i].x, v[i]);
         }
         // the staging buffer is free once the forward sweep has read it: refill it two ahead
-        dt_pair<MODE != kLineWta>(v, co, tq, dq, lane, rank * nwl + wl, nwl_all, sa, sb, a.s2, mul,
+        dt_pair<MODE != kLineWta, true>(v, co, tq, dq, lane, rank * nwl + wl, nwl_all, sa, sb, a.s2, mul,
                 [&]() {
                     prefetch(pf, n_s & 1);
                     advance(pf);
