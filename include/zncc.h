@@ -362,6 +362,15 @@ const char* zncc_status_string(zncc_status status);
  *                        runs out and records fault bit 2 (see zncc_device_faults) while the
  *                        results stay those of a normal run. A check of the bounded-wait path
  *                        that faults, traps and hangs nothing
+ *   ZNCC_TUNE_AHAT_JOIN  (F16 storage) how the line pairs wait for the A_hat chain on the
+ *                        second stream: 1 = the first vertical pair waits for the whole chain;
+ *                        2 = line pair p waits for A_hat pass p only, so that the later passes
+ *                        run beside the first line pairs; 0 (automatic) = 2 where an A_hat pass
+ *                        block (4 warps, 48 bytes per position of the longest line) needs at
+ *                        most 64 KB of shared memory and so fits beside the line pairs' blocks
+ *                        (1280x384x128: step 0.532 -> 0.519 ms), else 1 (1920x1080x256 with 2:
+ *                        5.73 -> 6.10 ms, the passes waiting for free SMs). The maps do not
+ *                        depend on it
  * A value a launch cannot use (too many threads or too much shared memory) makes the next
  * call fail with ZNCC_EUNSUPPORTED. Unknown keys give ZNCC_EINVAL. */
 typedef enum {
@@ -375,7 +384,8 @@ typedef enum {
     ZNCC_TUNE_ROW_LOADS = 8,
     ZNCC_TUNE_V_LPC = 9,
     ZNCC_TUNE_LINE_LOADS = 10,
-    ZNCC_TUNE_WAIT_DRILL = 11
+    ZNCC_TUNE_WAIT_DRILL = 11,
+    ZNCC_TUNE_AHAT_JOIN = 12
 } zncc_tune_key;
 zncc_status zncc_set_tuning(zncc_ctx* ctx, int key, int value);
 

@@ -11,8 +11,9 @@ runs apply it without searching:
 Knobs: the cost kernel's two-blocks-per-SM variant and disparity slices per block
 (band-tile depth), the lanes per chunk of the horizontal and vertical DT pairs (disparities
 per block = 4 x lanes), the adjacent columns per block of the vertical pairs that store the
-volume, and how the DT pairs stage their next slices (TMA tensor copies in the horizontal
-pairs, cp.async only, or TMA in both directions).
+volume, how the DT pairs stage their next slices (TMA tensor copies in the horizontal
+pairs, cp.async only, or TMA in both directions), and (F16) how the line pairs wait for the
+A_hat chain (whole chain before the first, or pass by pass).
 """
 
 from __future__ import annotations
@@ -30,11 +31,13 @@ CANDIDATES = {
     Z.ZNCC_TUNE_V_TQ: [0, 2, 4, 8],
     Z.ZNCC_TUNE_V_LPC: [0, 2],
     Z.ZNCC_TUNE_LINE_LOADS: [0, 1, 2],
+    Z.ZNCC_TUNE_AHAT_JOIN: [0, 1, 2],
 }
 NAMES = {Z.ZNCC_TUNE_ROW_MINB2: "row_minb2", Z.ZNCC_TUNE_ROW_SPB: "row_spb",
          Z.ZNCC_TUNE_H_TQ: "h_tq", Z.ZNCC_TUNE_V_TQ: "v_tq", Z.ZNCC_TUNE_AHAT_SMS: "ahat_sms",
          Z.ZNCC_TUNE_PLANE: "plane", Z.ZNCC_TUNE_PLANE_CS: "plane_cs", Z.ZNCC_TUNE_ROW_LOADS: "row_loads",
-         Z.ZNCC_TUNE_V_LPC: "v_lpc", Z.ZNCC_TUNE_LINE_LOADS: "line_loads"}
+         Z.ZNCC_TUNE_V_LPC: "v_lpc", Z.ZNCC_TUNE_LINE_LOADS: "line_loads",
+         Z.ZNCC_TUNE_AHAT_JOIN: "ahat_join"}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 _lock = threading.Lock()
 

@@ -105,6 +105,7 @@ struct zncc_ctx {
     int ahat_sms = 0;             // SMs the cost kernel leaves to the A_hat chain (0 = automatic)
     int h_tq = 0, v_tq = 0;       // DT pairs: forced lanes per chunk (0 = automatic)
     int v_lpc = 0;                // vertical store pairs: most columns per block (0 = automatic)
+    int ahat_join = 0;            // (F16) line pairs join the A_hat chain: 1 whole, 2 per pass, 0 automatic
     int plane_mode = 0;           // F32 fused runs: the plane-resident path where it applies
     int plane_force_cs = 0;       // its cluster size (0 = automatic)
     int plane_cs = -1;            // chosen cluster size (0: streaming path; -1: not chosen yet)
@@ -926,12 +927,15 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
                 return fail(lc, ZNCC_ENOMEM, io[i].c->err);
     // Side work beside the cost kernel, on a second stream: the column DT coefficients (the
     // cost kernel writes the rows') and, with F16 or I8 storage, the A_hat chain (small and
-    // latency-bound, one warp per line). With F16 storage line pair p waits for the side work
-    // it reads and no more: the coefficients and the A_hat passes up to p (pass p writes pair
-    // p's multipliers; the last pair's come from a separate kernel), so the later passes run
-    // beside the first line pairs instead of before them (1280x384x128, 3 iterations: step
-    // 0.549 -> 0.535 ms). FastDT's pairs measured slower that way (1.21 -> 1.23 ms), so there
-    // pair 2 waits for the whole side stream, as without multipliers. The cost kernel's
+    // latency-bound, one warp per line). With F16 storage line pair p may wait for the side
+    // work it reads and no more: the coefficients and the A_hat passes up to p (pass p writes
+    // pair p's multipliers; the last pair's come from a separate kernel), so the later passes
+    // run beside the first line pairs instead of before them. That pays where a pass's block
+    // fits beside the line pairs' blocks (1280x384x128, 3 iterations: step 0.549 -> 0.535 ms)
+    // and costs where it does not (1920x1080x256: 5.73 -> 6.10 ms, the passes waiting for
+    // free SMs), so it is taken where the pass needs at most 64 KB of shared memory, or as
+    // ZNCC_TUNE_AHAT_JOIN says. FastDT's pairs measured slower that way (1.21 -> 1.23 ms), so
+    // there pair 2 waits for the whole side stream, as without multipliers. The cost kernel's
     // 128-register variant holds one block per SM and leaves registers and shared memory for
     // the side kernels' blocks on every SM; its two-blocks-per-SM variant fills the registers,
     // so with the A_hat chain `reserve` SMs are left to it. FastDT needs A_hat_1 in the cost
@@ -966,7 +970,10 @@ zncc_status run_fused(zncc_ctx* lc, PairIO* io, int n, float sigma_s, float sigm
         }
         return ZNCC_OK;
     };
-    const bool per_pair = norm && dt == 1;
+    int longest = 0;
+    for (int i = 0; i < n; ++i) longest = std::max(longest, std::max(io[i].c->W, io[i].c->H));
+    const bool per_pair = norm && dt == 1 &&
+                          (lc->ahat_join == 2 || (lc->ahat_join == 0 && ahat_pass_smem_bytes(longest) <= 65536));
     zncc_status st = run_coef(lc, io, n, sigma_s, sigma_r, false);
     if (st == ZNCC_OK && !norm) st = mark(2);       // later pairs follow pair 2 on the main stream
     for (int p = p_first_side; norm && p <= npairs - 1 && st == ZNCC_OK; ++p) {
@@ -1564,6 +1571,10 @@ zncc_status zncc_set_tuning(zncc_ctx* c, int key, int value) {
             c->line_loads = value;
             break;
         case ZNCC_TUNE_WAIT_DRILL: c->wait_drill = value ? 1 : 0; break;
+        case ZNCC_TUNE_AHAT_JOIN:
+            if (value > 2) return fail(c, ZNCC_EINVAL, "A_hat join must be 0, 1 or 2");
+            c->ahat_join = value;
+            break;
         case ZNCC_TUNE_V_LPC:
             if (value != 0 && value != 1 && value != 2 && value != 4)
                 return fail(c, ZNCC_EINVAL, "columns per block must be 0, 1, 2 or 4");

@@ -274,8 +274,10 @@ __global__ void __launch_bounds__(32 * kAhatWarps) k_ahat_pair(const __grid_cons
     griddep_launch_dependents();
 }
 
+size_t ahat_pass_smem_bytes(int nmax) { return (size_t)kAhatWarps * kAhatArrays * nmax * sizeof(float); }
+
 cudaError_t launch_ahat_pair(const AhatBatch& b, cudaStream_t st) {
-    const size_t smem = (size_t)kAhatWarps * kAhatArrays * b.nmax * sizeof(float);
+    const size_t smem = ahat_pass_smem_bytes(b.nmax);
     cudaError_t e = set_max_smem((const void*)k_ahat_pair, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;

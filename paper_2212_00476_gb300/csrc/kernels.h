@@ -192,6 +192,8 @@ struct AhatBatch {
     AhatArgs p[kMaxBatch];
 };
 cudaError_t launch_ahat_pair(const AhatBatch& b, cudaStream_t st);
+// Dynamic shared memory of one A_hat pass-pair block for lines of at most nmax positions.
+size_t ahat_pass_smem_bytes(int nmax);
 long long dt_coef_threads(int W, int H);
 // The column coefficients only, coalesced: one block per 32 columns x 4 chunks; thread0 and
 // total_threads of the batch count blocks.

@@ -32,7 +32,7 @@ ZNCC_OK, ZNCC_EINVAL, ZNCC_ENOMEM, ZNCC_ECUDA, ZNCC_EBUSY, ZNCC_ENOTREADY, ZNCC_
 ZNCC_F32, ZNCC_F16, ZNCC_I8 = 0, 1, 2
 ZNCC_TUNE_ROW_MINB2, ZNCC_TUNE_ROW_SPB, ZNCC_TUNE_H_TQ, ZNCC_TUNE_V_TQ, ZNCC_TUNE_AHAT_SMS = 1, 2, 3, 4, 5
 ZNCC_TUNE_PLANE, ZNCC_TUNE_PLANE_CS, ZNCC_TUNE_ROW_LOADS, ZNCC_TUNE_V_LPC = 6, 7, 8, 9
-ZNCC_TUNE_LINE_LOADS, ZNCC_TUNE_WAIT_DRILL = 10, 11
+ZNCC_TUNE_LINE_LOADS, ZNCC_TUNE_WAIT_DRILL, ZNCC_TUNE_AHAT_JOIN = 10, 11, 12
 STATUS_NAMES = ["ZNCC_OK", "ZNCC_EINVAL", "ZNCC_ENOMEM", "ZNCC_ECUDA", "ZNCC_EBUSY",
                 "ZNCC_ENOTREADY", "ZNCC_ETIMEOUT", "ZNCC_EUNSUPPORTED"]
 

@@ -62,3 +62,15 @@ def test_null_context_and_status_strings(lib):
     assert lib.zncc_run(None, None, None, 0, 1.0, 1.0, 0, 0, None) == zncc.ZNCC_EINVAL
     for s, name in enumerate(zncc.STATUS_NAMES):
         assert lib.zncc_status_string(s).decode() == name
+
+
+def test_header_constants_match_the_binding():
+    """Every enumerator include/zncc.h gives a value (status codes, storage types, tuning keys)
+    has a constant of the same name and value in the Python binding."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "zncc.h")).read(), flags=re.S)
+    pairs = re.findall(r"\b(ZNCC_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)
+    tune = [n for n, _ in pairs if n.startswith("ZNCC_TUNE_")]
+    assert "ZNCC_TUNE_AHAT_JOIN" in tune and len(tune) >= 12
+    for name, value in pairs:
+        assert hasattr(zncc, name), name
+        assert getattr(zncc, name) == int(value), (name, getattr(zncc, name), value)

@@ -356,6 +356,45 @@ def test_fp16_storage_run_mismatch_rate_small():
     assert rate < 0.01, rate
 
 
+# (h, w, D): rows whose A_hat pass needs 15 KB of shared memory (automatic: pass by pass) and
+# 1400-pixel rows that need 67 KB (automatic: one join)
+@pytest.mark.parametrize("h,w,d", [(96, 320, 32), (40, 1400, 24)])
+def test_ahat_join_modes_give_the_same_map(h, w, d):
+    """ZNCC_TUNE_AHAT_JOIN: with F16 storage the line pairs wait for the A_hat chain on the
+    second stream as a whole (1) or pass by pass (2); 0 picks by the passes' shared memory.
+    Only the order of the launches differs, so the maps agree bit for bit, also when a
+    host-buffer run is captured as a graph and replayed, and stay within the F16 mismatch rate
+    of the oracle's."""
+    p = rand_pair(h, w, d, seed=h + w + d, disp="planes")
+    maps = []
+    for join in (0, 1, 2):
+        ctx = Z.ZnccContext(w, h, d, 9)
+        ctx.set_tuning(Z.ZNCC_TUNE_AHAT_JOIN, join)
+        disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, 3, Z.ZNCC_F16)
+        torch.cuda.synchronize()
+        maps.append(host_u16(disp).copy())
+        for _ in range(2):                          # issued, then replayed
+            host = np.zeros((h, w), np.uint16)
+            ctx.zncc_run_host(p.left, p.right, host, SIG_S, SIG_R, 3, Z.ZNCC_F16)
+            assert np.array_equal(host, maps[-1]), join
+        assert ctx.device_faults() == 0
+        ctx.close()
+    for m in maps[1:]:
+        assert np.array_equal(maps[0], m), int((maps[0] != m).sum())
+    ref, _ = oracle.run(p.left, p.right, d, 4, SIG_S, SIG_R, 3)
+    assert (maps[0] != ref).mean() < 0.01
+
+
+def test_ahat_join_rejects_other_values():
+    ctx = Z.ZnccContext(32, 16, 8, 3)
+    for bad in (-1, 3, 7):
+        with pytest.raises(Exception):
+            ctx.set_tuning(Z.ZNCC_TUNE_AHAT_JOIN, bad)
+    ctx.set_tuning(Z.ZNCC_TUNE_AHAT_JOIN, 2)
+    ctx.close()
+
+
 def test_run_host_repeated_calls_replay_the_same_work():
     """Repeated zncc_run_host calls with the same page-locked buffers and arguments are captured
     once as a CUDA graph and replayed; the replay reads the buffers' current contents, and a
