@@ -395,6 +395,38 @@ def test_ahat_join_rejects_other_values():
     ctx.close()
 
 
+# (h, w): pixel counts that leave 0, 1, 2 and 3 pixels past the last group of four
+@pytest.mark.parametrize("h,w", [(16, 48), (5, 7), (9, 26), (11, 27)])
+def test_fused_map_into_an_unaligned_buffer(h, w):
+    """The WTA finish converts four keys per thread and stores the four disparities at once
+    where the map is 8-byte aligned; a map one element into its buffer (2-byte aligned) takes
+    the element-wise stores, and the last pixels of a pair whose count is not a multiple of four
+    take the element-wise path too. Both maps equal an aligned run's, the elements around the
+    map keep their values, and the next run (the keys zeroed by the finish) gives the same map."""
+    d = 24
+    p = rand_pair(h, w, d, seed=900 + h * w, disp="planes")
+    ctx = Z.ZnccContext(w, h, d, 9)
+    ref = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.zncc_run(dev(p.left), dev(p.right), ref, SIG_S, SIG_R, 3, Z.ZNCC_F32)
+    buf = torch.full((h * w + 3,), -7, dtype=torch.int16, device="cuda")
+    view = buf[1:1 + h * w].view(h, w)
+    assert view.data_ptr() % 8 != 0
+    for _ in range(2):
+        ctx.zncc_run(dev(p.left), dev(p.right), view, SIG_S, SIG_R, 3, Z.ZNCC_F32)
+        torch.cuda.synchronize()
+        assert torch.equal(view, ref)
+    assert int(buf[0]) == -7 and int(buf[-1]) == -7 and int(buf[-2]) == -7
+    hbuf = np.full(h * w + 1, 7, np.uint16)             # a host map one element in, likewise
+    hview = hbuf[1:].reshape(h, w)
+    for _ in range(2):
+        ctx.zncc_run_host(p.left, p.right, hview, SIG_S, SIG_R, 3, Z.ZNCC_F32)
+        assert np.array_equal(hview, host_u16(ref)) and hbuf[0] == 7
+    assert ctx.device_faults() == 0
+    mref, gap = oracle.run(p.left, p.right, d, 4, SIG_S, SIG_R, 3)
+    check_disp(host_u16(ref), mref, gap, oracle.ones_response(p.left, SIG_S, SIG_R, 3), "finish")
+    ctx.close()
+
+
 def test_run_host_repeated_calls_replay_the_same_work():
     """Repeated zncc_run_host calls with the same page-locked buffers and arguments are captured
     once as a CUDA graph and replayed; the replay reads the buffers' current contents, and a
