@@ -99,6 +99,20 @@ def test_fastdt_run_matches_oracle(h, w, d, win, iters):
     assert diff.mean() <= RATE_I8, diff.mean()
 
 
+@pytest.mark.parametrize("h,w,d", [(24, 40, 1), (16, 20, 40)])
+def test_fastdt_degenerate_disparity_ranges(h, w, d):
+    """FastDT codes at D = 1 (every value coded against itself: the map is 0) and at D > W
+    (clamped target windows) match the oracle's FastDT chain away from its near-ties."""
+    p = make_pair(h, w, d, seed=5, disp="planes")
+    got = run_i8(p, d, 5, 3)
+    if d == 1:
+        assert (got == 0).all()
+    ref, gap = oracle.run_fastdt(p.left, p.right, d, 2, SIG_S, SIG_R, 3)
+    A = oracle.ones_response(p.left, SIG_S, SIG_R, 3)
+    bad = (got != ref) & ~(gap < GAP_TOL_I8 * A)
+    assert not bad.any(), int(bad.sum())
+
+
 def test_fastdt_lines_spanning_clusters_match_oracle():
     """Eight lanes per chunk on 1100-pixel rows: a row spans the two CTAs of a cluster in the
     horizontal pairs (the reference of d = 0 and the codes are per CTA)."""

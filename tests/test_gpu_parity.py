@@ -289,6 +289,37 @@ RUN_CASES = [(96, 320, 32, 9, 0), (96, 320, 32, 9, 1), (96, 320, 32, 9, 3), (37,
              (64, 200, 48, 15, 3)]
 
 
+# (h, w, D): one disparity (every map entry is 0) and a disparity range wider than the image
+# (target windows past the left edge read the clamped edge column)
+DEGENERATE_D = [(24, 40, 1), (16, 20, 40)]
+
+
+@pytest.mark.parametrize("h,w,d", DEGENERATE_D)
+@pytest.mark.parametrize("storage", [Z.ZNCC_F32, Z.ZNCC_F16])
+def test_degenerate_disparity_ranges(h, w, d, storage):
+    """The fused run at D = 1 gives the map 0 everywhere, and at D > W (many disparities with
+    equal, clamped target windows: ties go to the smallest d) matches the oracle away from
+    near-ties: 1e-5 of A_hat for F32, 0.05 of A_hat for F16 (above the half rounding of the
+    normalised stored pairs)."""
+    p = rand_pair(h, w, d, seed=5, disp="planes")
+    ctx = Z.ZnccContext(w, h, d, 5)
+    disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    ctx.zncc_run(dev(p.left), dev(p.right), disp, SIG_S, SIG_R, 3, storage)
+    torch.cuda.synchronize()
+    assert ctx.device_faults() == 0
+    got = host_u16(disp)
+    if d == 1:
+        assert (got == 0).all()
+    ref, gap = oracle.run(p.left, p.right, d, 2, SIG_S, SIG_R, 3)
+    A = oracle.ones_response(p.left, SIG_S, SIG_R, 3)
+    if storage == Z.ZNCC_F32:
+        check_disp(got, ref, gap, A, "degenerate D")
+    else:
+        bad = (got != ref) & ~(gap < 0.05 * A)
+        assert not bad.any(), int(bad.sum())
+    ctx.close()
+
+
 @pytest.mark.parametrize("h,w,d,win,iters", RUN_CASES)
 def test_fused_run_matches_oracle(h, w, d, win, iters):
     p = rand_pair(h, w, d, seed=h + w + d + win + iters)
